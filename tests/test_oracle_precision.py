@@ -1,0 +1,153 @@
+"""Pins of the reduced-precision emulation (operand rounding, scaling, splits, bounds)."""
+import math
+
+import numpy as np
+import pytest
+
+import synth
+from oracle import precision as P
+from oracle import spamm as S
+
+
+def _rne_frexp(x, sig_bits):
+    """Independent RNE: scale the frexp significand to sig_bits integer bits, np.rint (half-even)."""
+    x = np.asarray(x, dtype=np.float64)
+    m, e = np.frexp(x)
+    return np.ldexp(np.rint(np.ldexp(m, sig_bits)), e - sig_bits)
+
+
+def _samples(seed=1, n=20000):
+    g = np.random.Generator(np.random.PCG64(seed))
+    x = (g.standard_normal(n) * np.exp2(g.integers(-30, 30, n))).astype(np.float32)
+    # exact ties: values halfway between representable neighbours
+    ties = (np.arange(1, 200, dtype=np.float64) * 2 + 1) * 2.0 ** -9   # odd multiples of 2^-9
+    return np.concatenate([x, ties.astype(np.float32), -ties.astype(np.float32),
+                           np.float32([0.0, -0.0, 1.0, 3.4e38])])
+
+
+def test_bf16_rounding_matches_frexp_rint():
+    x = _samples()
+    got = P.round_bf16(x).astype(np.float64)
+    ref = _rne_frexp(x, 8)
+    finite = np.abs(ref) < 3.3e38
+    assert np.array_equal(got[finite], ref[finite])
+    assert np.isinf(P.round_bf16(np.float32([3.4e38])))[0]   # rounds past bf16 max
+
+
+def test_tf32_rounding_matches_frexp_rint():
+    x = _samples(2)
+    assert np.array_equal(P.round_tf32(x).astype(np.float64), _rne_frexp(x, 11))
+
+
+def test_fp16_library_rounding_agrees_with_bit_rounding_in_normal_range():
+    x = _samples(3)
+    x = x[(np.abs(x) >= 2.0 ** -14) & (np.abs(x) < 65000)]
+    assert np.array_equal(P.round_fp16(x), P.round_tf32(x))    # both keep 11 significant bits
+
+
+def test_block_exponent_range():
+    g = np.random.Generator(np.random.PCG64(4))
+    for _ in range(200):
+        blk = (g.standard_normal((8, 8)) * 2.0 ** g.integers(-60, 60)).astype(np.float32)
+        e = P.block_exponent(blk)
+        mx = float(np.max(np.abs(blk))) * 2.0 ** -e
+        assert 0.5 <= mx < 1.0
+    assert P.block_exponent(np.zeros((4, 4), np.float32)) == 0
+
+
+@pytest.mark.parametrize("fmt", ["bf16", "fp16", "tf32"])
+def test_split_residual_is_second_order(fmt):
+    g = np.random.Generator(np.random.PCG64(5))
+    blk = (g.standard_normal((64, 64)) * 3.0).astype(np.float32)
+    e, hi, lo = P.quantize_block(blk, fmt, True)
+    scaled = blk.astype(np.float64) * 2.0 ** -e
+    u = {"bf16": P.U_BF16, "fp16": P.U_FP16, "tf32": P.U_TF32}[fmt]
+    r1 = np.abs(scaled - hi)
+    assert (r1 <= u * np.abs(scaled) + 2.0 ** -25).all()
+    r2 = np.abs(scaled - hi - lo.astype(np.float64) * 2.0 ** -P.lo_shift(fmt))
+    assert (r2 <= u * u * np.abs(scaled) + 2.0 ** -36).all()
+
+
+@pytest.mark.parametrize("mode", [P.BF16, P.FP16, P.TF32X3, P.BF16_SPLIT, P.FP16_SPLIT])
+def test_exactly_representable_inputs_give_exact_products(mode):
+    """Small integers times powers of two are exact in every format: emulation == FP64 product."""
+    g = np.random.Generator(np.random.PCG64(6))
+    n, leaf = 128, 32
+    a = (g.integers(-8, 9, (n, n)) * 2.0 ** g.integers(-3, 3, (n, n))).astype(np.float32)
+    b = (g.integers(-8, 9, (n, n)) * 2.0 ** g.integers(-3, 3, (n, n))).astype(np.float32)
+    nA, nB = S.normmap(a, leaf), S.normmap(b, leaf)
+    surv = S.flat_survivors(nA, nB, float(np.median(S.triple_products(nA, nB))))
+    flags = surv.copy() if mode in (P.BF16_SPLIT, P.FP16_SPLIT) else None
+    emu = P.emulated_multiply(a, b, leaf, surv, mode, flags)
+    assert np.array_equal(emu, S.multiply_with_skipset(a, b, leaf, surv))
+
+
+@pytest.mark.parametrize("mode", [P.BF16, P.FP16, P.TF32X3, P.BF16_SPLIT, P.FP16_SPLIT])
+def test_apriori_bound_holds_for_emulation(mode):
+    n, leaf = 256, 64
+    a = synth.alg_decay_signed(n, 2.0, 41)
+    b = synth.exp_decay_normal(n, 0.05, 42)
+    nA, nB = S.normmap(a, leaf), S.normmap(b, leaf)
+    for tau in (0.0, 1e-3):
+        surv = S.flat_survivors(nA, nB, tau)
+        flags = None
+        if mode in (P.BF16_SPLIT, P.FP16_SPLIT):
+            flags = P.flag_mask(nA, nB, surv, -4, S.frobenius(a), S.frobenius(b))
+            assert flags.any() and (surv & ~flags).any()
+        emu = P.emulated_multiply(a, b, leaf, surv, mode, flags)
+        exact = S.multiply_with_skipset(a, b, leaf, surv)
+        err = S.frobenius(emu - exact)
+        bound = P.apriori_bound(nA, nB, surv, mode, leaf, flags)
+        assert err <= bound
+        # the bound is not vacuous: within a factor 1e4 of the measured error
+        assert err > 0 and bound < 1e4 * err
+
+
+def test_split_beats_plain_by_orders_of_magnitude():
+    n, leaf = 128, 64
+    a = synth.exp_decay_normal(n, 0.02, 43)
+    b = synth.exp_decay_normal(n, 0.02, 44)
+    nA, nB = S.normmap(a, leaf), S.normmap(b, leaf)
+    surv = S.flat_survivors(nA, nB, 0.0)
+    exact = S.multiply_with_skipset(a, b, leaf, surv)
+    for plain, split, u in ((P.BF16, P.BF16_SPLIT, P.U_BF16), (P.FP16, P.FP16_SPLIT, P.U_FP16)):
+        e1 = S.frobenius(P.emulated_multiply(a, b, leaf, surv, plain) - exact)
+        e2 = S.frobenius(P.emulated_multiply(a, b, leaf, surv, split, surv) - exact)
+        assert e2 < 2 * u * e1          # the split removes one factor u
+
+
+def test_flag_exponent_definition_brute_force():
+    """The returned binade is the largest m whose unflagged hi-only bound fits the budget."""
+    n, leaf = 256, 32
+    a = synth.alg_decay_signed(n, 2.0, 45)
+    b = synth.alg_decay_signed(n, 2.0, 46)
+    nA, nB = S.normmap(a, leaf), S.normmap(b, leaf)
+    na, nb = S.frobenius(a), S.frobenius(b)
+    surv = S.flat_survivors(nA, nB, 1e-6)
+    _, b2 = S.skipped_bounds(nA, nB, surv)
+    p = S.triple_products(nA, nB)[surv]
+    inv = 1.0 / (na * nb)
+    c1 = 2 * P.U_BF16 + P.U_BF16 ** 2
+    prev_m = None
+    for target in (1e-2, 1e-3, 1e-4, 1e-5, 1e-7):
+        m = P.flag_exponent(nA, nB, surv, "bf16", target, b2, na, nb)
+        budget = 0.5 * (target * na * nb - b2)
+        def fits(mm):
+            return budget >= 0 and c1 * math.fsum(p[np.floor(np.log2(p * inv)) < mm].tolist()) <= budget
+        if budget < 0:
+            assert m == P.FLAG_BIN_MIN - 1
+        else:
+            assert fits(m) and (m == 1 or not fits(m + 1))
+        if prev_m is not None:
+            assert m <= prev_m                 # tighter targets flag more
+        prev_m = m
+
+
+def test_relative_bin_is_floor_log2():
+    g = np.random.Generator(np.random.PCG64(7))
+    p = np.exp2(g.uniform(-150, 0, 5000))
+    p = np.concatenate([p, np.exp2(np.arange(-150, 1, dtype=np.float64)), [0.0]])
+    b = P.relative_bin(p, 1.0)
+    ref = np.where(p > 0, np.maximum(np.floor(np.log2(np.where(p > 0, p, 1.0))), P.FLAG_BIN_MIN),
+                   P.FLAG_BIN_MIN)
+    assert np.array_equal(b, ref.astype(np.int64))
