@@ -1,0 +1,384 @@
+"""SpAMM benchmark: one JSON line per run (rank 0).
+
+A step is one pass of the hot path over the workload with inputs resident in
+HBM: norm map of A, norm map of B, the pair test / work-queue plan at tau,
+and the multiply that writes C.  The default workload is the mixed-precision
+decay case: N = 8192, a_ij = (|i-j|+1)^-3 * s_ij (s = +-1, A and B
+independent), leaf 64.  The metric is dense-equivalent throughput 2 N^3 / t
+(TFLOP/s); ms_per_step gives the time.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                       [--precision fp32|bf16|...] [--tau T]
+With N > 1 (torchrun) every rank runs an independent replica (the path does
+not shard); the value is the sum over ranks, timed by the slowest rank.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+# the CPU baseline is timed single-threaded: pin BLAS before numpy loads
+os.environ.setdefault("OPENBLAS_NUM_THREADS", "1")
+os.environ.setdefault("OMP_NUM_THREADS", "1")
+os.environ.setdefault("MKL_NUM_THREADS", "1")
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+METRIC = "SpAMM time & TFLOP/s at fixed rel. error vs plain FP32 SpAMM & cuBLAS; roofline %"
+N_DEFAULT, LEAF_DEFAULT = 8192, 64
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return {"hbm_gbs": p["hbm_gbs"], "bf16_tflops": p["bf16_tflops"],
+                "bf16_tflops_sustained": p.get("bf16_tflops_sustained"),
+                "sm_max_mhz": p.get("sm_max_mhz", 2070.0), "source": "measured"}
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
+                "sm_max_mhz": 2070.0, "source": "fallback"}
+
+
+def workload(n: int):
+    a = synth.alg_decay_signed(n, 3.0, synth.config_seed(1, operand="A"))
+    b = synth.alg_decay_signed(n, 3.0, synth.config_seed(1, operand="B"))
+    return a, b
+
+
+# ---------------------------------------------------------------------------
+# Clock sampling during the timed region
+# ---------------------------------------------------------------------------
+
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.QUERY}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        self.lines = []
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+                self.lines = [ln for ln in out.splitlines() if ln.strip()]
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in getattr(self, "lines", []):
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": mx, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# CPU baseline: the oracle as it stands on a bounded sample of the workload
+# ---------------------------------------------------------------------------
+
+def cpu_baseline(a, b, leaf, tau, rows, nB_full=None, gpu_c=None):
+    """Times the oracle on `rows` output block-rows: norm maps of those block-rows
+    of A and of B (the per-block-row share of both norm passes), the pair test of
+    those rows against all of B's blocks, and their block products.  The full job
+    is `bd / len(rows)` such shares.  Returns (dict, nB_full)."""
+    from oracle import spamm as OS
+    n = a.shape[0]
+    bd = OS.num_blocks(n, leaf)
+    if nB_full is None:
+        nB_full = OS.normmap(b, leaf)          # needed by the tests; not timed
+    t0 = time.perf_counter()
+    nA_rows = OS.normmap_rows(a, leaf, rows)
+    _ = OS.normmap_rows(b, leaf, rows)          # B's share of the norm pass
+    out = OS.spamm_rows(a, b, leaf, tau, rows, nA_rows, nB_full)
+    dt = time.perf_counter() - t0
+    t_full = dt * bd / len(rows)
+    res = {"value": 2.0 * n ** 3 / t_full / 1e12, "unit": "TFLOP/s (dense-equivalent)",
+           "cores": 1, "kind": "oracle",
+           "sample": f"{len(rows)} of {bd} output block-rows (norm maps of those block-rows of "
+                     f"A and B, their pair tests and block products), {dt:.1f} s, "
+                     f"extrapolated x{bd / len(rows):.0f}",
+           "seconds_full_extrapolated": t_full}
+    if gpu_c is not None:
+        errs, refs = 0.0, 0.0
+        for i, (c, _) in out.items():
+            g = gpu_c[i * leaf:min(n, (i + 1) * leaf)].astype(np.float64)
+            errs += float(np.sum((g - c) ** 2))
+            refs += float(np.sum(c ** 2))
+        res["rel_err_vs_oracle_sampled_rows"] = (errs / refs) ** 0.5 if refs > 0 else 0.0
+    return res, nB_full
+
+
+# ---------------------------------------------------------------------------
+# The GPU arm
+# ---------------------------------------------------------------------------
+
+def run_ours(args, rank, world):
+    import torch
+    import paper_2103_13042_gb300 as P
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    n, leaf, tau = args.n, args.leaf, args.tau
+    prec = P.PRECISIONS[args.precision]
+    a_h, b_h = workload(n)
+    A = torch.from_numpy(a_h).to(dev)
+    B = torch.from_numpy(b_h).to(dev)
+    C = torch.empty_like(A)
+    bd = P.num_blocks(n, leaf)
+    nA = torch.empty((bd, bd), dtype=torch.float64, device=dev)
+    nB = torch.empty_like(nA)
+    plan = P.Plan(n, leaf, prec)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        P.spamm_normmap(A, leaf, nA, stream)
+        P.spamm_normmap(B, leaf, nB, stream)
+        plan.plan(nA, nB, tau, args.target, stream)
+        plan.multiply(A, B, C, stream)
+
+    launches_per_step = 2 + 5 + 1
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    st = plan.stats()
+
+    # per-call breakdown (events on the launching stream)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
+    parts = {"normmap_A": [], "normmap_B": [], "plan": [], "multiply": []}
+    for _ in range(max(3, args.steps // 2)):
+        ev[0].record(stream)
+        P.spamm_normmap(A, leaf, nA, stream)
+        ev[1].record(stream)
+        P.spamm_normmap(B, leaf, nB, stream)
+        ev[2].record(stream)
+        plan.plan(nA, nB, tau, args.target, stream)
+        ev[3].record(stream)
+        plan.multiply(A, B, C, stream)
+        ev[4].record(stream)
+        torch.cuda.synchronize()
+        for k, name in enumerate(parts):
+            parts[name].append(ev[k].elapsed_time(ev[k + 1]))
+    part_ms = {k: statistics.median(v) for k, v in parts.items()}
+
+    # timed region: K steps
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        time.sleep(0.3)
+        e0.record(stream)
+        for _ in range(args.steps):
+            step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        time.sleep(0.3)
+    barrier()
+    ms = e0.elapsed_time(e1) / args.steps
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+
+    # end to end through the public API with host buffers (pinned)
+    a_pin = torch.from_numpy(a_h).pin_memory()
+    b_pin = torch.from_numpy(b_h).pin_memory()
+    c_pin = torch.empty_like(a_pin).pin_memory()
+    e2e_steps = max(3, args.steps // 2)
+
+    def e2e_step():
+        A.copy_(a_pin, non_blocking=True)
+        B.copy_(b_pin, non_blocking=True)
+        step()
+        c_pin.copy_(C, non_blocking=True)
+
+    e2e_step()
+    torch.cuda.synchronize()
+    barrier()
+    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    f0.record(stream)
+    for _ in range(e2e_steps):
+        e2e_step()
+    f1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = f0.elapsed_time(f1) / e2e_steps
+    if world > 1:
+        t = torch.tensor([e2e_ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+
+    if rank != 0:
+        return None
+    peaks = load_peaks()
+    dense = 2.0 * n ** 3
+    value = dense / (ms * 1e-3) / 1e12 * world
+    # roofline of the dominant kernel
+    norm_ms = 0.5 * (part_ms["normmap_A"] + part_ms["normmap_B"])
+    mul_ms = part_ms["multiply"]
+    if norm_ms >= mul_ms:
+        bytes_ = 4.0 * n * n + 8.0 * bd * bd
+        ach = bytes_ / (norm_ms * 1e-3) / 1e9
+        roof = {"kernel": "normmap", "bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"],
+                "unit": "GB/s", "frac": ach / peaks["hbm_gbs"], "traffic": None,
+                "per_launch_ms": norm_ms, "algorithmic_bytes": bytes_,
+                "peak_source": peaks["source"]}
+    else:
+        flops = 2.0 * leaf ** 3 * st["survivors"]
+        if prec == P.FP32:
+            peak = 152 * 128 * 2 * peaks["sm_max_mhz"] * 1e6 / 1e12
+            ach = flops / (mul_ms * 1e-3) / 1e12
+            roof = {"kernel": "multiply_simt", "bound": "alu", "achieved": ach, "peak": peak,
+                    "unit": "TFLOP/s", "frac": ach / peak, "traffic": None,
+                    "per_launch_ms": mul_ms, "algorithmic_flops": flops,
+                    "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x max SM clock"}
+        else:
+            peak = peaks["bf16_tflops"]
+            ach = flops / (mul_ms * 1e-3) / 1e12
+            roof = {"kernel": "multiply_tc", "bound": "tensor", "achieved": ach, "peak": peak,
+                    "unit": "TFLOP/s", "frac": ach / peak, "traffic": None,
+                    "per_launch_ms": mul_ms, "algorithmic_flops": flops,
+                    "peak_source": peaks["source"]}
+    line = {
+        "metric": METRIC, "value": value, "unit": "TFLOP/s (dense-equivalent, 2N^3/t)",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": {"fp32": "f32"}.get(args.precision, args.precision),
+        "data": "synthetic (seeded algebraic-decay matrices)",
+        "config": {"workload": f"algebraic decay (|i-j|+1)^-3 * (+-1), N={n}, leaf {leaf}, "
+                               f"tau={tau:g}, {args.precision}",
+                   "n": n, "leaf": leaf, "tau": tau, "precision": args.precision,
+                   "target_rel_err": args.target, "parallelism": f"replicas x{world}",
+                   "l2": "inputs larger than L2 (A, B, C 268 MB each vs 126 MB L2)",
+                   "survivors": st["survivors"], "valid_ratio": st["valid_ratio"],
+                   "skipped_bound2_rel": st["skipped_bound2"] / (st["norm_a"] * st["norm_b"])},
+        "breakdown_ms": part_ms,
+        "e2e": {"value": dense / (e2e_ms * 1e-3) / 1e12 * world,
+                "unit": "TFLOP/s (dense-equivalent, 2N^3/t)", "ms_per_step": e2e_ms,
+                "h2d_bytes_per_step": 2 * 4 * n * n, "d2h_bytes_per_step": 4 * n * n},
+        "gpu_launches": launches_per_step * args.steps,
+        "roofline": roof,
+        "clocks": clk.summary(),
+    }
+    if not args.no_cpu_baseline:
+        c_host = C.cpu().numpy()
+        cb, _ = cpu_baseline(a_h, b_h, leaf, tau, rows=list(range(args.cpu_rows)), gpu_c=c_host)
+        line["cpu_baseline"] = cb
+    return line
+
+
+# ---------------------------------------------------------------------------
+# Reference arm: the oracle as it stands, on the host cores
+# ---------------------------------------------------------------------------
+
+def run_reference(args):
+    a_h, b_h = workload(args.n)
+    leaf, tau = args.leaf, args.tau
+    rows = list(range(args.cpu_rows))
+    nB = None
+    for _ in range(args.warmup):
+        _, nB = cpu_baseline(a_h, b_h, leaf, tau, rows, nB)
+    vals = []
+    t0 = time.perf_counter()
+    cb = None
+    for _ in range(args.steps):
+        cb, nB = cpu_baseline(a_h, b_h, leaf, tau, rows, nB)
+        vals.append(cb["value"])
+    wall = time.perf_counter() - t0
+    value = statistics.median(vals)
+    return {
+        "impl": "reference", "metric": METRIC, "value": value,
+        "unit": "TFLOP/s (dense-equivalent, 2N^3/t)", "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": cb["seconds_full_extrapolated"] * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (seeded algebraic-decay matrices)",
+        "config": {"workload": f"algebraic decay (|i-j|+1)^-3 * (+-1), N={args.n}, leaf {leaf}, "
+                               f"tau={tau:g}, {args.precision}",
+                   "n": args.n, "leaf": leaf, "tau": tau, "precision": args.precision},
+        "cpu_baseline": {"value": value, "unit": cb["unit"], "cores": 1, "kind": "oracle",
+                         "sample": cb["sample"]},
+        "e2e": {"value": value, "unit": "TFLOP/s (dense-equivalent, 2N^3/t)",
+                "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "wall_seconds": wall,
+    }
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="fp32")
+    ap.add_argument("--tau", type=float, default=1e-4)
+    ap.add_argument("--target", type=float, default=1e-5)
+    ap.add_argument("--n", type=int, default=N_DEFAULT)
+    ap.add_argument("--leaf", type=int, default=LEAF_DEFAULT)
+    ap.add_argument("--cpu-rows", type=int, default=2)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        print(json.dumps(run_reference(args)), flush=True)
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    line = run_ours(args, rank, world)
+    if line is not None:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

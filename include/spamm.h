@@ -1,0 +1,199 @@
+/*
+ * spamm.h -- C ABI of the GB300 (sm_103a) norm-pruned block SpAMM library.
+ *
+ * Method: arXiv 2103.13042, "Accelerating Sparse Approximate Matrix
+ * Multiplication on GPUs".  For square N x N FP32 matrices A, B, a leaf size
+ * b and a threshold tau >= 0 it computes (Section 2.1 problem statement,
+ * alpha = 1, beta = 0)
+ *
+ *     C[i,j] = sum over k with ||A[i,k]||_F * ||B[k,j]||_F >= tau of A[i,k] B[k,j]
+ *
+ * where X[i,k] is the b x b leaf block starting at row i*b, column k*b
+ * (Section 3 notation; matrices are zero padded to a multiple of b), and the
+ * norms are the Frobenius norms of Eq. 2.  The flat leaf-level test is the
+ * GPU re-design of Section 3.1, equivalent to the recursive test of
+ * Algorithm 1.  A block product is skipped iff its norm product is < tau:
+ * a tie is multiplied and a NaN product is never skipped.
+ *
+ * Conventions for every entry point:
+ *  - Matrices are FP32, row-major, leading dimension n, in DEVICE memory
+ *    owned by the caller.  A, B and C must not alias.  Every pointer must be
+ *    16-byte aligned (SPAMM_ERR_INVALID_ARG otherwise).
+ *  - bd = ceil(n / leaf).  Norm maps are FP64 bd x bd row-major device arrays.
+ *  - leaf is 32, 64 or 128 (SPAMM_ERR_UNSUPPORTED otherwise); n >= 1.
+ *  - tau must be >= 0 and not NaN; +infinity skips every finite product.
+ *  - `stream` is a cudaStream_t (NULL = the legacy default stream).  All
+ *    calls are asynchronous on it unless stated; errors found on the host are
+ *    returned before anything is enqueued; launch failures return
+ *    SPAMM_ERR_CUDA.  Device-side checks (bounds, bounded waits) latch a code
+ *    in a device status word that spamm_last_device_status reads.
+ *  - Nothing aborts or throws.  The library never reads host memory that the
+ *    caller did not pass.
+ */
+#ifndef SPAMM_H
+#define SPAMM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  SPAMM_OK = 0,
+  SPAMM_ERR_INVALID_ARG = 1,   /* bad size, NaN/negative tau, NULL or misaligned pointer */
+  SPAMM_ERR_UNSUPPORTED = 2,   /* leaf or precision not implemented for this shape */
+  SPAMM_ERR_CUDA = 3,          /* a CUDA runtime call or kernel launch failed */
+  SPAMM_ERR_NO_MEMORY = 4,     /* workspace too small or device allocation failed */
+  SPAMM_ERR_TIMEOUT = 5,       /* a bounded device wait ran out (status word) */
+  SPAMM_ERR_DEVICE_FAULT = 6   /* a device-side bounds check failed (status word) */
+} spamm_status_t;
+
+/* Arithmetic of the block products (Section 3.3 multiplies in FP32 on SIMT
+ * and in FP16 on tensor cores; the others extend that):
+ *  FP32        FP32 operands, FP32 FMA accumulation on the SIMT cores.
+ *  TF32X3      tensor cores, each operand split hi + lo in TF32, three
+ *              products hi*hi + hi*lo + lo*hi, FP32 accumulation.
+ *  BF16, FP16  tensor cores; every leaf block scaled by a power of two
+ *              2^-e (e = frexp exponent of its max |entry|) and rounded to
+ *              nearest-even; FP32 accumulation; the product is rescaled by
+ *              2^(ea + eb).
+ *  *_SPLIT     as BF16/FP16, plus the lo parts on the dominant triples
+ *              (see spamm_plan's target_rel_err). */
+typedef enum {
+  SPAMM_FP32 = 0,
+  SPAMM_TF32X3 = 1,
+  SPAMM_BF16 = 2,
+  SPAMM_FP16 = 3,
+  SPAMM_BF16_SPLIT = 4,
+  SPAMM_FP16_SPLIT = 5
+} spamm_precision_t;
+
+/* Plan statistics (Section 3.5.1 valid multiplications, Section 3.5.2 valid
+ * ratio, and the skipped-product bounds):
+ *   survivors      S, number of multiplied leaf triples
+ *   valid_ratio    S / bd^3
+ *   skipped_bound1 sum over skipped triples of ||A_ik|| ||B_kj||
+ *   skipped_bound2 sqrt(sum over tiles of (sum over skipped k of the product)^2);
+ *                  ||AB - C||_F <= skipped_bound2 <= skipped_bound1 (exact arithmetic)
+ *   norm_a, norm_b ||A||_F, ||B||_F recovered from the norm maps
+ *   max_tile_survivors  largest per-tile count (kmax)
+ *   nonempty_tiles tiles with at least one survivor
+ *   flag_exponent  split modes: triples with floor(log2(p/(|A||B|))) >= this get hi+lo
+ *   flagged        number of such triples */
+typedef struct {
+  int64_t survivors;
+  int64_t nonempty_tiles;
+  int64_t flagged;
+  double valid_ratio;
+  double skipped_bound1;
+  double skipped_bound2;
+  double norm_a;
+  double norm_b;
+  int32_t leaf;
+  int32_t bd;
+  int32_t max_tile_survivors;
+  int32_t flag_exponent;
+} spamm_stats_t;
+
+typedef struct spamm_plan_s* spamm_plan_t;
+
+/* ---------------------------------------------------------------------------
+ * spamm_normmap -- Get-norm step (Section 3.2, Eq. 2).
+ *   X        device, FP32 n x n row-major (ld = n), 16-byte aligned.
+ *   normmap  device, FP64 [bd * bd] row-major: normmap[I*bd+K] = ||X[I,K]||_F
+ *            over the zero-padded block.  Written completely.
+ * Squares are formed exactly (FP32 products split by FMA), accumulated in
+ * compensated double-FP32 groups and combined in FP64, so the result is
+ * within 3e-13 relative of the exactly rounded norm (NaN entries give NaN;
+ * an infinite entry gives NaN or +Inf, both of which survive every test).
+ * ------------------------------------------------------------------------- */
+spamm_status_t spamm_normmap(const float* X, int64_t n, int32_t leaf, double* normmap,
+                             void* stream);
+
+/* ---------------------------------------------------------------------------
+ * Plans -- the pair test and work-queue build (Algorithm 2's bitmap and
+ * map_offset, built once for all output tiles).
+ *
+ * spamm_plan_workspace_size: device bytes a plan for (n, leaf, precision)
+ *   needs; the worst case (every triple surviving) is provisioned.
+ * spamm_plan_create: allocates the plan.  `workspace` (device, 256-byte
+ *   aligned, >= the size above) is used when non-NULL and stays owned by the
+ *   caller; with NULL the library allocates and frees it itself.  Blocking
+ *   only when it allocates.  The plan belongs to the current device.
+ * spamm_plan_destroy: frees the plan (synchronises the device first).
+ * ------------------------------------------------------------------------- */
+spamm_status_t spamm_plan_workspace_size(int64_t n, int32_t leaf, spamm_precision_t precision,
+                                         size_t* bytes);
+spamm_status_t spamm_plan_create(spamm_plan_t* plan, int64_t n, int32_t leaf,
+                                 spamm_precision_t precision, void* workspace, size_t ws_bytes);
+spamm_status_t spamm_plan_destroy(spamm_plan_t plan);
+
+/* ---------------------------------------------------------------------------
+ * spamm_plan -- evaluate the skip rule of Algorithm 1 / Algorithm 2 for every
+ * leaf triple (i, k, j) and build per-output-tile work queues.
+ *   normA, normB  device FP64 [bd*bd] norm maps from spamm_normmap.
+ *   tau           threshold; skip iff normA[i,k] * normB[k,j] < tau (FP64).
+ *   target_rel_err split modes only: the relative error ||C - AB||_F /
+ *                 (||A||_F ||B||_F) the caller aims for.  Triples get the
+ *                 hi+lo product from the largest relative norm product
+ *                 down until the hi-only bound of the rest fits half of
+ *                 (target * ||A|| ||B|| - skipped_bound2).  Ignored otherwise.
+ * The decision is taken in FP32 on a mantissa/exponent form and re-taken in
+ * FP64 whenever the FP32 value lies within 2^-20 relative of tau, so it is
+ * exactly the FP64 test for the given norm maps.  Survivors of a tile are
+ * listed in increasing k.  Asynchronous; the plan may be executed by
+ * spamm_multiply once this returns.
+ * ------------------------------------------------------------------------- */
+spamm_status_t spamm_plan(spamm_plan_t plan, const double* normA, const double* normB,
+                          double tau, double target_rel_err, void* stream);
+
+/* spamm_plan_stats: copies the plan's statistics to *stats (host).  Blocks
+ * until the plan's work on `stream` is done. */
+spamm_status_t spamm_plan_stats(spamm_plan_t plan, spamm_stats_t* stats, void* stream);
+
+/* spamm_plan_export: copies the work queues to host arrays for inspection.
+ *   tile_ptr  host int32 [bd*bd + 1] (may be NULL): CSR offsets, tile t = i*bd + j
+ *   k_idx     host uint16 [survivors] (may be NULL): surviving k of each tile in
+ *             increasing order; bit 15 set marks a split (hi+lo) triple.
+ *   cap       capacity of k_idx in entries (SPAMM_ERR_NO_MEMORY if too small).
+ * Blocks until the plan's work on `stream` is done. */
+spamm_status_t spamm_plan_export(spamm_plan_t plan, int32_t* tile_ptr, uint16_t* k_idx,
+                                 int64_t cap, void* stream);
+
+/* ---------------------------------------------------------------------------
+ * spamm_multiply -- the multiplication step (Section 3.3, Algorithm 2 /
+ * Algorithm 3) over the plan's work queues:
+ *   C[i,j] = sum over listed k of A[i,k] B[k,j], every tile written (beta = 0;
+ *   tiles without survivors become zeros).
+ *   A, B  device FP32 n x n (ld = n); C device FP32 n x n, written completely.
+ * The precision is the plan's.  Tensor-core modes first round the blocks the
+ * plan uses into plan-owned operand buffers.  Asynchronous.
+ * ------------------------------------------------------------------------- */
+spamm_status_t spamm_multiply(spamm_plan_t plan, const float* A, const float* B, float* C,
+                              void* stream);
+
+/* ---------------------------------------------------------------------------
+ * Error measures (Eq. 6): E = AB - SpAMM(A, B, tau).
+ * spamm_frobenius_diff: *out = ||X - Y||_F over `count` FP32 entries
+ *   (Y may be NULL for ||X||_F).  FP64 accumulation of exact FP32 squares.
+ *   X, Y device; out host.  Blocks until done.
+ * ------------------------------------------------------------------------- */
+spamm_status_t spamm_frobenius_diff(const float* X, const float* Y, int64_t count, double* out,
+                                    void* stream);
+
+/* ---------------------------------------------------------------------------
+ * Status helpers.
+ * spamm_status_string: static description of a status code.
+ * spamm_last_device_status: reads and clears the library's device status word
+ *   for the current device (0 = clean, else a spamm_status_t).  Blocks.
+ * ------------------------------------------------------------------------- */
+const char* spamm_status_string(spamm_status_t status);
+spamm_status_t spamm_last_device_status(void* stream, int32_t* code);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SPAMM_H */

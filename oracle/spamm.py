@@ -270,3 +270,43 @@ def spamm(a: np.ndarray, b: np.ndarray, leaf: int, tau: float):
     b1, b2 = skipped_bounds(nA, nB, surv)
     return {"C": c, "surv": surv, "nA": nA, "nB": nB, "S": int(surv.sum()),
             "valid_ratio": valid_ratio(surv), "bound1": b1, "bound2": b2}
+
+
+# ---------------------------------------------------------------------------
+# Block-row samples (bounded CPU timing of the same workload)
+# ---------------------------------------------------------------------------
+
+def normmap_rows(x: np.ndarray, leaf: int, rows) -> np.ndarray:
+    """Eq. 2 norms of the leaf blocks in block-rows ``rows`` only ([len(rows), bd])."""
+    n = x.shape[0]
+    bd = num_blocks(n, leaf)
+    out = np.zeros((len(rows), bd))
+    for r, i in enumerate(rows):
+        strip = np.zeros((leaf, bd * leaf))
+        lo, hi = i * leaf, min(n, (i + 1) * leaf)
+        strip[:hi - lo, :n] = x[lo:hi]
+        for k in range(bd):
+            blk = strip[:, k * leaf:(k + 1) * leaf]
+            out[r, k] = math.sqrt(math.fsum((blk * blk).ravel().tolist()))
+    return out
+
+
+def spamm_rows(a: np.ndarray, b: np.ndarray, leaf: int, tau: float, rows,
+               nA_rows: np.ndarray, nB: np.ndarray) -> dict:
+    """Block-rows ``rows`` of C by the flat rule: {i: (C strip [leaf, n], surviving (k, j))}."""
+    n = a.shape[0]
+    bd = num_blocks(n, leaf)
+    pb = padded64(b, leaf)
+    out = {}
+    for r, i in enumerate(rows):
+        lo, hi = i * leaf, min(n, (i + 1) * leaf)
+        a_strip = np.zeros((leaf, bd * leaf))
+        a_strip[:hi - lo, :n] = a[lo:hi]
+        surv = survives(nA_rows[r][:, None] * nB, tau)          # [k, j]
+        c = np.zeros((leaf, bd * leaf))
+        for j in range(bd):
+            for k in np.nonzero(surv[:, j])[0]:
+                c[:, j * leaf:(j + 1) * leaf] += (a_strip[:, k * leaf:(k + 1) * leaf]
+                                                  @ block(pb, leaf, k, j))
+        out[i] = (c[:hi - lo, :n], surv)
+    return out

@@ -1,0 +1,206 @@
+"""Python binding of the GB300 SpAMM library (ctypes over ``lib/libspamm.so``).
+
+Argument marshalling only: every step runs in the library's CUDA kernels.
+Tensors are passed as raw device pointers (``data_ptr()``), streams as
+``torch.cuda.current_stream().cuda_stream``.  The names follow the C ABI in
+``include/spamm.h``.  There is no CPU fallback: if the library is missing,
+loading it raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "lib", "libspamm.so")
+
+FP32, TF32X3, BF16, FP16, BF16_SPLIT, FP16_SPLIT = range(6)
+PRECISIONS = {"fp32": FP32, "tf32x3": TF32X3, "bf16": BF16, "fp16": FP16,
+              "bf16_split": BF16_SPLIT, "fp16_split": FP16_SPLIT}
+
+STATUS = {0: "SPAMM_OK", 1: "SPAMM_ERR_INVALID_ARG", 2: "SPAMM_ERR_UNSUPPORTED",
+          3: "SPAMM_ERR_CUDA", 4: "SPAMM_ERR_NO_MEMORY", 5: "SPAMM_ERR_TIMEOUT",
+          6: "SPAMM_ERR_DEVICE_FAULT"}
+
+
+class SpammError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        super().__init__(f"{where}: {STATUS.get(code, code)}")
+        self.code = code
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("survivors", ctypes.c_int64), ("nonempty_tiles", ctypes.c_int64),
+                ("flagged", ctypes.c_int64), ("valid_ratio", ctypes.c_double),
+                ("skipped_bound1", ctypes.c_double), ("skipped_bound2", ctypes.c_double),
+                ("norm_a", ctypes.c_double), ("norm_b", ctypes.c_double),
+                ("leaf", ctypes.c_int32), ("bd", ctypes.c_int32),
+                ("max_tile_survivors", ctypes.c_int32), ("flag_exponent", ctypes.c_int32)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+_lib = None
+
+_VP, _I64, _I32, _D = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_double
+_SIGS = {
+    "spamm_normmap": [_VP, _I64, _I32, _VP, _VP],
+    "spamm_plan_workspace_size": [_I64, _I32, _I32, ctypes.POINTER(ctypes.c_size_t)],
+    "spamm_plan_create": [ctypes.POINTER(_VP), _I64, _I32, _I32, _VP, ctypes.c_size_t],
+    "spamm_plan_destroy": [_VP],
+    "spamm_plan": [_VP, _VP, _VP, _D, _D, _VP],
+    "spamm_plan_stats": [_VP, ctypes.POINTER(Stats), _VP],
+    "spamm_plan_export": [_VP, _VP, _VP, _I64, _VP],
+    "spamm_multiply": [_VP, _VP, _VP, _VP, _VP],
+    "spamm_frobenius_diff": [_VP, _VP, _I64, ctypes.POINTER(_D), _VP],
+    "spamm_last_device_status": [_VP, ctypes.POINTER(_I32)],
+}
+
+
+def lib():
+    """The loaded library (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"libspamm.so not built ({LIB_PATH}); run "
+                               "`python -m paper_2103_13042_gb300.build`")
+        l = ctypes.CDLL(LIB_PATH)
+        for name, args in _SIGS.items():
+            f = getattr(l, name)
+            f.argtypes = args
+            f.restype = ctypes.c_int
+        l.spamm_status_string.argtypes = [ctypes.c_int]
+        l.spamm_status_string.restype = ctypes.c_char_p
+        _lib = l
+    return _lib
+
+
+def _check(code: int, where: str):
+    if code != 0:
+        raise SpammError(code, where)
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    return getattr(stream, "cuda_stream", stream)
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def num_blocks(n: int, leaf: int) -> int:
+    return -(-n // leaf)
+
+
+# ---------------------------------------------------------------------------
+# Entry points (same names as the C ABI)
+# ---------------------------------------------------------------------------
+
+def spamm_normmap(X, leaf: int, out=None, stream=None):
+    """Leaf Frobenius norms of the n x n FP32 device tensor X -> FP64 [bd, bd] tensor."""
+    import torch
+    n = X.shape[0]
+    bd = num_blocks(n, leaf)
+    if out is None:
+        out = torch.empty((bd, bd), dtype=torch.float64, device=X.device)
+    _check(lib().spamm_normmap(_ptr(X), n, leaf, _ptr(out), _stream(stream)), "spamm_normmap")
+    return out
+
+
+class Plan:
+    """Owns a spamm_plan_t (work queues for one (n, leaf, precision))."""
+
+    def __init__(self, n: int, leaf: int, precision: int = FP32, workspace=None):
+        self.n, self.leaf, self.precision = n, leaf, precision
+        self.bd = num_blocks(n, leaf)
+        h = ctypes.c_void_p()
+        ws_ptr, ws_bytes = (None, 0) if workspace is None else (_ptr(workspace),
+                                                                 workspace.numel() * workspace.element_size())
+        _check(lib().spamm_plan_create(ctypes.byref(h), n, leaf, precision, ws_ptr, ws_bytes),
+               "spamm_plan_create")
+        self.handle = h
+        self._workspace = workspace
+
+    @staticmethod
+    def workspace_size(n: int, leaf: int, precision: int = FP32) -> int:
+        b = ctypes.c_size_t()
+        _check(lib().spamm_plan_workspace_size(n, leaf, precision, ctypes.byref(b)),
+               "spamm_plan_workspace_size")
+        return b.value
+
+    def close(self):
+        if self.handle:
+            lib().spamm_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def plan(self, normA, normB, tau: float, target_rel_err: float = 1e-5, stream=None):
+        _check(lib().spamm_plan(self.handle, _ptr(normA), _ptr(normB), float(tau),
+                                float(target_rel_err), _stream(stream)), "spamm_plan")
+        return self
+
+    def stats(self, stream=None) -> dict:
+        s = Stats()
+        _check(lib().spamm_plan_stats(self.handle, ctypes.byref(s), _stream(stream)),
+               "spamm_plan_stats")
+        return s.as_dict()
+
+    def export(self, stream=None):
+        """(tile_ptr int32[bd*bd+1], k_idx uint16[S]) as numpy arrays."""
+        import numpy as np
+        st = self.stats(stream)
+        tp = np.zeros(self.bd * self.bd + 1, dtype=np.int32)
+        kk = np.zeros(max(1, st["survivors"]), dtype=np.uint16)
+        _check(lib().spamm_plan_export(self.handle, tp.ctypes.data_as(ctypes.c_void_p),
+                                       kk.ctypes.data_as(ctypes.c_void_p), kk.size,
+                                       _stream(stream)), "spamm_plan_export")
+        return tp, kk[:st["survivors"]]
+
+    def multiply(self, A, B, C, stream=None):
+        _check(lib().spamm_multiply(self.handle, _ptr(A), _ptr(B), _ptr(C), _stream(stream)),
+               "spamm_multiply")
+        return C
+
+
+def spamm_plan(normA, normB, n: int, leaf: int, tau: float, precision: int = FP32,
+               target_rel_err: float = 1e-5, stream=None) -> Plan:
+    return Plan(n, leaf, precision).plan(normA, normB, tau, target_rel_err, stream)
+
+
+def spamm_multiply(plan: Plan, A, B, C=None, stream=None):
+    import torch
+    if C is None:
+        C = torch.empty_like(A)
+    return plan.multiply(A, B, C, stream)
+
+
+def spamm_frobenius_diff(X, Y=None, stream=None) -> float:
+    out = ctypes.c_double()
+    _check(lib().spamm_frobenius_diff(_ptr(X), _ptr(Y), X.numel(), ctypes.byref(out),
+                                      _stream(stream)), "spamm_frobenius_diff")
+    return out.value
+
+
+def spamm_last_device_status(stream=None) -> int:
+    c = ctypes.c_int32()
+    _check(lib().spamm_last_device_status(_stream(stream), ctypes.byref(c)),
+           "spamm_last_device_status")
+    return c.value
+
+
+def spamm(A, B, leaf: int, tau: float, precision: int = FP32, target_rel_err: float = 1e-5,
+          stream=None):
+    """One SpAMM call through the library: norm maps, plan, multiply. Returns (C, plan)."""
+    nA = spamm_normmap(A, leaf, stream=stream)
+    nB = spamm_normmap(B, leaf, stream=stream)
+    plan = spamm_plan(nA, nB, A.shape[0], leaf, tau, precision, target_rel_err, stream)
+    C = spamm_multiply(plan, A, B, stream=stream)
+    return C, plan

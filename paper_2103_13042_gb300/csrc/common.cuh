@@ -1,0 +1,180 @@
+// Shared device/host helpers of the SpAMM library (sm_103a).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/spamm.h"
+
+#define SPAMM_CUDA_TRY(call)                                   \
+  do {                                                         \
+    cudaError_t _e = (call);                                   \
+    if (_e != cudaSuccess) return SPAMM_ERR_CUDA;              \
+  } while (0)
+
+#define SPAMM_LAUNCH_CHECK()                                   \
+  do {                                                         \
+    if (cudaPeekAtLastError() != cudaSuccess) {                \
+      (void)cudaGetLastError();                                \
+      return SPAMM_ERR_CUDA;                                   \
+    }                                                          \
+  } while (0)
+
+namespace spamm {
+
+constexpr int kMaxBd = 1024;          // k indices are stored in 10 bits of a uint16
+constexpr uint16_t kSplitFlag = 0x8000;
+constexpr int kFlagBinMin = -200;     // relative products below 2^-200 share one bin
+constexpr int kFlagBins = 202;        // bins -200 .. 1
+
+inline int64_t num_blocks(int64_t n, int32_t leaf) { return (n + leaf - 1) / leaf; }
+
+// Device status word of the current device (defined in api.cu).
+int32_t* device_status_word();
+
+// ---------------------------------------------------------------------------
+// Error-free transformations (Knuth TwoSum, FMA-based TwoProd) in FP32.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  float z = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, z)), __fsub_rn(b, z));
+}
+
+// (hi, lo) += x^2 with x^2 split exactly and the pair renormalised afterwards.
+// Relative error of each step <= 2u^2 for non-negative terms (u = 2^-24).
+__device__ __forceinline__ void dw_add_square(float x, float& hi, float& lo) {
+  float p = __fmul_rn(x, x);
+  float pe = __fmaf_rn(x, x, -p);
+  float s, e;
+  two_sum(hi, p, s, e);
+  float t = __fadd_rn(lo, __fadd_rn(e, pe));
+  hi = __fadd_rn(s, t);
+  lo = __fsub_rn(t, __fsub_rn(hi, s));
+}
+
+// ---------------------------------------------------------------------------
+// Sum of squares with a moving power-of-two scale: value = (hi + lo) * 4^e.
+// Squares of FP32 entries below 2^-63 underflow in FP32, so every group of
+// entries is first scaled by 2^-g (g = exponent of the group's largest
+// magnitude; exact), squared exactly, and merged into the running pair after
+// aligning the two scales.  Contributions smaller than 2^-90 of the running
+// sum are dropped (far below the 2^-43 accuracy target).
+// ---------------------------------------------------------------------------
+constexpr int kSumSqEmpty = -100000;
+
+struct SumSq {
+  float hi, lo;
+  int e;
+};
+
+__device__ __forceinline__ SumSq sumsq_empty() { return SumSq{0.0f, 0.0f, kSumSqEmpty}; }
+
+// 2^k as a normal FP32 for -126 <= k <= 127.
+__device__ __forceinline__ float pow2f(int k) { return __uint_as_float((uint32_t)(k + 127) << 23); }
+
+// Scale exponent of a group from its largest magnitude (NaN ignored, Inf kept).
+__device__ __forceinline__ int group_exponent(float max_abs) {
+  const int ef = (int)((__float_as_uint(max_abs) >> 23) & 0xffu);
+  const int g = ef - 127;                 // max_abs in [2^g, 2^(g+1)); -127 when subnormal
+  return g > 126 ? 126 : g;
+}
+
+// acc += (hi + lo) * 4^g.
+__device__ __forceinline__ void sumsq_merge(SumSq& acc, float hi, float lo, int g) {
+  if (!(hi != 0.0f || lo != 0.0f)) {
+    if (hi != hi || lo != lo) acc.hi = hi + lo;  // keep NaN
+    return;
+  }
+  if (acc.e == kSumSqEmpty) {
+    acc.hi = hi;
+    acc.lo = lo;
+    acc.e = g;
+    return;
+  }
+  int d = acc.e - g;
+  if (d < 0) {  // the group dominates: rescale the accumulator
+    if (-2 * d > 90) {
+      acc.hi = hi;
+      acc.lo = lo;
+      acc.e = g;
+      return;
+    }
+    const float f = pow2f(2 * d);
+    acc.hi *= f;
+    acc.lo *= f;
+    acc.e = g;
+  } else if (d > 0) {
+    if (2 * d > 90) return;
+    const float f = pow2f(-2 * d);
+    hi *= f;
+    lo *= f;
+  }
+  float s, e;
+  two_sum(acc.hi, hi, s, e);
+  const float t = __fadd_rn(__fadd_rn(acc.lo, lo), e);
+  acc.hi = __fadd_rn(s, t);
+  acc.lo = __fsub_rn(t, __fsub_rn(acc.hi, s));
+}
+
+// Exact-squares sum of one group of N entries into acc.
+template <int N>
+__device__ __forceinline__ void sumsq_group(SumSq& acc, const float (&v)[N]) {
+  float mx = 0.0f;
+#pragma unroll
+  for (int q = 0; q < N; ++q) mx = fmaxf(mx, fabsf(v[q]));
+  if (mx == 0.0f) {
+    bool nan = false;
+#pragma unroll
+    for (int q = 0; q < N; ++q) nan |= (v[q] != v[q]);
+    if (nan) {
+      acc.hi = __int_as_float(0x7fffffff);
+      acc.e = 0;
+    }
+    return;
+  }
+  const int g = group_exponent(mx);
+  const float sc = pow2f(-g);
+  float hi = 0.0f, lo = 0.0f;
+#pragma unroll
+  for (int q = 0; q < N; ++q) dw_add_square(__fmul_rn(v[q], sc), hi, lo);
+  sumsq_merge(acc, hi, lo, g);
+}
+
+// The accumulated value in FP64.
+__device__ __forceinline__ double sumsq_value(const SumSq& a) {
+  if (a.e == kSumSqEmpty) return (double)a.hi;   // 0, or NaN
+  return ldexp((double)a.hi + (double)a.lo, 2 * a.e);
+}
+
+// ---------------------------------------------------------------------------
+// Mantissa/exponent form of a non-negative FP64 value for the FP32 pre-screen:
+//   x = m * 2^e, m in [0.5, 1] rounded to FP32.  kind: 0 finite > 0, 1 zero,
+//   2 non-finite (Inf or NaN).
+// ---------------------------------------------------------------------------
+struct Screen {
+  float m;
+  int32_t e;
+};
+
+constexpr int32_t kZeroExp = -100000;      // zero: never survives a positive tau
+constexpr int32_t kNonFiniteExp = 100000;  // Inf/NaN: always survives
+
+__device__ __forceinline__ Screen make_screen(double x) {
+  Screen s;
+  if (!(x == x) || isinf(x)) {
+    s.m = 1.0f;
+    s.e = kNonFiniteExp;
+  } else if (x == 0.0) {
+    s.m = 0.0f;
+    s.e = kZeroExp;
+  } else {
+    int e;
+    double m = frexp(x, &e);
+    s.m = __double2float_rn(m);  // in [0.5, 1]
+    s.e = e;
+  }
+  return s;
+}
+
+}  // namespace spamm

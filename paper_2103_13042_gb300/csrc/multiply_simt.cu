@@ -1,0 +1,215 @@
+// Plain FP32 multiply on the SIMT cores (Section 3.3's FP32 multiplication
+// kernel; the baseline the tensor-core modes are measured against).
+//
+// Persistent CTAs walk the plan's tile order (most survivors first, empty
+// tiles last) with a grid stride.  A non-empty tile (i, j) streams its
+// surviving k in 32-wide slices of the inner dimension: the A slice
+// A[i, k][:, s:s+32] is stored transposed and the B slice B[k, j][s:s+32, :]
+// as is, both in shared memory, double buffered through registers so the next
+// slice's global loads overlap the current slice's FMAs.  Each of the 256
+// threads keeps a (leaf/16) x (leaf/16) register tile of C and accumulates
+// in FP32 FMA over every surviving k.  Empty tiles are written as zeros with
+// coalesced float4 stores (beta = 0).
+#include "plan.cuh"
+
+namespace spamm {
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kSlice = 32;
+
+template <int LEAF, bool VEC>
+struct SimtTile {
+  static constexpr int TM = LEAF / 16;                    // C rows (and cols) per thread
+  static constexpr int kLoadsA = LEAF * kSlice / 4 / kThreads;  // float4 per thread per slice
+};
+
+// Loads 4 consecutive floats of row r, columns c..c+3, zero outside [0, n).
+template <bool VEC>
+__device__ __forceinline__ float4 load4(const float* __restrict__ M, int64_t n, int64_t r,
+                                        int64_t c) {
+  if (r >= n) return make_float4(0.f, 0.f, 0.f, 0.f);
+  const float* p = M + r * n + c;
+  if (VEC && c + 3 < n) return __ldg(reinterpret_cast<const float4*>(p));
+  float4 v;
+  v.x = c < n ? __ldg(p) : 0.f;
+  v.y = c + 1 < n ? __ldg(p + 1) : 0.f;
+  v.z = c + 2 < n ? __ldg(p + 2) : 0.f;
+  v.w = c + 3 < n ? __ldg(p + 3) : 0.f;
+  return v;
+}
+
+// TM consecutive floats from 16-byte (TM >= 4) or 8-byte (TM = 2) aligned shared memory.
+template <int TM>
+__device__ __forceinline__ void read_row(const float* p, float* out) {
+  if constexpr (TM >= 4) {
+#pragma unroll
+    for (int v = 0; v < TM; v += 4) {
+      const float4 x = *reinterpret_cast<const float4*>(p + v);
+      out[v] = x.x; out[v + 1] = x.y; out[v + 2] = x.z; out[v + 3] = x.w;
+    }
+  } else {
+    const float2 x = *reinterpret_cast<const float2*>(p);
+    out[0] = x.x; out[1] = x.y;
+  }
+}
+
+template <int TM>
+__device__ __forceinline__ void write_row(float* p, const float* v) {
+  if constexpr (TM >= 4) {
+#pragma unroll
+    for (int q = 0; q < TM; q += 4)
+      *reinterpret_cast<float4*>(p + q) = make_float4(v[q], v[q + 1], v[q + 2], v[q + 3]);
+  } else {
+    *reinterpret_cast<float2*>(p) = make_float2(v[0], v[1]);
+  }
+}
+
+template <int LEAF, bool VEC>
+__global__ void __launch_bounds__(kThreads)
+    simt_kernel(const float* __restrict__ A, const float* __restrict__ B, float* __restrict__ C,
+                int64_t n, int bd, const int* __restrict__ order,
+                const int* __restrict__ tile_ptr, const uint16_t* __restrict__ k_idx) {
+  using T = SimtTile<LEAF, VEC>;
+  constexpr int TM = T::TM;
+  constexpr int kLoads = T::kLoadsA;
+  // A slice transposed: sA[buf][s][r] (r = row within the leaf), B slice sB[buf][s][c]
+  extern __shared__ __align__(16) float smem[];
+  float (*sA)[kSlice][LEAF + 4] = reinterpret_cast<float (*)[kSlice][LEAF + 4]>(smem);
+  float (*sB)[kSlice][LEAF + 4] =
+      reinterpret_cast<float (*)[kSlice][LEAF + 4]>(smem + 2 * kSlice * (LEAF + 4));
+
+  const int tid = threadIdx.x;
+  const int tx = tid % 16, ty = tid / 16;
+  const int64_t tiles = (int64_t)bd * bd;
+
+  for (int64_t w = blockIdx.x; w < tiles; w += gridDim.x) {
+    const int t = order[w];
+    const int i = t / bd, j = t % bd;
+    const int beg = tile_ptr[t], end = tile_ptr[t + 1];
+    const int64_t r0 = (int64_t)i * LEAF, c0 = (int64_t)j * LEAF;
+
+    if (beg == end) {  // empty tile: zeros, coalesced
+      for (int e = tid * 4; e < LEAF * LEAF; e += kThreads * 4) {
+        const int64_t r = r0 + e / LEAF, c = c0 + e % LEAF;
+        if (r < n) {
+          float* p = C + r * n + c;
+          if (VEC && c + 3 < n) {
+            *reinterpret_cast<float4*>(p) = make_float4(0.f, 0.f, 0.f, 0.f);
+          } else {
+            for (int q = 0; q < 4; ++q)
+              if (c + q < n) p[q] = 0.f;
+          }
+        }
+      }
+      continue;
+    }
+
+    float acc[TM][TM];
+#pragma unroll
+    for (int a = 0; a < TM; ++a)
+#pragma unroll
+      for (int b = 0; b < TM; ++b) acc[a][b] = 0.f;
+
+    const int nslices = (end - beg) * (LEAF / kSlice);
+    float4 ra[kLoads], rb[kLoads];
+
+    // slice q -> (k, s0): A rows r0.., cols k*LEAF + s0..; B rows k*LEAF + s0.., cols c0..
+    auto fetch = [&](int q) {
+      const int k = k_idx[beg + q / (LEAF / kSlice)] & 0x3ff;
+      const int s0 = (q % (LEAF / kSlice)) * kSlice;
+#pragma unroll
+      for (int l = 0; l < kLoads; ++l) {
+        const int e = (tid + l * kThreads) * 4;      // element index in the slice
+        // A slice: LEAF rows x 32 cols, float4 along the columns
+        const int ar = e / kSlice, ac = e % kSlice;
+        ra[l] = load4<VEC>(A, n, r0 + ar, (int64_t)k * LEAF + s0 + ac);
+        // B slice: 32 rows x LEAF cols, float4 along the columns
+        const int br = e / LEAF, bc = e % LEAF;
+        rb[l] = load4<VEC>(B, n, (int64_t)k * LEAF + s0 + br, c0 + bc);
+      }
+    };
+    auto stash = [&](int buf) {
+#pragma unroll
+      for (int l = 0; l < kLoads; ++l) {
+        const int e = (tid + l * kThreads) * 4;
+        const int ar = e / kSlice, ac = e % kSlice;
+        sA[buf][ac + 0][ar] = ra[l].x;
+        sA[buf][ac + 1][ar] = ra[l].y;
+        sA[buf][ac + 2][ar] = ra[l].z;
+        sA[buf][ac + 3][ar] = ra[l].w;
+        const int br = e / LEAF, bc = e % LEAF;
+        *reinterpret_cast<float4*>(&sB[buf][br][bc]) = rb[l];
+      }
+    };
+
+    fetch(0);
+    __syncthreads();  // previous tile's readers are done with both buffers
+    stash(0);
+    __syncthreads();
+    for (int q = 0; q < nslices; ++q) {
+      const int buf = q & 1;
+      if (q + 1 < nslices) fetch(q + 1);
+#pragma unroll 8
+      for (int s = 0; s < kSlice; ++s) {
+        float a[TM], b[TM];
+        read_row<TM>(&sA[buf][s][ty * TM], a);
+        read_row<TM>(&sB[buf][s][tx * TM], b);
+#pragma unroll
+        for (int u = 0; u < TM; ++u)
+#pragma unroll
+          for (int v = 0; v < TM; ++v) acc[u][v] = __fmaf_rn(a[u], b[v], acc[u][v]);
+      }
+      if (q + 1 < nslices) stash(buf ^ 1);
+      __syncthreads();
+    }
+
+#pragma unroll
+    for (int u = 0; u < TM; ++u) {
+      const int64_t r = r0 + ty * TM + u;
+      if (r >= n) continue;
+      const int64_t c = c0 + tx * TM;
+      float* p = C + r * n + c;
+      if (VEC && c + TM - 1 < n) {
+        write_row<TM>(p, acc[u]);
+      } else {
+#pragma unroll
+        for (int q = 0; q < TM; ++q)
+          if (c + q < n) p[q] = acc[u][q];
+      }
+    }
+  }
+}
+
+template <int LEAF, bool VEC>
+cudaError_t launch(const PlanBuffers& b, const float* A, const float* B, float* C, int64_t n,
+                   cudaStream_t s) {
+  constexpr size_t smem = 4 * kSlice * (LEAF + 4) * sizeof(float);
+  int dev = 0, sms = 0, per_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaFuncSetAttribute(simt_kernel<LEAF, VEC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)smem);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, simt_kernel<LEAF, VEC>, kThreads, smem);
+  const int64_t tiles = (int64_t)b.bd * b.bd;
+  const int grid = (int)std::min<int64_t>(tiles, (int64_t)sms * std::max(1, per_sm));
+  simt_kernel<LEAF, VEC><<<grid, kThreads, smem, s>>>(A, B, C, n, b.bd, b.order, b.tile_ptr,
+                                                      b.k_idx);
+  return cudaPeekAtLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_multiply_simt(const PlanBuffers& b, const float* A, const float* B, float* C,
+                                 int64_t n, int32_t leaf, cudaStream_t s) {
+  const bool vec = (n % 4) == 0;
+  switch (leaf) {
+    case 32: return vec ? launch<32, true>(b, A, B, C, n, s) : launch<32, false>(b, A, B, C, n, s);
+    case 64: return vec ? launch<64, true>(b, A, B, C, n, s) : launch<64, false>(b, A, B, C, n, s);
+    case 128:
+      return vec ? launch<128, true>(b, A, B, C, n, s) : launch<128, false>(b, A, B, C, n, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace spamm

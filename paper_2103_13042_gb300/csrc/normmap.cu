@@ -1,0 +1,108 @@
+// Get-norm step (Section 3.2, Eq. 2): normmap[I*bd+K] = ||X[I,K]||_F.
+//
+// GB300 design.  The kernel is a single streaming pass over X: a CTA covers
+// one block-row strip (leaf rows) and a window of columns; each thread owns a
+// fixed column slot (a float4 when n % 4 == 0, else one float) and walks the
+// strip's rows, so every warp load is a contiguous, coalesced 512-byte
+// (or 128-byte) row segment.  FP64 arithmetic runs at 1/72 of FP32 rate on
+// this part, so every group of 32 entries is scaled by a power of two (no
+// FP32 underflow of tiny squares), squared exactly with FMA and accumulated
+// as an unevaluated FP32 pair with an explicit scale exponent; FP64 is used
+// only once per thread and in the final combine.  The threads of one block column are
+// then combined with FP64 warp shuffles (and shared memory when a block
+// column spans several warps); one FP64 sqrt per block.
+#include "common.cuh"
+
+namespace spamm {
+namespace {
+
+constexpr int kThreads = 256;
+
+template <int VEC, int LEAF>
+__global__ void __launch_bounds__(kThreads) normmap_kernel(const float* __restrict__ X, int64_t n,
+                                                          int bd, double* __restrict__ out) {
+  constexpr int kCols = kThreads * VEC;               // columns per CTA window
+  constexpr int kThreadsPerBlockCol = LEAF / VEC;     // threads sharing one output
+  constexpr int kRowsPerGroup = 32 / VEC;             // rows per 32-square group
+  const int I = blockIdx.y;
+  const int64_t col0 = (int64_t)blockIdx.x * kCols + (int64_t)threadIdx.x * VEC;
+  const int64_t row0 = (int64_t)I * LEAF;
+  const int64_t row1 = (n < row0 + LEAF) ? n : row0 + LEAF;
+  const bool active = col0 < n;
+
+  SumSq ss = sumsq_empty();
+  if (active) {
+    const float* p = X + row0 * n + col0;
+    for (int64_t r = row0; r < row1; r += kRowsPerGroup) {
+      const int rows = (int)((row1 - r) < kRowsPerGroup ? (row1 - r) : kRowsPerGroup);
+      float v[32];
+#pragma unroll
+      for (int q = 0; q < kRowsPerGroup; ++q) {
+        if (q < rows) {
+          if constexpr (VEC == 4) {
+            float4 t = __ldcs(reinterpret_cast<const float4*>(p + (int64_t)q * n));
+            v[4 * q] = t.x; v[4 * q + 1] = t.y; v[4 * q + 2] = t.z; v[4 * q + 3] = t.w;
+          } else {
+            v[q] = __ldcs(p + (int64_t)q * n);
+          }
+        } else {
+#pragma unroll
+          for (int c = 0; c < VEC; ++c) v[VEC * q + c] = 0.0f;
+        }
+      }
+      sumsq_group<32>(ss, v);
+      p += (int64_t)kRowsPerGroup * n;
+    }
+  }
+  double acc = sumsq_value(ss);
+
+  // Combine the threads of a block column.
+  if constexpr (kThreadsPerBlockCol <= 32) {
+#pragma unroll
+    for (int off = kThreadsPerBlockCol / 2; off > 0; off >>= 1)
+      acc += __shfl_xor_sync(0xffffffffu, acc, off);
+    if ((threadIdx.x % kThreadsPerBlockCol) == 0 && active) {
+      const int64_t K = col0 / LEAF;
+      out[(int64_t)I * bd + K] = sqrt(acc);
+    }
+  } else {
+    __shared__ double warp_sum[kThreads / 32];
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+    if ((threadIdx.x & 31) == 0) warp_sum[threadIdx.x / 32] = acc;
+    __syncthreads();
+    constexpr int kWarpsPerBlockCol = kThreadsPerBlockCol / 32;
+    if ((threadIdx.x % kThreadsPerBlockCol) == 0 && active) {
+      double s = 0.0;
+      const int w0 = threadIdx.x / 32;
+#pragma unroll
+      for (int w = 0; w < kWarpsPerBlockCol; ++w) s += warp_sum[w0 + w];
+      const int64_t K = col0 / LEAF;
+      out[(int64_t)I * bd + K] = sqrt(s);
+    }
+  }
+}
+
+template <int VEC, int LEAF>
+cudaError_t launch(const float* X, int64_t n, int bd, double* out, cudaStream_t s) {
+  constexpr int kCols = kThreads * VEC;
+  dim3 grid((unsigned)((n + kCols - 1) / kCols), (unsigned)bd);
+  normmap_kernel<VEC, LEAF><<<grid, kThreads, 0, s>>>(X, n, bd, out);
+  return cudaPeekAtLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_normmap(const float* X, int64_t n, int32_t leaf, double* out,
+                           cudaStream_t s) {
+  const int bd = (int)num_blocks(n, leaf);
+  const bool vec = (n % 4) == 0 && (reinterpret_cast<uintptr_t>(X) % 16) == 0;
+  switch (leaf) {
+    case 32: return vec ? launch<4, 32>(X, n, bd, out, s) : launch<1, 32>(X, n, bd, out, s);
+    case 64: return vec ? launch<4, 64>(X, n, bd, out, s) : launch<1, 64>(X, n, bd, out, s);
+    case 128: return vec ? launch<4, 128>(X, n, bd, out, s) : launch<1, 128>(X, n, bd, out, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace spamm

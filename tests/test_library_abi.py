@@ -1,0 +1,55 @@
+"""The C-ABI library loads on a CPU-only machine and exports every declared symbol."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "spamm.h")
+
+
+def declared_functions():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"^\s*(?:const\s+char\s*\*|spamm_status_t)\s+(spamm_\w+)\s*\(",
+                                 src, flags=re.M)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    import paper_2103_13042_gb300 as P
+    if not os.path.exists(P.LIB_PATH):
+        from paper_2103_13042_gb300 import build
+        build.build()
+    return P.lib()
+
+
+def test_header_declares_the_core_entry_points():
+    names = declared_functions()
+    for core in ("spamm_normmap", "spamm_plan", "spamm_multiply"):
+        assert core in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_status_strings(lib):
+    for code in range(7):
+        assert lib.spamm_status_string(code)
+
+
+def test_argument_validation_without_gpu(lib):
+    """Host-side checks run before any CUDA call, so they work with no GPU."""
+    b = ctypes.c_size_t()
+    assert lib.spamm_plan_workspace_size(0, 64, 0, ctypes.byref(b)) == 1        # n < 1
+    assert lib.spamm_plan_workspace_size(1024, 48, 0, ctypes.byref(b)) == 2     # leaf
+    assert lib.spamm_plan_workspace_size(1024, 64, 9, ctypes.byref(b)) == 1     # precision
+    assert lib.spamm_plan_workspace_size(1024, 64, 0, ctypes.byref(b)) == 0
+    assert b.value > 1024 // 64 * 1024 // 64 * 1024 // 64 * 2                   # holds k_idx
+    assert lib.spamm_normmap(None, 1024, 64, None, None) == 1
+    assert lib.spamm_normmap(ctypes.c_void_p(16), 1024, 40, ctypes.c_void_p(16), None) == 2
+    assert lib.spamm_normmap(ctypes.c_void_p(18), 1024, 64, ctypes.c_void_p(16), None) == 1
+    assert lib.spamm_plan(None, None, None, 0.0, 0.0, None) == 1
