@@ -184,6 +184,29 @@ spamm_status_t spamm_frobenius_diff(const float* X, const float* Y, int64_t coun
                                     void* stream);
 
 /* ---------------------------------------------------------------------------
+ * spamm_multiply_fp32_noalloc -- the whole FP32 product (norm maps, plan,
+ * SIMT multiply, identical arithmetic to spamm_normmap + spamm_plan +
+ * spamm_multiply with SPAMM_FP32) without any device allocation.  The paper
+ * has no counterpart: this serves callers that cannot allocate device memory
+ * where they call it (a host framework whose pool already holds the device
+ * memory, a plugin host that forbids allocation, a loop that cannot take
+ * the synchronisation an allocation may bring).
+ *   A, B, C   device FP32 n x n (ld = n), 16-byte aligned, C written completely.
+ *   n, leaf   ceil(n / leaf) must be <= 64 (n <= 2048 at leaf 32, 4096 at 64,
+ *             8192 at 128); larger sizes return SPAMM_ERR_UNSUPPORTED and
+ *             enqueue nothing.
+ *   tau       as for spamm_plan.
+ * Its scratch is a 1 MiB array in the library's device memory (static, one
+ * per device, kept until the process exits).  The first call on a device
+ * looks that array up with cudaGetSymbolAddress: make it before any stream
+ * capture on that device.  Every call on a device shares the array and
+ * leaves its contents behind; calls that overlap on the GPU race on it and
+ * must be serialised by the caller.  Asynchronous on `stream`.
+ * ------------------------------------------------------------------------- */
+spamm_status_t spamm_multiply_fp32_noalloc(const float* A, const float* B, float* C, int64_t n,
+                                           int32_t leaf, double tau, void* stream);
+
+/* ---------------------------------------------------------------------------
  * Status helpers.
  * spamm_status_string: static description of a status code.
  * spamm_last_device_status: reads and clears the library's device status word

@@ -54,6 +54,7 @@ _SIGS = {
     "spamm_multiply": [_VP, _VP, _VP, _VP, _VP],
     "spamm_frobenius_diff": [_VP, _VP, _I64, ctypes.POINTER(_D), _VP],
     "spamm_last_device_status": [_VP, ctypes.POINTER(_I32)],
+    "spamm_multiply_fp32_noalloc": [_VP, _VP, _VP, _I64, _I32, _D, _VP],
 }
 
 
@@ -187,6 +188,14 @@ def spamm_frobenius_diff(X, Y=None, stream=None) -> float:
     _check(lib().spamm_frobenius_diff(_ptr(X), _ptr(Y), X.numel(), ctypes.byref(out),
                                       _stream(stream)), "spamm_frobenius_diff")
     return out.value
+
+
+def spamm_multiply_fp32_noalloc(A, B, C, leaf: int, tau: float, stream=None):
+    """FP32 SpAMM with no device allocation (static library scratch; ceil(n/leaf) <= 64)."""
+    _check(lib().spamm_multiply_fp32_noalloc(_ptr(A), _ptr(B), _ptr(C), A.shape[0], leaf,
+                                             float(tau), _stream(stream)),
+           "spamm_multiply_fp32_noalloc")
+    return C
 
 
 def spamm_last_device_status(stream=None) -> int:

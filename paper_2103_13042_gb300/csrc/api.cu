@@ -79,8 +79,12 @@ double hi_unit(spamm_precision_t p) {
 
 size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
+}  // namespace
+
+namespace spamm {
+
 // Lays the plan buffers out in one allocation; returns the total size.
-size_t layout(int bd, PlanBuffers* b, char* base) {
+size_t plan_layout(int bd, PlanBuffers* b, char* base) {
   const size_t tiles = (size_t)bd * bd;
   const size_t parts = (size_t)plan_part_count(bd);
   size_t off = 0;
@@ -109,6 +113,10 @@ size_t layout(int bd, PlanBuffers* b, char* base) {
   if (b) *b = t;
   return align_up(off, 256);
 }
+
+}  // namespace spamm
+
+namespace {
 
 spamm_status_t check_shape(int64_t n, int32_t leaf) {
   if (n < 1) return SPAMM_ERR_INVALID_ARG;
@@ -154,7 +162,7 @@ spamm_status_t spamm_plan_workspace_size(int64_t n, int32_t leaf, spamm_precisio
   if (st != SPAMM_OK) return st;
   if (!precision_ok(precision)) return SPAMM_ERR_INVALID_ARG;
   if (!bytes) return SPAMM_ERR_INVALID_ARG;
-  *bytes = layout((int)num_blocks(n, leaf), nullptr, nullptr);
+  *bytes = plan_layout((int)num_blocks(n, leaf), nullptr, nullptr);
   return SPAMM_OK;
 }
 
@@ -167,7 +175,7 @@ spamm_status_t spamm_plan_create(spamm_plan_t* plan, int64_t n, int32_t leaf,
   if (!precision_ok(precision)) return SPAMM_ERR_INVALID_ARG;
   if (precision != SPAMM_FP32) return SPAMM_ERR_UNSUPPORTED;  // tensor-core modes: see multiply_tc
   const int bd = (int)num_blocks(n, leaf);
-  const size_t need = layout(bd, nullptr, nullptr);
+  const size_t need = plan_layout(bd, nullptr, nullptr);
   spamm_plan_s* p = new (std::nothrow) spamm_plan_s();
   if (!p) return SPAMM_ERR_NO_MEMORY;
   p->n = n;
@@ -192,7 +200,7 @@ spamm_status_t spamm_plan_create(spamm_plan_t* plan, int64_t n, int32_t leaf,
     }
     p->owns = true;
   }
-  layout(bd, &p->buf, static_cast<char*>(p->base));
+  plan_layout(bd, &p->buf, static_cast<char*>(p->base));
   *plan = p;
   return SPAMM_OK;
 }

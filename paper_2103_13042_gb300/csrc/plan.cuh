@@ -38,6 +38,10 @@ cudaError_t run_plan(PlanBuffers& b, const double* nA, const double* nB, double 
                      double target_rel, int split, double c1, cudaStream_t s);
 int64_t plan_part_count(int bd);
 
+// Carves the plan buffers for a bd x bd grid out of `base` (NULL: size only);
+// returns the bytes needed (256-byte aligned pieces).
+size_t plan_layout(int bd, PlanBuffers* b, char* base);
+
 cudaError_t launch_normmap(const float* X, int64_t n, int32_t leaf, double* out, cudaStream_t s);
 
 cudaError_t launch_multiply_simt(const PlanBuffers& b, const float* A, const float* B, float* C,
