@@ -5,6 +5,7 @@
 #include <new>
 
 #include "plan.cuh"
+#include "tc_common.cuh"
 
 using namespace spamm;
 
@@ -17,6 +18,7 @@ struct spamm_plan_s {
   void* base = nullptr;     // workspace
   bool owns = false;
   PlanBuffers buf{};
+  OperandImages img{};      // tensor-core modes only
 };
 
 namespace spamm {
@@ -110,7 +112,43 @@ size_t plan_layout(int bd, PlanBuffers* b, char* base) {
   t.tile_ptr = reinterpret_cast<int*>(take((tiles + 1) * sizeof(int)));
   t.order = reinterpret_cast<int*>(take(tiles * sizeof(int)));
   t.k_idx = reinterpret_cast<uint16_t*>(take(tiles * (size_t)bd * sizeof(uint16_t)));
+  t.needA = reinterpret_cast<uint8_t*>(take(tiles));
+  t.needB = reinterpret_cast<uint8_t*>(take(tiles));
   if (b) *b = t;
+  return align_up(off, 256);
+}
+
+bool is_tensor_mode(spamm_precision_t p) { return p != SPAMM_FP32; }
+
+bool has_lo(spamm_precision_t p) {
+  return p == SPAMM_BF16_SPLIT || p == SPAMM_FP16_SPLIT || p == SPAMM_TF32X3;
+}
+
+// Operand images of the tensor-core modes, carved after the plan buffers.
+size_t images_layout(int bd, int leaf, spamm_precision_t prec, OperandImages* img, char* base) {
+  OperandImages t{};
+  if (!is_tensor_mode(prec)) {
+    if (img) *img = t;
+    return 0;
+  }
+  const size_t tiles = (size_t)bd * bd;
+  const size_t blk = (size_t)leaf * leaf * (prec == SPAMM_TF32X3 ? 4 : 2);
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    off = align_up(off, 256);
+    char* p = base ? base + off : nullptr;
+    off += bytes;
+    return p;
+  };
+  t.a_hi = reinterpret_cast<uint8_t*>(take(tiles * blk));
+  t.b_hi = reinterpret_cast<uint8_t*>(take(tiles * blk));
+  if (has_lo(prec)) {
+    t.a_lo = reinterpret_cast<uint8_t*>(take(tiles * blk));
+    t.b_lo = reinterpret_cast<uint8_t*>(take(tiles * blk));
+  }
+  t.ea = reinterpret_cast<int32_t*>(take(tiles * sizeof(int32_t)));
+  t.eb = reinterpret_cast<int32_t*>(take(tiles * sizeof(int32_t)));
+  if (img) *img = t;
   return align_up(off, 256);
 }
 
@@ -162,7 +200,9 @@ spamm_status_t spamm_plan_workspace_size(int64_t n, int32_t leaf, spamm_precisio
   if (st != SPAMM_OK) return st;
   if (!precision_ok(precision)) return SPAMM_ERR_INVALID_ARG;
   if (!bytes) return SPAMM_ERR_INVALID_ARG;
-  *bytes = plan_layout((int)num_blocks(n, leaf), nullptr, nullptr);
+  if (is_tensor_mode(precision) && leaf == 32) return SPAMM_ERR_UNSUPPORTED;
+  const int bd = (int)num_blocks(n, leaf);
+  *bytes = plan_layout(bd, nullptr, nullptr) + images_layout(bd, leaf, precision, nullptr, nullptr);
   return SPAMM_OK;
 }
 
@@ -173,9 +213,10 @@ spamm_status_t spamm_plan_create(spamm_plan_t* plan, int64_t n, int32_t leaf,
   spamm_status_t st = check_shape(n, leaf);
   if (st != SPAMM_OK) return st;
   if (!precision_ok(precision)) return SPAMM_ERR_INVALID_ARG;
-  if (precision != SPAMM_FP32) return SPAMM_ERR_UNSUPPORTED;  // tensor-core modes: see multiply_tc
+  if (is_tensor_mode(precision) && leaf == 32) return SPAMM_ERR_UNSUPPORTED;
   const int bd = (int)num_blocks(n, leaf);
-  const size_t need = plan_layout(bd, nullptr, nullptr);
+  const size_t plan_bytes = plan_layout(bd, nullptr, nullptr);
+  const size_t need = plan_bytes + images_layout(bd, leaf, precision, nullptr, nullptr);
   spamm_plan_s* p = new (std::nothrow) spamm_plan_s();
   if (!p) return SPAMM_ERR_NO_MEMORY;
   p->n = n;
@@ -201,6 +242,7 @@ spamm_status_t spamm_plan_create(spamm_plan_t* plan, int64_t n, int32_t leaf,
     p->owns = true;
   }
   plan_layout(bd, &p->buf, static_cast<char*>(p->base));
+  images_layout(bd, leaf, precision, &p->img, static_cast<char*>(p->base) + plan_bytes);
   *plan = p;
   return SPAMM_OK;
 }
@@ -287,7 +329,17 @@ spamm_status_t spamm_multiply(spamm_plan_t plan, const float* A, const float* B,
     case SPAMM_FP32:
       e = launch_multiply_simt(plan->buf, A, B, C, plan->n, plan->leaf, (cudaStream_t)stream);
       break;
-    default: return SPAMM_ERR_UNSUPPORTED;
+    default: {
+      int32_t* status = device_status_word();
+      if (!status) return SPAMM_ERR_NO_MEMORY;
+      const cudaStream_t s = (cudaStream_t)stream;
+      e = launch_quantize(plan->precision, plan->leaf, A, B, plan->n, plan->bd, plan->buf.needA,
+                          plan->buf.needB, plan->img, s);
+      if (e == cudaSuccess) e = launch_zero_empty_tiles(plan->buf, C, plan->n, plan->leaf, s);
+      if (e == cudaSuccess)
+        e = launch_multiply_tc(plan->precision, plan->leaf, plan->buf, plan->img, C, plan->n,
+                               status, s);
+    }
   }
   if (e != cudaSuccess) {
     (void)cudaGetLastError();

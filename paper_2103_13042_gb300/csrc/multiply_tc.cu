@@ -1,0 +1,460 @@
+// Tensor-core multiply (Section 3.3 / Algorithm 3, rebuilt for tcgen05):
+//   C[i,j] = sum over listed k of 2^(ea[i,k] + eb[k,j]) * (Ahi Bhi [+ 2^-s (Ahi Blo + Alo Bhi)])
+// over the plan's non-empty tiles, most survivors first.
+//
+// One persistent CTA per SM, six warps with fixed roles:
+//   warp 0   TMA producer: walks the CTA's tiles and their surviving k,
+//            waits for a free shared-memory stage and copies the operand
+//            image chunks (A hi, B hi, and the lo parts of split triples)
+//            with one bulk copy each; per-stage metadata marks run starts,
+//            tile ends and split triples.
+//   warp 1   allocates tensor memory and issues the MMAs from one thread:
+//            consecutive k of a tile with the same exponent sum (and split
+//            flag) form a run accumulated in one TMEM accumulator; runs
+//            alternate between two accumulators so the epilogue of one
+//            overlaps the MMAs of the next.  Each stage is released by
+//            tcgen05.commit when its MMAs have read it.
+//   warps 2+  epilogue (4 warps per 64 output columns): for each run, load
+//            the accumulator rows (one TMEM lane per output row, 64 columns
+//            per warp), rescale by 2^(ea+eb) in FP32 and add to the tile's
+//            register accumulator; at a tile's last run store the rows to C.
+// Every wait is bounded in wall time; on expiry the CTA raises an abort flag
+// (and SPAMM_ERR_TIMEOUT in the status word), the roles leave their loops,
+// outstanding copies and MMAs are drained with bounded waits, and TMEM is
+// released.
+#include "tc_common.cuh"
+
+namespace spamm {
+namespace {
+
+using namespace tc;
+
+constexpr int kRunRing = 16;
+constexpr uint64_t kWaitLimitNs = 2000000000ull;   // 2 s: a safety net, never hit normally
+constexpr uint64_t kDrainLimitNs = 100000000ull;   // 100 ms for the abort drain
+
+struct StageMeta {
+  int32_t flags;   // 1: first chunk of a run, 2: last chunk of a tile, 4: split, 8: end of work
+  int32_t s;       // exponent sum of the run
+  int32_t tile;
+  int32_t pad;
+};
+
+struct RunRec {
+  int32_t tile, s, split, last;
+};
+
+struct TcParams {
+  const uint8_t* a_hi;
+  const uint8_t* a_lo;
+  const uint8_t* b_hi;
+  const uint8_t* b_lo;
+  const int32_t* ea;
+  const int32_t* eb;
+  const int* order;
+  const int* tile_ptr;
+  const uint16_t* k_idx;
+  const PlanDevice* pd;
+  float* C;
+  int64_t n;
+  int bd;
+  int32_t* status;
+};
+
+template <uint32_t FMT, int LEAF, int SPLITMODE>
+struct TcCfg {
+  using L = TcLayout<FMT, LEAF>;
+  static constexpr bool kHasLo = SPLITMODE != 0;
+  static constexpr int M = LEAF, N = LEAF;
+  static constexpr int kEpiWarps = 4 * (N / 64);          // 64 columns per epilogue warp
+  static constexpr int kThreads = 64 + 32 * kEpiWarps;
+  static constexpr uint32_t kStageBytes = L::kChunkBytes * 2 * (kHasLo ? 2 : 1);
+  static constexpr int kStagesFit = (200 * 1024) / kStageBytes;
+  static constexpr int kStages = kStagesFit > 16 ? 16 : kStagesFit;
+  static constexpr int kAccCols = N * (kHasLo ? 2 : 1);
+  static constexpr uint32_t kTmemCols = 2 * kAccCols;               // 128, 256 or 512
+  static constexpr uint32_t kIdesc = idesc(FMT, M, N);
+  static constexpr size_t kBarOffset = (size_t)kStages * kStageBytes;
+  static constexpr int kNumBars = 2 * kStages + 4 + 2 * kRunRing + 1;
+  static constexpr size_t kMetaOffset = kBarOffset + (size_t)kNumBars * 8;
+  static constexpr size_t kRunOffset = kMetaOffset + (size_t)kStages * sizeof(StageMeta);
+  static constexpr size_t kMiscOffset = kRunOffset + (size_t)kRunRing * sizeof(RunRec);
+  static constexpr size_t kSmemBytes = kMiscOffset + 64 + 1024;     // + alignment slack
+  static_assert(kStages >= 2, "at least two pipeline stages");
+  static_assert(kTmemCols >= 32 && kTmemCols <= 512, "TMEM columns");
+  static_assert(kSmemBytes <= 227 * 1024, "shared memory");
+};
+
+// Bounded wait that also returns when another role raised the abort flag.
+__device__ __forceinline__ bool wait_ab(uint64_t* bar, uint32_t parity, volatile int* abort_flag,
+                                        int32_t* status) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const uint64_t t0 = globaltimer_ns();
+  for (uint32_t it = 1;; ++it) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if ((it & 63u) == 0) {
+      if (*abort_flag) return false;
+      if (globaltimer_ns() - t0 > kWaitLimitNs) {
+        *abort_flag = 1;
+        atomicExch(status, (int32_t)SPAMM_ERR_TIMEOUT);
+        return false;
+      }
+    }
+  }
+}
+
+template <uint32_t FMT>
+__device__ __forceinline__ void mma(uint32_t d, uint64_t a, uint64_t b, uint32_t id,
+                                    uint32_t accumulate) {
+  if constexpr (FMT == kFmtTF32) mma_tf32(d, a, b, id, accumulate);
+  else mma_f16(d, a, b, id, accumulate);
+}
+
+template <uint32_t FMT, int LEAF, int SPLITMODE>
+__global__ void __launch_bounds__(TcCfg<FMT, LEAF, SPLITMODE>::kThreads, 1)
+    tc_multiply_kernel(TcParams p) {
+  using Cfg = TcCfg<FMT, LEAF, SPLITMODE>;
+  using L = typename Cfg::L;
+  constexpr int S = Cfg::kStages, N = Cfg::N;
+  constexpr uint32_t CH = L::kChunkBytes;
+
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem =
+      reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + Cfg::kBarOffset);
+  uint64_t* full = bars;
+  uint64_t* empty = bars + S;
+  uint64_t* acc_full = bars + 2 * S;
+  uint64_t* acc_empty = acc_full + 2;
+  uint64_t* run_full = acc_empty + 2;
+  uint64_t* run_empty = run_full + kRunRing;
+  uint64_t* drain = run_empty + kRunRing;
+  StageMeta* meta = reinterpret_cast<StageMeta*>(smem + Cfg::kMetaOffset);
+  RunRec* runs = reinterpret_cast<RunRec*>(smem + Cfg::kRunOffset);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + Cfg::kMiscOffset);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + Cfg::kMiscOffset + 4);
+
+  const int warp = threadIdx.x / 32, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < S; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&acc_full[b], 1);
+      mbar_init(&acc_empty[b], Cfg::kEpiWarps);
+    }
+    for (int r = 0; r < kRunRing; ++r) {
+      mbar_init(&run_full[r], 1);
+      mbar_init(&run_empty[r], Cfg::kEpiWarps);
+    }
+    mbar_init(drain, 1);
+    *abort_flag = 0;
+    fence_mbarrier_init();
+  }
+  if (warp == 1) {
+    tmem_alloc(tmem_slot, Cfg::kTmemCols);
+    tmem_relinquish();
+  }
+  fence_before_sync();
+  __syncthreads();
+  fence_after_sync();
+  const uint32_t tmem = *tmem_slot;
+  const int bd = p.bd;
+  const int ne = p.pd->nonempty;
+
+  if (warp == 0) {
+    // ------------------------------------------------------------ producer
+    if (lane == 0) {
+      uint32_t stage = 0, phase = 0;
+      uint32_t issued = 0, issued_phase = 0;   // bit s: stage s has a copy in flight / its parity
+      bool ok = true;
+      for (int w = blockIdx.x; w < ne && ok; w += gridDim.x) {
+        const int t = p.order[w];
+        const int i = t / bd, j = t % bd;
+        const int beg = p.tile_ptr[t], end = p.tile_ptr[t + 1];
+        int32_t prev_key = 0;
+        for (int q = beg; q < end && ok; ++q) {
+          const uint32_t ent = p.k_idx[q];
+          const int k = (int)(ent & 0x3ffu);
+          const bool split = SPLITMODE == 2 || (SPLITMODE == 1 && (ent & 0x8000u));
+          const int32_t s = p.ea[(int64_t)i * bd + k] + p.eb[(int64_t)k * bd + j];
+          const int32_t key = s * 2 + (split ? 1 : 0);
+          const bool first = q == beg || key != prev_key;
+          prev_key = key;
+          const bool last = q == end - 1;
+          const int64_t oa = ((int64_t)i * bd + k) * L::kBlockBytes;
+          const int64_t ob = ((int64_t)k * bd + j) * L::kBlockBytes;
+          for (int c = 0; c < L::kNch; ++c) {
+            if (!wait_ab(&empty[stage], phase ^ 1u, abort_flag, p.status)) {
+              ok = false;
+              break;
+            }
+            StageMeta m;
+            m.flags = (first && c == 0 ? 1 : 0) | (last && c == L::kNch - 1 ? 2 : 0) |
+                      (split ? 4 : 0);
+            m.s = s;
+            m.tile = t;
+            m.pad = 0;
+            meta[stage] = m;
+            mbar_arrive_expect_tx(&full[stage], CH * 2 * (split ? 2 : 1));
+            uint8_t* sb = smem + (size_t)stage * Cfg::kStageBytes;
+            bulk_g2s(sb, p.a_hi + oa + c * CH, CH, &full[stage]);
+            bulk_g2s(sb + CH, p.b_hi + ob + c * CH, CH, &full[stage]);
+            if constexpr (Cfg::kHasLo) {
+              if (split) {
+                bulk_g2s(sb + 2 * CH, p.a_lo + oa + c * CH, CH, &full[stage]);
+                bulk_g2s(sb + 3 * CH, p.b_lo + ob + c * CH, CH, &full[stage]);
+              }
+            }
+            issued |= 1u << stage;
+            issued_phase = (issued_phase & ~(1u << stage)) | (phase << stage);
+            if (++stage == S) {
+              stage = 0;
+              phase ^= 1u;
+            }
+          }
+        }
+      }
+      if (ok && wait_ab(&empty[stage], phase ^ 1u, abort_flag, p.status)) {
+        meta[stage].flags = 8;   // end of work
+        mbar_arrive(&full[stage]);
+      }
+      if (*abort_flag) {   // let every copy this thread issued land before the CTA exits
+        for (int s = 0; s < S; ++s)
+          if (issued & (1u << s)) (void)mbar_wait(&full[s], (issued_phase >> s) & 1u, kDrainLimitNs);
+      }
+    }
+  } else if (warp == 1) {
+    // ------------------------------------------------------------ MMA issuer
+    if (lane == 0) {
+      uint32_t stage = 0, phase = 0, slot = 0, slot_phase = 0;
+      int run = -1, runs_opened = 0;
+      bool open = false, split_run = false, ok = true;
+      int32_t run_s = 0, run_tile = 0;
+      uint32_t acc_hh = 0, acc_x = 0, d_hh = tmem, d_x = tmem + N;
+      auto close_run = [&](int last) -> bool {
+        if (!wait_ab(&run_empty[slot], slot_phase ^ 1u, abort_flag, p.status)) return false;
+        runs[slot] = RunRec{run_tile, run_s, split_run ? 1 : 0, last};
+        mbar_arrive(&run_full[slot]);
+        if (++slot == kRunRing) {
+          slot = 0;
+          slot_phase ^= 1u;
+        }
+        mma_commit(&acc_full[run & 1]);
+        open = false;
+        return true;
+      };
+      for (;;) {
+        if (!wait_ab(&full[stage], phase, abort_flag, p.status)) {
+          ok = false;
+          break;
+        }
+        const StageMeta m = meta[stage];
+        if (m.flags & 8) break;
+        fence_after_sync();
+        if (m.flags & 1) {
+          if (open && !close_run(0)) {
+            ok = false;
+            break;
+          }
+          run = runs_opened++;
+          const int buf = run & 1;
+          if (!wait_ab(&acc_empty[buf], (((uint32_t)run >> 1) & 1u) ^ 1u, abort_flag, p.status)) {
+            ok = false;
+            break;
+          }
+          fence_after_sync();
+          d_hh = tmem + (uint32_t)(buf * Cfg::kAccCols);
+          d_x = d_hh + N;
+          acc_hh = 0;
+          acc_x = 0;
+          open = true;
+          split_run = (m.flags & 4) != 0;
+          run_s = m.s;
+          run_tile = m.tile;
+        }
+        const uint32_t a0 = smem_u32(smem + (size_t)stage * Cfg::kStageBytes);
+        const uint32_t b0 = a0 + CH, al = a0 + 2 * CH, bl = a0 + 3 * CH;
+#pragma unroll
+        for (int ks = 0; ks < 4; ++ks) {
+          const uint64_t ad = sdesc_k_sw128(a0 + 32 * ks);
+          const uint64_t bdsc = sdesc_k_sw128(b0 + 32 * ks);
+          mma<FMT>(d_hh, ad, bdsc, Cfg::kIdesc, acc_hh);
+          acc_hh = 1;
+          if constexpr (Cfg::kHasLo) {
+            if (split_run) {
+              mma<FMT>(d_x, ad, sdesc_k_sw128(bl + 32 * ks), Cfg::kIdesc, acc_x);
+              acc_x = 1;
+              mma<FMT>(d_x, sdesc_k_sw128(al + 32 * ks), bdsc, Cfg::kIdesc, 1);
+            }
+          }
+        }
+        mma_commit(&empty[stage]);
+        if ((m.flags & 2) && !close_run(1)) {
+          ok = false;
+          break;
+        }
+        if (++stage == S) {
+          stage = 0;
+          phase ^= 1u;
+        }
+      }
+      if (ok && wait_ab(&run_empty[slot], slot_phase ^ 1u, abort_flag, p.status)) {
+        runs[slot] = RunRec{-1, 0, 0, 1};   // end of work
+        mbar_arrive(&run_full[slot]);
+      }
+      mma_commit(drain);   // every MMA this thread issued has finished before TMEM is freed
+      (void)mbar_wait(drain, 0, kDrainLimitNs);
+    }
+  } else {
+    // ------------------------------------------------------------ epilogue
+    constexpr int NC = 64;                       // columns owned by this warp
+    const int quarter = warp & 3;
+    const int col0 = ((warp - 2) / 4) * NC;
+    const int row = Cfg::M == 128 ? quarter * 32 + lane : quarter * 16 + lane;
+    const bool lane_has_row = Cfg::M == 128 || lane < 16;
+    const float lo_w = 1.0f / (float)(1 << L::kLoShift);
+    float acc[NC];
+#pragma unroll
+    for (int c = 0; c < NC; ++c) acc[c] = 0.0f;
+    uint32_t slot = 0, slot_phase = 0;
+    int run = 0;
+    for (;;) {
+      if (!wait_ab(&run_full[slot], slot_phase, abort_flag, p.status)) break;
+      const RunRec r = runs[slot];
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&run_empty[slot]);
+      if (++slot == kRunRing) {
+        slot = 0;
+        slot_phase ^= 1u;
+      }
+      if (r.tile < 0) break;
+      const int buf = run & 1;
+      if (!wait_ab(&acc_full[buf], ((uint32_t)run >> 1) & 1u, abort_flag, p.status)) break;
+      fence_after_sync();
+      const float scale = ldexpf(1.0f, r.s);
+      const uint32_t base = tmem + (uint32_t)(buf * Cfg::kAccCols + col0) +
+                            ((uint32_t)(quarter * 32) << 16);
+#pragma unroll
+      for (int c0 = 0; c0 < NC; c0 += 32) {
+        float v[32];
+        tmem_ld32(base + c0, v);
+        if constexpr (Cfg::kHasLo) {
+          if (r.split) {
+            float x[32];
+            tmem_ld32(base + N + c0, x);
+#pragma unroll
+            for (int q = 0; q < 32; ++q) v[q] = fmaf(x[q], lo_w, v[q]);
+          }
+        }
+#pragma unroll
+        for (int q = 0; q < 32; ++q) acc[c0 + q] = fmaf(v[q], scale, acc[c0 + q]);
+      }
+      fence_before_sync();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&acc_empty[buf]);
+      ++run;
+      if (r.last) {
+        const int i = r.tile / bd, j = r.tile % bd;
+        const int64_t gr = (int64_t)i * LEAF + row;
+        if (lane_has_row && gr < p.n) {
+          float* dst = p.C + gr * p.n + (int64_t)j * LEAF + col0;
+          const int64_t cols = p.n - (int64_t)j * LEAF - col0;
+          if (cols >= NC && (p.n & 3) == 0) {
+#pragma unroll
+            for (int c = 0; c < NC; c += 4)
+              *reinterpret_cast<float4*>(dst + c) =
+                  make_float4(acc[c], acc[c + 1], acc[c + 2], acc[c + 3]);
+          } else {
+#pragma unroll
+            for (int c = 0; c < NC; ++c)
+              if (c < cols) dst[c] = acc[c];
+          }
+        }
+#pragma unroll
+        for (int c = 0; c < NC; ++c) acc[c] = 0.0f;
+      }
+    }
+  }
+
+  fence_before_sync();
+  __syncthreads();
+  if (warp == 1) {
+    __syncwarp();
+    fence_after_sync();
+    tmem_dealloc(tmem, Cfg::kTmemCols);
+  }
+}
+
+__global__ void __launch_bounds__(256)
+    zero_tiles_kernel(const int* __restrict__ order, const PlanDevice* __restrict__ pd, int bd,
+                      float* __restrict__ C, int64_t n, int leaf) {
+  const int ne = pd->nonempty;
+  const int64_t tiles = (int64_t)bd * bd;
+  const int lane = threadIdx.x & 31;
+  const int64_t gw = (int64_t)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+  const int64_t nw = (int64_t)gridDim.x * (blockDim.x / 32);
+  for (int64_t w = ne + gw; w < tiles; w += nw) {
+    const int t = order[w];
+    const int64_t r0 = (int64_t)(t / bd) * leaf, c0 = (int64_t)(t % bd) * leaf;
+    const int64_t rows = min((int64_t)leaf, n - r0), cols = min((int64_t)leaf, n - c0);
+    if ((n & 3) == 0 && cols == leaf) {
+      const int per_row = leaf / 4;
+      for (int e = lane; e < rows * per_row; e += 32) {
+        const int64_t r = e / per_row, c4 = e % per_row;
+        *reinterpret_cast<float4*>(C + (r0 + r) * n + c0 + 4 * c4) = make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+    } else {
+      for (int64_t e = lane; e < rows * cols; e += 32) C[(r0 + e / cols) * n + c0 + e % cols] = 0.f;
+    }
+  }
+}
+
+template <uint32_t FMT, int LEAF, int SPLITMODE>
+cudaError_t launch_tc(const TcParams& prm, cudaStream_t s) {
+  using Cfg = TcCfg<FMT, LEAF, SPLITMODE>;
+  auto kern = tc_multiply_kernel<FMT, LEAF, SPLITMODE>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)Cfg::kSmemBytes);
+  if (e != cudaSuccess) return e;
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  kern<<<sms, Cfg::kThreads, Cfg::kSmemBytes, s>>>(prm);
+  return cudaPeekAtLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_zero_empty_tiles(const PlanBuffers& b, float* C, int64_t n, int leaf,
+                                    cudaStream_t s) {
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  zero_tiles_kernel<<<sms * 8, 256, 0, s>>>(b.order, b.pd, b.bd, C, n, leaf);
+  return cudaPeekAtLastError();
+}
+
+cudaError_t launch_multiply_tc(spamm_precision_t prec, int leaf, const PlanBuffers& b,
+                               const OperandImages& img, float* C, int64_t n, int32_t* status,
+                               cudaStream_t s) {
+  TcParams prm{img.a_hi, img.a_lo, img.b_hi, img.b_lo, img.ea,  img.eb, b.order, b.tile_ptr,
+               b.k_idx,  b.pd,     C,        n,        b.bd,    status};
+  const bool l64 = leaf == 64;
+  switch (prec) {
+    case SPAMM_BF16:
+      return l64 ? launch_tc<kFmtBF16, 64, 0>(prm, s) : launch_tc<kFmtBF16, 128, 0>(prm, s);
+    case SPAMM_FP16:
+      return l64 ? launch_tc<kFmtF16, 64, 0>(prm, s) : launch_tc<kFmtF16, 128, 0>(prm, s);
+    case SPAMM_BF16_SPLIT:
+      return l64 ? launch_tc<kFmtBF16, 64, 1>(prm, s) : launch_tc<kFmtBF16, 128, 1>(prm, s);
+    case SPAMM_FP16_SPLIT:
+      return l64 ? launch_tc<kFmtF16, 64, 1>(prm, s) : launch_tc<kFmtF16, 128, 1>(prm, s);
+    case SPAMM_TF32X3:
+      return l64 ? launch_tc<kFmtTF32, 64, 2>(prm, s) : launch_tc<kFmtTF32, 128, 2>(prm, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace spamm

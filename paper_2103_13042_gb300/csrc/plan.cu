@@ -205,7 +205,7 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32)
     count_kernel(const Screen* __restrict__ sA, const Screen* __restrict__ sBT,
                  const double* __restrict__ nA, const double* __restrict__ nB, int bd,
                  TauScreen T, int split, PlanDevice* __restrict__ pd, int* __restrict__ cnt,
-                 CountParts parts) {
+                 CountParts parts, uint8_t* __restrict__ needA, uint8_t* __restrict__ needB) {
   __shared__ double s_bin_sum[kFlagBins];
   __shared__ int s_bin_cnt[kFlagBins];
   __shared__ long long s_S[kWarpsPerCta];
@@ -266,7 +266,11 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32)
       atomicAdd(&s_bin_cnt[run_bin - kFlagBinMin], run_cnt);
     }
     skipped = ext_value(ext_warp_sum(sk));
-    if (lane == 0) cnt[t] = count;
+    if (lane == 0) {
+      cnt[t] = count;
+      needA[t] = 0;   // the fill kernel sets the blocks survivors use
+      needB[t] = 0;
+    }
   }
   if (lane == 0) {
     s_S[warp] = t < tiles ? count : 0;
@@ -419,7 +423,8 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32)
     fill_kernel(const Screen* __restrict__ sA, const Screen* __restrict__ sBT,
                 const double* __restrict__ nA, const double* __restrict__ nB, int bd, TauScreen T,
                 int split, const PlanDevice* __restrict__ pd, const int* __restrict__ cnt,
-                const int* __restrict__ tile_ptr, uint16_t* __restrict__ k_idx) {
+                const int* __restrict__ tile_ptr, uint16_t* __restrict__ k_idx,
+                uint8_t* __restrict__ needA, uint8_t* __restrict__ needB) {
   const int warp = threadIdx.x / 32, lane = threadIdx.x & 31;
   const int64_t t = (int64_t)blockIdx.x * kWarpsPerCta + warp;
   if (t >= (int64_t)bd * bd) return;
@@ -442,6 +447,8 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32)
         if (rel_bin(p, inv) >= m) v |= kSplitFlag;
       }
       k_idx[base + __popc(ball & ((1u << lane) - 1u))] = v;
+      needA[(int64_t)i * bd + k] = 1;   // benign: every writer stores 1
+      needB[(int64_t)k * bd + j] = 1;
     }
     base += __popc(ball);
   }
@@ -460,11 +467,12 @@ cudaError_t run_plan(PlanBuffers& b, const double* nA, const double* nB, double 
   const int count_ctas = (int)((tiles + kWarpsPerCta - 1) / kWarpsPerCta);
   CountParts parts{b.part_S, b.part_kmax, b.part_ne, b.part_b1, b.part_b2};
   count_kernel<<<count_ctas, kWarpsPerCta * 32, 0, s>>>(b.sA, b.sBT, nA, nB, bd, T, split, b.pd,
-                                                        b.cnt, parts);
+                                                        b.cnt, parts, b.needA, b.needB);
   finalize_kernel<<<1, kFinThreads, 0, s>>>(b.cnt, bd, parts, count_ctas, split, c1, target_rel,
                                             b.pd, b.tile_ptr, b.order);
   fill_kernel<<<count_ctas, kWarpsPerCta * 32, 0, s>>>(b.sA, b.sBT, nA, nB, bd, T, split, b.pd,
-                                                       b.cnt, b.tile_ptr, b.k_idx);
+                                                       b.cnt, b.tile_ptr, b.k_idx, b.needA,
+                                                       b.needB);
   return cudaPeekAtLastError();
 }
 

@@ -31,6 +31,8 @@ struct PlanBuffers {
   int* tile_ptr;       // [bd*bd + 1] CSR offsets
   int* order;          // [bd*bd] tiles, most survivors first, empty tiles last
   uint16_t* k_idx;     // [bd^3] surviving k per tile (bit 15: split triple)
+  uint8_t* needA;      // [bd*bd] 1 if block A[i,k] takes part in some surviving triple
+  uint8_t* needB;      // [bd*bd] 1 if block B[k,j] takes part in some surviving triple
   PlanDevice* pd;
 };
 

