@@ -4,8 +4,14 @@ A step is one pass of the hot path over the workload with inputs resident in
 HBM: norm map of A, norm map of B, the pair test / work-queue plan at tau,
 and the multiply that writes C.  The default workload is the mixed-precision
 decay case: N = 8192, a_ij = (|i-j|+1)^-3 * s_ij (s = +-1, A and B
-independent), leaf 64.  The metric is dense-equivalent throughput 2 N^3 / t
-(TFLOP/s); ms_per_step gives the time.
+independent), leaf 64, BF16 block products with power-of-two block scaling,
+FP32 accumulation and hi+lo products on the dominant blocks, at the fixed
+relative error ||C - AB||_F / (||A||_F ||B||_F) <= 1e-5: tau = 1e-2 is the
+largest tau of the 1e-1..1e-7 sweep whose pruning error stays below it
+(1.4e-7), and the split flags keep the rounding inside the rest of the
+budget.  The metric is dense-equivalent throughput 2 N^3 / t (TFLOP/s);
+ms_per_step gives the time.  The plain FP32 SpAMM and cuBLAS SGEMM (TF32 off)
+are timed on the same GPU as baselines.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
                        [--precision fp32|bf16|...] [--tau T]
@@ -169,13 +175,16 @@ def run_ours(args, rank, world):
     plan = P.Plan(n, leaf, prec)
     stream = torch.cuda.current_stream()
 
-    def step():
-        P.spamm_normmap(A, leaf, nA, stream)
-        P.spamm_normmap(B, leaf, nB, stream)
-        plan.plan(nA, nB, tau, args.target, stream)
-        plan.multiply(A, B, C, stream)
+    def step(st=None):
+        st = st if st is not None else torch.cuda.current_stream()
+        P.spamm_normmap(A, leaf, nA, st)
+        P.spamm_normmap(B, leaf, nB, st)
+        plan.plan(nA, nB, tau, args.target, st)
+        plan.multiply(A, B, C, st)
 
-    launches_per_step = 2 + 5 + 1
+    # our kernels per step: 2 norm maps, 4 plan kernels, multiply (SIMT: multiply +
+    # zero-fill; tensor cores: quantize + zero-fill + multiply)
+    launches_per_step = 2 + 4 + (2 if prec == P.FP32 else 3)
 
     def barrier():
         if world > 1:
@@ -204,15 +213,41 @@ def run_ours(args, rank, world):
             parts[name].append(ev[k].elapsed_time(ev[k + 1]))
     part_ms = {k: statistics.median(v) for k, v in parts.items()}
 
-    # timed region: K steps
+    # eager per-step time (host enqueues every call)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    eager_ms = e0.elapsed_time(e1) / args.steps
+
+    # the same API calls captured once into a CUDA graph (the library enqueues
+    # no allocation or synchronisation after the first call), replayed K times
+    graph = None
+    if not args.eager:
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph):
+            step()
+        for _ in range(3):
+            graph.replay()
+        torch.cuda.synchronize()
+
+    def timed_step():
+        if graph is not None:
+            graph.replay()
+        else:
+            step()
+
+    # timed region: K steps
     barrier()
     torch.cuda.synchronize()
     with ClockSampler(local) as clk:
         time.sleep(0.3)
         e0.record(stream)
         for _ in range(args.steps):
-            step()
+            timed_step()
         e1.record(stream)
         torch.cuda.synchronize()
         time.sleep(0.3)
@@ -250,6 +285,39 @@ def run_ours(args, rank, world):
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         e2e_ms = float(t.item())
 
+    # baselines on the same GPU: plain FP32 SpAMM (same tau) and cuBLAS SGEMM
+    base = {}
+    if not args.no_baselines:
+        plan32 = P.Plan(n, leaf, P.FP32)
+        C32 = torch.empty_like(A)
+
+        def step32():
+            P.spamm_normmap(A, leaf, nA, stream)
+            P.spamm_normmap(B, leaf, nB, stream)
+            plan32.plan(nA, nB, tau, args.target, stream)
+            plan32.multiply(A, B, C32, stream)
+
+        def timed(fn, reps):
+            for _ in range(3):
+                fn()
+            g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            g0.record(stream)
+            for _ in range(reps):
+                fn()
+            g1.record(stream)
+            torch.cuda.synchronize()
+            return g0.elapsed_time(g1) / reps
+
+        base["fp32_spamm_ms"] = timed(step32, max(3, args.steps // 2))
+        prev = torch.backends.cuda.matmul.allow_tf32
+        torch.backends.cuda.matmul.allow_tf32 = False
+        base["cublas_sgemm_ms"] = timed(lambda: torch.matmul(A, B, out=C32), 3)
+        torch.backends.cuda.matmul.allow_tf32 = prev
+        base["speedup_vs_fp32_spamm"] = base["fp32_spamm_ms"] / ms
+        base["speedup_vs_cublas_sgemm"] = base["cublas_sgemm_ms"] / ms
+        del plan32, C32
+
     if rank != 0:
         return None
     peaks = load_peaks()
@@ -285,16 +353,20 @@ def run_ours(args, rank, world):
         "metric": METRIC, "value": value, "unit": "TFLOP/s (dense-equivalent, 2N^3/t)",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": {"fp32": "f32"}.get(args.precision, args.precision),
+        "dtype": {"fp32": "f32", "tf32x3": "tf32", "bf16_split": "bf16",
+                  "fp16_split": "f16", "fp16": "f16"}.get(args.precision, args.precision),
         "data": "synthetic (seeded algebraic-decay matrices)",
         "config": {"workload": f"algebraic decay (|i-j|+1)^-3 * (+-1), N={n}, leaf {leaf}, "
                                f"tau={tau:g}, {args.precision}",
                    "n": n, "leaf": leaf, "tau": tau, "precision": args.precision,
                    "target_rel_err": args.target, "parallelism": f"replicas x{world}",
+                   "launch": "eager" if graph is None else "cuda-graph replay of the API calls",
+                   "ms_per_step_eager": eager_ms,
                    "l2": "inputs larger than L2 (A, B, C 268 MB each vs 126 MB L2)",
                    "survivors": st["survivors"], "valid_ratio": st["valid_ratio"],
                    "skipped_bound2_rel": st["skipped_bound2"] / (st["norm_a"] * st["norm_b"])},
         "breakdown_ms": part_ms,
+        "baselines_same_gpu": base,
         "e2e": {"value": dense / (e2e_ms * 1e-3) / 1e12 * world,
                 "unit": "TFLOP/s (dense-equivalent, 2N^3/t)", "ms_per_step": e2e_ms,
                 "h2d_bytes_per_step": 2 * 4 * n * n, "d2h_bytes_per_step": 4 * n * n},
@@ -351,13 +423,15 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="fp32")
-    ap.add_argument("--tau", type=float, default=1e-4)
+    ap.add_argument("--precision", default="bf16_split")
+    ap.add_argument("--tau", type=float, default=1e-2)
     ap.add_argument("--target", type=float, default=1e-5)
     ap.add_argument("--n", type=int, default=N_DEFAULT)
     ap.add_argument("--leaf", type=int, default=LEAF_DEFAULT)
     ap.add_argument("--cpu-rows", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-baselines", action="store_true")
+    ap.add_argument("--eager", action="store_true", help="time host-enqueued calls, no graph")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 

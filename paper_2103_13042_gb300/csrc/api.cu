@@ -19,6 +19,8 @@ struct spamm_plan_s {
   bool owns = false;
   PlanBuffers buf{};
   OperandImages img{};      // tensor-core modes only
+  cudaStream_t side = nullptr;        // zero-fill of empty tiles runs here, overlapped
+  cudaEvent_t fork = nullptr, join = nullptr;
 };
 
 namespace spamm {
@@ -106,8 +108,10 @@ size_t plan_layout(int bd, PlanBuffers* b, char* base) {
   t.part_S = reinterpret_cast<long long*>(take(parts * sizeof(long long)));
   t.part_kmax = reinterpret_cast<int*>(take(parts * sizeof(int)));
   t.part_ne = reinterpret_cast<int*>(take(parts * sizeof(int)));
-  t.part_b1 = reinterpret_cast<double*>(take(parts * sizeof(double)));
-  t.part_b2 = reinterpret_cast<double*>(take(parts * sizeof(double)));
+  t.part_b1 = reinterpret_cast<ExtSum*>(take(parts * sizeof(ExtSum)));
+  t.part_b2 = reinterpret_cast<ExtSum*>(take(parts * sizeof(ExtSum)));
+  t.cta_base = reinterpret_cast<int*>(take(parts * sizeof(int)));
+  t.cta_ebase = reinterpret_cast<int*>(take(parts * sizeof(int)));
   t.cnt = reinterpret_cast<int*>(take(tiles * sizeof(int)));
   t.tile_ptr = reinterpret_cast<int*>(take((tiles + 1) * sizeof(int)));
   t.order = reinterpret_cast<int*>(take(tiles * sizeof(int)));
@@ -243,6 +247,17 @@ spamm_status_t spamm_plan_create(spamm_plan_t* plan, int64_t n, int32_t leaf,
   }
   plan_layout(bd, &p->buf, static_cast<char*>(p->base));
   images_layout(bd, leaf, precision, &p->img, static_cast<char*>(p->base) + plan_bytes);
+  if (cudaStreamCreateWithFlags(&p->side, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&p->fork, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&p->join, cudaEventDisableTiming) != cudaSuccess) {
+    (void)cudaGetLastError();
+    if (p->side) cudaStreamDestroy(p->side);
+    if (p->fork) cudaEventDestroy(p->fork);
+    if (p->join) cudaEventDestroy(p->join);
+    if (p->owns) cudaFree(p->base);
+    delete p;
+    return SPAMM_ERR_CUDA;
+  }
   *plan = p;
   return SPAMM_OK;
 }
@@ -250,8 +265,11 @@ spamm_status_t spamm_plan_create(spamm_plan_t* plan, int64_t n, int32_t leaf,
 spamm_status_t spamm_plan_destroy(spamm_plan_t plan) {
   if (!plan) return SPAMM_ERR_INVALID_ARG;
   spamm_status_t st = SPAMM_OK;
+  if (cudaDeviceSynchronize() != cudaSuccess) st = SPAMM_ERR_CUDA;
+  if (plan->side) cudaStreamDestroy(plan->side);
+  if (plan->fork) cudaEventDestroy(plan->fork);
+  if (plan->join) cudaEventDestroy(plan->join);
   if (plan->owns && plan->base) {
-    if (cudaDeviceSynchronize() != cudaSuccess) st = SPAMM_ERR_CUDA;
     if (cudaFree(plan->base) != cudaSuccess) st = SPAMM_ERR_CUDA;
   }
   delete plan;
@@ -324,23 +342,30 @@ spamm_status_t spamm_multiply(spamm_plan_t plan, const float* A, const float* B,
   if (!plan || !A || !B || !C) return SPAMM_ERR_INVALID_ARG;
   if (!aligned16(A) || !aligned16(B) || !aligned16(C)) return SPAMM_ERR_INVALID_ARG;
   if (A == C || B == C) return SPAMM_ERR_INVALID_ARG;
-  cudaError_t e = cudaSuccess;
-  switch (plan->precision) {
-    case SPAMM_FP32:
-      e = launch_multiply_simt(plan->buf, A, B, C, plan->n, plan->leaf, (cudaStream_t)stream);
-      break;
-    default: {
-      int32_t* status = device_status_word();
-      if (!status) return SPAMM_ERR_NO_MEMORY;
-      const cudaStream_t s = (cudaStream_t)stream;
+  int32_t* status = nullptr;
+  if (plan->precision != SPAMM_FP32) {
+    status = device_status_word();
+    if (!status) return SPAMM_ERR_NO_MEMORY;
+  }
+  const cudaStream_t s = (cudaStream_t)stream;
+  // empty tiles (zeros, HBM-write bound) on the side stream, overlapped with
+  // the rounding and multiply of the non-empty tiles (disjoint parts of C)
+  cudaError_t e = cudaEventRecord(plan->fork, s);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(plan->side, plan->fork, 0);
+  if (e == cudaSuccess) e = launch_zero_empty_tiles(plan->buf, C, plan->n, plan->leaf, plan->side);
+  if (e == cudaSuccess) e = cudaEventRecord(plan->join, plan->side);
+  if (e == cudaSuccess) {
+    if (plan->precision == SPAMM_FP32) {
+      e = launch_multiply_simt(plan->buf, A, B, C, plan->n, plan->leaf, s);
+    } else {
       e = launch_quantize(plan->precision, plan->leaf, A, B, plan->n, plan->bd, plan->buf.needA,
                           plan->buf.needB, plan->img, s);
-      if (e == cudaSuccess) e = launch_zero_empty_tiles(plan->buf, C, plan->n, plan->leaf, s);
       if (e == cudaSuccess)
         e = launch_multiply_tc(plan->precision, plan->leaf, plan->buf, plan->img, C, plan->n,
                                status, s);
     }
   }
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(s, plan->join, 0);
   if (e != cudaSuccess) {
     (void)cudaGetLastError();
     return SPAMM_ERR_CUDA;

@@ -1,16 +1,17 @@
 // Plain FP32 multiply on the SIMT cores (Section 3.3's FP32 multiplication
 // kernel; the baseline the tensor-core modes are measured against).
 //
-// Persistent CTAs walk the plan's tile order (most survivors first, empty
-// tiles last) with a grid stride.  A non-empty tile (i, j) streams its
+// Persistent CTAs walk the plan's non-empty tiles (most survivors first) with
+// a grid stride; the caller writes the empty tiles with the coalesced
+// zero-fill kernel.  A non-empty tile (i, j) streams its
 // surviving k in 32-wide slices of the inner dimension: the A slice
 // A[i, k][:, s:s+32] is stored transposed and the B slice B[k, j][s:s+32, :]
 // as is, both in shared memory, double buffered through registers so the next
 // slice's global loads overlap the current slice's FMAs.  Each of the 256
 // threads keeps a (leaf/16) x (leaf/16) register tile of C and accumulates
 // in FP32 FMA over every surviving k.  Empty tiles are written as zeros with
-// coalesced float4 stores (beta = 0).
-#include "plan.cuh"
+// coalesced float4 stores (beta = 0) by that kernel.
+#include "tc_common.cuh"
 
 namespace spamm {
 namespace {
@@ -69,7 +70,8 @@ template <int LEAF, bool VEC>
 __global__ void __launch_bounds__(kThreads)
     simt_kernel(const float* __restrict__ A, const float* __restrict__ B, float* __restrict__ C,
                 int64_t n, int bd, const int* __restrict__ order,
-                const int* __restrict__ tile_ptr, const uint16_t* __restrict__ k_idx) {
+                const int* __restrict__ tile_ptr, const uint16_t* __restrict__ k_idx,
+                const PlanDevice* __restrict__ pd) {
   using T = SimtTile<LEAF, VEC>;
   constexpr int TM = T::TM;
   constexpr int kLoads = T::kLoadsA;
@@ -81,29 +83,13 @@ __global__ void __launch_bounds__(kThreads)
 
   const int tid = threadIdx.x;
   const int tx = tid % 16, ty = tid / 16;
-  const int64_t tiles = (int64_t)bd * bd;
+  const int64_t ne = pd->nonempty;   // empty tiles are zero-filled by another kernel
 
-  for (int64_t w = blockIdx.x; w < tiles; w += gridDim.x) {
+  for (int64_t w = blockIdx.x; w < ne; w += gridDim.x) {
     const int t = order[w];
     const int i = t / bd, j = t % bd;
     const int beg = tile_ptr[t], end = tile_ptr[t + 1];
     const int64_t r0 = (int64_t)i * LEAF, c0 = (int64_t)j * LEAF;
-
-    if (beg == end) {  // empty tile: zeros, coalesced
-      for (int e = tid * 4; e < LEAF * LEAF; e += kThreads * 4) {
-        const int64_t r = r0 + e / LEAF, c = c0 + e % LEAF;
-        if (r < n) {
-          float* p = C + r * n + c;
-          if (VEC && c + 3 < n) {
-            *reinterpret_cast<float4*>(p) = make_float4(0.f, 0.f, 0.f, 0.f);
-          } else {
-            for (int q = 0; q < 4; ++q)
-              if (c + q < n) p[q] = 0.f;
-          }
-        }
-      }
-      continue;
-    }
 
     float acc[TM][TM];
 #pragma unroll
@@ -194,7 +180,7 @@ cudaError_t launch(const PlanBuffers& b, const float* A, const float* B, float* 
   const int64_t tiles = (int64_t)b.bd * b.bd;
   const int grid = (int)std::min<int64_t>(tiles, (int64_t)sms * std::max(1, per_sm));
   simt_kernel<LEAF, VEC><<<grid, kThreads, smem, s>>>(A, B, C, n, b.bd, b.order, b.tile_ptr,
-                                                      b.k_idx);
+                                                      b.k_idx, b.pd);
   return cudaPeekAtLastError();
 }
 

@@ -2,19 +2,23 @@
 //   C[i,j] = sum over listed k of 2^(ea[i,k] + eb[k,j]) * (Ahi Bhi [+ 2^-s (Ahi Blo + Alo Bhi)])
 // over the plan's non-empty tiles, most survivors first.
 //
-// One persistent CTA per SM, six warps with fixed roles:
-//   warp 0   TMA producer: walks the CTA's tiles and their surviving k,
-//            waits for a free shared-memory stage and copies the operand
-//            image chunks (A hi, B hi, and the lo parts of split triples)
-//            with one bulk copy each; per-stage metadata marks run starts,
-//            tile ends and split triples.
+// One persistent CTA per SM, warps with fixed roles:
+//   warp 2   scheduler: takes the CTA's tiles 32 at a time (one descriptor
+//            per lane), flattens their surviving k into one list and loads
+//            it 32 entries per round (k, then the exponent sum ea + eb),
+//            marks run starts and tile ends with warp shuffles, and publishes
+//            the records into a shared-memory ring of 32-entry groups.
+//   warp 0   TMA producer: reads the records, waits for a free shared-memory
+//            stage and copies the operand image chunks (A hi, B hi, and the
+//            lo parts of split triples) with one bulk copy each; per-stage
+//            metadata marks run starts, tile ends and split triples.
 //   warp 1   allocates tensor memory and issues the MMAs from one thread:
 //            consecutive k of a tile with the same exponent sum (and split
 //            flag) form a run accumulated in one TMEM accumulator; runs
 //            alternate between two accumulators so the epilogue of one
 //            overlaps the MMAs of the next.  Each stage is released by
 //            tcgen05.commit when its MMAs have read it.
-//   warps 2+  epilogue (4 warps per 64 output columns): for each run, load
+//   warps 3+  epilogue (4 warps per 64 output columns): for each run, load
 //            the accumulator rows (one TMEM lane per output row, 64 columns
 //            per warp), rescale by 2^(ea+eb) in FP32 and add to the tile's
 //            register accumulator; at a tile's last run store the rows to C.
@@ -30,6 +34,8 @@ namespace {
 using namespace tc;
 
 constexpr int kRunRing = 16;
+constexpr int kGroups = 4;           // scheduler ring: groups of 32 entry records
+constexpr int kFirstEpiWarp = 3;
 constexpr uint64_t kWaitLimitNs = 2000000000ull;   // 2 s: a safety net, never hit normally
 constexpr uint64_t kDrainLimitNs = 100000000ull;   // 100 ms for the abort drain
 
@@ -43,6 +49,11 @@ struct StageMeta {
 struct RunRec {
   int32_t tile, s, split, last;
 };
+
+// Entry record published by the scheduler: x = tile, y = k, z = exponent sum,
+// w = flags (1: first of a run, 2: last of its tile, 4: split).  A group holds
+// up to 32 records; its count sits in the misc area (0 count = end of work).
+enum : int { kEntFirst = 1, kEntLast = 2, kEntSplit = 4 };
 
 struct TcParams {
   const uint8_t* a_hi;
@@ -67,18 +78,25 @@ struct TcCfg {
   static constexpr bool kHasLo = SPLITMODE != 0;
   static constexpr int M = LEAF, N = LEAF;
   static constexpr int kEpiWarps = 4 * (N / 64);          // 64 columns per epilogue warp
-  static constexpr int kThreads = 64 + 32 * kEpiWarps;
+  static constexpr int kThreads = 32 * kFirstEpiWarp + 32 * kEpiWarps;
   static constexpr uint32_t kStageBytes = L::kChunkBytes * 2 * (kHasLo ? 2 : 1);
   static constexpr int kStagesFit = (200 * 1024) / kStageBytes;
   static constexpr int kStages = kStagesFit > 16 ? 16 : kStagesFit;
   static constexpr int kAccCols = N * (kHasLo ? 2 : 1);
   static constexpr uint32_t kTmemCols = 2 * kAccCols;               // 128, 256 or 512
   static constexpr uint32_t kIdesc = idesc(FMT, M, N);
+  // every region starts on a 16-byte boundary (128-bit shared-memory accesses)
+  static constexpr size_t up16(size_t x) { return (x + 15) / 16 * 16; }
   static constexpr size_t kBarOffset = (size_t)kStages * kStageBytes;
-  static constexpr int kNumBars = 2 * kStages + 4 + 2 * kRunRing + 1;
-  static constexpr size_t kMetaOffset = kBarOffset + (size_t)kNumBars * 8;
-  static constexpr size_t kRunOffset = kMetaOffset + (size_t)kStages * sizeof(StageMeta);
-  static constexpr size_t kMiscOffset = kRunOffset + (size_t)kRunRing * sizeof(RunRec);
+  static constexpr int kNumBars = 2 * kStages + 4 + 2 * kRunRing + 1 + 2 * kGroups;
+  static constexpr size_t kMetaOffset = up16(kBarOffset + (size_t)kNumBars * 8);
+  static constexpr size_t kRunOffset = up16(kMetaOffset + (size_t)kStages * sizeof(StageMeta));
+  static constexpr size_t kEntOffset = up16(kRunOffset + (size_t)kRunRing * sizeof(RunRec));
+  static constexpr size_t kMiscOffset =
+      up16(kEntOffset + (size_t)kGroups * 32 * sizeof(int4) + kGroups * sizeof(int));
+  static_assert(kMetaOffset % 16 == 0 && kRunOffset % 16 == 0 && kEntOffset % 16 == 0 &&
+                    kMiscOffset % 16 == 0 && kBarOffset % 1024 == 0,
+                "shared-memory regions aligned");
   static constexpr size_t kSmemBytes = kMiscOffset + 64 + 1024;     // + alignment slack
   static_assert(kStages >= 2, "at least two pipeline stages");
   static_assert(kTmemCols >= 32 && kTmemCols <= 512, "TMEM columns");
@@ -129,8 +147,12 @@ __global__ void __launch_bounds__(TcCfg<FMT, LEAF, SPLITMODE>::kThreads, 1)
   uint64_t* run_full = acc_empty + 2;
   uint64_t* run_empty = run_full + kRunRing;
   uint64_t* drain = run_empty + kRunRing;
+  uint64_t* ent_full = drain + 1;
+  uint64_t* ent_empty = ent_full + kGroups;
   StageMeta* meta = reinterpret_cast<StageMeta*>(smem + Cfg::kMetaOffset);
   RunRec* runs = reinterpret_cast<RunRec*>(smem + Cfg::kRunOffset);
+  int4* ents = reinterpret_cast<int4*>(smem + Cfg::kEntOffset);
+  int* ent_count = reinterpret_cast<int*>(smem + Cfg::kEntOffset + kGroups * 32 * sizeof(int4));
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + Cfg::kMiscOffset);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + Cfg::kMiscOffset + 4);
 
@@ -149,6 +171,10 @@ __global__ void __launch_bounds__(TcCfg<FMT, LEAF, SPLITMODE>::kThreads, 1)
       mbar_init(&run_empty[r], Cfg::kEpiWarps);
     }
     mbar_init(drain, 1);
+    for (int g = 0; g < kGroups; ++g) {
+      mbar_init(&ent_full[g], 1);
+      mbar_init(&ent_empty[g], 1);
+    }
     *abort_flag = 0;
     fence_mbarrier_init();
   }
@@ -163,26 +189,109 @@ __global__ void __launch_bounds__(TcCfg<FMT, LEAF, SPLITMODE>::kThreads, 1)
   const int bd = p.bd;
   const int ne = p.pd->nonempty;
 
-  if (warp == 0) {
+  if (warp == 2) {
+    // ------------------------------------------------------------ scheduler
+    uint32_t grp = 0, gphase = 0;
+    int gfill = 0;            // records already in the current group
+    bool ok = wait_ab(&ent_empty[0], 1u, abort_flag, p.status);
+    auto publish = [&]() -> bool {   // hands the current group to the producer
+      __threadfence_block();
+      __syncwarp();
+      if (lane == 0) {
+        ent_count[grp] = gfill;
+        mbar_arrive(&ent_full[grp]);
+      }
+      if (++grp == kGroups) {
+        grp = 0;
+        gphase ^= 1u;
+      }
+      gfill = 0;
+      return wait_ab(&ent_empty[grp], gphase ^ 1u, abort_flag, p.status);
+    };
+    for (int base = blockIdx.x; base < ne && ok; base += 32 * gridDim.x) {
+      const int w = base + lane * gridDim.x;
+      const bool valid = w < ne;
+      int t = 0, beg = 0, end = 0;
+      if (valid) {
+        t = p.order[w];
+        beg = p.tile_ptr[t];
+        end = p.tile_ptr[t + 1];
+      }
+      const int cnt = end - beg;
+      int incl = cnt;
+#pragma unroll
+      for (int off = 1; off < 32; off <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, incl, off);
+        if (lane >= off) incl += y;
+      }
+      const int excl = incl - cnt;
+      const int total = __shfl_sync(0xffffffffu, incl, 31);
+      int32_t carry_key = 0;
+      int carry_tile = -1;
+      for (int f0 = 0; f0 < total && ok; f0 += 32) {
+        const int f = f0 + lane;
+        const bool act = f < total;
+        // owning tile slot: the last lane u with excl[u] <= f
+        int u = 0;
+#pragma unroll
+        for (int step = 16; step > 0; step >>= 1) {
+          const int cand = u + step;
+          const int ex = __shfl_sync(0xffffffffu, excl, cand & 31);
+          if (cand < 32 && ex <= f) u = cand;
+        }
+        const int tu = __shfl_sync(0xffffffffu, t, u);
+        const int bu = __shfl_sync(0xffffffffu, beg, u);
+        const int xu = __shfl_sync(0xffffffffu, excl, u);
+        const int iu = __shfl_sync(0xffffffffu, incl, u);
+        const int q = bu + (f - xu);
+        uint32_t ent = 0;
+        if (act) ent = p.k_idx[q];
+        const int k = (int)(ent & 0x3ffu);
+        const int i = tu / bd, j = tu % bd;
+        int32_t sexp = 0;
+        if (act) sexp = p.ea[(int64_t)i * bd + k] + p.eb[(int64_t)k * bd + j];
+        const bool split = SPLITMODE == 2 || (SPLITMODE == 1 && (ent & 0x8000u));
+        const int32_t key = sexp * 2 + (split ? 1 : 0);
+        int32_t pkey = __shfl_up_sync(0xffffffffu, key, 1);
+        int ptile = __shfl_up_sync(0xffffffffu, tu, 1);
+        if (lane == 0) {
+          pkey = carry_key;
+          ptile = carry_tile;
+        }
+        const bool first = ptile != tu || pkey != key;
+        const bool last = f == iu - 1;
+        carry_key = __shfl_sync(0xffffffffu, key, 31);
+        carry_tile = __shfl_sync(0xffffffffu, tu, 31);
+        const int nact = min(32, total - f0);
+        if (gfill + nact > 32) ok = publish();
+        if (!ok) break;
+        if (act)
+          ents[grp * 32 + gfill + lane] =
+              make_int4(tu, k, sexp, (first ? kEntFirst : 0) | (last ? kEntLast : 0) |
+                                         (split ? kEntSplit : 0));
+        gfill += nact;
+      }
+    }
+    if (ok && gfill > 0) ok = publish();
+    if (ok) publish();   // an empty group: end of work
+  } else if (warp == 0) {
     // ------------------------------------------------------------ producer
     if (lane == 0) {
-      uint32_t stage = 0, phase = 0;
+      uint32_t stage = 0, phase = 0, grp = 0, gphase = 0;
       uint32_t issued = 0, issued_phase = 0;   // bit s: stage s has a copy in flight / its parity
       bool ok = true;
-      for (int w = blockIdx.x; w < ne && ok; w += gridDim.x) {
-        const int t = p.order[w];
-        const int i = t / bd, j = t % bd;
-        const int beg = p.tile_ptr[t], end = p.tile_ptr[t + 1];
-        int32_t prev_key = 0;
-        for (int q = beg; q < end && ok; ++q) {
-          const uint32_t ent = p.k_idx[q];
-          const int k = (int)(ent & 0x3ffu);
-          const bool split = SPLITMODE == 2 || (SPLITMODE == 1 && (ent & 0x8000u));
-          const int32_t s = p.ea[(int64_t)i * bd + k] + p.eb[(int64_t)k * bd + j];
-          const int32_t key = s * 2 + (split ? 1 : 0);
-          const bool first = q == beg || key != prev_key;
-          prev_key = key;
-          const bool last = q == end - 1;
+      for (;;) {
+        if (!wait_ab(&ent_full[grp], gphase, abort_flag, p.status)) {
+          ok = false;
+          break;
+        }
+        const int nrec = ent_count[grp];
+        if (nrec == 0) break;
+        for (int r = 0; r < nrec && ok; ++r) {
+          const int4 rec = ents[grp * 32 + r];
+          const int t = rec.x, k = rec.y, flags = rec.w;
+          const int i = t / bd, j = t % bd;
+          const bool split = (flags & kEntSplit) != 0;
           const int64_t oa = ((int64_t)i * bd + k) * L::kBlockBytes;
           const int64_t ob = ((int64_t)k * bd + j) * L::kBlockBytes;
           for (int c = 0; c < L::kNch; ++c) {
@@ -191,9 +300,9 @@ __global__ void __launch_bounds__(TcCfg<FMT, LEAF, SPLITMODE>::kThreads, 1)
               break;
             }
             StageMeta m;
-            m.flags = (first && c == 0 ? 1 : 0) | (last && c == L::kNch - 1 ? 2 : 0) |
-                      (split ? 4 : 0);
-            m.s = s;
+            m.flags = ((flags & kEntFirst) && c == 0 ? 1 : 0) |
+                      ((flags & kEntLast) && c == L::kNch - 1 ? 2 : 0) | (split ? 4 : 0);
+            m.s = rec.z;
             m.tile = t;
             m.pad = 0;
             meta[stage] = m;
@@ -214,6 +323,11 @@ __global__ void __launch_bounds__(TcCfg<FMT, LEAF, SPLITMODE>::kThreads, 1)
               phase ^= 1u;
             }
           }
+        }
+        mbar_arrive(&ent_empty[grp]);
+        if (++grp == kGroups) {
+          grp = 0;
+          gphase ^= 1u;
         }
       }
       if (ok && wait_ab(&empty[stage], phase ^ 1u, abort_flag, p.status)) {
@@ -311,7 +425,7 @@ __global__ void __launch_bounds__(TcCfg<FMT, LEAF, SPLITMODE>::kThreads, 1)
     // ------------------------------------------------------------ epilogue
     constexpr int NC = 64;                       // columns owned by this warp
     const int quarter = warp & 3;
-    const int col0 = ((warp - 2) / 4) * NC;
+    const int col0 = ((warp - kFirstEpiWarp) / 4) * NC;
     const int row = Cfg::M == 128 ? quarter * 32 + lane : quarter * 16 + lane;
     const bool lane_has_row = Cfg::M == 128 || lane < 16;
     const float lo_w = 1.0f / (float)(1 << L::kLoShift);

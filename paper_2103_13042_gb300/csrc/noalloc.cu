@@ -24,7 +24,7 @@
 //    two host threads) race on the array and give wrong results: serialise them.
 #include <mutex>
 
-#include "plan.cuh"
+#include "tc_common.cuh"
 
 namespace spamm {
 namespace {
@@ -97,6 +97,7 @@ extern "C" spamm_status_t spamm_multiply_fp32_noalloc(const float* A, const floa
   if (e == cudaSuccess) e = launch_normmap(B, n, leaf, nB, s);
   if (e == cudaSuccess) e = run_plan(buf, nA, nB, tau, 0.0, 0, 0.0, s);
   if (e == cudaSuccess) e = launch_multiply_simt(buf, A, B, C, n, leaf, s);
+  if (e == cudaSuccess) e = launch_zero_empty_tiles(buf, C, n, leaf, s);
   if (e != cudaSuccess) {
     (void)cudaGetLastError();
     return SPAMM_ERR_CUDA;

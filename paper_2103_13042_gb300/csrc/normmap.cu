@@ -1,16 +1,18 @@
 // Get-norm step (Section 3.2, Eq. 2): normmap[I*bd+K] = ||X[I,K]||_F.
 //
-// GB300 design.  The kernel is a single streaming pass over X: a CTA covers
-// one block-row strip (leaf rows) and a window of columns; each thread owns a
-// fixed column slot (a float4 when n % 4 == 0, else one float) and walks the
-// strip's rows, so every warp load is a contiguous, coalesced 512-byte
-// (or 128-byte) row segment.  FP64 arithmetic runs at 1/72 of FP32 rate on
-// this part, so every group of 32 entries is scaled by a power of two (no
-// FP32 underflow of tiny squares), squared exactly with FMA and accumulated
-// as an unevaluated FP32 pair with an explicit scale exponent; FP64 is used
-// only once per thread and in the final combine.  The threads of one block column are
-// then combined with FP64 warp shuffles (and shared memory when a block
-// column spans several warps); one FP64 sqrt per block.
+// GB300 design.  A single streaming pass over X: a CTA covers one block-row
+// strip (leaf rows) and a window of columns; each thread owns a fixed column
+// slot (a float4 when n % 4 == 0, else one float) and walks the strip's rows,
+// so every warp load is a contiguous row segment (512 or 128 bytes), loads
+// are streamed (evict-first) and eight rows of loads are in flight per group.
+// FP64 arithmetic runs at 1/72 of the FP32 rate on this part, so every group
+// of 32 entries is scaled by a power of two (no FP32 underflow of tiny
+// squares), squared exactly with FMA and accumulated as an unevaluated FP32
+// pair with an explicit scale exponent; the threads of a block column are
+// combined in that FP32 form (warp shuffles, and shared memory when a block
+// column spans several warps), and the square root is taken with an FP32
+// Newton step on the exact residual, so a block costs three FP64
+// instructions.
 #include "common.cuh"
 
 namespace spamm {
@@ -18,12 +20,20 @@ namespace {
 
 constexpr int kThreads = 256;
 
+__device__ __forceinline__ void merge_from(SumSq& a, float h, float l, int e) {
+  if (e == kSumSqEmpty) {
+    if (h != h) a.hi = h;   // NaN from an otherwise empty partner
+  } else {
+    sumsq_merge(a, h, l, e);
+  }
+}
+
 template <int VEC, int LEAF>
-__global__ void __launch_bounds__(kThreads) normmap_kernel(const float* __restrict__ X, int64_t n,
-                                                          int bd, double* __restrict__ out) {
+__global__ void __launch_bounds__(kThreads)
+    normmap_kernel(const float* __restrict__ X, int64_t n, int bd, double* __restrict__ out) {
   constexpr int kCols = kThreads * VEC;               // columns per CTA window
   constexpr int kThreadsPerBlockCol = LEAF / VEC;     // threads sharing one output
-  constexpr int kRowsPerGroup = 32 / VEC;             // rows per 32-square group
+  constexpr int kRowsPerGroup = 32 / VEC;             // rows per 32-entry group
   const int I = blockIdx.y;
   const int64_t col0 = (int64_t)blockIdx.x * kCols + (int64_t)threadIdx.x * VEC;
   const int64_t row0 = (int64_t)I * LEAF;
@@ -40,8 +50,11 @@ __global__ void __launch_bounds__(kThreads) normmap_kernel(const float* __restri
       for (int q = 0; q < kRowsPerGroup; ++q) {
         if (q < rows) {
           if constexpr (VEC == 4) {
-            float4 t = __ldcs(reinterpret_cast<const float4*>(p + (int64_t)q * n));
-            v[4 * q] = t.x; v[4 * q + 1] = t.y; v[4 * q + 2] = t.z; v[4 * q + 3] = t.w;
+            const float4 t = __ldcs(reinterpret_cast<const float4*>(p + (int64_t)q * n));
+            v[4 * q] = t.x;
+            v[4 * q + 1] = t.y;
+            v[4 * q + 2] = t.z;
+            v[4 * q + 3] = t.w;
           } else {
             v[q] = __ldcs(p + (int64_t)q * n);
           }
@@ -54,31 +67,32 @@ __global__ void __launch_bounds__(kThreads) normmap_kernel(const float* __restri
       p += (int64_t)kRowsPerGroup * n;
     }
   }
-  double acc = sumsq_value(ss);
 
-  // Combine the threads of a block column.
+  // combine the threads of a block column in the FP32-pair form
   if constexpr (kThreadsPerBlockCol <= 32) {
 #pragma unroll
-    for (int off = kThreadsPerBlockCol / 2; off > 0; off >>= 1)
-      acc += __shfl_xor_sync(0xffffffffu, acc, off);
-    if ((threadIdx.x % kThreadsPerBlockCol) == 0 && active) {
-      const int64_t K = col0 / LEAF;
-      out[(int64_t)I * bd + K] = sqrt(acc);
+    for (int off = kThreadsPerBlockCol / 2; off > 0; off >>= 1) {
+      const float h = __shfl_xor_sync(0xffffffffu, ss.hi, off);
+      const float l = __shfl_xor_sync(0xffffffffu, ss.lo, off);
+      const int e = __shfl_xor_sync(0xffffffffu, ss.e, off);
+      merge_from(ss, h, l, e);
     }
+    if ((threadIdx.x % kThreadsPerBlockCol) == 0 && active)
+      out[(int64_t)I * bd + col0 / LEAF] = sumsq_sqrt(ss);
   } else {
-    __shared__ double warp_sum[kThreads / 32];
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
-    if ((threadIdx.x & 31) == 0) warp_sum[threadIdx.x / 32] = acc;
+    __shared__ SumSq warp_sum[kThreads / 32];
+    ss = sumsq_warp_sum(ss);
+    if ((threadIdx.x & 31) == 0) warp_sum[threadIdx.x / 32] = ss;
     __syncthreads();
     constexpr int kWarpsPerBlockCol = kThreadsPerBlockCol / 32;
     if ((threadIdx.x % kThreadsPerBlockCol) == 0 && active) {
-      double s = 0.0;
-      const int w0 = threadIdx.x / 32;
+      SumSq s = warp_sum[threadIdx.x / 32];
 #pragma unroll
-      for (int w = 0; w < kWarpsPerBlockCol; ++w) s += warp_sum[w0 + w];
-      const int64_t K = col0 / LEAF;
-      out[(int64_t)I * bd + K] = sqrt(s);
+      for (int w = 1; w < kWarpsPerBlockCol; ++w) {
+        const SumSq o = warp_sum[threadIdx.x / 32 + w];
+        merge_from(s, o.hi, o.lo, o.e);
+      }
+      out[(int64_t)I * bd + col0 / LEAF] = sumsq_sqrt(s);
     }
   }
 }

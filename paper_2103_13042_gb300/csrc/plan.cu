@@ -1,17 +1,24 @@
 // Pair test and work-queue build (Algorithm 1 skip rule, Algorithm 2 bitmap and
 // map_offset, Section 3.5.1 valid multiplications), for all output tiles at once.
 //
-// Kernels, in stream order:
+// Stream order (after one memset that clears the plan's accumulators):
 //   prep      FP64 norm maps -> FP32 mantissa/exponent "screen" forms (B transposed
-//             so a tile's k-run is contiguous) and partial sums of squared norms.
-//   norms     ||A||_F, ||B||_F and 1/(||A|| ||B||); clears the accumulators.
-//   count     one warp per output tile (i, j): lanes test k = lane, lane+32, ...;
-//             ballot + popc count the survivors; skipped products are summed
-//             for the bounds; split modes bin surviving products by binade.
-//   finalize  one CTA: exclusive scan of the counts (CSR tile_ptr), statistics,
-//             the split-flag binade, and the longest-first tile order.
-//   fill      one warp per non-empty tile: the same test again; ballot ranks
-//             place the surviving k (increasing) at tile_ptr[t] + rank.
+//             so a tile's k-run is contiguous) and per-CTA sums of squared norms.
+//   count     CTAs own 32 consecutive tiles, one warp per tile at a time: lanes
+//             test k = lane, lane+32, ...; ballot + popc count the survivors;
+//             skipped products are summed for the bounds; split modes bin the
+//             surviving products by binade; per-CTA totals and a histogram of
+//             the per-tile counts.
+//   finalize  one CTA over the per-CTA totals: their exclusive scans (the CSR
+//             base of each CTA's tiles), statistics, the split-flag binade and
+//             the bucket starts of the longest-first order.
+//   fill      same tile partition: CSR offsets from the CTA base plus a warp
+//             scan; the same test again, ballot ranks place the surviving k
+//             (increasing) at tile_ptr[t] + rank; tiles take their
+//             longest-first slot from a per-count cursor, empty tiles go last
+//             in index order.
+#include <cstddef>
+
 #include "common.cuh"
 #include "plan.cuh"
 
@@ -62,13 +69,9 @@ __device__ __forceinline__ bool survives(Screen a, Screen b, const double* nA_pt
   return !(p < T.tau);
 }
 
-// Extended-range FP32 sum: value = m * 2^e with an integer exponent, so sums of
-// relative products far below the FP32 range (decay matrices reach 1e-80 and
-// less) keep ~24 bits.  Terms below 2^-40 of the running sum are dropped.
-struct ExtSum {
-  float m;
-  int e;
-};
+// Extended-range FP32 sums (ExtSum, value m * 2^e): sums of relative products
+// far below the FP32 range (decay matrices reach 1e-80 and less) keep ~24
+// bits.  Terms below 2^-40 of the running sum are dropped.
 
 // Binade of a positive normal FP32 value.
 __device__ __forceinline__ int fexp(float x) {
@@ -127,9 +130,24 @@ __device__ __forceinline__ int rel_bin(double p, double inv) {
   return b < kFlagBinMin ? kFlagBinMin : (b > 1 ? 1 : b);
 }
 
+// The same binade decided from the screen forms in FP32, re-decided in FP64
+// only when the FP32 product lies within 2^-20 of a power of two.
+__device__ __forceinline__ int rel_bin_screened(Screen a, Screen b, float inv_m, int inv_e,
+                                                const double* pa, const double* pb, double inv) {
+  if (a.e == kZeroExp || b.e == kZeroExp) return kFlagBinMin;
+  if (a.e == kNonFiniteExp || b.e == kNonFiniteExp || !(inv > 0.0))
+    return rel_bin(__dmul_rn(*pa, *pb), inv);
+  const float q = __fmul_rn(__fmul_rn(a.m, b.m), inv_m);   // in [0.125, 1]
+  const uint32_t frac = __float_as_uint(q) & 0x7fffffu;
+  if (frac < 8u || frac > 0x7fffffu - 8u) return rel_bin(__dmul_rn(*pa, *pb), inv);
+  const int b0 = a.e + b.e + inv_e + ((int)((__float_as_uint(q) >> 23) & 0xffu) - 127);
+  return b0 < kFlagBinMin ? kFlagBinMin : (b0 > 1 ? 1 : b0);
+}
+
 __global__ void prep_kernel(const double* __restrict__ nA, const double* __restrict__ nB, int bd,
                             Screen* __restrict__ sA, Screen* __restrict__ sBT,
-                            double* __restrict__ part_a, double* __restrict__ part_b) {
+                            double* __restrict__ part_a, double* __restrict__ part_b,
+                            PlanDevice* __restrict__ pd) {
   const int64_t total = (int64_t)bd * bd;
   const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   double qa = 0.0, qb = 0.0;
@@ -160,45 +178,43 @@ __global__ void prep_kernel(const double* __restrict__ nA, const double* __restr
     part_a[blockIdx.x] = sa;
     part_b[blockIdx.x] = sb;
   }
+  // the last CTA to finish sums the partials in a fixed order (deterministic)
+  __shared__ bool s_last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) s_last = atomicAdd(&pd->ticket, 1u) == gridDim.x - 1;
+  __syncthreads();
+  if (s_last && threadIdx.x < 32) {
+    __threadfence();
+    const int lane = threadIdx.x;
+    double a = 0.0, b = 0.0;
+    for (int i = lane; i < (int)gridDim.x; i += 32) {
+      a += __ldcg(part_a + i);
+      b += __ldcg(part_b + i);
+    }
+    for (int off = 16; off > 0; off >>= 1) {
+      a += __shfl_xor_sync(0xffffffffu, a, off);
+      b += __shfl_xor_sync(0xffffffffu, b, off);
+    }
+    if (lane == 0) {
+      const double na = sqrt(a), nb = sqrt(b), ab = na * nb;
+      pd->norm_a = na;
+      pd->norm_b = nb;
+      pd->inv_ab = ab > 0.0 ? 1.0 / ab : 0.0;
+    }
+  }
 }
 
-__global__ void norms_kernel(const double* __restrict__ part_a, const double* __restrict__ part_b,
-                             int nparts, PlanDevice* __restrict__ pd) {
-  __shared__ double sa[256], sb[256];
-  double a = 0.0, b = 0.0;
-  for (int i = threadIdx.x; i < nparts; i += blockDim.x) {
-    a += part_a[i];
-    b += part_b[i];
-  }
-  sa[threadIdx.x] = a;
-  sb[threadIdx.x] = b;
-  __syncthreads();
-  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
-    if ((int)threadIdx.x < s) {
-      sa[threadIdx.x] += sa[threadIdx.x + s];
-      sb[threadIdx.x] += sb[threadIdx.x + s];
-    }
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) {
-    const double na = sqrt(sa[0]), nb = sqrt(sb[0]);
-    pd->norm_a = na;
-    pd->norm_b = nb;
-    const double ab = na * nb;
-    pd->inv_ab = ab > 0.0 ? 1.0 / ab : 0.0;
-  }
-  for (int i = threadIdx.x; i < kFlagBins; i += blockDim.x) {
-    pd->bin_sum[i] = 0.0;
-    pd->bin_cnt[i] = 0;
-  }
-}
+
+constexpr int kTilesPerCta = 32;   // count and fill: 8 warps x 4 tiles
+constexpr int kTileRounds = kTilesPerCta / kWarpsPerCta;
 
 struct CountParts {
   long long* S;
   int* kmax;
   int* nonempty;
-  double* b1;
-  double* b2sq;
+  ExtSum* b1;
+  ExtSum* b2sq;
 };
 
 __global__ void __launch_bounds__(kWarpsPerCta * 32)
@@ -210,42 +226,45 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32)
   __shared__ int s_bin_cnt[kFlagBins];
   __shared__ long long s_S[kWarpsPerCta];
   __shared__ int s_kmax[kWarpsPerCta], s_ne[kWarpsPerCta];
-  __shared__ double s_b1[kWarpsPerCta], s_b2[kWarpsPerCta];
+  __shared__ ExtSum s_b1[kWarpsPerCta], s_b2[kWarpsPerCta];
+  const int warp = threadIdx.x / 32, lane = threadIdx.x & 31;
   if (split) {
     for (int i = threadIdx.x; i < kFlagBins; i += blockDim.x) {
       s_bin_sum[i] = 0.0;
       s_bin_cnt[i] = 0;
     }
-    __syncthreads();
   }
-  const int warp = threadIdx.x / 32, lane = threadIdx.x & 31;
-  const int64_t t = (int64_t)blockIdx.x * kWarpsPerCta + warp;
+  __syncthreads();
+  const double inv = pd->inv_ab;   // written by the prep kernel
+  int inv_e;
+  const float inv_m = (float)frexp(inv, &inv_e);
   const int64_t tiles = (int64_t)bd * bd;
-  int count = 0;
-  double skipped = 0.0;
-  if (t < tiles) {
+  long long wS = 0;
+  int wkmax = 0, wne = 0;
+  ExtSum wb1{0.0f, 0}, wb2{0.0f, 0};
+  for (int r = 0; r < kTileRounds; ++r) {
+    const int64_t t = (int64_t)blockIdx.x * kTilesPerCta + warp + (int64_t)r * kWarpsPerCta;
+    if (t >= tiles) break;
     const int i = (int)(t / bd), j = (int)(t % bd);
     const Screen* ra = sA + (int64_t)i * bd;
     const Screen* rb = sBT + (int64_t)j * bd;
-    const double inv = pd->inv_ab;
-    int inv_e;
-    const float inv_m = (float)frexp(inv, &inv_e);
-    ExtSum sk{0.0f, 0};  // skipped relative products
+    ExtSum sk{0.0f, 0};
+    int count = 0;
     int run_bin = kFlagBinMin - 1, run_cnt = 0;
     double run_sum = 0.0;
+#pragma unroll 4
     for (int k0 = 0; k0 < bd; k0 += 32) {
       const int k = k0 + lane;
       bool s = false;
-      Screen a{}, b{};
       if (k < bd) {
-        a = ra[k];
-        b = rb[k];
+        const Screen a = ra[k], b = rb[k];
         s = survives(a, b, nA + (int64_t)i * bd + k, nB + (int64_t)k * bd + j, T);
         if (!s) {
           ext_add_rel(sk, a, b, inv_m, inv_e);
         } else if (split) {
           const double p = __dmul_rn(nA[(int64_t)i * bd + k], nB[(int64_t)k * bd + j]);
-          const int bin = rel_bin(p, inv);
+          const int bin = rel_bin_screened(a, b, inv_m, inv_e, nA + (int64_t)i * bd + k,
+                                           nB + (int64_t)k * bd + j, inv);
           if (bin != run_bin) {
             if (run_cnt) {
               atomicAdd(&s_bin_sum[run_bin - kFlagBinMin], run_sum);
@@ -265,31 +284,37 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32)
       atomicAdd(&s_bin_sum[run_bin - kFlagBinMin], run_sum);
       atomicAdd(&s_bin_cnt[run_bin - kFlagBinMin], run_cnt);
     }
-    skipped = ext_value(ext_warp_sum(sk));
+    const ExtSum tot = ext_warp_sum(sk);   // no FP64: the FP64 pipe is narrow here
     if (lane == 0) {
       cnt[t] = count;
       needA[t] = 0;   // the fill kernel sets the blocks survivors use
       needB[t] = 0;
+      if (count > 0) atomicAdd(&pd->hist[count], 1);
+      ext_add(wb1, tot.m, tot.e);
+      ext_add(wb2, __fmul_rn(tot.m, tot.m), 2 * tot.e);
     }
+    wS += count;
+    wkmax = max(wkmax, count);
+    wne += count > 0;
   }
   if (lane == 0) {
-    s_S[warp] = t < tiles ? count : 0;
-    s_kmax[warp] = t < tiles ? count : 0;
-    s_ne[warp] = (t < tiles && count > 0) ? 1 : 0;
-    s_b1[warp] = t < tiles ? skipped : 0.0;
-    s_b2[warp] = t < tiles ? skipped * skipped : 0.0;
+    s_S[warp] = wS;
+    s_kmax[warp] = wkmax;
+    s_ne[warp] = wne;
+    s_b1[warp] = wb1;
+    s_b2[warp] = wb2;
   }
   __syncthreads();
   if (threadIdx.x == 0) {
     long long S = 0;
     int km = 0, ne = 0;
-    double b1 = 0.0, b2 = 0.0;
+    ExtSum b1{0.0f, 0}, b2{0.0f, 0};
     for (int w = 0; w < kWarpsPerCta; ++w) {
       S += s_S[w];
       km = max(km, s_kmax[w]);
       ne += s_ne[w];
-      b1 += s_b1[w];
-      b2 += s_b2[w];
+      ext_add(b1, s_b1[w].m, s_b1[w].e);
+      ext_add(b2, s_b2[w].m, s_b2[w].e);
     }
     parts.S[blockIdx.x] = S;
     parts.kmax[blockIdx.x] = km;
@@ -298,7 +323,6 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32)
     parts.b2sq[blockIdx.x] = b2;
   }
   if (split) {
-    __syncthreads();
     for (int i = threadIdx.x; i < kFlagBins; i += blockDim.x) {
       if (s_bin_cnt[i]) {
         atomicAdd(&pd->bin_sum[i], s_bin_sum[i]);
@@ -310,147 +334,216 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32)
 
 constexpr int kFinThreads = 1024;
 
+// Block-wide exclusive scan of one value per thread (Hillis-Steele in smem).
+template <typename V>
+__device__ V block_exclusive_scan(V x, V* sh, V& total) {
+  const int tid = threadIdx.x;
+  sh[tid] = x;
+  __syncthreads();
+  for (int off = 1; off < kFinThreads; off <<= 1) {
+    const V y = tid >= off ? sh[tid - off] : V(0);
+    __syncthreads();
+    sh[tid] += y;
+    __syncthreads();
+  }
+  const V incl = sh[tid];
+  total = sh[kFinThreads - 1];
+  __syncthreads();
+  return incl - x;
+}
+
 __global__ void __launch_bounds__(kFinThreads)
-    finalize_kernel(const int* __restrict__ cnt, int bd, CountParts parts, int nparts, int split,
-                    double c1, double target_rel, PlanDevice* __restrict__ pd,
-                    int* __restrict__ tile_ptr, int* __restrict__ order) {
+    finalize_kernel(int bd, CountParts parts, int nparts, int split, double c1,
+                    double target_rel, PlanDevice* __restrict__ pd, int* __restrict__ cta_base,
+                    int* __restrict__ cta_ebase) {
   __shared__ long long s_ll[kFinThreads];
-  __shared__ double s_d1[kFinThreads], s_d2[kFinThreads];
-  __shared__ int s_i1[kFinThreads], s_i2[kFinThreads];
-  __shared__ int s_hist[kMaxBd + 1];
+  __shared__ ExtSum s_x[kFinThreads];
+  __shared__ int s_i[kFinThreads];
   const int tid = threadIdx.x;
   const int64_t tiles = (int64_t)bd * bd;
 
-  // 1. statistics from the count kernel's per-CTA parts
-  long long S = 0;
-  int km = 0, ne = 0;
-  double b1 = 0.0, b2 = 0.0;
-  for (int p = tid; p < nparts; p += kFinThreads) {
-    S += parts.S[p];
-    km = max(km, parts.kmax[p]);
-    ne += parts.nonempty[p];
-    b1 += parts.b1[p];
-    b2 += parts.b2sq[p];
+
+  // per-CTA survivor and empty-tile bases: each thread scans a contiguous chunk
+  const int chunk = (nparts + kFinThreads - 1) / kFinThreads;
+  const int p0 = min(nparts, chunk * tid), p1 = min(nparts, p0 + chunk);
+  long long locS = 0;
+  int locE = 0, locK = 0;
+  ExtSum locB1{0.0f, 0}, locB2{0.0f, 0};
+  for (int q = p0; q < p1; ++q) {
+    locS += parts.S[q];
+    const int64_t rest = tiles - (int64_t)q * kTilesPerCta;
+    const int ntile = (int)(rest < kTilesPerCta ? rest : kTilesPerCta);
+    locE += ntile - parts.nonempty[q];
+    locK = max(locK, parts.kmax[q]);
+    ext_add(locB1, parts.b1[q].m, parts.b1[q].e);
+    ext_add(locB2, parts.b2sq[q].m, parts.b2sq[q].e);
   }
-  s_ll[tid] = S;
-  s_i1[tid] = km;
-  s_i2[tid] = ne;
-  s_d1[tid] = b1;
-  s_d2[tid] = b2;
-  for (int i = tid; i <= bd; i += kFinThreads) s_hist[i] = 0;
+  long long totS;
+  long long baseS = block_exclusive_scan<long long>(locS, s_ll, totS);
+  long long totE;
+  long long baseE = block_exclusive_scan<long long>((long long)locE, s_ll, totE);
+  for (int q = p0; q < p1; ++q) {
+    cta_base[q] = (int)baseS;
+    baseS += parts.S[q];
+    const int64_t rest = tiles - (int64_t)q * kTilesPerCta;
+    const int ntile = (int)(rest < kTilesPerCta ? rest : kTilesPerCta);
+    cta_ebase[q] = (int)baseE;
+    baseE += ntile - parts.nonempty[q];
+  }
+  // max and the extended-range sums (FP32 only)
+  s_i[tid] = locK;
+  s_x[tid] = locB1;
   __syncthreads();
   for (int s = kFinThreads / 2; s > 0; s >>= 1) {
     if (tid < s) {
-      s_ll[tid] += s_ll[tid + s];
-      s_i1[tid] = max(s_i1[tid], s_i1[tid + s]);
-      s_i2[tid] += s_i2[tid + s];
-      s_d1[tid] += s_d1[tid + s];
-      s_d2[tid] += s_d2[tid + s];
+      s_i[tid] = max(s_i[tid], s_i[tid + s]);
+      ext_add(s_x[tid], s_x[tid + s].m, s_x[tid + s].e);
     }
     __syncthreads();
   }
-  if (tid == 0) {
+  const int kmax = s_i[0];
+  const ExtSum b1x = s_x[0];
+  __syncthreads();
+  s_x[tid] = locB2;
+  __syncthreads();
+  for (int s = kFinThreads / 2; s > 0; s >>= 1) {
+    if (tid < s) ext_add(s_x[tid], s_x[tid + s].m, s_x[tid + s].e);
+    __syncthreads();
+  }
+  const ExtSum b2x = s_x[0];
+  __syncthreads();
+
+  // longest-first bucket starts: counts bd .. 1 in decreasing order
+  const int c = bd - tid;          // thread tid owns count c (valid for c >= 1)
+  const long long h = (c >= 1) ? pd->hist[c] : 0;
+  long long tot_ne;
+  const long long start = block_exclusive_scan<long long>(h, s_ll, tot_ne);
+  if (c >= 1) pd->cursor[c] = (int)start;
+
+  // split flag binade (one warp): m = the largest mm in [kFlagBinMin - 1, 1]
+  // with c1 * sum_{bins < mm} p <= budget; bins are prefix-summed in a fixed
+  // order (7 consecutive bins per lane, then a warp scan of the lane totals).
+  if (tid < 32) {
     const double ab = pd->norm_a * pd->norm_b;
-    pd->survivors = s_ll[0];
-    pd->max_tile = s_i1[0];
-    pd->nonempty = s_i2[0];
-    pd->bound1 = s_d1[0] * ab;
-    pd->bound2 = sqrt(s_d2[0]) * ab;
-    pd->valid_ratio = (double)s_ll[0] / ((double)bd * (double)bd * (double)bd);
-    // split flag binade: largest m with c1 * sum_{bin < m} p <= budget
+    const double b1 = ext_value(b1x);
+    const double bound2 = sqrt(ext_value(b2x)) * ab;
+    constexpr int PER = (kFlagBins + 31) / 32;   // 7
+    const int lane = tid;
     int m = kFlagBinMin - 1;
     long long flagged = 0;
     if (split) {
-      const double budget = 0.5 * (target_rel * ab - pd->bound2);
+      const double budget = 0.5 * (target_rel * ab - bound2);
+      double v[PER];
+      double run = 0.0;
+#pragma unroll
+      for (int q = 0; q < PER; ++q) {
+        const int b = lane * PER + q;
+        v[q] = b < kFlagBins ? pd->bin_sum[b] : 0.0;
+        run += v[q];
+      }
+      double incl = run;
+      for (int off = 1; off < 32; off <<= 1) {
+        const double y = __shfl_up_sync(0xffffffffu, incl, off);
+        if (lane >= off) incl += y;
+      }
+      double below = incl - run;     // sum of the bins before this lane's first
+      int best = kFlagBinMin - 1;
       if (budget >= 0.0) {
-        double below = 0.0;
-        for (int mm = kFlagBinMin - 1; mm <= 1; ++mm) {
-          // below = sum over bins < mm
-          if (mm - 1 >= kFlagBinMin) below += pd->bin_sum[mm - 1 - kFlagBinMin];
-          if (c1 * below <= budget) m = mm;
+        // mm = kFlagBinMin + b has below(mm) = sum of bins < b (index form)
+#pragma unroll
+        for (int q = 0; q < PER; ++q) {
+          const int b = lane * PER + q;       // candidate mm = kFlagBinMin + b
+          if (b < kFlagBins && c1 * below <= budget) best = kFlagBinMin + b;
+          below += v[q];
         }
       }
-      for (int b = kFlagBinMin; b <= 1; ++b)
-        if (b >= m) flagged += (long long)pd->bin_cnt[b - kFlagBinMin];
+      for (int off = 16; off > 0; off >>= 1) best = max(best, __shfl_xor_sync(0xffffffffu, best, off));
+      m = best;
+      long long f = 0;
+      for (int b = lane; b < kFlagBins; b += 32)
+        if (kFlagBinMin + b >= m) f += (long long)pd->bin_cnt[b];
+      for (int off = 16; off > 0; off >>= 1) f += __shfl_xor_sync(0xffffffffu, f, off);
+      flagged = f;
     }
-    pd->flag_exp = m;
-    pd->flagged = flagged;
-  }
-  __syncthreads();
-
-  // 2. exclusive scan of per-tile counts -> tile_ptr (chunk per thread)
-  const int64_t chunk = (tiles + kFinThreads - 1) / kFinThreads;
-  const int64_t c0 = min(tiles, chunk * tid), c1e = min(tiles, c0 + chunk);
-  long long local = 0;
-  for (int64_t t = c0; t < c1e; ++t) {
-    const int c = cnt[t];
-    local += c;
-    atomicAdd(&s_hist[c], 1);
-  }
-  s_ll[tid] = local;
-  __syncthreads();
-  for (int off = 1; off < kFinThreads; off <<= 1) {   // Hillis-Steele inclusive scan
-    long long v = tid >= off ? s_ll[tid - off] : 0;
-    __syncthreads();
-    s_ll[tid] += v;
-    __syncthreads();
-  }
-  long long run = s_ll[tid] - local;
-  for (int64_t t = c0; t < c1e; ++t) {
-    tile_ptr[t] = (int)run;
-    run += cnt[t];
-  }
-  if (tid == kFinThreads - 1) tile_ptr[tiles] = (int)s_ll[kFinThreads - 1];
-  __syncthreads();
-
-  // 3. longest-first order: bucket offsets in decreasing count
-  if (tid == 0) {
-    int acc = 0;
-    for (int c = bd; c >= 0; --c) {
-      const int h = s_hist[c];
-      s_hist[c] = acc;
-      acc += h;
+    if (lane == 0) {
+      pd->survivors = totS;
+      pd->max_tile = kmax;
+      pd->nonempty = (int)(tiles - totE);
+      pd->bound1 = b1 * ab;
+      pd->bound2 = bound2;
+      pd->valid_ratio = (double)totS / ((double)bd * (double)bd * (double)bd);
+      pd->flag_exp = m;
+      pd->flagged = flagged;
     }
-  }
-  __syncthreads();
-  for (int64_t t = c0; t < c1e; ++t) {
-    const int pos = atomicAdd(&s_hist[cnt[t]], 1);
-    order[pos] = (int)t;
   }
 }
 
 __global__ void __launch_bounds__(kWarpsPerCta * 32)
     fill_kernel(const Screen* __restrict__ sA, const Screen* __restrict__ sBT,
                 const double* __restrict__ nA, const double* __restrict__ nB, int bd, TauScreen T,
-                int split, const PlanDevice* __restrict__ pd, const int* __restrict__ cnt,
-                const int* __restrict__ tile_ptr, uint16_t* __restrict__ k_idx,
+                int split, PlanDevice* __restrict__ pd, const int* __restrict__ cnt,
+                const int* __restrict__ cta_base, const int* __restrict__ cta_ebase,
+                int* __restrict__ tile_ptr, int* __restrict__ order, uint16_t* __restrict__ k_idx,
                 uint8_t* __restrict__ needA, uint8_t* __restrict__ needB) {
+  __shared__ int s_ptr[kTilesPerCta];
   const int warp = threadIdx.x / 32, lane = threadIdx.x & 31;
-  const int64_t t = (int64_t)blockIdx.x * kWarpsPerCta + warp;
-  if (t >= (int64_t)bd * bd) return;
-  if (cnt[t] == 0) return;
-  const int i = (int)(t / bd), j = (int)(t % bd);
-  const Screen* ra = sA + (int64_t)i * bd;
-  const Screen* rb = sBT + (int64_t)j * bd;
-  const double inv = pd->inv_ab;
-  const int m = pd->flag_exp;
-  int base = tile_ptr[t];
-  for (int k0 = 0; k0 < bd; k0 += 32) {
-    const int k = k0 + lane;
-    bool s = false;
-    if (k < bd) s = survives(ra[k], rb[k], nA + (int64_t)i * bd + k, nB + (int64_t)k * bd + j, T);
-    const unsigned ball = __ballot_sync(0xffffffffu, s);
-    if (s) {
-      uint16_t v = (uint16_t)k;
-      if (split) {
-        const double p = __dmul_rn(nA[(int64_t)i * bd + k], nB[(int64_t)k * bd + j]);
-        if (rel_bin(p, inv) >= m) v |= kSplitFlag;
-      }
-      k_idx[base + __popc(ball & ((1u << lane) - 1u))] = v;
-      needA[(int64_t)i * bd + k] = 1;   // benign: every writer stores 1
-      needB[(int64_t)k * bd + j] = 1;
+  const int64_t tiles = (int64_t)bd * bd;
+  const int64_t t0 = (int64_t)blockIdx.x * kTilesPerCta;
+  if (warp == 0) {   // CSR offsets and the empty tiles' slots (kTilesPerCta == 32 lanes)
+    const int64_t t = t0 + lane;
+    const int c = t < tiles ? cnt[t] : 0;
+    int incl = c;
+    for (int off = 1; off < 32; off <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, incl, off);
+      if (lane >= off) incl += y;
     }
-    base += __popc(ball);
+    const int ptr = cta_base[blockIdx.x] + incl - c;
+    s_ptr[lane] = ptr;
+    const unsigned empty = __ballot_sync(0xffffffffu, t < tiles && c == 0);
+    if (t < tiles) {
+      tile_ptr[t] = ptr;
+      if (t == tiles - 1) tile_ptr[tiles] = ptr + c;
+      if (c == 0)
+        order[pd->nonempty + cta_ebase[blockIdx.x] + __popc(empty & ((1u << lane) - 1u))] = (int)t;
+    }
+  }
+  __syncthreads();
+  const double inv = pd->inv_ab;
+  int inv_e;
+  const float inv_m = (float)frexp(inv, &inv_e);
+  const int m = pd->flag_exp;
+  for (int r = 0; r < kTileRounds; ++r) {
+    const int lt = warp + r * kWarpsPerCta;
+    const int64_t t = t0 + lt;
+    if (t >= tiles) break;
+    const int c = cnt[t];
+    if (c == 0) continue;
+    if (lane == 0) order[atomicAdd(&pd->cursor[c], 1)] = (int)t;
+    const int i = (int)(t / bd), j = (int)(t % bd);
+    const Screen* ra = sA + (int64_t)i * bd;
+    const Screen* rb = sBT + (int64_t)j * bd;
+    int base = s_ptr[lt];
+    for (int k0 = 0; k0 < bd; k0 += 32) {
+      const int k = k0 + lane;
+      bool s = false;
+      Screen a{}, b{};
+      if (k < bd) {
+        a = ra[k];
+        b = rb[k];
+        s = survives(a, b, nA + (int64_t)i * bd + k, nB + (int64_t)k * bd + j, T);
+      }
+      const unsigned ball = __ballot_sync(0xffffffffu, s);
+      if (s) {
+        uint16_t v = (uint16_t)k;
+        if (split && rel_bin_screened(a, b, inv_m, inv_e, nA + (int64_t)i * bd + k,
+                                      nB + (int64_t)k * bd + j, inv) >= m)
+          v |= kSplitFlag;
+        k_idx[base + __popc(ball & ((1u << lane) - 1u))] = v;
+        needA[(int64_t)i * bd + k] = 1;   // benign: every writer stores 1
+        needB[(int64_t)k * bd + j] = 1;
+      }
+      base += __popc(ball);
+    }
   }
 }
 
@@ -460,25 +553,30 @@ cudaError_t run_plan(PlanBuffers& b, const double* nA, const double* nB, double 
                      double target_rel, int split, double c1, cudaStream_t s) {
   const int bd = b.bd;
   const int64_t tiles = (int64_t)bd * bd;
+  // clear the accumulators (count histogram, split bins)
+  const size_t acc_off = offsetof(PlanDevice, hist);
+  cudaError_t e = cudaMemsetAsync(reinterpret_cast<char*>(b.pd) + acc_off, 0,
+                                  sizeof(PlanDevice) - acc_off, s);
+  if (e != cudaSuccess) return e;
   const int prep_ctas = (int)((tiles + 255) / 256);
-  prep_kernel<<<prep_ctas, 256, 0, s>>>(nA, nB, bd, b.sA, b.sBT, b.part_a, b.part_b);
-  norms_kernel<<<1, 256, 0, s>>>(b.part_a, b.part_b, prep_ctas, b.pd);
+  prep_kernel<<<prep_ctas, 256, 0, s>>>(nA, nB, bd, b.sA, b.sBT, b.part_a, b.part_b, b.pd);
   const TauScreen T = make_tau_screen(tau);
-  const int count_ctas = (int)((tiles + kWarpsPerCta - 1) / kWarpsPerCta);
+  const int count_ctas = (int)((tiles + kTilesPerCta - 1) / kTilesPerCta);
   CountParts parts{b.part_S, b.part_kmax, b.part_ne, b.part_b1, b.part_b2};
   count_kernel<<<count_ctas, kWarpsPerCta * 32, 0, s>>>(b.sA, b.sBT, nA, nB, bd, T, split, b.pd,
                                                         b.cnt, parts, b.needA, b.needB);
-  finalize_kernel<<<1, kFinThreads, 0, s>>>(b.cnt, bd, parts, count_ctas, split, c1, target_rel,
-                                            b.pd, b.tile_ptr, b.order);
+  finalize_kernel<<<1, kFinThreads, 0, s>>>(bd, parts, count_ctas, split, c1, target_rel, b.pd,
+                                            b.cta_base, b.cta_ebase);
   fill_kernel<<<count_ctas, kWarpsPerCta * 32, 0, s>>>(b.sA, b.sBT, nA, nB, bd, T, split, b.pd,
-                                                       b.cnt, b.tile_ptr, b.k_idx, b.needA,
+                                                       b.cnt, b.cta_base, b.cta_ebase,
+                                                       b.tile_ptr, b.order, b.k_idx, b.needA,
                                                        b.needB);
   return cudaPeekAtLastError();
 }
 
 int64_t plan_part_count(int bd) {
   const int64_t tiles = (int64_t)bd * bd;
-  return std::max<int64_t>((tiles + 255) / 256, (tiles + kWarpsPerCta - 1) / kWarpsPerCta);
+  return std::max<int64_t>((tiles + 255) / 256, (tiles + kTilesPerCta - 1) / kTilesPerCta);
 }
 
 }  // namespace spamm

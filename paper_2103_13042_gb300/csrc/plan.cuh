@@ -5,14 +5,25 @@
 
 namespace spamm {
 
-// Scalars the plan kernels produce (one per plan, in device memory).
+// Scalars the plan kernels produce (one per plan, in device memory).  The
+// members from `hist` on are accumulators cleared at the start of every plan.
 struct PlanDevice {
   double norm_a, norm_b, inv_ab;
   double bound1, bound2, valid_ratio;
   long long survivors, flagged;
   int max_tile, nonempty, flag_exp, pad_;
-  double bin_sum[kFlagBins];
+  int cursor[kMaxBd + 2];                   // next longest-first slot per survivor count
+  int hist[kMaxBd + 2];                     // number of tiles per survivor count (>= 1)
+  unsigned int ticket;                      // prep CTAs that have finished
+  unsigned int pad2_;
+  double bin_sum[kFlagBins];                // surviving products per relative binade
   unsigned long long bin_cnt[kFlagBins];
+};
+
+// Extended-range FP32 sum: value = m * 2^e with an integer exponent.
+struct ExtSum {
+  float m;
+  int e;
 };
 
 // Device buffers of one plan (carved from one workspace allocation).
@@ -25,8 +36,10 @@ struct PlanBuffers {
   long long* part_S;   // per-CTA partials (count)
   int* part_kmax;
   int* part_ne;
-  double* part_b1;
-  double* part_b2;
+  ExtSum* part_b1;     // per-CTA sums of skipped relative products
+  ExtSum* part_b2;     // per-CTA sums of their squares per tile
+  int* cta_base;       // per count-CTA: first k_idx slot of its tiles
+  int* cta_ebase;      // per count-CTA: empty tiles before its tiles
   int* cnt;            // [bd*bd] survivors per tile
   int* tile_ptr;       // [bd*bd + 1] CSR offsets
   int* order;          // [bd*bd] tiles, most survivors first, empty tiles last

@@ -20,6 +20,7 @@ namespace spamm {
 namespace {
 
 constexpr int kThreads = 256;
+constexpr int kChunk = 64;   // candidate blocks per need-flag scan (two warps)
 
 // Round to nearest even, keeping 10 explicit significand bits (TF32), on the
 // IEEE bit pattern; NaN/Inf pass through unchanged.
@@ -61,24 +62,55 @@ __global__ void __launch_bounds__(kThreads)
   constexpr int UNITS = NCH * LEAF * 8;           // 16-byte pieces per block image
   extern __shared__ float tile[];                 // [LEAF][LEAF + 1]
   __shared__ float warp_max[kThreads / 32];
+  __shared__ int s_list[kChunk];
   const int64_t tiles = (int64_t)bd * bd;
   const float lo_scale = (float)(1 << L::kLoShift);
 
-  for (int64_t w = blockIdx.x; w < 2 * tiles; w += gridDim.x) {
+  // Candidates (A blocks, then B blocks) in chunks of kChunk: the first two
+  // warps read one need flag each, thread 0 lists the needed ones in order,
+  // then the CTA rounds them one block at a time.
+  const int64_t nchunks = (2 * tiles + kChunk - 1) / kChunk;
+  for (int64_t chunk = blockIdx.x; chunk < nchunks; chunk += gridDim.x) {
+    if (threadIdx.x < kChunk) {
+      const int64_t cand = chunk * kChunk + threadIdx.x;
+      bool need = false;
+      if (cand < 2 * tiles) need = cand >= tiles ? needB[cand - tiles] != 0 : needA[cand] != 0;
+      s_list[threadIdx.x] = need ? 1 : 0;
+    }
+    __syncthreads();
+    // compact (kChunk entries; thread 0 is enough and keeps the order)
+    __shared__ int s_total;
+    if (threadIdx.x == 0) {
+      int tot = 0;
+      for (int q = 0; q < kChunk; ++q)
+        if (s_list[q]) s_list[tot++] = q;
+      s_total = tot;
+    }
+    __syncthreads();
+    const int total = s_total;
+  for (int li = 0; li < total; ++li) {
+    const int64_t w = chunk * kChunk + s_list[li];
     const bool isB = w >= tiles;
     const int64_t blk = isB ? w - tiles : w;
-    if (!(isB ? needB[blk] : needA[blk])) continue;
     const float* X = isB ? B : A;
     const int64_t r0 = (blk / bd) * LEAF, c0 = (blk % bd) * LEAF;
 
-    // stage the block (zero outside the matrix) and its largest magnitude
+    // stage the block (zero outside the matrix) and its largest magnitude;
+    // all loads are issued before the first shared-memory store
+    constexpr int PER_T = LEAF * LEAF / kThreads;
+    float vals[PER_T];
+#pragma unroll
+    for (int q = 0; q < PER_T; ++q) {
+      const int e = threadIdx.x + q * kThreads;
+      const int64_t gr = r0 + e / LEAF, gc = c0 + e % LEAF;
+      vals[q] = (gr < n && gc < n) ? __ldg(X + gr * n + gc) : 0.0f;
+    }
     float mx = 0.0f;
-    for (int e = threadIdx.x; e < LEAF * LEAF; e += kThreads) {
-      const int r = e / LEAF, c = e % LEAF;
-      const int64_t gr = r0 + r, gc = c0 + c;
-      const float v = (gr < n && gc < n) ? __ldg(X + gr * n + gc) : 0.0f;
-      tile[r * (LEAF + 1) + c] = v;
-      mx = fmaxf(mx, fabsf(v));
+#pragma unroll
+    for (int q = 0; q < PER_T; ++q) {
+      const int e = threadIdx.x + q * kThreads;
+      tile[(e / LEAF) * (LEAF + 1) + e % LEAF] = vals[q];
+      mx = fmaxf(mx, fabsf(vals[q]));
     }
     for (int off = 16; off > 0; off >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, off));
     if ((threadIdx.x & 31) == 0) warp_max[threadIdx.x / 32] = mx;
@@ -124,6 +156,8 @@ __global__ void __launch_bounds__(kThreads)
     }
     __syncthreads();   // the tile is reused by the next block
   }
+    __syncthreads();   // s_list / s_total are rewritten by the next chunk
+  }
 }
 
 template <uint32_t FMT, int LEAF, bool SPLIT>
@@ -137,8 +171,8 @@ cudaError_t launch_q(const float* A, const float* B, int64_t n, int bd, const ui
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, quantize_kernel<FMT, LEAF, SPLIT>,
                                                 kThreads, smem);
-  const int64_t work = 2LL * bd * bd;
-  const int grid = (int)std::min<int64_t>(work, (int64_t)sms * std::max(1, per_sm));
+  const int64_t chunks = (2LL * bd * bd + kChunk - 1) / kChunk;
+  const int grid = (int)std::min<int64_t>(chunks, (int64_t)sms * std::max(1, per_sm));
   quantize_kernel<FMT, LEAF, SPLIT><<<grid, kThreads, smem, s>>>(A, B, n, bd, needA, needB, img);
   return cudaPeekAtLastError();
 }
