@@ -4,23 +4,14 @@
 #include <mutex>
 #include <new>
 
-#include "plan.cuh"
-#include "tc_common.cuh"
+#include "engine.cuh"
 
 using namespace spamm;
 
 struct spamm_plan_s {
   int64_t n = 0;
-  int32_t leaf = 0;
   int32_t bd = 0;
-  spamm_precision_t precision = SPAMM_FP32;
-  int device = 0;
-  void* base = nullptr;     // workspace
-  bool owns = false;
-  PlanBuffers buf{};
-  OperandImages img{};      // tensor-core modes only
-  cudaStream_t side = nullptr;        // zero-fill of empty tiles runs here, overlapped
-  cudaEvent_t fork = nullptr, join = nullptr;
+  spamm::Engine eng;
 };
 
 namespace spamm {
@@ -31,6 +22,8 @@ int32_t* g_status[kMaxDevices] = {};
 std::mutex g_status_mu;
 constexpr int kReduceParts = 1024;
 double* g_reduce[kMaxDevices] = {};   // [kReduceParts + 1] per device
+
+size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 }  // namespace
 
 int32_t* device_status_word() {
@@ -58,15 +51,14 @@ static double* reduce_scratch() {
   return g_reduce[dev];
 }
 
-}  // namespace spamm
+bool is_tensor_mode(spamm_precision_t p) { return p != SPAMM_FP32; }
 
-namespace {
-
-bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
-bool leaf_ok(int32_t leaf) { return leaf == 32 || leaf == 64 || leaf == 128; }
-bool precision_ok(spamm_precision_t p) { return p >= SPAMM_FP32 && p <= SPAMM_FP16_SPLIT; }
-bool is_split(spamm_precision_t p) {
+bool has_lo(spamm_precision_t p) {
   return p == SPAMM_BF16_SPLIT || p == SPAMM_FP16_SPLIT || p == SPAMM_TF32X3;
+}
+
+bool uses_split_flags(spamm_precision_t p) {
+  return p == SPAMM_BF16_SPLIT || p == SPAMM_FP16_SPLIT;
 }
 
 // Unit roundoff of the hi part of each precision (for the split-flag budget).
@@ -81,84 +73,125 @@ double hi_unit(spamm_precision_t p) {
   }
 }
 
-size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
-
-}  // namespace
-
-namespace spamm {
-
-// Lays the plan buffers out in one allocation; returns the total size.
-size_t plan_layout(int bd, PlanBuffers* b, char* base) {
-  const size_t tiles = (size_t)bd * bd;
-  const size_t parts = (size_t)plan_part_count(bd);
-  size_t off = 0;
-  auto take = [&](size_t bytes) {
-    off = align_up(off, 256);
-    char* p = base ? base + off : nullptr;
-    off += bytes;
-    return p;
-  };
-  PlanBuffers t{};
-  t.bd = bd;
-  t.pd = reinterpret_cast<PlanDevice*>(take(sizeof(PlanDevice)));
-  t.sA = reinterpret_cast<Screen*>(take(tiles * sizeof(Screen)));
-  t.sBT = reinterpret_cast<Screen*>(take(tiles * sizeof(Screen)));
-  t.part_a = reinterpret_cast<double*>(take(parts * sizeof(double)));
-  t.part_b = reinterpret_cast<double*>(take(parts * sizeof(double)));
-  t.part_S = reinterpret_cast<long long*>(take(parts * sizeof(long long)));
-  t.part_kmax = reinterpret_cast<int*>(take(parts * sizeof(int)));
-  t.part_ne = reinterpret_cast<int*>(take(parts * sizeof(int)));
-  t.part_b1 = reinterpret_cast<ExtSum*>(take(parts * sizeof(ExtSum)));
-  t.part_b2 = reinterpret_cast<ExtSum*>(take(parts * sizeof(ExtSum)));
-  t.cta_base = reinterpret_cast<int*>(take(parts * sizeof(int)));
-  t.cta_ebase = reinterpret_cast<int*>(take(parts * sizeof(int)));
-  t.cnt = reinterpret_cast<int*>(take(tiles * sizeof(int)));
-  t.tile_ptr = reinterpret_cast<int*>(take((tiles + 1) * sizeof(int)));
-  t.order = reinterpret_cast<int*>(take(tiles * sizeof(int)));
-  t.k_idx = reinterpret_cast<uint16_t*>(take(tiles * (size_t)bd * sizeof(uint16_t)));
-  t.needA = reinterpret_cast<uint8_t*>(take(tiles));
-  t.needB = reinterpret_cast<uint8_t*>(take(tiles));
-  if (b) *b = t;
-  return align_up(off, 256);
-}
-
-bool is_tensor_mode(spamm_precision_t p) { return p != SPAMM_FP32; }
-
-bool has_lo(spamm_precision_t p) {
-  return p == SPAMM_BF16_SPLIT || p == SPAMM_FP16_SPLIT || p == SPAMM_TF32X3;
-}
-
-// Operand images of the tensor-core modes, carved after the plan buffers.
-size_t images_layout(int bd, int leaf, spamm_precision_t prec, OperandImages* img, char* base) {
+size_t engine_layout(std::vector<Inst>& insts, int leaf, spamm_precision_t prec, size_t extra,
+                     PlanBuffers* buf, OperandImages* img, char* base) {
+  size_t off = align_up(extra, 256);
+  PlanBuffers b{};
+  const size_t plan_bytes =
+      plan_layout(insts.data(), (int)insts.size(), &b, base ? base + off : nullptr);
+  off += plan_bytes;
   OperandImages t{};
-  if (!is_tensor_mode(prec)) {
-    if (img) *img = t;
-    return 0;
+  if (is_tensor_mode(prec)) {
+    const size_t tiles = (size_t)b.tiles;
+    const size_t blk = (size_t)leaf * leaf * (prec == SPAMM_TF32X3 ? 4 : 2);
+    auto take = [&](size_t bytes) {
+      off = align_up(off, 256);
+      char* p = base ? base + off : nullptr;
+      off += bytes;
+      return p;
+    };
+    t.a_hi = reinterpret_cast<uint8_t*>(take(tiles * blk));
+    t.b_hi = reinterpret_cast<uint8_t*>(take(tiles * blk));
+    if (has_lo(prec)) {
+      t.a_lo = reinterpret_cast<uint8_t*>(take(tiles * blk));
+      t.b_lo = reinterpret_cast<uint8_t*>(take(tiles * blk));
+    }
+    t.ea = reinterpret_cast<int32_t*>(take(tiles * sizeof(int32_t)));
+    t.eb = reinterpret_cast<int32_t*>(take(tiles * sizeof(int32_t)));
   }
-  const size_t tiles = (size_t)bd * bd;
-  const size_t blk = (size_t)leaf * leaf * (prec == SPAMM_TF32X3 ? 4 : 2);
-  size_t off = 0;
-  auto take = [&](size_t bytes) {
-    off = align_up(off, 256);
-    char* p = base ? base + off : nullptr;
-    off += bytes;
-    return p;
-  };
-  t.a_hi = reinterpret_cast<uint8_t*>(take(tiles * blk));
-  t.b_hi = reinterpret_cast<uint8_t*>(take(tiles * blk));
-  if (has_lo(prec)) {
-    t.a_lo = reinterpret_cast<uint8_t*>(take(tiles * blk));
-    t.b_lo = reinterpret_cast<uint8_t*>(take(tiles * blk));
-  }
-  t.ea = reinterpret_cast<int32_t*>(take(tiles * sizeof(int32_t)));
-  t.eb = reinterpret_cast<int32_t*>(take(tiles * sizeof(int32_t)));
+  if (buf) *buf = b;
   if (img) *img = t;
   return align_up(off, 256);
+}
+
+spamm_status_t engine_init(Engine& e, std::vector<Inst> insts, int leaf, spamm_precision_t prec,
+                           size_t extra, void* workspace, size_t ws_bytes) {
+  e.leaf = leaf;
+  e.precision = prec;
+  e.extra_bytes = extra;
+  e.insts = std::move(insts);
+  const size_t need = engine_layout(e.insts, leaf, prec, extra, nullptr, nullptr, nullptr);
+  if (cudaGetDevice(&e.device) != cudaSuccess) return SPAMM_ERR_CUDA;
+  if (workspace) {
+    if (reinterpret_cast<uintptr_t>(workspace) & 255u) return SPAMM_ERR_INVALID_ARG;
+    if (ws_bytes < need) return SPAMM_ERR_NO_MEMORY;
+    e.base = workspace;
+  } else {
+    if (cudaMalloc(&e.base, need) != cudaSuccess) {
+      (void)cudaGetLastError();
+      e.base = nullptr;
+      return SPAMM_ERR_NO_MEMORY;
+    }
+    e.owns = true;
+  }
+  engine_layout(e.insts, leaf, prec, extra, &e.buf, &e.img, static_cast<char*>(e.base));
+  if (cudaStreamCreateWithFlags(&e.side, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&e.fork, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&e.join, cudaEventDisableTiming) != cudaSuccess) {
+    (void)cudaGetLastError();
+    engine_free(e);
+    return SPAMM_ERR_CUDA;
+  }
+  return SPAMM_OK;
+}
+
+spamm_status_t engine_free(Engine& e) {
+  spamm_status_t st = SPAMM_OK;
+  if (e.side) cudaStreamDestroy(e.side);
+  if (e.fork) cudaEventDestroy(e.fork);
+  if (e.join) cudaEventDestroy(e.join);
+  e.side = nullptr;
+  e.fork = e.join = nullptr;
+  if (e.owns && e.base) {
+    if (cudaFree(e.base) != cudaSuccess) st = SPAMM_ERR_CUDA;
+  }
+  e.base = nullptr;
+  e.owns = false;
+  return st;
+}
+
+cudaError_t engine_multiply(Engine& e, const InstRef& ref, int32_t* status, cudaStream_t s) {
+  // empty tiles (zeros, HBM-write bound) on the side stream, overlapped with
+  // the rounding and multiply of the non-empty tiles (disjoint parts of C)
+  cudaError_t err = cudaEventRecord(e.fork, s);
+  if (err == cudaSuccess) err = cudaStreamWaitEvent(e.side, e.fork, 0);
+  if (err == cudaSuccess) err = launch_zero_empty_tiles(ref, e.buf, e.leaf, e.side);
+  if (err == cudaSuccess) err = cudaEventRecord(e.join, e.side);
+  if (err == cudaSuccess) {
+    if (e.precision == SPAMM_FP32) {
+      err = launch_multiply_simt(ref, e.buf, e.leaf, s);
+    } else {
+      err = launch_quantize(e.precision, e.leaf, ref, e.buf, e.img, s);
+      if (err == cudaSuccess) err = launch_multiply_tc(e.precision, e.leaf, ref, e.buf, e.img, status, s);
+    }
+  }
+  if (err == cudaSuccess) err = cudaStreamWaitEvent(s, e.join, 0);
+  return err;
+}
+
+void fill_stats(const PlanDevice& h, int leaf, int bd, spamm_stats_t* stats) {
+  std::memset(stats, 0, sizeof(*stats));
+  stats->survivors = h.survivors;
+  stats->nonempty_tiles = h.nonempty;
+  stats->flagged = h.flagged;
+  stats->valid_ratio = h.valid_ratio;
+  stats->skipped_bound1 = h.bound1;
+  stats->skipped_bound2 = h.bound2;
+  stats->norm_a = h.norm_a;
+  stats->norm_b = h.norm_b;
+  stats->leaf = leaf;
+  stats->bd = bd;
+  stats->max_tile_survivors = h.max_tile;
+  stats->flag_exponent = h.flag_exp;
 }
 
 }  // namespace spamm
 
 namespace {
+
+bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+bool leaf_ok(int32_t leaf) { return leaf == 32 || leaf == 64 || leaf == 128; }
+bool precision_ok(spamm_precision_t p) { return p >= SPAMM_FP32 && p <= SPAMM_FP16_SPLIT; }
 
 spamm_status_t check_shape(int64_t n, int32_t leaf) {
   if (n < 1) return SPAMM_ERR_INVALID_ARG;
@@ -166,6 +199,14 @@ spamm_status_t check_shape(int64_t n, int32_t leaf) {
   if (num_blocks(n, leaf) > kMaxBd) return SPAMM_ERR_UNSUPPORTED;
   if (n > (int64_t)1 << 20) return SPAMM_ERR_UNSUPPORTED;
   return SPAMM_OK;
+}
+
+std::vector<Inst> single_inst(int64_t n, int leaf) {
+  std::vector<Inst> v(1);
+  v[0] = Inst{};
+  v[0].n = n;
+  v[0].bd = (int)num_blocks(n, leaf);
+  return v;
 }
 
 }  // namespace
@@ -205,8 +246,8 @@ spamm_status_t spamm_plan_workspace_size(int64_t n, int32_t leaf, spamm_precisio
   if (!precision_ok(precision)) return SPAMM_ERR_INVALID_ARG;
   if (!bytes) return SPAMM_ERR_INVALID_ARG;
   if (is_tensor_mode(precision) && leaf == 32) return SPAMM_ERR_UNSUPPORTED;
-  const int bd = (int)num_blocks(n, leaf);
-  *bytes = plan_layout(bd, nullptr, nullptr) + images_layout(bd, leaf, precision, nullptr, nullptr);
+  std::vector<Inst> v = single_inst(n, leaf);
+  *bytes = engine_layout(v, leaf, precision, 0, nullptr, nullptr, nullptr);
   return SPAMM_OK;
 }
 
@@ -218,45 +259,14 @@ spamm_status_t spamm_plan_create(spamm_plan_t* plan, int64_t n, int32_t leaf,
   if (st != SPAMM_OK) return st;
   if (!precision_ok(precision)) return SPAMM_ERR_INVALID_ARG;
   if (is_tensor_mode(precision) && leaf == 32) return SPAMM_ERR_UNSUPPORTED;
-  const int bd = (int)num_blocks(n, leaf);
-  const size_t plan_bytes = plan_layout(bd, nullptr, nullptr);
-  const size_t need = plan_bytes + images_layout(bd, leaf, precision, nullptr, nullptr);
   spamm_plan_s* p = new (std::nothrow) spamm_plan_s();
   if (!p) return SPAMM_ERR_NO_MEMORY;
   p->n = n;
-  p->leaf = leaf;
-  p->bd = bd;
-  p->precision = precision;
-  if (cudaGetDevice(&p->device) != cudaSuccess) {
+  p->bd = (int)num_blocks(n, leaf);
+  st = engine_init(p->eng, single_inst(n, leaf), leaf, precision, 0, workspace, ws_bytes);
+  if (st != SPAMM_OK) {
     delete p;
-    return SPAMM_ERR_CUDA;
-  }
-  if (workspace) {
-    if (ws_bytes < need || (reinterpret_cast<uintptr_t>(workspace) & 255u)) {
-      delete p;
-      return ws_bytes < need ? SPAMM_ERR_NO_MEMORY : SPAMM_ERR_INVALID_ARG;
-    }
-    p->base = workspace;
-  } else {
-    if (cudaMalloc(&p->base, need) != cudaSuccess) {
-      (void)cudaGetLastError();
-      delete p;
-      return SPAMM_ERR_NO_MEMORY;
-    }
-    p->owns = true;
-  }
-  plan_layout(bd, &p->buf, static_cast<char*>(p->base));
-  images_layout(bd, leaf, precision, &p->img, static_cast<char*>(p->base) + plan_bytes);
-  if (cudaStreamCreateWithFlags(&p->side, cudaStreamNonBlocking) != cudaSuccess ||
-      cudaEventCreateWithFlags(&p->fork, cudaEventDisableTiming) != cudaSuccess ||
-      cudaEventCreateWithFlags(&p->join, cudaEventDisableTiming) != cudaSuccess) {
-    (void)cudaGetLastError();
-    if (p->side) cudaStreamDestroy(p->side);
-    if (p->fork) cudaEventDestroy(p->fork);
-    if (p->join) cudaEventDestroy(p->join);
-    if (p->owns) cudaFree(p->base);
-    delete p;
-    return SPAMM_ERR_CUDA;
+    return st;
   }
   *plan = p;
   return SPAMM_OK;
@@ -266,12 +276,7 @@ spamm_status_t spamm_plan_destroy(spamm_plan_t plan) {
   if (!plan) return SPAMM_ERR_INVALID_ARG;
   spamm_status_t st = SPAMM_OK;
   if (cudaDeviceSynchronize() != cudaSuccess) st = SPAMM_ERR_CUDA;
-  if (plan->side) cudaStreamDestroy(plan->side);
-  if (plan->fork) cudaEventDestroy(plan->fork);
-  if (plan->join) cudaEventDestroy(plan->join);
-  if (plan->owns && plan->base) {
-    if (cudaFree(plan->base) != cudaSuccess) st = SPAMM_ERR_CUDA;
-  }
+  if (engine_free(plan->eng) != SPAMM_OK) st = SPAMM_ERR_CUDA;
   delete plan;
   return st;
 }
@@ -281,12 +286,19 @@ spamm_status_t spamm_plan(spamm_plan_t plan, const double* normA, const double* 
   if (!plan || !normA || !normB) return SPAMM_ERR_INVALID_ARG;
   if (!aligned16(normA) || !aligned16(normB)) return SPAMM_ERR_INVALID_ARG;
   if (std::isnan(tau) || tau < 0.0) return SPAMM_ERR_INVALID_ARG;
-  const bool split = is_split(plan->precision) && plan->precision != SPAMM_TF32X3;
+  Engine& e = plan->eng;
+  const bool split = uses_split_flags(e.precision);
   if (split && !(target_rel_err >= 0.0)) return SPAMM_ERR_INVALID_ARG;
-  const double u = hi_unit(plan->precision);
-  cudaError_t e = run_plan(plan->buf, normA, normB, tau, target_rel_err, split ? 1 : 0,
-                           2.0 * u + u * u, (cudaStream_t)stream);
-  if (e != cudaSuccess) {
+  const double u = hi_unit(e.precision);
+  Inst& in = e.insts[0];
+  in.nA = normA;
+  in.nB = normB;
+  in.T = make_tau_screen(tau);
+  in.split = split ? 1 : 0;
+  in.target_rel = split ? target_rel_err : 0.0;
+  in.c1 = split ? 2.0 * u + u * u : 0.0;
+  cudaError_t err = run_plan(make_ref(e.insts.data(), nullptr, 1), e.buf, (cudaStream_t)stream);
+  if (err != cudaSuccess) {
     (void)cudaGetLastError();
     return SPAMM_ERR_CUDA;
   }
@@ -296,22 +308,10 @@ spamm_status_t spamm_plan(spamm_plan_t plan, const double* normA, const double* 
 spamm_status_t spamm_plan_stats(spamm_plan_t plan, spamm_stats_t* stats, void* stream) {
   if (!plan || !stats) return SPAMM_ERR_INVALID_ARG;
   PlanDevice h;
-  SPAMM_CUDA_TRY(cudaMemcpyAsync(&h, plan->buf.pd, sizeof(PlanDevice), cudaMemcpyDeviceToHost,
+  SPAMM_CUDA_TRY(cudaMemcpyAsync(&h, plan->eng.buf.pd, sizeof(PlanDevice), cudaMemcpyDeviceToHost,
                                  (cudaStream_t)stream));
   SPAMM_CUDA_TRY(cudaStreamSynchronize((cudaStream_t)stream));
-  std::memset(stats, 0, sizeof(*stats));
-  stats->survivors = h.survivors;
-  stats->nonempty_tiles = h.nonempty;
-  stats->flagged = h.flagged;
-  stats->valid_ratio = h.valid_ratio;
-  stats->skipped_bound1 = h.bound1;
-  stats->skipped_bound2 = h.bound2;
-  stats->norm_a = h.norm_a;
-  stats->norm_b = h.norm_b;
-  stats->leaf = plan->leaf;
-  stats->bd = plan->bd;
-  stats->max_tile_survivors = h.max_tile;
-  stats->flag_exponent = h.flag_exp;
+  fill_stats(h, plan->eng.leaf, plan->bd, stats);
   return SPAMM_OK;
 }
 
@@ -319,18 +319,23 @@ spamm_status_t spamm_plan_export(spamm_plan_t plan, int32_t* tile_ptr, uint16_t*
                                  int64_t cap, void* stream) {
   if (!plan) return SPAMM_ERR_INVALID_ARG;
   cudaStream_t s = (cudaStream_t)stream;
-  const int64_t tiles = (int64_t)plan->bd * plan->bd;
-  int32_t total = 0;
-  SPAMM_CUDA_TRY(cudaMemcpyAsync(&total, plan->buf.tile_ptr + tiles, sizeof(int32_t),
+  const PlanBuffers& b = plan->eng.buf;
+  const int64_t tiles = b.tiles;
+  // a single instance's queues are one contiguous CSR in tile order
+  std::vector<int32_t> cnt((size_t)tiles);
+  SPAMM_CUDA_TRY(cudaMemcpyAsync(cnt.data(), b.cnt, (size_t)tiles * sizeof(int32_t),
                                  cudaMemcpyDeviceToHost, s));
   SPAMM_CUDA_TRY(cudaStreamSynchronize(s));
-  if (tile_ptr)
-    SPAMM_CUDA_TRY(cudaMemcpyAsync(tile_ptr, plan->buf.tile_ptr, (tiles + 1) * sizeof(int32_t),
-                                   cudaMemcpyDeviceToHost, s));
+  int64_t total = 0;
+  for (int64_t t = 0; t < tiles; ++t) {
+    if (tile_ptr) tile_ptr[t] = (int32_t)total;
+    total += cnt[(size_t)t];
+  }
+  if (tile_ptr) tile_ptr[tiles] = (int32_t)total;
   if (k_idx) {
     if (cap < total) return SPAMM_ERR_NO_MEMORY;
     if (total > 0)
-      SPAMM_CUDA_TRY(cudaMemcpyAsync(k_idx, plan->buf.k_idx, (size_t)total * sizeof(uint16_t),
+      SPAMM_CUDA_TRY(cudaMemcpyAsync(k_idx, b.k_idx, (size_t)total * sizeof(uint16_t),
                                      cudaMemcpyDeviceToHost, s));
   }
   SPAMM_CUDA_TRY(cudaStreamSynchronize(s));
@@ -342,31 +347,19 @@ spamm_status_t spamm_multiply(spamm_plan_t plan, const float* A, const float* B,
   if (!plan || !A || !B || !C) return SPAMM_ERR_INVALID_ARG;
   if (!aligned16(A) || !aligned16(B) || !aligned16(C)) return SPAMM_ERR_INVALID_ARG;
   if (A == C || B == C) return SPAMM_ERR_INVALID_ARG;
+  Engine& e = plan->eng;
   int32_t* status = nullptr;
-  if (plan->precision != SPAMM_FP32) {
+  if (e.precision != SPAMM_FP32) {
     status = device_status_word();
     if (!status) return SPAMM_ERR_NO_MEMORY;
   }
-  const cudaStream_t s = (cudaStream_t)stream;
-  // empty tiles (zeros, HBM-write bound) on the side stream, overlapped with
-  // the rounding and multiply of the non-empty tiles (disjoint parts of C)
-  cudaError_t e = cudaEventRecord(plan->fork, s);
-  if (e == cudaSuccess) e = cudaStreamWaitEvent(plan->side, plan->fork, 0);
-  if (e == cudaSuccess) e = launch_zero_empty_tiles(plan->buf, C, plan->n, plan->leaf, plan->side);
-  if (e == cudaSuccess) e = cudaEventRecord(plan->join, plan->side);
-  if (e == cudaSuccess) {
-    if (plan->precision == SPAMM_FP32) {
-      e = launch_multiply_simt(plan->buf, A, B, C, plan->n, plan->leaf, s);
-    } else {
-      e = launch_quantize(plan->precision, plan->leaf, A, B, plan->n, plan->bd, plan->buf.needA,
-                          plan->buf.needB, plan->img, s);
-      if (e == cudaSuccess)
-        e = launch_multiply_tc(plan->precision, plan->leaf, plan->buf, plan->img, C, plan->n,
-                               status, s);
-    }
-  }
-  if (e == cudaSuccess) e = cudaStreamWaitEvent(s, plan->join, 0);
-  if (e != cudaSuccess) {
+  Inst& in = e.insts[0];
+  in.A = A;
+  in.B = B;
+  in.C = C;
+  cudaError_t err = engine_multiply(e, make_ref(e.insts.data(), nullptr, 1), status,
+                                    (cudaStream_t)stream);
+  if (err != cudaSuccess) {
     (void)cudaGetLastError();
     return SPAMM_ERR_CUDA;
   }

@@ -1,0 +1,53 @@
+// Host-side engine shared by single plans and batches: one workspace holding
+// the plan buffers and operand images of a table of instances, plus the
+// streams and events of the multiply.
+#pragma once
+
+#include <vector>
+
+#include "plan.cuh"
+#include "tc_common.cuh"
+
+namespace spamm {
+
+struct Engine {
+  int32_t leaf = 0;
+  spamm_precision_t precision = SPAMM_FP32;
+  int device = 0;
+  void* base = nullptr;        // workspace
+  bool owns = false;           // allocated by the library
+  std::vector<Inst> insts;     // host copy of the instance table (layout fields filled)
+  PlanBuffers buf{};
+  OperandImages img{};         // tensor-core modes only
+  size_t extra_bytes = 0;      // caller-defined area at the start of the workspace
+  cudaStream_t side = nullptr; // zero-fill of empty tiles runs here, overlapped
+  cudaEvent_t fork = nullptr, join = nullptr;
+};
+
+bool is_tensor_mode(spamm_precision_t p);
+bool has_lo(spamm_precision_t p);
+bool uses_split_flags(spamm_precision_t p);   // BF16/FP16 split: flag budget in the plan
+double hi_unit(spamm_precision_t p);
+
+// Bytes of the workspace for `insts` (bd fields set) with `extra` bytes in
+// front; fills the layout of `insts`, `buf` and `img` when `base` is non-null.
+size_t engine_layout(std::vector<Inst>& insts, int leaf, spamm_precision_t prec, size_t extra,
+                     PlanBuffers* buf, OperandImages* img, char* base);
+
+// Sets up `e` for `insts` (only n and bd read): allocates the workspace when
+// `workspace` is null, creates the side stream and events.
+spamm_status_t engine_init(Engine& e, std::vector<Inst> insts, int leaf, spamm_precision_t prec,
+                           size_t extra, void* workspace, size_t ws_bytes);
+spamm_status_t engine_free(Engine& e);
+
+// Enqueues the multiply of every instance of `ref` on `s` (zero-fill of the
+// empty tiles forked to the side stream and joined back).
+cudaError_t engine_multiply(Engine& e, const InstRef& ref, int32_t* status, cudaStream_t s);
+
+void fill_stats(const PlanDevice& h, int leaf, int bd, spamm_stats_t* out);
+
+// Lazily allocated device status word of the current device (tensor-core
+// kernels latch timeouts there).
+int32_t* device_status_word();
+
+}  // namespace spamm

@@ -1,9 +1,9 @@
 // Plain FP32 multiply on the SIMT cores (Section 3.3's FP32 multiplication
 // kernel; the baseline the tensor-core modes are measured against).
 //
-// Persistent CTAs walk the plan's non-empty tiles (most survivors first) with
-// a grid stride; the caller writes the empty tiles with the coalesced
-// zero-fill kernel.  A non-empty tile (i, j) streams its
+// Persistent CTAs walk the non-empty tiles of all instances (most survivors
+// first) with a grid stride; the caller writes the empty tiles with the
+// coalesced zero-fill kernel.  A non-empty tile (i, j) streams its
 // surviving k in 32-wide slices of the inner dimension: the A slice
 // A[i, k][:, s:s+32] is stored transposed and the B slice B[k, j][s:s+32, :]
 // as is, both in shared memory, double buffered through registers so the next
@@ -19,19 +19,18 @@ namespace {
 constexpr int kThreads = 256;
 constexpr int kSlice = 32;
 
-template <int LEAF, bool VEC>
+template <int LEAF>
 struct SimtTile {
   static constexpr int TM = LEAF / 16;                    // C rows (and cols) per thread
   static constexpr int kLoadsA = LEAF * kSlice / 4 / kThreads;  // float4 per thread per slice
 };
 
 // Loads 4 consecutive floats of row r, columns c..c+3, zero outside [0, n).
-template <bool VEC>
 __device__ __forceinline__ float4 load4(const float* __restrict__ M, int64_t n, int64_t r,
-                                        int64_t c) {
+                                        int64_t c, bool vec) {
   if (r >= n) return make_float4(0.f, 0.f, 0.f, 0.f);
   const float* p = M + r * n + c;
-  if (VEC && c + 3 < n) return __ldg(reinterpret_cast<const float4*>(p));
+  if (vec && c + 3 < n) return __ldg(reinterpret_cast<const float4*>(p));
   float4 v;
   v.x = c < n ? __ldg(p) : 0.f;
   v.y = c + 1 < n ? __ldg(p + 1) : 0.f;
@@ -66,13 +65,9 @@ __device__ __forceinline__ void write_row(float* p, const float* v) {
   }
 }
 
-template <int LEAF, bool VEC>
-__global__ void __launch_bounds__(kThreads)
-    simt_kernel(const float* __restrict__ A, const float* __restrict__ B, float* __restrict__ C,
-                int64_t n, int bd, const int* __restrict__ order,
-                const int* __restrict__ tile_ptr, const uint16_t* __restrict__ k_idx,
-                const PlanDevice* __restrict__ pd) {
-  using T = SimtTile<LEAF, VEC>;
+template <int LEAF>
+__global__ void __launch_bounds__(kThreads) simt_kernel(InstRef R, PlanBuffers Bf) {
+  using T = SimtTile<LEAF>;
   constexpr int TM = T::TM;
   constexpr int kLoads = T::kLoadsA;
   // A slice transposed: sA[buf][s][r] (r = row within the leaf), B slice sB[buf][s][c]
@@ -83,12 +78,21 @@ __global__ void __launch_bounds__(kThreads)
 
   const int tid = threadIdx.x;
   const int tx = tid % 16, ty = tid / 16;
-  const int64_t ne = pd->nonempty;   // empty tiles are zero-filled by another kernel
+  const int64_t ne = Bf.bdev->nonempty;   // empty tiles are zero-filled by another kernel
 
   for (int64_t w = blockIdx.x; w < ne; w += gridDim.x) {
-    const int t = order[w];
-    const int i = t / bd, j = t % bd;
-    const int beg = tile_ptr[t], end = tile_ptr[t + 1];
+    const int g = Bf.order[w];
+    const Inst& in = R.at(inst_of_tile(R, g));
+    const int bd = in.bd;
+    const int64_t n = in.n;
+    const float* __restrict__ A = in.A;
+    const float* __restrict__ B = in.B;
+    float* __restrict__ C = in.C;
+    const bool VEC = (n % 4) == 0;
+    const uint16_t* __restrict__ k_idx = Bf.k_idx;
+    const int64_t t = g - in.tile0;
+    const int i = (int)(t / bd), j = (int)(t % bd);
+    const int beg = Bf.tile_beg[g], end = beg + Bf.cnt[g];
     const int64_t r0 = (int64_t)i * LEAF, c0 = (int64_t)j * LEAF;
 
     float acc[TM][TM];
@@ -109,10 +113,10 @@ __global__ void __launch_bounds__(kThreads)
         const int e = (tid + l * kThreads) * 4;      // element index in the slice
         // A slice: LEAF rows x 32 cols, float4 along the columns
         const int ar = e / kSlice, ac = e % kSlice;
-        ra[l] = load4<VEC>(A, n, r0 + ar, (int64_t)k * LEAF + s0 + ac);
+        ra[l] = load4(A, n, r0 + ar, (int64_t)k * LEAF + s0 + ac, VEC);
         // B slice: 32 rows x LEAF cols, float4 along the columns
         const int br = e / LEAF, bc = e % LEAF;
-        rb[l] = load4<VEC>(B, n, (int64_t)k * LEAF + s0 + br, c0 + bc);
+        rb[l] = load4(B, n, (int64_t)k * LEAF + s0 + br, c0 + bc, VEC);
       }
     };
     auto stash = [&](int buf) {
@@ -167,33 +171,28 @@ __global__ void __launch_bounds__(kThreads)
   }
 }
 
-template <int LEAF, bool VEC>
-cudaError_t launch(const PlanBuffers& b, const float* A, const float* B, float* C, int64_t n,
-                   cudaStream_t s) {
+template <int LEAF>
+cudaError_t launch(const InstRef& ref, const PlanBuffers& b, cudaStream_t s) {
   constexpr size_t smem = 4 * kSlice * (LEAF + 4) * sizeof(float);
   int dev = 0, sms = 0, per_sm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  cudaFuncSetAttribute(simt_kernel<LEAF, VEC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       (int)smem);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, simt_kernel<LEAF, VEC>, kThreads, smem);
-  const int64_t tiles = (int64_t)b.bd * b.bd;
-  const int grid = (int)std::min<int64_t>(tiles, (int64_t)sms * std::max(1, per_sm));
-  simt_kernel<LEAF, VEC><<<grid, kThreads, smem, s>>>(A, B, C, n, b.bd, b.order, b.tile_ptr,
-                                                      b.k_idx, b.pd);
+  cudaFuncSetAttribute(simt_kernel<LEAF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, simt_kernel<LEAF>, kThreads, smem);
+  const int grid = (int)std::max<int64_t>(
+      1, std::min<int64_t>(b.tiles, (int64_t)sms * std::max(1, per_sm)));
+  simt_kernel<LEAF><<<grid, kThreads, smem, s>>>(ref, b);
   return cudaPeekAtLastError();
 }
 
 }  // namespace
 
-cudaError_t launch_multiply_simt(const PlanBuffers& b, const float* A, const float* B, float* C,
-                                 int64_t n, int32_t leaf, cudaStream_t s) {
-  const bool vec = (n % 4) == 0;
+cudaError_t launch_multiply_simt(const InstRef& ref, const PlanBuffers& b, int leaf,
+                                 cudaStream_t s) {
   switch (leaf) {
-    case 32: return vec ? launch<32, true>(b, A, B, C, n, s) : launch<32, false>(b, A, B, C, n, s);
-    case 64: return vec ? launch<64, true>(b, A, B, C, n, s) : launch<64, false>(b, A, B, C, n, s);
-    case 128:
-      return vec ? launch<128, true>(b, A, B, C, n, s) : launch<128, false>(b, A, B, C, n, s);
+    case 32: return launch<32>(ref, b, s);
+    case 64: return launch<64>(ref, b, s);
+    case 128: return launch<128>(ref, b, s);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -50,25 +50,16 @@ struct RunRec {
   int32_t tile, s, split, last;
 };
 
-// Entry record published by the scheduler: x = tile, y = k, z = exponent sum,
-// w = flags (1: first of a run, 2: last of its tile, 4: split).  A group holds
-// up to 32 records; its count sits in the misc area (0 count = end of work).
+// Entry record published by the scheduler: x = global block of A_ik, y =
+// global block of B_kj, z = exponent sum * 16 + flags (1: first of a run,
+// 2: last of its tile, 4: split), w = global tile.  A group holds up to 32
+// records; its count sits in the misc area (0 count = end of work).
 enum : int { kEntFirst = 1, kEntLast = 2, kEntSplit = 4 };
 
 struct TcParams {
-  const uint8_t* a_hi;
-  const uint8_t* a_lo;
-  const uint8_t* b_hi;
-  const uint8_t* b_lo;
-  const int32_t* ea;
-  const int32_t* eb;
-  const int* order;
-  const int* tile_ptr;
-  const uint16_t* k_idx;
-  const PlanDevice* pd;
-  float* C;
-  int64_t n;
-  int bd;
+  InstRef R;
+  PlanBuffers Bf;
+  OperandImages img;
   int32_t* status;
 };
 
@@ -186,8 +177,7 @@ __global__ void __launch_bounds__(TcCfg<FMT, LEAF, SPLITMODE>::kThreads, 1)
   __syncthreads();
   fence_after_sync();
   const uint32_t tmem = *tmem_slot;
-  const int bd = p.bd;
-  const int ne = p.pd->nonempty;
+  const int ne = p.Bf.bdev->nonempty;
 
   if (warp == 2) {
     // ------------------------------------------------------------ scheduler
@@ -211,11 +201,15 @@ __global__ void __launch_bounds__(TcCfg<FMT, LEAF, SPLITMODE>::kThreads, 1)
     for (int base = blockIdx.x; base < ne && ok; base += 32 * gridDim.x) {
       const int w = base + lane * gridDim.x;
       const bool valid = w < ne;
-      int t = 0, beg = 0, end = 0;
+      int t = 0, beg = 0, end = 0, bdl = 1;
+      int64_t t0 = 0;
       if (valid) {
-        t = p.order[w];
-        beg = p.tile_ptr[t];
-        end = p.tile_ptr[t + 1];
+        t = p.Bf.order[w];                       // global tile
+        const Inst& in = p.R.at(inst_of_tile(p.R, t));
+        t0 = in.tile0;
+        bdl = in.bd;
+        beg = p.Bf.tile_beg[t];
+        end = beg + p.Bf.cnt[t];
       }
       const int cnt = end - beg;
       int incl = cnt;
@@ -243,13 +237,17 @@ __global__ void __launch_bounds__(TcCfg<FMT, LEAF, SPLITMODE>::kThreads, 1)
         const int bu = __shfl_sync(0xffffffffu, beg, u);
         const int xu = __shfl_sync(0xffffffffu, excl, u);
         const int iu = __shfl_sync(0xffffffffu, incl, u);
+        const int bdu = __shfl_sync(0xffffffffu, bdl, u);
+        const int64_t t0u = __shfl_sync(0xffffffffu, t0, u);
         const int q = bu + (f - xu);
         uint32_t ent = 0;
-        if (act) ent = p.k_idx[q];
+        if (act) ent = p.Bf.k_idx[q];
         const int k = (int)(ent & 0x3ffu);
-        const int i = tu / bd, j = tu % bd;
+        const int64_t lt = (int64_t)tu - t0u;
+        const int i = (int)(lt / bdu), j = (int)(lt % bdu);
+        const int ga = (int)(t0u + (int64_t)i * bdu + k), gb = (int)(t0u + (int64_t)k * bdu + j);
         int32_t sexp = 0;
-        if (act) sexp = p.ea[(int64_t)i * bd + k] + p.eb[(int64_t)k * bd + j];
+        if (act) sexp = p.img.ea[ga] + p.img.eb[gb];
         const bool split = SPLITMODE == 2 || (SPLITMODE == 1 && (ent & 0x8000u));
         const int32_t key = sexp * 2 + (split ? 1 : 0);
         int32_t pkey = __shfl_up_sync(0xffffffffu, key, 1);
@@ -267,8 +265,10 @@ __global__ void __launch_bounds__(TcCfg<FMT, LEAF, SPLITMODE>::kThreads, 1)
         if (!ok) break;
         if (act)
           ents[grp * 32 + gfill + lane] =
-              make_int4(tu, k, sexp, (first ? kEntFirst : 0) | (last ? kEntLast : 0) |
-                                         (split ? kEntSplit : 0));
+              make_int4(ga, gb,
+                        sexp * 16 + ((first ? kEntFirst : 0) | (last ? kEntLast : 0) |
+                                     (split ? kEntSplit : 0)),
+                        tu);
         gfill += nact;
       }
     }
@@ -289,11 +289,10 @@ __global__ void __launch_bounds__(TcCfg<FMT, LEAF, SPLITMODE>::kThreads, 1)
         if (nrec == 0) break;
         for (int r = 0; r < nrec && ok; ++r) {
           const int4 rec = ents[grp * 32 + r];
-          const int t = rec.x, k = rec.y, flags = rec.w;
-          const int i = t / bd, j = t % bd;
+          const int flags = rec.z & 15, sexp = rec.z >> 4;   // arithmetic shift
           const bool split = (flags & kEntSplit) != 0;
-          const int64_t oa = ((int64_t)i * bd + k) * L::kBlockBytes;
-          const int64_t ob = ((int64_t)k * bd + j) * L::kBlockBytes;
+          const int64_t oa = (int64_t)rec.x * L::kBlockBytes;
+          const int64_t ob = (int64_t)rec.y * L::kBlockBytes;
           for (int c = 0; c < L::kNch; ++c) {
             if (!wait_ab(&empty[stage], phase ^ 1u, abort_flag, p.status)) {
               ok = false;
@@ -302,18 +301,18 @@ __global__ void __launch_bounds__(TcCfg<FMT, LEAF, SPLITMODE>::kThreads, 1)
             StageMeta m;
             m.flags = ((flags & kEntFirst) && c == 0 ? 1 : 0) |
                       ((flags & kEntLast) && c == L::kNch - 1 ? 2 : 0) | (split ? 4 : 0);
-            m.s = rec.z;
-            m.tile = t;
+            m.s = sexp;
+            m.tile = rec.w;
             m.pad = 0;
             meta[stage] = m;
             mbar_arrive_expect_tx(&full[stage], CH * 2 * (split ? 2 : 1));
             uint8_t* sb = smem + (size_t)stage * Cfg::kStageBytes;
-            bulk_g2s(sb, p.a_hi + oa + c * CH, CH, &full[stage]);
-            bulk_g2s(sb + CH, p.b_hi + ob + c * CH, CH, &full[stage]);
+            bulk_g2s(sb, p.img.a_hi + oa + c * CH, CH, &full[stage]);
+            bulk_g2s(sb + CH, p.img.b_hi + ob + c * CH, CH, &full[stage]);
             if constexpr (Cfg::kHasLo) {
               if (split) {
-                bulk_g2s(sb + 2 * CH, p.a_lo + oa + c * CH, CH, &full[stage]);
-                bulk_g2s(sb + 3 * CH, p.b_lo + ob + c * CH, CH, &full[stage]);
+                bulk_g2s(sb + 2 * CH, p.img.a_lo + oa + c * CH, CH, &full[stage]);
+                bulk_g2s(sb + 3 * CH, p.img.b_lo + ob + c * CH, CH, &full[stage]);
               }
             }
             issued |= 1u << stage;
@@ -470,12 +469,15 @@ __global__ void __launch_bounds__(TcCfg<FMT, LEAF, SPLITMODE>::kThreads, 1)
       if (lane == 0) mbar_arrive(&acc_empty[buf]);
       ++run;
       if (r.last) {
-        const int i = r.tile / bd, j = r.tile % bd;
+        const Inst& in = p.R.at(inst_of_tile(p.R, r.tile));
+        const int bd = in.bd;
+        const int64_t n = in.n, lt = (int64_t)r.tile - in.tile0;
+        const int i = (int)(lt / bd), j = (int)(lt % bd);
         const int64_t gr = (int64_t)i * LEAF + row;
-        if (lane_has_row && gr < p.n) {
-          float* dst = p.C + gr * p.n + (int64_t)j * LEAF + col0;
-          const int64_t cols = p.n - (int64_t)j * LEAF - col0;
-          if (cols >= NC && (p.n & 3) == 0) {
+        if (lane_has_row && gr < n) {
+          float* dst = in.C + gr * n + (int64_t)j * LEAF + col0;
+          const int64_t cols = n - (int64_t)j * LEAF - col0;
+          if (cols >= NC && (n & 3) == 0) {
 #pragma unroll
             for (int c = 0; c < NC; c += 4)
               *reinterpret_cast<float4*>(dst + c) =
@@ -501,26 +503,36 @@ __global__ void __launch_bounds__(TcCfg<FMT, LEAF, SPLITMODE>::kThreads, 1)
   }
 }
 
+// Zeros for every tile without survivors: each warp reads the counts of 32
+// consecutive global tiles (coalesced) and writes the empty ones, row by row.
 __global__ void __launch_bounds__(256)
-    zero_tiles_kernel(const int* __restrict__ order, const PlanDevice* __restrict__ pd, int bd,
-                      float* __restrict__ C, int64_t n, int leaf) {
-  const int ne = pd->nonempty;
-  const int64_t tiles = (int64_t)bd * bd;
+    zero_tiles_kernel(InstRef R, PlanBuffers Bf, int leaf) {
   const int lane = threadIdx.x & 31;
   const int64_t gw = (int64_t)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
   const int64_t nw = (int64_t)gridDim.x * (blockDim.x / 32);
-  for (int64_t w = ne + gw; w < tiles; w += nw) {
-    const int t = order[w];
-    const int64_t r0 = (int64_t)(t / bd) * leaf, c0 = (int64_t)(t % bd) * leaf;
-    const int64_t rows = min((int64_t)leaf, n - r0), cols = min((int64_t)leaf, n - c0);
-    if ((n & 3) == 0 && cols == leaf) {
-      const int per_row = leaf / 4;
-      for (int e = lane; e < rows * per_row; e += 32) {
-        const int64_t r = e / per_row, c4 = e % per_row;
-        *reinterpret_cast<float4*>(C + (r0 + r) * n + c0 + 4 * c4) = make_float4(0.f, 0.f, 0.f, 0.f);
+  for (int64_t g0 = gw * 32; g0 < Bf.tiles; g0 += nw * 32) {
+    const int64_t gl = g0 + lane;
+    const bool empty = gl < Bf.tiles && Bf.cnt[gl] == 0;
+    unsigned mask = __ballot_sync(0xffffffffu, empty);
+    while (mask) {
+      const int b = __ffs(mask) - 1;
+      mask &= mask - 1;
+      const int64_t g = g0 + b;
+      const Inst& in = R.at(inst_of_tile(R, g));
+      const int64_t n = in.n, lt = g - in.tile0;
+      const int64_t r0 = (lt / in.bd) * leaf, c0 = (lt % in.bd) * leaf;
+      const int64_t rows = min((int64_t)leaf, n - r0), cols = min((int64_t)leaf, n - c0);
+      float* C = in.C;
+      if ((n & 3) == 0 && cols == leaf) {
+        const int per_row = leaf / 4;
+        for (int e = lane; e < rows * per_row; e += 32) {
+          const int64_t r = e / per_row, c4 = e % per_row;
+          *reinterpret_cast<float4*>(C + (r0 + r) * n + c0 + 4 * c4) =
+              make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+      } else {
+        for (int64_t e = lane; e < rows * cols; e += 32) C[(r0 + e / cols) * n + c0 + e % cols] = 0.f;
       }
-    } else {
-      for (int64_t e = lane; e < rows * cols; e += 32) C[(r0 + e / cols) * n + c0 + e % cols] = 0.f;
     }
   }
 }
@@ -541,20 +553,21 @@ cudaError_t launch_tc(const TcParams& prm, cudaStream_t s) {
 
 }  // namespace
 
-cudaError_t launch_zero_empty_tiles(const PlanBuffers& b, float* C, int64_t n, int leaf,
+cudaError_t launch_zero_empty_tiles(const InstRef& ref, const PlanBuffers& b, int leaf,
                                     cudaStream_t s) {
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  zero_tiles_kernel<<<sms * 8, 256, 0, s>>>(b.order, b.pd, b.bd, C, n, leaf);
+  const int64_t warps = (b.tiles + 31) / 32;
+  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((warps + 7) / 8, (int64_t)sms * 8));
+  zero_tiles_kernel<<<grid, 256, 0, s>>>(ref, b, leaf);
   return cudaPeekAtLastError();
 }
 
-cudaError_t launch_multiply_tc(spamm_precision_t prec, int leaf, const PlanBuffers& b,
-                               const OperandImages& img, float* C, int64_t n, int32_t* status,
+cudaError_t launch_multiply_tc(spamm_precision_t prec, int leaf, const InstRef& ref,
+                               const PlanBuffers& b, const OperandImages& img, int32_t* status,
                                cudaStream_t s) {
-  TcParams prm{img.a_hi, img.a_lo, img.b_hi, img.b_lo, img.ea,  img.eb, b.order, b.tile_ptr,
-               b.k_idx,  b.pd,     C,        n,        b.bd,    status};
+  TcParams prm{ref, b, img, status};
   const bool l64 = leaf == 64;
   switch (prec) {
     case SPAMM_BF16:

@@ -78,7 +78,10 @@ extern "C" spamm_status_t spamm_multiply_fp32_noalloc(const float* A, const floa
 
   // scratch: [normA | normB | plan buffers]
   const size_t norm_bytes = round256((size_t)bd * bd * sizeof(double));
-  const size_t plan_bytes = plan_layout(bd, nullptr, nullptr);
+  Inst inst{};
+  inst.n = n;
+  inst.bd = bd;
+  const size_t plan_bytes = plan_layout(&inst, 1, nullptr, nullptr);
   if (2 * norm_bytes + plan_bytes > kNoAllocBytes) return SPAMM_ERR_UNSUPPORTED;
 
   void* base = nullptr;
@@ -90,14 +93,21 @@ extern "C" spamm_status_t spamm_multiply_fp32_noalloc(const float* A, const floa
   double* nA = reinterpret_cast<double*>(p);
   double* nB = reinterpret_cast<double*>(p + norm_bytes);
   PlanBuffers buf{};
-  plan_layout(bd, &buf, p + 2 * norm_bytes);
+  plan_layout(&inst, 1, &buf, p + 2 * norm_bytes);
+  inst.A = A;
+  inst.B = B;
+  inst.C = C;
+  inst.nA = nA;
+  inst.nB = nB;
+  inst.T = make_tau_screen(tau);
+  const InstRef ref = make_ref(&inst, nullptr, 1);
 
   const cudaStream_t s = (cudaStream_t)stream;
   cudaError_t e = launch_normmap(A, n, leaf, nA, s);
   if (e == cudaSuccess) e = launch_normmap(B, n, leaf, nB, s);
-  if (e == cudaSuccess) e = run_plan(buf, nA, nB, tau, 0.0, 0, 0.0, s);
-  if (e == cudaSuccess) e = launch_multiply_simt(buf, A, B, C, n, leaf, s);
-  if (e == cudaSuccess) e = launch_zero_empty_tiles(buf, C, n, leaf, s);
+  if (e == cudaSuccess) e = run_plan(ref, buf, s);
+  if (e == cudaSuccess) e = launch_multiply_simt(ref, buf, leaf, s);
+  if (e == cudaSuccess) e = launch_zero_empty_tiles(ref, buf, leaf, s);
   if (e != cudaSuccess) {
     (void)cudaGetLastError();
     return SPAMM_ERR_CUDA;

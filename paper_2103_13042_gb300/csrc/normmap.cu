@@ -13,7 +13,7 @@
 // column spans several warps), and the square root is taken with an FP32
 // Newton step on the exact residual, so a block costs three FP64
 // instructions.
-#include "common.cuh"
+#include "plan.cuh"
 
 namespace spamm {
 namespace {
@@ -28,14 +28,14 @@ __device__ __forceinline__ void merge_from(SumSq& a, float h, float l, int e) {
   }
 }
 
+// One CTA: block row I, column window wx of X (kThreads * VEC columns).
 template <int VEC, int LEAF>
-__global__ void __launch_bounds__(kThreads)
-    normmap_kernel(const float* __restrict__ X, int64_t n, int bd, double* __restrict__ out) {
+__device__ __forceinline__ void norm_strip(const float* __restrict__ X, int64_t n, int bd,
+                                           double* __restrict__ out, int I, int64_t wx) {
   constexpr int kCols = kThreads * VEC;               // columns per CTA window
   constexpr int kThreadsPerBlockCol = LEAF / VEC;     // threads sharing one output
   constexpr int kRowsPerGroup = 32 / VEC;             // rows per 32-entry group
-  const int I = blockIdx.y;
-  const int64_t col0 = (int64_t)blockIdx.x * kCols + (int64_t)threadIdx.x * VEC;
+  const int64_t col0 = wx * kCols + (int64_t)threadIdx.x * VEC;
   const int64_t row0 = (int64_t)I * LEAF;
   const int64_t row1 = (n < row0 + LEAF) ? n : row0 + LEAF;
   const bool active = col0 < n;
@@ -98,6 +98,32 @@ __global__ void __launch_bounds__(kThreads)
 }
 
 template <int VEC, int LEAF>
+__global__ void __launch_bounds__(kThreads)
+    normmap_kernel(const float* __restrict__ X, int64_t n, int bd, double* __restrict__ out) {
+  norm_strip<VEC, LEAF>(X, n, bd, out, blockIdx.y, blockIdx.x);
+}
+
+// Batched form: one CTA per (job, block row, window); a job is one operand of
+// one instance, aligned (float4) or not.
+template <int LEAF>
+__global__ void __launch_bounds__(kThreads)
+    normmap_batched_kernel(const NormJob* __restrict__ jobs, int njobs) {
+  int lo = 0, hi = njobs - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) / 2;
+    if (jobs[mid].cta0 <= (int)blockIdx.x) lo = mid;
+    else hi = mid - 1;
+  }
+  const NormJob jb = jobs[lo];
+  const int64_t local = (int64_t)blockIdx.x - jb.cta0;
+  const int64_t windows = (jb.n + kThreads * (jb.vec ? 4 : 1) - 1) / (kThreads * (jb.vec ? 4 : 1));
+  const int I = (int)(local / windows);
+  const int64_t wx = local % windows;
+  if (jb.vec) norm_strip<4, LEAF>(jb.X, jb.n, jb.bd, jb.out, I, wx);
+  else norm_strip<1, LEAF>(jb.X, jb.n, jb.bd, jb.out, I, wx);
+}
+
+template <int VEC, int LEAF>
 cudaError_t launch(const float* X, int64_t n, int bd, double* out, cudaStream_t s) {
   constexpr int kCols = kThreads * VEC;
   dim3 grid((unsigned)((n + kCols - 1) / kCols), (unsigned)bd);
@@ -117,6 +143,23 @@ cudaError_t launch_normmap(const float* X, int64_t n, int32_t leaf, double* out,
     case 128: return vec ? launch<4, 128>(X, n, bd, out, s) : launch<1, 128>(X, n, bd, out, s);
     default: return cudaErrorInvalidValue;
   }
+}
+
+int normjob_ctas(const NormJob& j) {
+  const int64_t cols = kThreads * (j.vec ? 4 : 1);
+  return (int)(((j.n + cols - 1) / cols) * j.bd);
+}
+
+cudaError_t launch_normmap_jobs(const NormJob* dev_jobs, int njobs, int total_ctas, int leaf,
+                                cudaStream_t s) {
+  if (total_ctas <= 0) return cudaSuccess;
+  switch (leaf) {
+    case 32: normmap_batched_kernel<32><<<total_ctas, kThreads, 0, s>>>(dev_jobs, njobs); break;
+    case 64: normmap_batched_kernel<64><<<total_ctas, kThreads, 0, s>>>(dev_jobs, njobs); break;
+    case 128: normmap_batched_kernel<128><<<total_ctas, kThreads, 0, s>>>(dev_jobs, njobs); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaPeekAtLastError();
 }
 
 }  // namespace spamm

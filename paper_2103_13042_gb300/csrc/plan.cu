@@ -1,39 +1,32 @@
 // Pair test and work-queue build (Algorithm 1 skip rule, Algorithm 2 bitmap and
-// map_offset, Section 3.5.1 valid multiplications), for all output tiles at once.
+// map_offset, Section 3.5.1 valid multiplications), for all output tiles of
+// all instances of a table at once.
 //
-// Stream order (after one memset that clears the plan's accumulators):
+// Stream order (after one memset that clears the accumulators):
 //   prep      FP64 norm maps -> FP32 mantissa/exponent "screen" forms (B transposed
-//             so a tile's k-run is contiguous) and per-CTA sums of squared norms.
-//   count     CTAs own 32 consecutive tiles, one warp per tile at a time: lanes
-//             test k = lane, lane+32, ...; ballot + popc count the survivors;
-//             skipped products are summed for the bounds; split modes bin the
-//             surviving products by binade; per-CTA totals and a histogram of
-//             the per-tile counts.
-//   finalize  one CTA over the per-CTA totals: their exclusive scans (the CSR
-//             base of each CTA's tiles), statistics, the split-flag binade and
-//             the bucket starts of the longest-first order.
-//   fill      same tile partition: CSR offsets from the CTA base plus a warp
+//             so a tile's k-run is contiguous) and per-CTA sums of squared norms;
+//             the last CTA of each instance forms ||A||_F, ||B||_F.
+//   count     each CTA owns 32 consecutive tiles of one instance, one warp per
+//             tile at a time: lanes test k = lane, lane+32, ...; ballot + popc
+//             count the survivors; skipped products are summed for the bounds;
+//             split modes bin the surviving products by binade; per-CTA totals
+//             and a batch-wide histogram of the per-tile counts.
+//   finalize  one CTA per instance over its CTAs' totals: their exclusive scan
+//             (the first k_idx slot of each CTA's tiles), statistics and the
+//             split-flag binade; the last of these CTAs turns the histogram into
+//             the bucket starts of the batch-wide longest-first order.
+//   fill      same tile partition: first slots from the CTA base plus a warp
 //             scan; the same test again, ballot ranks place the surviving k
-//             (increasing) at tile_ptr[t] + rank; tiles take their
-//             longest-first slot from a per-count cursor, empty tiles go last
-//             in index order.
+//             (increasing) at tile_beg[t] + rank; non-empty tiles take their
+//             longest-first slot from a per-count cursor.
 #include <cstddef>
+#include <cstring>
+#include <vector>
 
 #include "common.cuh"
 #include "plan.cuh"
 
 namespace spamm {
-namespace {
-
-constexpr int kWarpsPerCta = 8;
-
-struct TauScreen {
-  double tau;
-  float m_lo, m_hi;
-  int32_t e;
-  int all;   // tau == 0: every triple survives
-  int none;  // tau == +Inf: only non-finite products survive
-};
 
 TauScreen make_tau_screen(double tau) {
   TauScreen t{};
@@ -50,6 +43,14 @@ TauScreen make_tau_screen(double tau) {
   }
   return t;
 }
+
+namespace {
+
+constexpr int kWarpsPerCta = 8;
+constexpr int kTilesPerCta = 32;   // count and fill: 8 warps x 4 tiles
+constexpr int kTileRounds = kTilesPerCta / kWarpsPerCta;
+constexpr int kPrepThreads = 256;
+constexpr int kFinThreads = 1024;
 
 // Exactly !(na * nb < tau) in FP64, decided in FP32 whenever that is safe.
 __device__ __forceinline__ bool survives(Screen a, Screen b, const double* nA_ptr,
@@ -144,18 +145,29 @@ __device__ __forceinline__ int rel_bin_screened(Screen a, Screen b, float inv_m,
   return b0 < kFlagBinMin ? kFlagBinMin : (b0 > 1 ? 1 : b0);
 }
 
-__global__ void prep_kernel(const double* __restrict__ nA, const double* __restrict__ nB, int bd,
-                            Screen* __restrict__ sA, Screen* __restrict__ sBT,
-                            double* __restrict__ part_a, double* __restrict__ part_b,
-                            PlanDevice* __restrict__ pd) {
+
+__device__ __forceinline__ int inst_of_prep_cta(const InstRef& r, int cta) {
+  return find_inst(r, cta, [](const Inst& x) { return (int64_t)x.prep0; });
+}
+__device__ __forceinline__ int inst_of_count_cta(const InstRef& r, int cta) {
+  return find_inst(r, cta, [](const Inst& x) { return (int64_t)x.count0; });
+}
+
+__global__ void __launch_bounds__(kPrepThreads)
+    prep_kernel(InstRef R, PlanBuffers Bf) {
+  const int ii = inst_of_prep_cta(R, blockIdx.x);
+  const Inst& in = R.at(ii);
+  const int bd = in.bd;
   const int64_t total = (int64_t)bd * bd;
-  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int lc = blockIdx.x - in.prep0;
+  const int nctas = (int)((total + kPrepThreads - 1) / kPrepThreads);
+  const int64_t idx = (int64_t)lc * kPrepThreads + threadIdx.x;
   double qa = 0.0, qb = 0.0;
   if (idx < total) {
-    const double a = nA[idx], b = nB[idx];
-    sA[idx] = make_screen(a);
+    const double a = in.nA[idx], b = in.nB[idx];
+    Bf.sA[in.tile0 + idx] = make_screen(a);
     const int64_t k = idx / bd, j = idx % bd;
-    sBT[j * bd + k] = make_screen(b);
+    Bf.sBT[in.tile0 + j * bd + k] = make_screen(b);
     qa = a * a;
     qb = b * b;
   }
@@ -163,7 +175,7 @@ __global__ void prep_kernel(const double* __restrict__ nA, const double* __restr
     qa += __shfl_xor_sync(0xffffffffu, qa, off);
     qb += __shfl_xor_sync(0xffffffffu, qb, off);
   }
-  __shared__ double wa[8], wb[8];
+  __shared__ double wa[kPrepThreads / 32], wb[kPrepThreads / 32];
   if ((threadIdx.x & 31) == 0) {
     wa[threadIdx.x / 32] = qa;
     wb[threadIdx.x / 32] = qb;
@@ -171,26 +183,26 @@ __global__ void prep_kernel(const double* __restrict__ nA, const double* __restr
   __syncthreads();
   if (threadIdx.x == 0) {
     double sa = 0.0, sb = 0.0;
-    for (int w = 0; w < (int)(blockDim.x / 32); ++w) {
+    for (int w = 0; w < kPrepThreads / 32; ++w) {
       sa += wa[w];
       sb += wb[w];
     }
-    part_a[blockIdx.x] = sa;
-    part_b[blockIdx.x] = sb;
+    Bf.part_a[blockIdx.x] = sa;
+    Bf.part_b[blockIdx.x] = sb;
   }
-  // the last CTA to finish sums the partials in a fixed order (deterministic)
+  // the last CTA of the instance sums its partials in a fixed order (deterministic)
   __shared__ bool s_last;
   __threadfence();
   __syncthreads();
-  if (threadIdx.x == 0) s_last = atomicAdd(&pd->ticket, 1u) == gridDim.x - 1;
+  if (threadIdx.x == 0) s_last = atomicAdd(&in.pd->ticket, 1u) == (unsigned)nctas - 1u;
   __syncthreads();
   if (s_last && threadIdx.x < 32) {
     __threadfence();
     const int lane = threadIdx.x;
     double a = 0.0, b = 0.0;
-    for (int i = lane; i < (int)gridDim.x; i += 32) {
-      a += __ldcg(part_a + i);
-      b += __ldcg(part_b + i);
+    for (int i = lane; i < nctas; i += 32) {
+      a += __ldcg(Bf.part_a + in.prep0 + i);
+      b += __ldcg(Bf.part_b + in.prep0 + i);
     }
     for (int off = 16; off > 0; off >>= 1) {
       a += __shfl_xor_sync(0xffffffffu, a, off);
@@ -198,36 +210,28 @@ __global__ void prep_kernel(const double* __restrict__ nA, const double* __restr
     }
     if (lane == 0) {
       const double na = sqrt(a), nb = sqrt(b), ab = na * nb;
-      pd->norm_a = na;
-      pd->norm_b = nb;
-      pd->inv_ab = ab > 0.0 ? 1.0 / ab : 0.0;
+      in.pd->norm_a = na;
+      in.pd->norm_b = nb;
+      in.pd->inv_ab = ab > 0.0 ? 1.0 / ab : 0.0;
     }
   }
 }
 
-
-constexpr int kTilesPerCta = 32;   // count and fill: 8 warps x 4 tiles
-constexpr int kTileRounds = kTilesPerCta / kWarpsPerCta;
-
-struct CountParts {
-  long long* S;
-  int* kmax;
-  int* nonempty;
-  ExtSum* b1;
-  ExtSum* b2sq;
-};
-
 __global__ void __launch_bounds__(kWarpsPerCta * 32)
-    count_kernel(const Screen* __restrict__ sA, const Screen* __restrict__ sBT,
-                 const double* __restrict__ nA, const double* __restrict__ nB, int bd,
-                 TauScreen T, int split, PlanDevice* __restrict__ pd, int* __restrict__ cnt,
-                 CountParts parts, uint8_t* __restrict__ needA, uint8_t* __restrict__ needB) {
+    count_kernel(InstRef R, PlanBuffers Bf) {
   __shared__ double s_bin_sum[kFlagBins];
   __shared__ int s_bin_cnt[kFlagBins];
   __shared__ long long s_S[kWarpsPerCta];
   __shared__ int s_kmax[kWarpsPerCta], s_ne[kWarpsPerCta];
   __shared__ ExtSum s_b1[kWarpsPerCta], s_b2[kWarpsPerCta];
   const int warp = threadIdx.x / 32, lane = threadIdx.x & 31;
+  const int ii = inst_of_count_cta(R, blockIdx.x);
+  const Inst& in = R.at(ii);
+  const int bd = in.bd, split = in.split;
+  const TauScreen T = in.T;
+  const double* nA = in.nA;
+  const double* nB = in.nB;
+  PlanDevice* pd = in.pd;
   if (split) {
     for (int i = threadIdx.x; i < kFlagBins; i += blockDim.x) {
       s_bin_sum[i] = 0.0;
@@ -239,15 +243,16 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32)
   int inv_e;
   const float inv_m = (float)frexp(inv, &inv_e);
   const int64_t tiles = (int64_t)bd * bd;
+  const int64_t lt0 = (int64_t)(blockIdx.x - in.count0) * kTilesPerCta;
   long long wS = 0;
   int wkmax = 0, wne = 0;
   ExtSum wb1{0.0f, 0}, wb2{0.0f, 0};
   for (int r = 0; r < kTileRounds; ++r) {
-    const int64_t t = (int64_t)blockIdx.x * kTilesPerCta + warp + (int64_t)r * kWarpsPerCta;
+    const int64_t t = lt0 + warp + (int64_t)r * kWarpsPerCta;
     if (t >= tiles) break;
     const int i = (int)(t / bd), j = (int)(t % bd);
-    const Screen* ra = sA + (int64_t)i * bd;
-    const Screen* rb = sBT + (int64_t)j * bd;
+    const Screen* ra = Bf.sA + in.tile0 + (int64_t)i * bd;
+    const Screen* rb = Bf.sBT + in.tile0 + (int64_t)j * bd;
     ExtSum sk{0.0f, 0};
     int count = 0;
     int run_bin = kFlagBinMin - 1, run_cnt = 0;
@@ -286,10 +291,11 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32)
     }
     const ExtSum tot = ext_warp_sum(sk);   // no FP64: the FP64 pipe is narrow here
     if (lane == 0) {
-      cnt[t] = count;
-      needA[t] = 0;   // the fill kernel sets the blocks survivors use
-      needB[t] = 0;
-      if (count > 0) atomicAdd(&pd->hist[count], 1);
+      const int64_t g = in.tile0 + t;
+      Bf.cnt[g] = count;
+      Bf.needA[g] = 0;   // the fill kernel sets the blocks survivors use
+      Bf.needB[g] = 0;
+      if (count > 0) atomicAdd(&Bf.bdev->hist[count], 1);
       ext_add(wb1, tot.m, tot.e);
       ext_add(wb2, __fmul_rn(tot.m, tot.m), 2 * tot.e);
     }
@@ -316,11 +322,11 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32)
       ext_add(b1, s_b1[w].m, s_b1[w].e);
       ext_add(b2, s_b2[w].m, s_b2[w].e);
     }
-    parts.S[blockIdx.x] = S;
-    parts.kmax[blockIdx.x] = km;
-    parts.nonempty[blockIdx.x] = ne;
-    parts.b1[blockIdx.x] = b1;
-    parts.b2sq[blockIdx.x] = b2;
+    Bf.part_S[blockIdx.x] = S;
+    Bf.part_kmax[blockIdx.x] = km;
+    Bf.part_ne[blockIdx.x] = ne;
+    Bf.part_b1[blockIdx.x] = b1;
+    Bf.part_b2[blockIdx.x] = b2;
   }
   if (split) {
     for (int i = threadIdx.x; i < kFlagBins; i += blockDim.x) {
@@ -331,8 +337,6 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32)
     }
   }
 }
-
-constexpr int kFinThreads = 1024;
 
 // Block-wide exclusive scan of one value per thread (Hillis-Steele in smem).
 template <typename V>
@@ -353,43 +357,39 @@ __device__ V block_exclusive_scan(V x, V* sh, V& total) {
 }
 
 __global__ void __launch_bounds__(kFinThreads)
-    finalize_kernel(int bd, CountParts parts, int nparts, int split, double c1,
-                    double target_rel, PlanDevice* __restrict__ pd, int* __restrict__ cta_base,
-                    int* __restrict__ cta_ebase) {
+    finalize_kernel(InstRef R, PlanBuffers Bf) {
   __shared__ long long s_ll[kFinThreads];
   __shared__ ExtSum s_x[kFinThreads];
   __shared__ int s_i[kFinThreads];
   const int tid = threadIdx.x;
+  const Inst& in = R.at(blockIdx.x);
+  const int bd = in.bd;
   const int64_t tiles = (int64_t)bd * bd;
+  const int nparts = (int)(((int64_t)bd * bd + kTilesPerCta - 1) / kTilesPerCta);
+  PlanDevice* pd = in.pd;
 
-
-  // per-CTA survivor and empty-tile bases: each thread scans a contiguous chunk
+  // per-CTA first k_idx slots: each thread scans a contiguous chunk
   const int chunk = (nparts + kFinThreads - 1) / kFinThreads;
   const int p0 = min(nparts, chunk * tid), p1 = min(nparts, p0 + chunk);
   long long locS = 0;
-  int locE = 0, locK = 0;
+  int locK = 0, locNE = 0;
   ExtSum locB1{0.0f, 0}, locB2{0.0f, 0};
   for (int q = p0; q < p1; ++q) {
-    locS += parts.S[q];
-    const int64_t rest = tiles - (int64_t)q * kTilesPerCta;
-    const int ntile = (int)(rest < kTilesPerCta ? rest : kTilesPerCta);
-    locE += ntile - parts.nonempty[q];
-    locK = max(locK, parts.kmax[q]);
-    ext_add(locB1, parts.b1[q].m, parts.b1[q].e);
-    ext_add(locB2, parts.b2sq[q].m, parts.b2sq[q].e);
+    const int cq = in.count0 + q;
+    locS += Bf.part_S[cq];
+    locNE += Bf.part_ne[cq];
+    locK = max(locK, Bf.part_kmax[cq]);
+    ext_add(locB1, Bf.part_b1[cq].m, Bf.part_b1[cq].e);
+    ext_add(locB2, Bf.part_b2[cq].m, Bf.part_b2[cq].e);
   }
   long long totS;
-  long long baseS = block_exclusive_scan<long long>(locS, s_ll, totS);
-  long long totE;
-  long long baseE = block_exclusive_scan<long long>((long long)locE, s_ll, totE);
+  long long baseS = block_exclusive_scan<long long>(locS, s_ll, totS) + in.kidx0;
   for (int q = p0; q < p1; ++q) {
-    cta_base[q] = (int)baseS;
-    baseS += parts.S[q];
-    const int64_t rest = tiles - (int64_t)q * kTilesPerCta;
-    const int ntile = (int)(rest < kTilesPerCta ? rest : kTilesPerCta);
-    cta_ebase[q] = (int)baseE;
-    baseE += ntile - parts.nonempty[q];
+    Bf.cta_base[in.count0 + q] = (int)baseS;
+    baseS += Bf.part_S[in.count0 + q];
   }
+  long long totNE;
+  (void)block_exclusive_scan<long long>((long long)locNE, s_ll, totNE);
   // max and the extended-range sums (FP32 only)
   s_i[tid] = locK;
   s_x[tid] = locB1;
@@ -413,13 +413,6 @@ __global__ void __launch_bounds__(kFinThreads)
   const ExtSum b2x = s_x[0];
   __syncthreads();
 
-  // longest-first bucket starts: counts bd .. 1 in decreasing order
-  const int c = bd - tid;          // thread tid owns count c (valid for c >= 1)
-  const long long h = (c >= 1) ? pd->hist[c] : 0;
-  long long tot_ne;
-  const long long start = block_exclusive_scan<long long>(h, s_ll, tot_ne);
-  if (c >= 1) pd->cursor[c] = (int)start;
-
   // split flag binade (one warp): m = the largest mm in [kFlagBinMin - 1, 1]
   // with c1 * sum_{bins < mm} p <= budget; bins are prefix-summed in a fixed
   // order (7 consecutive bins per lane, then a warp scan of the lane totals).
@@ -431,8 +424,8 @@ __global__ void __launch_bounds__(kFinThreads)
     const int lane = tid;
     int m = kFlagBinMin - 1;
     long long flagged = 0;
-    if (split) {
-      const double budget = 0.5 * (target_rel * ab - bound2);
+    if (in.split) {
+      const double budget = 0.5 * (in.target_rel * ab - bound2);
       double v[PER];
       double run = 0.0;
 #pragma unroll
@@ -449,11 +442,10 @@ __global__ void __launch_bounds__(kFinThreads)
       double below = incl - run;     // sum of the bins before this lane's first
       int best = kFlagBinMin - 1;
       if (budget >= 0.0) {
-        // mm = kFlagBinMin + b has below(mm) = sum of bins < b (index form)
 #pragma unroll
         for (int q = 0; q < PER; ++q) {
           const int b = lane * PER + q;       // candidate mm = kFlagBinMin + b
-          if (b < kFlagBins && c1 * below <= budget) best = kFlagBinMin + b;
+          if (b < kFlagBins && in.c1 * below <= budget) best = kFlagBinMin + b;
           below += v[q];
         }
       }
@@ -468,7 +460,7 @@ __global__ void __launch_bounds__(kFinThreads)
     if (lane == 0) {
       pd->survivors = totS;
       pd->max_tile = kmax;
-      pd->nonempty = (int)(tiles - totE);
+      pd->nonempty = (int)totNE;
       pd->bound1 = b1 * ab;
       pd->bound2 = bound2;
       pd->valid_ratio = (double)totS / ((double)bd * (double)bd * (double)bd);
@@ -476,53 +468,65 @@ __global__ void __launch_bounds__(kFinThreads)
       pd->flagged = flagged;
     }
   }
+
+  // the last finalize CTA: bucket starts of the batch-wide longest-first order
+  __shared__ bool s_last;
+  __threadfence();
+  __syncthreads();
+  if (tid == 0) s_last = atomicAdd(&Bf.bdev->ticket, 1u) == gridDim.x - 1u;
+  __syncthreads();
+  if (s_last) {
+    __threadfence();
+    const int c = kMaxBd - tid;      // thread tid owns count c (counts 1 .. kMaxBd)
+    const long long h = (c >= 1) ? __ldcg(&Bf.bdev->hist[c]) : 0;
+    long long tot_ne;
+    const long long start = block_exclusive_scan<long long>(h, s_ll, tot_ne);
+    if (c >= 1) Bf.bdev->cursor[c] = (int)start;
+    if (tid == 0) Bf.bdev->nonempty = (int)tot_ne;
+  }
 }
 
 __global__ void __launch_bounds__(kWarpsPerCta * 32)
-    fill_kernel(const Screen* __restrict__ sA, const Screen* __restrict__ sBT,
-                const double* __restrict__ nA, const double* __restrict__ nB, int bd, TauScreen T,
-                int split, PlanDevice* __restrict__ pd, const int* __restrict__ cnt,
-                const int* __restrict__ cta_base, const int* __restrict__ cta_ebase,
-                int* __restrict__ tile_ptr, int* __restrict__ order, uint16_t* __restrict__ k_idx,
-                uint8_t* __restrict__ needA, uint8_t* __restrict__ needB) {
-  __shared__ int s_ptr[kTilesPerCta];
+    fill_kernel(InstRef R, PlanBuffers Bf) {
+  __shared__ int s_beg[kTilesPerCta];
   const int warp = threadIdx.x / 32, lane = threadIdx.x & 31;
+  const int ii = inst_of_count_cta(R, blockIdx.x);
+  const Inst& in = R.at(ii);
+  const int bd = in.bd, split = in.split;
+  const TauScreen T = in.T;
+  const double* nA = in.nA;
+  const double* nB = in.nB;
   const int64_t tiles = (int64_t)bd * bd;
-  const int64_t t0 = (int64_t)blockIdx.x * kTilesPerCta;
-  if (warp == 0) {   // CSR offsets and the empty tiles' slots (kTilesPerCta == 32 lanes)
-    const int64_t t = t0 + lane;
-    const int c = t < tiles ? cnt[t] : 0;
+  const int64_t lt0 = (int64_t)(blockIdx.x - in.count0) * kTilesPerCta;
+  if (warp == 0) {   // first k_idx slot of each of the CTA's tiles (kTilesPerCta == 32 lanes)
+    const int64_t t = lt0 + lane;
+    const int c = t < tiles ? Bf.cnt[in.tile0 + t] : 0;
     int incl = c;
     for (int off = 1; off < 32; off <<= 1) {
       const int y = __shfl_up_sync(0xffffffffu, incl, off);
       if (lane >= off) incl += y;
     }
-    const int ptr = cta_base[blockIdx.x] + incl - c;
-    s_ptr[lane] = ptr;
-    const unsigned empty = __ballot_sync(0xffffffffu, t < tiles && c == 0);
-    if (t < tiles) {
-      tile_ptr[t] = ptr;
-      if (t == tiles - 1) tile_ptr[tiles] = ptr + c;
-      if (c == 0)
-        order[pd->nonempty + cta_ebase[blockIdx.x] + __popc(empty & ((1u << lane) - 1u))] = (int)t;
-    }
+    const int beg = Bf.cta_base[blockIdx.x] + incl - c;
+    s_beg[lane] = beg;
+    if (t < tiles) Bf.tile_beg[in.tile0 + t] = beg;
   }
   __syncthreads();
-  const double inv = pd->inv_ab;
+  const double inv = in.pd->inv_ab;
   int inv_e;
   const float inv_m = (float)frexp(inv, &inv_e);
-  const int m = pd->flag_exp;
+  const int m = in.pd->flag_exp;
   for (int r = 0; r < kTileRounds; ++r) {
     const int lt = warp + r * kWarpsPerCta;
-    const int64_t t = t0 + lt;
+    const int64_t t = lt0 + lt;
     if (t >= tiles) break;
-    const int c = cnt[t];
+    const int64_t g = in.tile0 + t;
+    const int c = Bf.cnt[g];
     if (c == 0) continue;
-    if (lane == 0) order[atomicAdd(&pd->cursor[c], 1)] = (int)t;
+    if (lane == 0) Bf.order[atomicAdd(&Bf.bdev->cursor[c], 1)] = (int)g;
     const int i = (int)(t / bd), j = (int)(t % bd);
-    const Screen* ra = sA + (int64_t)i * bd;
-    const Screen* rb = sBT + (int64_t)j * bd;
-    int base = s_ptr[lt];
+    const Screen* ra = Bf.sA + in.tile0 + (int64_t)i * bd;
+    const Screen* rb = Bf.sBT + in.tile0 + (int64_t)j * bd;
+    int base = s_beg[lt];
     for (int k0 = 0; k0 < bd; k0 += 32) {
       const int k = k0 + lane;
       bool s = false;
@@ -538,9 +542,9 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32)
         if (split && rel_bin_screened(a, b, inv_m, inv_e, nA + (int64_t)i * bd + k,
                                       nB + (int64_t)k * bd + j, inv) >= m)
           v |= kSplitFlag;
-        k_idx[base + __popc(ball & ((1u << lane) - 1u))] = v;
-        needA[(int64_t)i * bd + k] = 1;   // benign: every writer stores 1
-        needB[(int64_t)k * bd + j] = 1;
+        Bf.k_idx[base + __popc(ball & ((1u << lane) - 1u))] = v;
+        Bf.needA[in.tile0 + (int64_t)i * bd + k] = 1;   // benign: every writer stores 1
+        Bf.needB[in.tile0 + (int64_t)k * bd + j] = 1;
       }
       base += __popc(ball);
     }
@@ -549,34 +553,77 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32)
 
 }  // namespace
 
-cudaError_t run_plan(PlanBuffers& b, const double* nA, const double* nB, double tau,
-                     double target_rel, int split, double c1, cudaStream_t s) {
-  const int bd = b.bd;
-  const int64_t tiles = (int64_t)bd * bd;
-  // clear the accumulators (count histogram, split bins)
-  const size_t acc_off = offsetof(PlanDevice, hist);
-  cudaError_t e = cudaMemsetAsync(reinterpret_cast<char*>(b.pd) + acc_off, 0,
-                                  sizeof(PlanDevice) - acc_off, s);
-  if (e != cudaSuccess) return e;
-  const int prep_ctas = (int)((tiles + 255) / 256);
-  prep_kernel<<<prep_ctas, 256, 0, s>>>(nA, nB, bd, b.sA, b.sBT, b.part_a, b.part_b, b.pd);
-  const TauScreen T = make_tau_screen(tau);
-  const int count_ctas = (int)((tiles + kTilesPerCta - 1) / kTilesPerCta);
-  CountParts parts{b.part_S, b.part_kmax, b.part_ne, b.part_b1, b.part_b2};
-  count_kernel<<<count_ctas, kWarpsPerCta * 32, 0, s>>>(b.sA, b.sBT, nA, nB, bd, T, split, b.pd,
-                                                        b.cnt, parts, b.needA, b.needB);
-  finalize_kernel<<<1, kFinThreads, 0, s>>>(bd, parts, count_ctas, split, c1, target_rel, b.pd,
-                                            b.cta_base, b.cta_ebase);
-  fill_kernel<<<count_ctas, kWarpsPerCta * 32, 0, s>>>(b.sA, b.sBT, nA, nB, bd, T, split, b.pd,
-                                                       b.cnt, b.cta_base, b.cta_ebase,
-                                                       b.tile_ptr, b.order, b.k_idx, b.needA,
-                                                       b.needB);
-  return cudaPeekAtLastError();
+int prep_ctas_of(int bd) { return (int)(((int64_t)bd * bd + kPrepThreads - 1) / kPrepThreads); }
+int count_ctas_of(int bd) { return (int)(((int64_t)bd * bd + kTilesPerCta - 1) / kTilesPerCta); }
+
+size_t plan_layout(Inst* insts, int count, PlanBuffers* b, char* base) {
+  int64_t tiles = 0, kslots = 0;
+  int prep = 0, cnt = 0;
+  for (int i = 0; i < count; ++i) {
+    const int64_t bd = insts[i].bd;
+    insts[i].tile0 = tiles;
+    insts[i].kidx0 = kslots;
+    insts[i].prep0 = prep;
+    insts[i].count0 = cnt;
+    tiles += bd * bd;
+    kslots += bd * bd * bd;
+    prep += prep_ctas_of((int)bd);
+    cnt += count_ctas_of((int)bd);
+  }
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    off = (off + 255) / 256 * 256;
+    char* p = base ? base + off : nullptr;
+    off += bytes;
+    return p;
+  };
+  PlanBuffers t{};
+  t.tiles = tiles;
+  t.kslots = kslots;
+  t.prep_ctas = prep;
+  t.count_ctas = cnt;
+  t.pd = reinterpret_cast<PlanDevice*>(take((size_t)count * sizeof(PlanDevice)));
+  t.bdev = reinterpret_cast<BatchDevice*>(take(sizeof(BatchDevice)));
+  t.sA = reinterpret_cast<Screen*>(take((size_t)tiles * sizeof(Screen)));
+  t.sBT = reinterpret_cast<Screen*>(take((size_t)tiles * sizeof(Screen)));
+  t.part_a = reinterpret_cast<double*>(take((size_t)prep * sizeof(double)));
+  t.part_b = reinterpret_cast<double*>(take((size_t)prep * sizeof(double)));
+  t.part_S = reinterpret_cast<long long*>(take((size_t)cnt * sizeof(long long)));
+  t.part_kmax = reinterpret_cast<int*>(take((size_t)cnt * sizeof(int)));
+  t.part_ne = reinterpret_cast<int*>(take((size_t)cnt * sizeof(int)));
+  t.part_b1 = reinterpret_cast<ExtSum*>(take((size_t)cnt * sizeof(ExtSum)));
+  t.part_b2 = reinterpret_cast<ExtSum*>(take((size_t)cnt * sizeof(ExtSum)));
+  t.cta_base = reinterpret_cast<int*>(take((size_t)cnt * sizeof(int)));
+  t.cnt = reinterpret_cast<int*>(take((size_t)tiles * sizeof(int)));
+  t.tile_beg = reinterpret_cast<int*>(take((size_t)tiles * sizeof(int)));
+  t.order = reinterpret_cast<int*>(take((size_t)tiles * sizeof(int)));
+  t.k_idx = reinterpret_cast<uint16_t*>(take((size_t)kslots * sizeof(uint16_t)));
+  t.needA = reinterpret_cast<uint8_t*>(take((size_t)tiles));
+  t.needB = reinterpret_cast<uint8_t*>(take((size_t)tiles));
+  for (int i = 0; i < count; ++i) insts[i].pd = t.pd ? t.pd + i : nullptr;
+  if (b) *b = t;
+  return (off + 255) / 256 * 256;
 }
 
-int64_t plan_part_count(int bd) {
-  const int64_t tiles = (int64_t)bd * bd;
-  return std::max<int64_t>((tiles + 255) / 256, (tiles + kTilesPerCta - 1) / kTilesPerCta);
+InstRef make_ref(const Inst* host_insts, const Inst* dev_table, int count) {
+  InstRef r{};
+  r.count = count;
+  r.table = dev_table;
+  if (!dev_table) r.one = host_insts[0];
+  return r;
+}
+
+cudaError_t run_plan(const InstRef& ref, const PlanBuffers& b, cudaStream_t s) {
+  // clear the per-instance statistics and the batch-wide order state (laid
+  // out back to back, one memset)
+  const size_t clear = reinterpret_cast<const char*>(b.bdev + 1) - reinterpret_cast<const char*>(b.pd);
+  cudaError_t e = cudaMemsetAsync(b.pd, 0, clear, s);
+  if (e != cudaSuccess) return e;
+  prep_kernel<<<b.prep_ctas, kPrepThreads, 0, s>>>(ref, b);
+  count_kernel<<<b.count_ctas, kWarpsPerCta * 32, 0, s>>>(ref, b);
+  finalize_kernel<<<ref.count, kFinThreads, 0, s>>>(ref, b);
+  fill_kernel<<<b.count_ctas, kWarpsPerCta * 32, 0, s>>>(ref, b);
+  return cudaPeekAtLastError();
 }
 
 }  // namespace spamm

@@ -1,23 +1,46 @@
 // Device-side plan state shared by the plan and multiply kernels.
+//
+// Every kernel works on a table of SpAMM instances (one entry for a single
+// product, many for a batch).  Instance i owns bd_i^2 tiles, numbered
+// globally from tile0_i = sum of bd^2 of the instances before it; leaf blocks
+// of A and B use the same numbering (block (I, K) of instance i is
+// tile0_i + I * bd_i + K).  Its surviving k indices live in k_idx slots from
+// kidx0_i = sum of bd^3 of the instances before it.  All instances of a
+// table share one leaf size.
 #pragma once
 
 #include "common.cuh"
 
 namespace spamm {
 
-// Scalars the plan kernels produce (one per plan, in device memory).  The
-// members from `hist` on are accumulators cleared at the start of every plan.
+// The threshold in the form the pair test uses (built on the host).
+struct TauScreen {
+  double tau;
+  float m_lo, m_hi;
+  int32_t e;
+  int all;   // tau == 0: every triple survives
+  int none;  // tau == +Inf: only non-finite products survive
+};
+
+TauScreen make_tau_screen(double tau);
+
+// Per-instance statistics; `ticket` and the bins are cleared before each plan.
 struct PlanDevice {
   double norm_a, norm_b, inv_ab;
   double bound1, bound2, valid_ratio;
   long long survivors, flagged;
-  int max_tile, nonempty, flag_exp, pad_;
-  int cursor[kMaxBd + 2];                   // next longest-first slot per survivor count
-  int hist[kMaxBd + 2];                     // number of tiles per survivor count (>= 1)
-  unsigned int ticket;                      // prep CTAs that have finished
-  unsigned int pad2_;
+  int max_tile, nonempty, flag_exp;
+  unsigned int ticket;                      // prep CTAs of this instance that have finished
   double bin_sum[kFlagBins];                // surviving products per relative binade
   unsigned long long bin_cnt[kFlagBins];
+};
+
+// Batch-wide state of the longest-first order (cleared before each plan).
+struct BatchDevice {
+  int hist[kMaxBd + 2];     // non-empty tiles per survivor count, over all instances
+  int cursor[kMaxBd + 2];   // next slot of each count's bucket in `order`
+  int nonempty;             // non-empty tiles over all instances
+  unsigned int ticket;      // finalize CTAs that have finished
 };
 
 // Extended-range FP32 sum: value = m * 2^e with an integer exponent.
@@ -26,41 +49,110 @@ struct ExtSum {
   int e;
 };
 
-// Device buffers of one plan (carved from one workspace allocation).
-struct PlanBuffers {
+// One SpAMM instance.
+struct Inst {
+  const float* A;
+  const float* B;
+  float* C;
+  const double* nA;     // norm maps [bd * bd]
+  const double* nB;
+  int64_t n;
   int bd;
-  Screen* sA;          // [bd*bd] screen form of normA, row-major
-  Screen* sBT;         // [bd*bd] screen form of normB, transposed (j-major)
-  double* part_a;      // per-CTA partial sums (prep)
-  double* part_b;
-  long long* part_S;   // per-CTA partials (count)
-  int* part_kmax;
-  int* part_ne;
-  ExtSum* part_b1;     // per-CTA sums of skipped relative products
-  ExtSum* part_b2;     // per-CTA sums of their squares per tile
-  int* cta_base;       // per count-CTA: first k_idx slot of its tiles
-  int* cta_ebase;      // per count-CTA: empty tiles before its tiles
-  int* cnt;            // [bd*bd] survivors per tile
-  int* tile_ptr;       // [bd*bd + 1] CSR offsets
-  int* order;          // [bd*bd] tiles, most survivors first, empty tiles last
-  uint16_t* k_idx;     // [bd^3] surviving k per tile (bit 15: split triple)
-  uint8_t* needA;      // [bd*bd] 1 if block A[i,k] takes part in some surviving triple
-  uint8_t* needB;      // [bd*bd] 1 if block B[k,j] takes part in some surviving triple
+  int split;            // 1: BF16/FP16 split mode (dominant triples get hi+lo)
+  int64_t tile0;        // first global tile / block index
+  int64_t kidx0;        // first k_idx slot
+  int prep0;            // first CTA of this instance in the prep grid
+  int count0;           // first CTA of this instance in the count and fill grids
+  double target_rel;    // split modes: relative error target
+  double c1;            // split modes: hi-only error coefficient 2u + u^2
+  TauScreen T;
   PlanDevice* pd;
 };
 
-cudaError_t run_plan(PlanBuffers& b, const double* nA, const double* nB, double tau,
-                     double target_rel, int split, double c1, cudaStream_t s);
-int64_t plan_part_count(int bd);
+// The instance table a kernel reads: a device array, or one instance passed
+// by value (then `table` is null).
+struct InstRef {
+  const Inst* table;
+  Inst one;
+  int count;
+  __device__ __forceinline__ const Inst& at(int i) const { return table ? table[i] : one; }
+};
 
-// Carves the plan buffers for a bd x bd grid out of `base` (NULL: size only);
-// returns the bytes needed (256-byte aligned pieces).
-size_t plan_layout(int bd, PlanBuffers* b, char* base);
+// Largest i with key(i) <= v over a non-decreasing key (0 for a single instance).
+template <typename Key>
+__device__ __forceinline__ int find_inst(const InstRef& r, int64_t v, Key key) {
+  if (r.count <= 1) return 0;
+  int lo = 0, hi = r.count - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) / 2;
+    if (key(r.at(mid)) <= v) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+__device__ __forceinline__ int inst_of_tile(const InstRef& r, int64_t g) {
+  return find_inst(r, g, [](const Inst& x) { return x.tile0; });
+}
+
+// Device buffers of a plan (carved from one workspace allocation).
+struct PlanBuffers {
+  int64_t tiles;       // sum of bd^2
+  int64_t kslots;      // sum of bd^3
+  int prep_ctas;       // prep grid
+  int count_ctas;      // count and fill grids
+  Screen* sA;          // [tiles] screen form of normA, row-major per instance
+  Screen* sBT;         // [tiles] screen form of normB, transposed per instance
+  double* part_a;      // [prep_ctas] partial sums of squared norms
+  double* part_b;
+  long long* part_S;   // [count_ctas] per-CTA partials of the count kernel
+  int* part_kmax;
+  int* part_ne;
+  ExtSum* part_b1;     // sums of skipped relative products
+  ExtSum* part_b2;     // sums of their per-tile squares
+  int* cta_base;       // [count_ctas] first k_idx slot of the CTA's tiles
+  int* cnt;            // [tiles] survivors per tile
+  int* tile_beg;       // [tiles] absolute first k_idx slot of the tile
+  int* order;          // [tiles] global ids of the non-empty tiles, most survivors first
+  uint16_t* k_idx;     // [kslots] surviving k per tile, increasing (bit 15: split triple)
+  uint8_t* needA;      // [tiles] 1 if block A[i,k] takes part in some surviving triple
+  uint8_t* needB;      // [tiles] 1 if block B[k,j] takes part in some surviving triple
+  PlanDevice* pd;      // [instances]
+  BatchDevice* bdev;
+};
+
+// Grid sizes of the plan kernels for one instance of bd x bd tiles.
+int prep_ctas_of(int bd);
+int count_ctas_of(int bd);
+
+// Fills the layout fields of `insts` (tile0, kidx0, prep0, count0) and of `b`;
+// carves the buffers from `base` when non-null.  Returns the bytes needed.
+size_t plan_layout(Inst* insts, int count, PlanBuffers* b, char* base);
+
+// Host wrapper of a table: `dev_table` holds a device copy (batches) or is
+// null (a single instance, passed by value).
+InstRef make_ref(const Inst* host_insts, const Inst* dev_table, int count);
+
+cudaError_t run_plan(const InstRef& ref, const PlanBuffers& b, cudaStream_t s);
 
 cudaError_t launch_normmap(const float* X, int64_t n, int32_t leaf, double* out, cudaStream_t s);
 
-cudaError_t launch_multiply_simt(const PlanBuffers& b, const float* A, const float* B, float* C,
-                                 int64_t n, int32_t leaf, cudaStream_t s);
+// Batched norm maps: one job per operand of an instance.
+struct NormJob {
+  const float* X;
+  double* out;
+  int64_t n;
+  int bd;
+  int vec;    // n % 4 == 0 and X 16-byte aligned: float4 loads
+  int cta0;   // first CTA of the job
+  int pad_;
+};
+int normjob_ctas(const NormJob& j);
+cudaError_t launch_normmap_jobs(const NormJob* dev_jobs, int njobs, int total_ctas, int leaf,
+                                cudaStream_t s);
+
+cudaError_t launch_multiply_simt(const InstRef& ref, const PlanBuffers& b, int leaf,
+                                 cudaStream_t s);
 
 cudaError_t launch_frobenius_diff(const float* X, const float* Y, int64_t count, double* partials,
                                   int nparts, double* out, cudaStream_t s);

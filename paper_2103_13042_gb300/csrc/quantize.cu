@@ -53,9 +53,7 @@ __device__ __forceinline__ uint32_t pack2(float a, float b) {
 
 template <uint32_t FMT, int LEAF, bool SPLIT>
 __global__ void __launch_bounds__(kThreads)
-    quantize_kernel(const float* __restrict__ A, const float* __restrict__ B, int64_t n, int bd,
-                    const uint8_t* __restrict__ needA, const uint8_t* __restrict__ needB,
-                    OperandImages img) {
+    quantize_kernel(InstRef R, PlanBuffers Bf, OperandImages img) {
   using L = TcLayout<FMT, LEAF>;
   constexpr int ELT = L::kElt, KC = L::kKc, NCH = L::kNch;
   constexpr int PER16 = 16 / ELT;                 // elements per 16-byte piece
@@ -63,7 +61,9 @@ __global__ void __launch_bounds__(kThreads)
   extern __shared__ float tile[];                 // [LEAF][LEAF + 1]
   __shared__ float warp_max[kThreads / 32];
   __shared__ int s_list[kChunk];
-  const int64_t tiles = (int64_t)bd * bd;
+  const int64_t tiles = Bf.tiles;      // global blocks of A (and of B)
+  const uint8_t* __restrict__ needA = Bf.needA;
+  const uint8_t* __restrict__ needB = Bf.needB;
   const float lo_scale = (float)(1 << L::kLoShift);
 
   // Candidates (A blocks, then B blocks) in chunks of kChunk: the first two
@@ -91,9 +91,12 @@ __global__ void __launch_bounds__(kThreads)
   for (int li = 0; li < total; ++li) {
     const int64_t w = chunk * kChunk + s_list[li];
     const bool isB = w >= tiles;
-    const int64_t blk = isB ? w - tiles : w;
-    const float* X = isB ? B : A;
-    const int64_t r0 = (blk / bd) * LEAF, c0 = (blk % bd) * LEAF;
+    const int64_t blk = isB ? w - tiles : w;      // global block number
+    const Inst& in = R.at(inst_of_tile(R, blk));
+    const int64_t n = in.n, lb = blk - in.tile0;
+    const int bd = in.bd;
+    const float* X = isB ? in.B : in.A;
+    const int64_t r0 = (lb / bd) * LEAF, c0 = (lb % bd) * LEAF;
 
     // stage the block (zero outside the matrix) and its largest magnitude;
     // all loads are issued before the first shared-memory store
@@ -161,8 +164,8 @@ __global__ void __launch_bounds__(kThreads)
 }
 
 template <uint32_t FMT, int LEAF, bool SPLIT>
-cudaError_t launch_q(const float* A, const float* B, int64_t n, int bd, const uint8_t* needA,
-                     const uint8_t* needB, const OperandImages& img, cudaStream_t s) {
+cudaError_t launch_q(const InstRef& ref, const PlanBuffers& b, const OperandImages& img,
+                     cudaStream_t s) {
   const size_t smem = (size_t)LEAF * (LEAF + 1) * sizeof(float);
   cudaFuncSetAttribute(quantize_kernel<FMT, LEAF, SPLIT>,
                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -171,33 +174,34 @@ cudaError_t launch_q(const float* A, const float* B, int64_t n, int bd, const ui
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, quantize_kernel<FMT, LEAF, SPLIT>,
                                                 kThreads, smem);
-  const int64_t chunks = (2LL * bd * bd + kChunk - 1) / kChunk;
-  const int grid = (int)std::min<int64_t>(chunks, (int64_t)sms * std::max(1, per_sm));
-  quantize_kernel<FMT, LEAF, SPLIT><<<grid, kThreads, smem, s>>>(A, B, n, bd, needA, needB, img);
+  const int64_t chunks = (2 * b.tiles + kChunk - 1) / kChunk;
+  const int grid =
+      (int)std::max<int64_t>(1, std::min<int64_t>(chunks, (int64_t)sms * std::max(1, per_sm)));
+  quantize_kernel<FMT, LEAF, SPLIT><<<grid, kThreads, smem, s>>>(ref, b, img);
   return cudaPeekAtLastError();
 }
 
 }  // namespace
 
-cudaError_t launch_quantize(spamm_precision_t prec, int leaf, const float* A, const float* B,
-                            int64_t n, int bd, const uint8_t* needA, const uint8_t* needB,
-                            const OperandImages& img, cudaStream_t s) {
+cudaError_t launch_quantize(spamm_precision_t prec, int leaf, const InstRef& ref,
+                            const PlanBuffers& b, const OperandImages& img, cudaStream_t s) {
+  const bool l64 = leaf == 64;
   switch (prec) {
     case SPAMM_BF16:
-      return leaf == 64 ? launch_q<tc::kFmtBF16, 64, false>(A, B, n, bd, needA, needB, img, s)
-                        : launch_q<tc::kFmtBF16, 128, false>(A, B, n, bd, needA, needB, img, s);
+      return l64 ? launch_q<tc::kFmtBF16, 64, false>(ref, b, img, s)
+                 : launch_q<tc::kFmtBF16, 128, false>(ref, b, img, s);
     case SPAMM_FP16:
-      return leaf == 64 ? launch_q<tc::kFmtF16, 64, false>(A, B, n, bd, needA, needB, img, s)
-                        : launch_q<tc::kFmtF16, 128, false>(A, B, n, bd, needA, needB, img, s);
+      return l64 ? launch_q<tc::kFmtF16, 64, false>(ref, b, img, s)
+                 : launch_q<tc::kFmtF16, 128, false>(ref, b, img, s);
     case SPAMM_BF16_SPLIT:
-      return leaf == 64 ? launch_q<tc::kFmtBF16, 64, true>(A, B, n, bd, needA, needB, img, s)
-                        : launch_q<tc::kFmtBF16, 128, true>(A, B, n, bd, needA, needB, img, s);
+      return l64 ? launch_q<tc::kFmtBF16, 64, true>(ref, b, img, s)
+                 : launch_q<tc::kFmtBF16, 128, true>(ref, b, img, s);
     case SPAMM_FP16_SPLIT:
-      return leaf == 64 ? launch_q<tc::kFmtF16, 64, true>(A, B, n, bd, needA, needB, img, s)
-                        : launch_q<tc::kFmtF16, 128, true>(A, B, n, bd, needA, needB, img, s);
+      return l64 ? launch_q<tc::kFmtF16, 64, true>(ref, b, img, s)
+                 : launch_q<tc::kFmtF16, 128, true>(ref, b, img, s);
     case SPAMM_TF32X3:
-      return leaf == 64 ? launch_q<tc::kFmtTF32, 64, true>(A, B, n, bd, needA, needB, img, s)
-                        : launch_q<tc::kFmtTF32, 128, true>(A, B, n, bd, needA, needB, img, s);
+      return l64 ? launch_q<tc::kFmtTF32, 64, true>(ref, b, img, s)
+                 : launch_q<tc::kFmtTF32, 128, true>(ref, b, img, s);
     default: return cudaErrorInvalidValue;
   }
 }

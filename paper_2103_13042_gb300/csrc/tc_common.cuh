@@ -27,15 +27,16 @@ struct TcLayout {
   static constexpr int kLoShift = FMT == tc::kFmtBF16 ? 8 : 11; // lo part scaled by 2^kLoShift
 };
 
-cudaError_t launch_quantize(spamm_precision_t prec, int leaf, const float* A, const float* B,
-                            int64_t n, int bd, const uint8_t* needA, const uint8_t* needB,
-                            const OperandImages& img, cudaStream_t s);
+// Operand images are indexed by the global block number (tile0 + I * bd + K).
+cudaError_t launch_quantize(spamm_precision_t prec, int leaf, const InstRef& ref,
+                            const PlanBuffers& b, const OperandImages& img, cudaStream_t s);
 
-cudaError_t launch_multiply_tc(spamm_precision_t prec, int leaf, const PlanBuffers& b,
-                               const OperandImages& img, float* C, int64_t n, int32_t* status,
+cudaError_t launch_multiply_tc(spamm_precision_t prec, int leaf, const InstRef& ref,
+                               const PlanBuffers& b, const OperandImages& img, int32_t* status,
                                cudaStream_t s);
 
-cudaError_t launch_zero_empty_tiles(const PlanBuffers& b, float* C, int64_t n, int leaf,
+// Writes zeros to every tile without survivors, of every instance.
+cudaError_t launch_zero_empty_tiles(const InstRef& ref, const PlanBuffers& b, int leaf,
                                     cudaStream_t s);
 
 }  // namespace spamm
