@@ -207,6 +207,64 @@ spamm_status_t spamm_multiply_fp32_noalloc(const float* A, const float* B, float
                                            int32_t leaf, double tau, void* stream);
 
 /* ---------------------------------------------------------------------------
+ * Batches -- many independent products of uneven n (each one exactly the
+ * product spamm_normmap + spamm_plan + spamm_multiply would give it alone,
+ * with its own tau, statistics and bounds) run as ONE launch of each kernel:
+ * one norm-map launch over both operands of every instance, one plan over
+ * all triples of all instances, one rounding launch and one persistent
+ * multiply whose work queue holds every non-empty output tile of the batch,
+ * most survivors first.  The paper plans one product at a time (Section 3);
+ * the batch is the serving form of the same rule.
+ *
+ * spamm_problem_t: one instance.  A, B, C device FP32 n x n (ld = n),
+ *   16-byte aligned; C is written completely and may overlap no A, B or C of
+ *   the batch.  tau as for spamm_plan.
+ * spamm_batch_workspace_size / spamm_batch_create: the shapes (n[count]),
+ *   leaf and precision are fixed at creation; pointers and tau may change on
+ *   every run.  `workspace` as for spamm_plan_create.  flags:
+ *   SPAMM_BATCH_GRAPH captures the launches of the first run into a CUDA
+ *   graph and replays it on later runs (the instance table is re-uploaded,
+ *   from pinned host memory, only when it changed).  Creation allocates host
+ *   staging memory and blocks.
+ * spamm_batch_run: enqueues the whole batch on `stream` (asynchronous).
+ *   target_rel_err as for spamm_plan (split modes only).
+ * spamm_batch_stats: per-instance statistics into stats[count]; blocks.
+ * spamm_batch_export: host copies of one instance's norm maps (FP64
+ *   [bd*bd] each) and work queues (as spamm_plan_export); every pointer may
+ *   be NULL; blocks.
+ * spamm_multiply_batched: create + run + stats (if non-NULL) + destroy, for a
+ *   one-off batch; allocates and blocks.
+ * spamm_batch_destroy: synchronises the device and frees the batch.
+ * ------------------------------------------------------------------------- */
+typedef struct {
+  const float* A;
+  const float* B;
+  float* C;
+  int64_t n;
+  double tau;
+} spamm_problem_t;
+
+typedef struct spamm_batch_s* spamm_batch_t;
+
+#define SPAMM_BATCH_GRAPH 1
+
+spamm_status_t spamm_batch_workspace_size(const int64_t* n, int32_t count, int32_t leaf,
+                                          spamm_precision_t precision, size_t* bytes);
+spamm_status_t spamm_batch_create(spamm_batch_t* batch, const int64_t* n, int32_t count,
+                                  int32_t leaf, spamm_precision_t precision, int32_t flags,
+                                  void* workspace, size_t ws_bytes);
+spamm_status_t spamm_batch_run(spamm_batch_t batch, const spamm_problem_t* problems,
+                               double target_rel_err, void* stream);
+spamm_status_t spamm_batch_stats(spamm_batch_t batch, spamm_stats_t* stats, void* stream);
+spamm_status_t spamm_batch_export(spamm_batch_t batch, int32_t index, double* normA,
+                                  double* normB, int32_t* tile_ptr, uint16_t* k_idx, int64_t cap,
+                                  void* stream);
+spamm_status_t spamm_multiply_batched(const spamm_problem_t* problems, int32_t count, int32_t leaf,
+                                      spamm_precision_t precision, double target_rel_err,
+                                      spamm_stats_t* stats, void* stream);
+spamm_status_t spamm_batch_destroy(spamm_batch_t batch);
+
+/* ---------------------------------------------------------------------------
  * Status helpers.
  * spamm_status_string: static description of a status code.
  * spamm_last_device_status: reads and clears the library's device status word

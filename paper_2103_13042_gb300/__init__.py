@@ -40,6 +40,14 @@ class Stats(ctypes.Structure):
         return {f: getattr(self, f) for f, _ in self._fields_}
 
 
+class Problem(ctypes.Structure):
+    """One instance of a batch (spamm_problem_t)."""
+    _fields_ = [("A", ctypes.c_void_p), ("B", ctypes.c_void_p), ("C", ctypes.c_void_p),
+                ("n", ctypes.c_int64), ("tau", ctypes.c_double)]
+
+
+BATCH_GRAPH = 1
+
 _lib = None
 
 _VP, _I64, _I32, _D = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_double
@@ -55,6 +63,14 @@ _SIGS = {
     "spamm_frobenius_diff": [_VP, _VP, _I64, ctypes.POINTER(_D), _VP],
     "spamm_last_device_status": [_VP, ctypes.POINTER(_I32)],
     "spamm_multiply_fp32_noalloc": [_VP, _VP, _VP, _I64, _I32, _D, _VP],
+    "spamm_batch_workspace_size": [_VP, _I32, _I32, _I32, ctypes.POINTER(ctypes.c_size_t)],
+    "spamm_batch_create": [ctypes.POINTER(_VP), _VP, _I32, _I32, _I32, _I32, _VP,
+                           ctypes.c_size_t],
+    "spamm_batch_run": [_VP, _VP, _D, _VP],
+    "spamm_batch_stats": [_VP, _VP, _VP],
+    "spamm_batch_export": [_VP, _I32, _VP, _VP, _VP, _VP, _I64, _VP],
+    "spamm_multiply_batched": [_VP, _I32, _I32, _I32, _D, _VP, _VP],
+    "spamm_batch_destroy": [_VP],
 }
 
 
@@ -196,6 +212,94 @@ def spamm_multiply_fp32_noalloc(A, B, C, leaf: int, tau: float, stream=None):
                                              float(tau), _stream(stream)),
            "spamm_multiply_fp32_noalloc")
     return C
+
+
+def _problems(As, Bs, Cs, taus):
+    arr = (Problem * len(As))()
+    for i, (A, B, C, t) in enumerate(zip(As, Bs, Cs, taus)):
+        arr[i] = Problem(A.data_ptr(), B.data_ptr(), C.data_ptr(), A.shape[0], float(t))
+    return arr
+
+
+class Batch:
+    """Owns a spamm_batch_t: many independent products of fixed shapes."""
+
+    def __init__(self, ns, leaf: int, precision: int = FP32, graph: bool = True, workspace=None):
+        self.ns = [int(n) for n in ns]
+        self.leaf, self.precision = leaf, precision
+        self.count = len(self.ns)
+        n_arr = (ctypes.c_int64 * self.count)(*self.ns)
+        ws_ptr, ws_bytes = (None, 0) if workspace is None else (
+            _ptr(workspace), workspace.numel() * workspace.element_size())
+        h = ctypes.c_void_p()
+        _check(lib().spamm_batch_create(ctypes.byref(h), ctypes.cast(n_arr, ctypes.c_void_p),
+                                        self.count, leaf, precision,
+                                        BATCH_GRAPH if graph else 0, ws_ptr, ws_bytes),
+               "spamm_batch_create")
+        self.handle = h
+        self._workspace = workspace
+        self._keep = None
+
+    @staticmethod
+    def workspace_size(ns, leaf: int, precision: int = FP32) -> int:
+        n_arr = (ctypes.c_int64 * len(ns))(*[int(n) for n in ns])
+        b = ctypes.c_size_t()
+        _check(lib().spamm_batch_workspace_size(ctypes.cast(n_arr, ctypes.c_void_p), len(ns),
+                                                leaf, precision, ctypes.byref(b)),
+               "spamm_batch_workspace_size")
+        return b.value
+
+    def run(self, As, Bs, Cs, taus, target_rel_err: float = 1e-5, stream=None):
+        probs = _problems(As, Bs, Cs, taus)
+        self._keep = probs
+        _check(lib().spamm_batch_run(self.handle, ctypes.cast(probs, ctypes.c_void_p),
+                                     float(target_rel_err), _stream(stream)), "spamm_batch_run")
+        return Cs
+
+    def stats(self, stream=None):
+        arr = (Stats * self.count)()
+        _check(lib().spamm_batch_stats(self.handle, ctypes.cast(arr, ctypes.c_void_p),
+                                       _stream(stream)), "spamm_batch_stats")
+        return [a.as_dict() for a in arr]
+
+    def export(self, index: int, stream=None):
+        """(normA, normB [bd, bd] float64, tile_ptr int32[bd*bd+1], k_idx uint16[S]) of one instance."""
+        import numpy as np
+        bd = num_blocks(self.ns[index], self.leaf)
+        nA = np.zeros((bd, bd)); nB = np.zeros((bd, bd))
+        tp = np.zeros(bd * bd + 1, dtype=np.int32)
+        _check(lib().spamm_batch_export(self.handle, index, nA.ctypes.data_as(ctypes.c_void_p),
+                                        nB.ctypes.data_as(ctypes.c_void_p),
+                                        tp.ctypes.data_as(ctypes.c_void_p), None, 0,
+                                        _stream(stream)), "spamm_batch_export")
+        kk = np.zeros(max(1, int(tp[-1])), dtype=np.uint16)
+        _check(lib().spamm_batch_export(self.handle, index, None, None, None,
+                                        kk.ctypes.data_as(ctypes.c_void_p), kk.size,
+                                        _stream(stream)), "spamm_batch_export")
+        return nA, nB, tp, kk[:int(tp[-1])]
+
+    def close(self):
+        if self.handle:
+            lib().spamm_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def spamm_multiply_batched(As, Bs, Cs, taus, leaf: int, precision: int = FP32,
+                           target_rel_err: float = 1e-5, stream=None):
+    """One-off batch (allocates and blocks). Returns the per-instance statistics."""
+    probs = _problems(As, Bs, Cs, taus)
+    arr = (Stats * len(As))()
+    _check(lib().spamm_multiply_batched(ctypes.cast(probs, ctypes.c_void_p), len(As), leaf,
+                                        precision, float(target_rel_err),
+                                        ctypes.cast(arr, ctypes.c_void_p), _stream(stream)),
+           "spamm_multiply_batched")
+    return [a.as_dict() for a in arr]
 
 
 def spamm_last_device_status(stream=None) -> int:

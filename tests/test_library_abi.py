@@ -53,3 +53,23 @@ def test_argument_validation_without_gpu(lib):
     assert lib.spamm_normmap(ctypes.c_void_p(16), 1024, 40, ctypes.c_void_p(16), None) == 2
     assert lib.spamm_normmap(ctypes.c_void_p(18), 1024, 64, ctypes.c_void_p(16), None) == 1
     assert lib.spamm_plan(None, None, None, 0.0, 0.0, None) == 1
+
+
+def test_batch_validation_without_gpu(lib):
+    """Batch shape checks run on the host before any CUDA call."""
+    b = ctypes.c_size_t()
+    ns = (ctypes.c_int64 * 3)(256, 1000, 4096)
+    assert lib.spamm_batch_workspace_size(ns, 3, 64, 2, ctypes.byref(b)) == 0
+    one = ctypes.c_size_t()
+    ns1 = (ctypes.c_int64 * 1)(4096)
+    assert lib.spamm_batch_workspace_size(ns1, 1, 64, 2, ctypes.byref(one)) == 0
+    assert b.value > one.value
+    assert lib.spamm_batch_workspace_size(ns, 0, 64, 2, ctypes.byref(b)) == 1     # count < 1
+    assert lib.spamm_batch_workspace_size(ns, 3, 32, 2, ctypes.byref(b)) == 2     # tensor at 32
+    assert lib.spamm_batch_workspace_size(ns, 3, 96, 0, ctypes.byref(b)) == 2     # leaf
+    bad = (ctypes.c_int64 * 2)(256, 0)
+    assert lib.spamm_batch_workspace_size(bad, 2, 64, 0, ctypes.byref(b)) == 1    # n < 1
+    h = ctypes.c_void_p()
+    assert lib.spamm_batch_create(ctypes.byref(h), ns, 3, 64, 0, 4, None, 0) == 1  # flags
+    assert lib.spamm_batch_run(None, None, 0.0, None) == 1
+    assert lib.spamm_batch_destroy(None) == 1
