@@ -224,14 +224,29 @@ spamm_status_t spamm_multiply_fp32_noalloc(const float* A, const float* B, float
  *   every run.  `workspace` as for spamm_plan_create.  flags:
  *   SPAMM_BATCH_GRAPH captures the launches of the first run into a CUDA
  *   graph and replays it on later runs (the instance table is re-uploaded,
- *   from pinned host memory, only when it changed).  Creation allocates host
- *   staging memory and blocks.
+ *   from pinned host memory, only when it changed).  SPAMM_BATCH_DYNAMIC
+ *   makes the persistent multiply take its tiles in 32-tile chunks from a
+ *   global counter instead of a fixed interleave.  SPAMM_BATCH_TIMING
+ *   records events around the three phases of every run (runs are then
+ *   enqueued directly, never from the graph) for spamm_batch_timings.
+ *   Creation allocates host staging memory and blocks.
  * spamm_batch_run: enqueues the whole batch on `stream` (asynchronous).
  *   target_rel_err as for spamm_plan (split modes only).
  * spamm_batch_stats: per-instance statistics into stats[count]; blocks.
  * spamm_batch_export: host copies of one instance's norm maps (FP64
  *   [bd*bd] each) and work queues (as spamm_plan_export); every pointer may
  *   be NULL; blocks.
+ * spamm_batch_timings: ms[3] = device time of the norm maps, the plan and
+ *   the multiply of the last run (SPAMM_BATCH_TIMING only); blocks.
+ * spamm_batch_autotune: times every candidate configuration on the given
+ *   problems and returns the fastest in *best: leaf 64 and 128 (32, 64 and
+ *   128 for FP32) times the static and dynamic multiply schedules, each
+ *   with graph replay, median of `reps` timed runs after two untimed ones.
+ *   results[*nresults] (both may be NULL) receives every candidate, ms < 0
+ *   for one that did not fit in memory; *nresults is set to the number of
+ *   candidates.  Every candidate writes the C buffers (different leaves give
+ *   different skip sets): run the chosen configuration afterwards.
+ *   Allocates and blocks.
  * spamm_multiply_batched: create + run + stats (if non-NULL) + destroy, for a
  *   one-off batch; allocates and blocks.
  * spamm_batch_destroy: synchronises the device and frees the batch.
@@ -247,6 +262,14 @@ typedef struct {
 typedef struct spamm_batch_s* spamm_batch_t;
 
 #define SPAMM_BATCH_GRAPH 1
+#define SPAMM_BATCH_DYNAMIC 2
+#define SPAMM_BATCH_TIMING 4
+
+typedef struct {
+  int32_t leaf;
+  int32_t flags;   /* SPAMM_BATCH_* flags of the configuration */
+  float ms;        /* median time of one run, < 0 if the candidate could not run */
+} spamm_tune_t;
 
 spamm_status_t spamm_batch_workspace_size(const int64_t* n, int32_t count, int32_t leaf,
                                           spamm_precision_t precision, size_t* bytes);
@@ -259,6 +282,11 @@ spamm_status_t spamm_batch_stats(spamm_batch_t batch, spamm_stats_t* stats, void
 spamm_status_t spamm_batch_export(spamm_batch_t batch, int32_t index, double* normA,
                                   double* normB, int32_t* tile_ptr, uint16_t* k_idx, int64_t cap,
                                   void* stream);
+spamm_status_t spamm_batch_timings(spamm_batch_t batch, float* ms);
+spamm_status_t spamm_batch_autotune(const spamm_problem_t* problems, int32_t count,
+                                    spamm_precision_t precision, double target_rel_err,
+                                    int32_t reps, void* stream, spamm_tune_t* best,
+                                    spamm_tune_t* results, int32_t* nresults);
 spamm_status_t spamm_multiply_batched(const spamm_problem_t* problems, int32_t count, int32_t leaf,
                                       spamm_precision_t precision, double target_rel_err,
                                       spamm_stats_t* stats, void* stream);

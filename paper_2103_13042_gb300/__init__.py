@@ -46,7 +46,16 @@ class Problem(ctypes.Structure):
                 ("n", ctypes.c_int64), ("tau", ctypes.c_double)]
 
 
-BATCH_GRAPH = 1
+BATCH_GRAPH, BATCH_DYNAMIC, BATCH_TIMING = 1, 2, 4
+
+
+class Tune(ctypes.Structure):
+    """One autotuner candidate (spamm_tune_t)."""
+    _fields_ = [("leaf", ctypes.c_int32), ("flags", ctypes.c_int32), ("ms", ctypes.c_float)]
+
+    def as_dict(self):
+        return {"leaf": self.leaf, "schedule": "dynamic" if self.flags & BATCH_DYNAMIC else "static",
+                "flags": self.flags, "ms": self.ms}
 
 _lib = None
 
@@ -71,6 +80,9 @@ _SIGS = {
     "spamm_batch_export": [_VP, _I32, _VP, _VP, _VP, _VP, _I64, _VP],
     "spamm_multiply_batched": [_VP, _I32, _I32, _I32, _D, _VP, _VP],
     "spamm_batch_destroy": [_VP],
+    "spamm_batch_timings": [_VP, _VP],
+    "spamm_batch_autotune": [_VP, _I32, _I32, _D, _I32, _VP, ctypes.POINTER(Tune), _VP,
+                             ctypes.POINTER(_I32)],
 }
 
 
@@ -224,7 +236,8 @@ def _problems(As, Bs, Cs, taus):
 class Batch:
     """Owns a spamm_batch_t: many independent products of fixed shapes."""
 
-    def __init__(self, ns, leaf: int, precision: int = FP32, graph: bool = True, workspace=None):
+    def __init__(self, ns, leaf: int, precision: int = FP32, graph: bool = True,
+                 workspace=None, dynamic: bool = False, timing: bool = False):
         self.ns = [int(n) for n in ns]
         self.leaf, self.precision = leaf, precision
         self.count = len(self.ns)
@@ -232,9 +245,10 @@ class Batch:
         ws_ptr, ws_bytes = (None, 0) if workspace is None else (
             _ptr(workspace), workspace.numel() * workspace.element_size())
         h = ctypes.c_void_p()
+        flags = ((BATCH_GRAPH if graph else 0) | (BATCH_DYNAMIC if dynamic else 0) |
+                 (BATCH_TIMING if timing else 0))
         _check(lib().spamm_batch_create(ctypes.byref(h), ctypes.cast(n_arr, ctypes.c_void_p),
-                                        self.count, leaf, precision,
-                                        BATCH_GRAPH if graph else 0, ws_ptr, ws_bytes),
+                                        self.count, leaf, precision, flags, ws_ptr, ws_bytes),
                "spamm_batch_create")
         self.handle = h
         self._workspace = workspace
@@ -278,6 +292,13 @@ class Batch:
                                         _stream(stream)), "spamm_batch_export")
         return nA, nB, tp, kk[:int(tp[-1])]
 
+    def timings(self):
+        """{"normmap", "plan", "multiply"} device ms of the last run (timing batches only)."""
+        ms = (ctypes.c_float * 3)()
+        _check(lib().spamm_batch_timings(self.handle, ctypes.cast(ms, ctypes.c_void_p)),
+               "spamm_batch_timings")
+        return {"normmap": ms[0], "plan": ms[1], "multiply": ms[2]}
+
     def close(self):
         if self.handle:
             lib().spamm_batch_destroy(self.handle)
@@ -288,6 +309,20 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+def spamm_batch_autotune(As, Bs, Cs, taus, precision: int = FP32, target_rel_err: float = 1e-5,
+                         reps: int = 3, stream=None):
+    """Times every (leaf, schedule) candidate on these problems: (best, all) as dicts."""
+    probs = _problems(As, Bs, Cs, taus)
+    best = Tune()
+    res = (Tune * 8)()
+    nres = ctypes.c_int32(8)
+    _check(lib().spamm_batch_autotune(ctypes.cast(probs, ctypes.c_void_p), len(As), precision,
+                                      float(target_rel_err), reps, _stream(stream),
+                                      ctypes.byref(best), ctypes.cast(res, ctypes.c_void_p),
+                                      ctypes.byref(nres)), "spamm_batch_autotune")
+    return best.as_dict(), [res[i].as_dict() for i in range(min(nres.value, 8))]
 
 
 def spamm_multiply_batched(As, Bs, Cs, taus, leaf: int, precision: int = FP32,

@@ -157,12 +157,15 @@ cudaError_t engine_multiply(Engine& e, const InstRef& ref, int32_t* status, cuda
   if (err == cudaSuccess) err = cudaStreamWaitEvent(e.side, e.fork, 0);
   if (err == cudaSuccess) err = launch_zero_empty_tiles(ref, e.buf, e.leaf, e.side);
   if (err == cudaSuccess) err = cudaEventRecord(e.join, e.side);
+  if (err == cudaSuccess && e.schedule == kScheduleDynamic)
+    err = cudaMemsetAsync(&e.buf.bdev->mul_ticket, 0, sizeof(int), s);
   if (err == cudaSuccess) {
     if (e.precision == SPAMM_FP32) {
-      err = launch_multiply_simt(ref, e.buf, e.leaf, s);
+      err = launch_multiply_simt(ref, e.buf, e.leaf, e.schedule, s);
     } else {
       err = launch_quantize(e.precision, e.leaf, ref, e.buf, e.img, s);
-      if (err == cudaSuccess) err = launch_multiply_tc(e.precision, e.leaf, ref, e.buf, e.img, status, s);
+      if (err == cudaSuccess)
+        err = launch_multiply_tc(e.precision, e.leaf, ref, e.buf, e.img, status, e.schedule, s);
     }
   }
   if (err == cudaSuccess) err = cudaStreamWaitEvent(s, e.join, 0);
@@ -295,6 +298,7 @@ spamm_status_t spamm_plan(spamm_plan_t plan, const double* normA, const double* 
   in.nB = normB;
   in.T = make_tau_screen(tau);
   in.split = split ? 1 : 0;
+  in.quant = is_tensor_mode(e.precision) ? 1 : 0;
   in.target_rel = split ? target_rel_err : 0.0;
   in.c1 = split ? 2.0 * u + u * u : 0.0;
   cudaError_t err = run_plan(make_ref(e.insts.data(), nullptr, 1), e.buf, (cudaStream_t)stream);

@@ -39,6 +39,8 @@ struct spamm_batch_s {
   cudaEvent_t ev_in = nullptr, ev_out = nullptr;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
+  cudaEvent_t phase[4] = {};     // SPAMM_BATCH_TIMING: before norms, after norms, plan, multiply
+  bool timed = false;            // a timed run has been enqueued
 };
 
 namespace {
@@ -122,12 +124,18 @@ InstRef batch_ref(const spamm_batch_s* b) {
   return make_ref(b->eng.insts.data(), b->insts_dev, b->count);
 }
 
-// The whole batch on one stream: norm maps, plan, multiply.
-cudaError_t enqueue(spamm_batch_s* b, cudaStream_t s) {
+// The whole batch on one stream: norm maps, plan, multiply (with phase
+// events when timing is on).
+cudaError_t enqueue(spamm_batch_s* b, cudaStream_t s, bool timing) {
   const InstRef ref = batch_ref(b);
-  cudaError_t e = launch_normmap_jobs(b->jobs_dev, 2 * b->count, b->norm_ctas, b->eng.leaf, s);
+  cudaError_t e = timing ? cudaEventRecord(b->phase[0], s) : cudaSuccess;
+  if (e == cudaSuccess)
+    e = launch_normmap_jobs(b->jobs_dev, 2 * b->count, b->norm_ctas, b->eng.leaf, s);
+  if (e == cudaSuccess && timing) e = cudaEventRecord(b->phase[1], s);
   if (e == cudaSuccess) e = run_plan(ref, b->eng.buf, s);
+  if (e == cudaSuccess && timing) e = cudaEventRecord(b->phase[2], s);
   if (e == cudaSuccess) e = engine_multiply(b->eng, ref, b->status, s);
+  if (e == cudaSuccess && timing) e = cudaEventRecord(b->phase[3], s);
   return e;
 }
 
@@ -144,6 +152,8 @@ void release(spamm_batch_s* b) {
   if (b->ev_in) cudaEventDestroy(b->ev_in);
   if (b->ev_out) cudaEventDestroy(b->ev_out);
   if (b->upload_done) cudaEventDestroy(b->upload_done);
+  for (cudaEvent_t& ev : b->phase)
+    if (ev) cudaEventDestroy(ev);
   if (b->staging) cudaFreeHost(b->staging);
   engine_free(b->eng);
   delete b;
@@ -171,7 +181,8 @@ spamm_status_t spamm_batch_create(spamm_batch_t* batch, const int64_t* n, int32_
   *batch = nullptr;
   spamm_status_t st = check_shapes(n, count, leaf, precision);
   if (st != SPAMM_OK) return st;
-  if (flags & ~SPAMM_BATCH_GRAPH) return SPAMM_ERR_INVALID_ARG;
+  if (flags & ~(SPAMM_BATCH_GRAPH | SPAMM_BATCH_DYNAMIC | SPAMM_BATCH_TIMING))
+    return SPAMM_ERR_INVALID_ARG;
   spamm_batch_s* b = new (std::nothrow) spamm_batch_s();
   if (!b) return SPAMM_ERR_NO_MEMORY;
   b->count = count;
@@ -185,6 +196,7 @@ spamm_status_t spamm_batch_create(spamm_batch_t* batch, const int64_t* n, int32_
     delete b;
     return st;
   }
+  b->eng.schedule = (flags & SPAMM_BATCH_DYNAMIC) ? kScheduleDynamic : kScheduleStatic;
   char* base = static_cast<char*>(b->eng.base);
   b->normA = reinterpret_cast<double*>(base);
   b->normB = reinterpret_cast<double*>(base + norm_bytes);
@@ -215,6 +227,15 @@ spamm_status_t spamm_batch_create(spamm_batch_t* batch, const int64_t* n, int32_
     if (!b->status) {
       release(b);
       return SPAMM_ERR_NO_MEMORY;
+    }
+  }
+  if (flags & SPAMM_BATCH_TIMING) {
+    for (cudaEvent_t& ev : b->phase) {
+      if (cudaEventCreate(&ev) != cudaSuccess) {
+        (void)cudaGetLastError();
+        release(b);
+        return SPAMM_ERR_CUDA;
+      }
     }
   }
   if (cudaMallocHost(&b->staging, b->table_bytes) != cudaSuccess ||
@@ -265,6 +286,7 @@ spamm_status_t spamm_batch_run(spamm_batch_t b, const spamm_problem_t* problems,
     in.nB = b->normB + in.tile0;
     in.T = make_tau_screen(problems[i].tau);
     in.split = split ? 1 : 0;
+    in.quant = is_tensor_mode(e.precision) ? 1 : 0;
     in.target_rel = split ? target_rel_err : 0.0;
     in.c1 = split ? 2.0 * u + u * u : 0.0;
     for (int op = 0; op < 2; ++op) {
@@ -292,13 +314,14 @@ spamm_status_t spamm_batch_run(spamm_batch_t b, const spamm_problem_t* problems,
   }
 
   cudaError_t err = cudaSuccess;
-  if (b->flags & SPAMM_BATCH_GRAPH) {
+  const bool timing = (b->flags & SPAMM_BATCH_TIMING) != 0;
+  if ((b->flags & SPAMM_BATCH_GRAPH) && !timing) {
     // every kernel argument is a pointer into the workspace or a grid size
     // fixed at creation, so one capture serves every later run
     if (!b->exec) {
       err = cudaStreamBeginCapture(b->main, cudaStreamCaptureModeThreadLocal);
       if (err == cudaSuccess) {
-        const cudaError_t e1 = enqueue(b, b->main);
+        const cudaError_t e1 = enqueue(b, b->main, false);
         cudaGraph_t g = nullptr;
         const cudaError_t e2 = cudaStreamEndCapture(b->main, &g);
         err = e1 != cudaSuccess ? e1 : e2;
@@ -317,7 +340,8 @@ spamm_status_t spamm_batch_run(spamm_batch_t b, const spamm_problem_t* problems,
     if (err == cudaSuccess) err = cudaEventRecord(b->ev_out, b->main);
     if (err == cudaSuccess) err = cudaStreamWaitEvent(s, b->ev_out, 0);
   } else {
-    err = enqueue(b, s);
+    err = enqueue(b, s, timing);
+    b->timed = timing && err == cudaSuccess;
   }
   if (err != cudaSuccess) {
     (void)cudaGetLastError();
@@ -369,6 +393,80 @@ spamm_status_t spamm_batch_export(spamm_batch_t b, int32_t index, double* normA,
   }
   SPAMM_CUDA_TRY(cudaStreamSynchronize(s));
   return SPAMM_OK;
+}
+
+spamm_status_t spamm_batch_timings(spamm_batch_t b, float* ms) {
+  if (!b || !ms) return SPAMM_ERR_INVALID_ARG;
+  if (!(b->flags & SPAMM_BATCH_TIMING) || !b->timed) return SPAMM_ERR_INVALID_ARG;
+  SPAMM_CUDA_TRY(cudaEventSynchronize(b->phase[3]));
+  for (int q = 0; q < 3; ++q)
+    SPAMM_CUDA_TRY(cudaEventElapsedTime(&ms[q], b->phase[q], b->phase[q + 1]));
+  return SPAMM_OK;
+}
+
+spamm_status_t spamm_batch_autotune(const spamm_problem_t* problems, int32_t count,
+                                    spamm_precision_t precision, double target_rel_err,
+                                    int32_t reps, void* stream, spamm_tune_t* best,
+                                    spamm_tune_t* results, int32_t* nresults) {
+  if (!problems || count < 1 || !best || reps < 1) return SPAMM_ERR_INVALID_ARG;
+  std::vector<int64_t> n((size_t)count);
+  for (int32_t i = 0; i < count; ++i) n[i] = problems[i].n;
+  const cudaStream_t s = (cudaStream_t)stream;
+  std::vector<int32_t> leaves = precision == SPAMM_FP32 ? std::vector<int32_t>{32, 64, 128}
+                                                        : std::vector<int32_t>{64, 128};
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+    (void)cudaGetLastError();
+    if (e0) cudaEventDestroy(e0);
+    return SPAMM_ERR_CUDA;
+  }
+  spamm_status_t st = SPAMM_OK;
+  int32_t nres = 0;
+  best->leaf = 0;
+  best->flags = 0;
+  best->ms = -1.0f;
+  for (int32_t leaf : leaves) {
+    for (int32_t sched : {0, SPAMM_BATCH_DYNAMIC}) {
+      spamm_tune_t r{leaf, SPAMM_BATCH_GRAPH | sched, -1.0f};
+      spamm_batch_t b = nullptr;
+      spamm_status_t cs = spamm_batch_create(&b, n.data(), count, leaf, precision, r.flags,
+                                             nullptr, 0);
+      if (cs == SPAMM_OK) {
+        std::vector<float> t;
+        // first run captures the graph, second warms it; then `reps` timed runs
+        for (int32_t q = 0; q < reps + 2 && cs == SPAMM_OK; ++q) {
+          if (q >= 2 && cudaEventRecord(e0, s) != cudaSuccess) cs = SPAMM_ERR_CUDA;
+          if (cs == SPAMM_OK) cs = spamm_batch_run(b, problems, target_rel_err, stream);
+          if (q >= 2 && cs == SPAMM_OK) {
+            float ms = 0.0f;
+            if (cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+                cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess)
+              cs = SPAMM_ERR_CUDA;
+            t.push_back(ms);
+          }
+        }
+        if (cs == SPAMM_OK && !t.empty()) {
+          std::sort(t.begin(), t.end());
+          r.ms = t[t.size() / 2];
+        }
+        const spamm_status_t ds = spamm_batch_destroy(b);
+        if (cs == SPAMM_OK) cs = ds;
+      }
+      if (cs != SPAMM_OK && cs != SPAMM_ERR_NO_MEMORY && cs != SPAMM_ERR_UNSUPPORTED) {
+        st = cs;   // a real failure ends the search
+      }
+      if (results && nresults && nres < *nresults) results[nres] = r;
+      ++nres;
+      if (r.ms >= 0.0f && (best->ms < 0.0f || r.ms < best->ms)) *best = r;
+      if (st != SPAMM_OK) break;
+    }
+    if (st != SPAMM_OK) break;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (nresults) *nresults = nres;
+  if (st == SPAMM_OK && best->ms < 0.0f) st = SPAMM_ERR_NO_MEMORY;
+  return st;
 }
 
 spamm_status_t spamm_multiply_batched(const spamm_problem_t* problems, int32_t count, int32_t leaf,

@@ -20,6 +20,7 @@ struct Engine {
   PlanBuffers buf{};
   OperandImages img{};         // tensor-core modes only
   size_t extra_bytes = 0;      // caller-defined area at the start of the workspace
+  int schedule = kScheduleStatic;
   cudaStream_t side = nullptr; // zero-fill of empty tiles runs here, overlapped
   cudaEvent_t fork = nullptr, join = nullptr;
 };

@@ -66,7 +66,7 @@ __device__ __forceinline__ void write_row(float* p, const float* v) {
 }
 
 template <int LEAF>
-__global__ void __launch_bounds__(kThreads) simt_kernel(InstRef R, PlanBuffers Bf) {
+__global__ void __launch_bounds__(kThreads) simt_kernel(InstRef R, PlanBuffers Bf, int dynamic) {
   using T = SimtTile<LEAF>;
   constexpr int TM = T::TM;
   constexpr int kLoads = T::kLoadsA;
@@ -80,9 +80,16 @@ __global__ void __launch_bounds__(kThreads) simt_kernel(InstRef R, PlanBuffers B
   const int tx = tid % 16, ty = tid / 16;
   const int64_t ne = Bf.bdev->nonempty;   // empty tiles are zero-filled by another kernel
 
-  for (int64_t w = blockIdx.x; w < ne; w += gridDim.x) {
+  __shared__ int s_next;
+  for (int64_t w = blockIdx.x;; w += gridDim.x) {
+    if (dynamic) {   // next tile from the global counter (its use ends at the loop's barrier)
+      if (tid == 0) s_next = atomicAdd(&Bf.bdev->mul_ticket, 1);
+      __syncthreads();
+      w = s_next;
+    }
+    if (w >= ne) break;
     const int g = Bf.order[w];
-    const Inst& in = R.at(inst_of_tile(R, g));
+    const Inst& in = R.at(inst_of(R, Bf, g));
     const int bd = in.bd;
     const int64_t n = in.n;
     const float* __restrict__ A = in.A;
@@ -172,7 +179,7 @@ __global__ void __launch_bounds__(kThreads) simt_kernel(InstRef R, PlanBuffers B
 }
 
 template <int LEAF>
-cudaError_t launch(const InstRef& ref, const PlanBuffers& b, cudaStream_t s) {
+cudaError_t launch(const InstRef& ref, const PlanBuffers& b, int schedule, cudaStream_t s) {
   constexpr size_t smem = 4 * kSlice * (LEAF + 4) * sizeof(float);
   int dev = 0, sms = 0, per_sm = 0;
   cudaGetDevice(&dev);
@@ -181,18 +188,18 @@ cudaError_t launch(const InstRef& ref, const PlanBuffers& b, cudaStream_t s) {
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, simt_kernel<LEAF>, kThreads, smem);
   const int grid = (int)std::max<int64_t>(
       1, std::min<int64_t>(b.tiles, (int64_t)sms * std::max(1, per_sm)));
-  simt_kernel<LEAF><<<grid, kThreads, smem, s>>>(ref, b);
+  simt_kernel<LEAF><<<grid, kThreads, smem, s>>>(ref, b, schedule == kScheduleDynamic);
   return cudaPeekAtLastError();
 }
 
 }  // namespace
 
 cudaError_t launch_multiply_simt(const InstRef& ref, const PlanBuffers& b, int leaf,
-                                 cudaStream_t s) {
+                                 int schedule, cudaStream_t s) {
   switch (leaf) {
-    case 32: return launch<32>(ref, b, s);
-    case 64: return launch<64>(ref, b, s);
-    case 128: return launch<128>(ref, b, s);
+    case 32: return launch<32>(ref, b, schedule, s);
+    case 64: return launch<64>(ref, b, schedule, s);
+    case 128: return launch<128>(ref, b, schedule, s);
     default: return cudaErrorInvalidValue;
   }
 }

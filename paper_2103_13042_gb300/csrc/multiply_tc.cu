@@ -15,8 +15,8 @@
 //   warp 1   allocates tensor memory and issues the MMAs from one thread:
 //            consecutive k of a tile with the same exponent sum (and split
 //            flag) form a run accumulated in one TMEM accumulator; runs
-//            alternate between two accumulators so the epilogue of one
-//            overlaps the MMAs of the next.  Each stage is released by
+//            rotate over as many accumulators as TMEM holds (2 to 8), so
+//            the epilogue of one overlaps the MMAs of the next ones.  Each stage is released by
 //            tcgen05.commit when its MMAs have read it.
 //   warps 3+  epilogue (4 warps per 64 output columns): for each run, load
 //            the accumulator rows (one TMEM lane per output row, 64 columns
@@ -61,6 +61,7 @@ struct TcParams {
   PlanBuffers Bf;
   OperandImages img;
   int32_t* status;
+  int dynamic;   // take 32-slot chunks of the order from Bf.bdev->mul_ticket
 };
 
 template <uint32_t FMT, int LEAF, int SPLITMODE>
@@ -71,26 +72,37 @@ struct TcCfg {
   static constexpr int kEpiWarps = 4 * (N / 64);          // 64 columns per epilogue warp
   static constexpr int kThreads = 32 * kFirstEpiWarp + 32 * kEpiWarps;
   static constexpr uint32_t kStageBytes = L::kChunkBytes * 2 * (kHasLo ? 2 : 1);
-  static constexpr int kStagesFit = (200 * 1024) / kStageBytes;
+  static constexpr int kStagesFit =
+      (200 * 1024 - kEpiWarps * (M == 128 ? 32 : 16) * (64 * 4 + 16)) / kStageBytes;
   static constexpr int kStages = kStagesFit > 16 ? 16 : kStagesFit;
   static constexpr int kAccCols = N * (kHasLo ? 2 : 1);
-  static constexpr uint32_t kTmemCols = 2 * kAccCols;               // 128, 256 or 512
+  // as many run accumulators as the 512 TMEM columns hold (2 to 8): the MMA
+  // issuer runs that many runs ahead of the epilogue
+  static constexpr int kNumAcc = 512 / kAccCols;
+  static constexpr uint32_t kTmemCols = kNumAcc * kAccCols;          // 512
   static constexpr uint32_t kIdesc = idesc(FMT, M, N);
   // every region starts on a 16-byte boundary (128-bit shared-memory accesses)
   static constexpr size_t up16(size_t x) { return (x + 15) / 16 * 16; }
   static constexpr size_t kBarOffset = (size_t)kStages * kStageBytes;
-  static constexpr int kNumBars = 2 * kStages + 4 + 2 * kRunRing + 1 + 2 * kGroups;
+  static constexpr int kNumBars = 2 * kStages + 2 * kNumAcc + 2 * kRunRing + 1 + 2 * kGroups;
   static constexpr size_t kMetaOffset = up16(kBarOffset + (size_t)kNumBars * 8);
   static constexpr size_t kRunOffset = up16(kMetaOffset + (size_t)kStages * sizeof(StageMeta));
   static constexpr size_t kEntOffset = up16(kRunOffset + (size_t)kRunRing * sizeof(RunRec));
-  static constexpr size_t kMiscOffset =
+  // epilogue staging for the bulk stores of C: per epilogue warp its rows
+  // (16 of M = 64, 32 of M = 128) of 64 columns, rows 272 bytes apart
+  static constexpr int kEpiRows = M == 128 ? 32 : 16;
+  static constexpr int kEpiRowBytes = 64 * 4 + 16;
+  static constexpr size_t kEpiOffset =
       up16(kEntOffset + (size_t)kGroups * 32 * sizeof(int4) + kGroups * sizeof(int));
+  static constexpr size_t kMiscOffset =
+      up16(kEpiOffset + (size_t)kEpiWarps * kEpiRows * kEpiRowBytes);
   static_assert(kMetaOffset % 16 == 0 && kRunOffset % 16 == 0 && kEntOffset % 16 == 0 &&
-                    kMiscOffset % 16 == 0 && kBarOffset % 1024 == 0,
+                    kEpiOffset % 16 == 0 && kMiscOffset % 16 == 0 && kBarOffset % 1024 == 0 &&
+                    kEpiRowBytes % 16 == 0,
                 "shared-memory regions aligned");
   static constexpr size_t kSmemBytes = kMiscOffset + 64 + 1024;     // + alignment slack
   static_assert(kStages >= 2, "at least two pipeline stages");
-  static_assert(kTmemCols >= 32 && kTmemCols <= 512, "TMEM columns");
+  static_assert(kTmemCols >= 32 && kTmemCols <= 512 && kNumAcc >= 2, "TMEM columns");
   static_assert(kSmemBytes <= 227 * 1024, "shared memory");
 };
 
@@ -133,9 +145,10 @@ __global__ void __launch_bounds__(TcCfg<FMT, LEAF, SPLITMODE>::kThreads, 1)
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + Cfg::kBarOffset);
   uint64_t* full = bars;
   uint64_t* empty = bars + S;
+  constexpr int NA = Cfg::kNumAcc;
   uint64_t* acc_full = bars + 2 * S;
-  uint64_t* acc_empty = acc_full + 2;
-  uint64_t* run_full = acc_empty + 2;
+  uint64_t* acc_empty = acc_full + NA;
+  uint64_t* run_full = acc_empty + NA;
   uint64_t* run_empty = run_full + kRunRing;
   uint64_t* drain = run_empty + kRunRing;
   uint64_t* ent_full = drain + 1;
@@ -153,7 +166,7 @@ __global__ void __launch_bounds__(TcCfg<FMT, LEAF, SPLITMODE>::kThreads, 1)
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], 1);
     }
-    for (int b = 0; b < 2; ++b) {
+    for (int b = 0; b < NA; ++b) {
       mbar_init(&acc_full[b], 1);
       mbar_init(&acc_empty[b], Cfg::kEpiWarps);
     }
@@ -198,14 +211,22 @@ __global__ void __launch_bounds__(TcCfg<FMT, LEAF, SPLITMODE>::kThreads, 1)
       gfill = 0;
       return wait_ab(&ent_empty[grp], gphase ^ 1u, abort_flag, p.status);
     };
-    for (int base = blockIdx.x; base < ne && ok; base += 32 * gridDim.x) {
-      const int w = base + lane * gridDim.x;
+    // static: this CTA's slots are blockIdx.x + (32 m + lane) * gridDim.x;
+    // dynamic: consecutive 32-slot chunks from the global counter
+    auto next_base = [&](int prev) -> int {
+      if (!p.dynamic) return prev < 0 ? (int)blockIdx.x : prev + 32 * (int)gridDim.x;
+      int b = 0;
+      if (lane == 0) b = atomicAdd(&p.Bf.bdev->mul_ticket, 32);
+      return __shfl_sync(0xffffffffu, b, 0);
+    };
+    for (int base = next_base(-1); base < ne && ok; base = next_base(base)) {
+      const int w = p.dynamic ? base + lane : base + lane * (int)gridDim.x;
       const bool valid = w < ne;
       int t = 0, beg = 0, end = 0, bdl = 1;
       int64_t t0 = 0;
       if (valid) {
         t = p.Bf.order[w];                       // global tile
-        const Inst& in = p.R.at(inst_of_tile(p.R, t));
+        const Inst& in = p.R.at(inst_of(p.R, p.Bf, t));
         t0 = in.tile0;
         bdl = in.bd;
         beg = p.Bf.tile_beg[t];
@@ -354,7 +375,7 @@ __global__ void __launch_bounds__(TcCfg<FMT, LEAF, SPLITMODE>::kThreads, 1)
           slot = 0;
           slot_phase ^= 1u;
         }
-        mma_commit(&acc_full[run & 1]);
+        mma_commit(&acc_full[run % NA]);
         open = false;
         return true;
       };
@@ -372,8 +393,8 @@ __global__ void __launch_bounds__(TcCfg<FMT, LEAF, SPLITMODE>::kThreads, 1)
             break;
           }
           run = runs_opened++;
-          const int buf = run & 1;
-          if (!wait_ab(&acc_empty[buf], (((uint32_t)run >> 1) & 1u) ^ 1u, abort_flag, p.status)) {
+          const int buf = run % NA;
+          if (!wait_ab(&acc_empty[buf], (((uint32_t)(run / NA)) & 1u) ^ 1u, abort_flag, p.status)) {
             ok = false;
             break;
           }
@@ -428,6 +449,8 @@ __global__ void __launch_bounds__(TcCfg<FMT, LEAF, SPLITMODE>::kThreads, 1)
     const int row = Cfg::M == 128 ? quarter * 32 + lane : quarter * 16 + lane;
     const bool lane_has_row = Cfg::M == 128 || lane < 16;
     const float lo_w = 1.0f / (float)(1 << L::kLoShift);
+    uint8_t* stage_row = smem + Cfg::kEpiOffset +
+                         ((size_t)(warp - kFirstEpiWarp) * Cfg::kEpiRows + lane) * Cfg::kEpiRowBytes;
     float acc[NC];
 #pragma unroll
     for (int c = 0; c < NC; ++c) acc[c] = 0.0f;
@@ -443,8 +466,8 @@ __global__ void __launch_bounds__(TcCfg<FMT, LEAF, SPLITMODE>::kThreads, 1)
         slot_phase ^= 1u;
       }
       if (r.tile < 0) break;
-      const int buf = run & 1;
-      if (!wait_ab(&acc_full[buf], ((uint32_t)run >> 1) & 1u, abort_flag, p.status)) break;
+      const int buf = run % NA;
+      if (!wait_ab(&acc_full[buf], ((uint32_t)(run / NA)) & 1u, abort_flag, p.status)) break;
       fence_after_sync();
       const float scale = ldexpf(1.0f, r.s);
       const uint32_t base = tmem + (uint32_t)(buf * Cfg::kAccCols + col0) +
@@ -469,7 +492,7 @@ __global__ void __launch_bounds__(TcCfg<FMT, LEAF, SPLITMODE>::kThreads, 1)
       if (lane == 0) mbar_arrive(&acc_empty[buf]);
       ++run;
       if (r.last) {
-        const Inst& in = p.R.at(inst_of_tile(p.R, r.tile));
+        const Inst& in = p.R.at(inst_of(p.R, p.Bf, r.tile));
         const int bd = in.bd;
         const int64_t n = in.n, lt = (int64_t)r.tile - in.tile0;
         const int i = (int)(lt / bd), j = (int)(lt % bd);
@@ -477,11 +500,19 @@ __global__ void __launch_bounds__(TcCfg<FMT, LEAF, SPLITMODE>::kThreads, 1)
         if (lane_has_row && gr < n) {
           float* dst = in.C + gr * n + (int64_t)j * LEAF + col0;
           const int64_t cols = n - (int64_t)j * LEAF - col0;
-          if (cols >= NC && (n & 3) == 0) {
+          if ((n & 3) == 0) {
+            // the row goes through shared memory and leaves as one bulk copy
+            // (n % 4 == 0: 16-byte aligned, cols % 4 == 0)
+            if (cols > 0) {
+              bulk_wait_read0();   // this lane's previous row has left the buffer
 #pragma unroll
-            for (int c = 0; c < NC; c += 4)
-              *reinterpret_cast<float4*>(dst + c) =
-                  make_float4(acc[c], acc[c + 1], acc[c + 2], acc[c + 3]);
+              for (int c = 0; c < NC; c += 4)
+                *reinterpret_cast<float4*>(stage_row + 4 * c) =
+                    make_float4(acc[c], acc[c + 1], acc[c + 2], acc[c + 3]);
+              fence_proxy_async_smem();
+              bulk_s2g(dst, smem_u32(stage_row), (uint32_t)(cols < NC ? cols : NC) * 4u);
+              bulk_commit();
+            }
           } else {
 #pragma unroll
             for (int c = 0; c < NC; ++c)
@@ -494,6 +525,7 @@ __global__ void __launch_bounds__(TcCfg<FMT, LEAF, SPLITMODE>::kThreads, 1)
     }
   }
 
+  if (warp >= kFirstEpiWarp) bulk_wait0();   // C rows written before the kernel ends
   fence_before_sync();
   __syncthreads();
   if (warp == 1) {
@@ -503,36 +535,42 @@ __global__ void __launch_bounds__(TcCfg<FMT, LEAF, SPLITMODE>::kThreads, 1)
   }
 }
 
-// Zeros for every tile without survivors: each warp reads the counts of 32
-// consecutive global tiles (coalesced) and writes the empty ones, row by row.
+// Zeros for every tile without survivors: the plan lists them after the
+// non-empty tiles in `order`.  One warp per tile (many independent warps keep
+// enough stores in flight for the HBM write rate); lane l owns column group
+// l % (leaf/4) and every (32 / (leaf/4))-th row, 16-byte streaming stores.
+template <int LEAF>
 __global__ void __launch_bounds__(256)
-    zero_tiles_kernel(InstRef R, PlanBuffers Bf, int leaf) {
+    zero_tiles_kernel(InstRef R, PlanBuffers Bf) {
+  constexpr int kPerRow = LEAF / 4;                         // float4 per tile row
+  constexpr int kRowStep = kPerRow >= 32 ? 1 : 32 / kPerRow; // rows per warp store
+  constexpr int kColSteps = kPerRow >= 32 ? kPerRow / 32 : 1;
   const int lane = threadIdx.x & 31;
-  const int64_t gw = (int64_t)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+  const int my_c4 = kPerRow >= 32 ? lane : lane % kPerRow;
+  const int my_r = kPerRow >= 32 ? 0 : lane / kPerRow;
+  const int ne = Bf.bdev->nonempty;
   const int64_t nw = (int64_t)gridDim.x * (blockDim.x / 32);
-  for (int64_t g0 = gw * 32; g0 < Bf.tiles; g0 += nw * 32) {
-    const int64_t gl = g0 + lane;
-    const bool empty = gl < Bf.tiles && Bf.cnt[gl] == 0;
-    unsigned mask = __ballot_sync(0xffffffffu, empty);
-    while (mask) {
-      const int b = __ffs(mask) - 1;
-      mask &= mask - 1;
-      const int64_t g = g0 + b;
-      const Inst& in = R.at(inst_of_tile(R, g));
-      const int64_t n = in.n, lt = g - in.tile0;
-      const int64_t r0 = (lt / in.bd) * leaf, c0 = (lt % in.bd) * leaf;
-      const int64_t rows = min((int64_t)leaf, n - r0), cols = min((int64_t)leaf, n - c0);
-      float* C = in.C;
-      if ((n & 3) == 0 && cols == leaf) {
-        const int per_row = leaf / 4;
-        for (int e = lane; e < rows * per_row; e += 32) {
-          const int64_t r = e / per_row, c4 = e % per_row;
-          *reinterpret_cast<float4*>(C + (r0 + r) * n + c0 + 4 * c4) =
-              make_float4(0.f, 0.f, 0.f, 0.f);
-        }
-      } else {
-        for (int64_t e = lane; e < rows * cols; e += 32) C[(r0 + e / cols) * n + c0 + e % cols] = 0.f;
+  for (int64_t e = ne + ((int64_t)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32); e < Bf.tiles;
+       e += nw) {
+    const int64_t g = Bf.order[e];
+    const Inst& in = R.at(inst_of(R, Bf, g));
+    const int64_t n = in.n, lt = g - in.tile0;
+    const int bd = in.bd;
+    const int ti = (int)(lt / bd), tj = (int)(lt - (int64_t)ti * bd);
+    const int64_t r0 = (int64_t)ti * LEAF, c0 = (int64_t)tj * LEAF;
+    const int rows = (int)min((int64_t)LEAF, n - r0), cols = (int)min((int64_t)LEAF, n - c0);
+    float* C = in.C;
+    if ((n & 3) == 0) {   // then cols % 4 == 0 and every float4 is aligned
+#pragma unroll
+      for (int cs = 0; cs < kColSteps; ++cs) {
+        const int c4 = my_c4 + 32 * cs;
+        if (4 * c4 >= cols) continue;
+        float4* p = reinterpret_cast<float4*>(C + (r0 + my_r) * n + c0 + 4 * c4);
+        const int64_t step = (int64_t)kRowStep * n / 4;
+        for (int r = my_r; r < rows; r += kRowStep, p += step) __stcs(p, make_float4(0.f, 0.f, 0.f, 0.f));
       }
+    } else {
+      for (int u = lane; u < rows * cols; u += 32) C[(r0 + u / cols) * n + c0 + u % cols] = 0.f;
     }
   }
 }
@@ -558,16 +596,21 @@ cudaError_t launch_zero_empty_tiles(const InstRef& ref, const PlanBuffers& b, in
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const int64_t warps = (b.tiles + 31) / 32;
-  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((warps + 7) / 8, (int64_t)sms * 8));
-  zero_tiles_kernel<<<grid, 256, 0, s>>>(ref, b, leaf);
+  // one wave of warps (the number of empty tiles is known on the device only)
+  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((b.tiles + 7) / 8, (int64_t)sms * 8));
+  switch (leaf) {
+    case 32: zero_tiles_kernel<32><<<grid, 256, 0, s>>>(ref, b); break;
+    case 64: zero_tiles_kernel<64><<<grid, 256, 0, s>>>(ref, b); break;
+    case 128: zero_tiles_kernel<128><<<grid, 256, 0, s>>>(ref, b); break;
+    default: return cudaErrorInvalidValue;
+  }
   return cudaPeekAtLastError();
 }
 
 cudaError_t launch_multiply_tc(spamm_precision_t prec, int leaf, const InstRef& ref,
                                const PlanBuffers& b, const OperandImages& img, int32_t* status,
-                               cudaStream_t s) {
-  TcParams prm{ref, b, img, status};
+                               int schedule, cudaStream_t s) {
+  TcParams prm{ref, b, img, status, schedule == kScheduleDynamic ? 1 : 0};
   const bool l64 = leaf == 64;
   switch (prec) {
     case SPAMM_BF16:

@@ -165,6 +165,7 @@ __global__ void __launch_bounds__(kPrepThreads)
   double qa = 0.0, qb = 0.0;
   if (idx < total) {
     const double a = in.nA[idx], b = in.nB[idx];
+    Bf.tile_inst[in.tile0 + idx] = ii;
     Bf.sA[in.tile0 + idx] = make_screen(a);
     const int64_t k = idx / bd, j = idx % bd;
     Bf.sBT[in.tile0 + j * bd + k] = make_screen(b);
@@ -293,8 +294,6 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32)
     if (lane == 0) {
       const int64_t g = in.tile0 + t;
       Bf.cnt[g] = count;
-      Bf.needA[g] = 0;   // the fill kernel sets the blocks survivors use
-      Bf.needB[g] = 0;
       if (count > 0) atomicAdd(&Bf.bdev->hist[count], 1);
       ext_add(wb1, tot.m, tot.e);
       ext_add(wb2, __fmul_rn(tot.m, tot.m), 2 * tot.e);
@@ -389,7 +388,11 @@ __global__ void __launch_bounds__(kFinThreads)
     baseS += Bf.part_S[in.count0 + q];
   }
   long long totNE;
-  (void)block_exclusive_scan<long long>((long long)locNE, s_ll, totNE);
+  long long baseNE = block_exclusive_scan<long long>((long long)locNE, s_ll, totNE);
+  for (int q = p0; q < p1; ++q) {
+    Bf.ne_cta_base[in.count0 + q] = (int)baseNE;
+    baseNE += Bf.part_ne[in.count0 + q];
+  }
   // max and the extended-range sums (FP32 only)
   s_i[tid] = locK;
   s_x[tid] = locB1;
@@ -483,6 +486,16 @@ __global__ void __launch_bounds__(kFinThreads)
     const long long start = block_exclusive_scan<long long>(h, s_ll, tot_ne);
     if (c >= 1) Bf.bdev->cursor[c] = (int)start;
     if (tid == 0) Bf.bdev->nonempty = (int)tot_ne;
+    // non-empty tiles before each instance (the empty-tile ranks of the fill kernel)
+    long long carry = 0;
+    for (int i0 = 0; i0 < R.count; i0 += kFinThreads) {
+      const int i = i0 + tid;
+      const long long v = i < R.count ? (long long)__ldcg(&R.at(i).pd->nonempty) : 0;
+      long long tot;
+      const long long ex = block_exclusive_scan<long long>(v, s_ll, tot);
+      if (i < R.count) R.at(i).pd->ne_base = (int)(carry + ex);
+      carry += tot;
+    }
   }
 }
 
@@ -492,12 +505,14 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32)
   const int warp = threadIdx.x / 32, lane = threadIdx.x & 31;
   const int ii = inst_of_count_cta(R, blockIdx.x);
   const Inst& in = R.at(ii);
-  const int bd = in.bd, split = in.split;
+  const int bd = in.bd, split = in.split, quant = in.quant;
   const TauScreen T = in.T;
   const double* nA = in.nA;
   const double* nB = in.nB;
   const int64_t tiles = (int64_t)bd * bd;
   const int64_t lt0 = (int64_t)(blockIdx.x - in.count0) * kTilesPerCta;
+  uint32_t* bitsA = Bf.need_bits;
+  uint32_t* bitsB = Bf.need_bits + Bf.need_words;
   if (warp == 0) {   // first k_idx slot of each of the CTA's tiles (kTilesPerCta == 32 lanes)
     const int64_t t = lt0 + lane;
     const int c = t < tiles ? Bf.cnt[in.tile0 + t] : 0;
@@ -509,6 +524,15 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32)
     const int beg = Bf.cta_base[blockIdx.x] + incl - c;
     s_beg[lane] = beg;
     if (t < tiles) Bf.tile_beg[in.tile0 + t] = beg;
+    // empty tiles go after all non-empty ones, in increasing global order: the
+    // rank of an empty tile is its number minus the non-empty tiles before it
+    const unsigned ne_mask = __ballot_sync(0xffffffffu, c > 0);
+    if (t < tiles && c == 0) {
+      const int64_t g = in.tile0 + t;
+      const int64_t ne_before = (int64_t)in.pd->ne_base + Bf.ne_cta_base[blockIdx.x] +
+                                __popc(ne_mask & ((1u << lane) - 1u));
+      Bf.order[Bf.bdev->nonempty + (g - ne_before)] = (int)g;
+    }
   }
   __syncthreads();
   const double inv = in.pd->inv_ab;
@@ -543,10 +567,27 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32)
                                       nB + (int64_t)k * bd + j, inv) >= m)
           v |= kSplitFlag;
         Bf.k_idx[base + __popc(ball & ((1u << lane) - 1u))] = v;
-        Bf.needA[in.tile0 + (int64_t)i * bd + k] = 1;   // benign: every writer stores 1
-        Bf.needB[in.tile0 + (int64_t)k * bd + j] = 1;
       }
       base += __popc(ball);
+      if (quant && ball) {
+        // list the A and B blocks of surviving triples, each once over the plan
+        const int64_t ga = in.tile0 + (int64_t)i * bd + k, gb = in.tile0 + (int64_t)k * bd + j;
+        bool newA = false, newB = false;
+        if (s) {
+          const uint32_t bitA = 1u << (ga & 31), bitB = 1u << (gb & 31);
+          newA = (atomicOr(&bitsA[ga >> 5], bitA) & bitA) == 0u;
+          newB = (atomicOr(&bitsB[gb >> 5], bitB) & bitB) == 0u;
+        }
+        const unsigned ma = __ballot_sync(0xffffffffu, newA), mb = __ballot_sync(0xffffffffu, newB);
+        if (ma | mb) {
+          int nb = 0;
+          if (lane == 0) nb = atomicAdd(&Bf.bdev->need_count, __popc(ma) + __popc(mb));
+          nb = __shfl_sync(0xffffffffu, nb, 0);
+          const unsigned lt = (1u << lane) - 1u;
+          if (newA) Bf.need_list[nb + __popc(ma & lt)] = (uint32_t)ga;
+          if (newB) Bf.need_list[nb + __popc(ma) + __popc(mb & lt)] = (uint32_t)gb | 0x80000000u;
+        }
+      }
     }
   }
 }
@@ -582,8 +623,10 @@ size_t plan_layout(Inst* insts, int count, PlanBuffers* b, char* base) {
   t.kslots = kslots;
   t.prep_ctas = prep;
   t.count_ctas = cnt;
+  t.need_words = (tiles + 31) / 32;
   t.pd = reinterpret_cast<PlanDevice*>(take((size_t)count * sizeof(PlanDevice)));
   t.bdev = reinterpret_cast<BatchDevice*>(take(sizeof(BatchDevice)));
+  t.need_bits = reinterpret_cast<uint32_t*>(take((size_t)(2 * t.need_words) * sizeof(uint32_t)));
   t.sA = reinterpret_cast<Screen*>(take((size_t)tiles * sizeof(Screen)));
   t.sBT = reinterpret_cast<Screen*>(take((size_t)tiles * sizeof(Screen)));
   t.part_a = reinterpret_cast<double*>(take((size_t)prep * sizeof(double)));
@@ -594,12 +637,13 @@ size_t plan_layout(Inst* insts, int count, PlanBuffers* b, char* base) {
   t.part_b1 = reinterpret_cast<ExtSum*>(take((size_t)cnt * sizeof(ExtSum)));
   t.part_b2 = reinterpret_cast<ExtSum*>(take((size_t)cnt * sizeof(ExtSum)));
   t.cta_base = reinterpret_cast<int*>(take((size_t)cnt * sizeof(int)));
+  t.ne_cta_base = reinterpret_cast<int*>(take((size_t)cnt * sizeof(int)));
   t.cnt = reinterpret_cast<int*>(take((size_t)tiles * sizeof(int)));
   t.tile_beg = reinterpret_cast<int*>(take((size_t)tiles * sizeof(int)));
   t.order = reinterpret_cast<int*>(take((size_t)tiles * sizeof(int)));
   t.k_idx = reinterpret_cast<uint16_t*>(take((size_t)kslots * sizeof(uint16_t)));
-  t.needA = reinterpret_cast<uint8_t*>(take((size_t)tiles));
-  t.needB = reinterpret_cast<uint8_t*>(take((size_t)tiles));
+  t.tile_inst = reinterpret_cast<int*>(take((size_t)tiles * sizeof(int)));
+  t.need_list = reinterpret_cast<uint32_t*>(take((size_t)(2 * tiles) * sizeof(uint32_t)));
   for (int i = 0; i < count; ++i) insts[i].pd = t.pd ? t.pd + i : nullptr;
   if (b) *b = t;
   return (off + 255) / 256 * 256;
@@ -616,7 +660,8 @@ InstRef make_ref(const Inst* host_insts, const Inst* dev_table, int count) {
 cudaError_t run_plan(const InstRef& ref, const PlanBuffers& b, cudaStream_t s) {
   // clear the per-instance statistics and the batch-wide order state (laid
   // out back to back, one memset)
-  const size_t clear = reinterpret_cast<const char*>(b.bdev + 1) - reinterpret_cast<const char*>(b.pd);
+  const size_t clear = reinterpret_cast<const char*>(b.need_bits + 2 * b.need_words) -
+                       reinterpret_cast<const char*>(b.pd);
   cudaError_t e = cudaMemsetAsync(b.pd, 0, clear, s);
   if (e != cudaSuccess) return e;
   prep_kernel<<<b.prep_ctas, kPrepThreads, 0, s>>>(ref, b);

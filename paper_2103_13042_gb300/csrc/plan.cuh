@@ -30,6 +30,7 @@ struct PlanDevice {
   double bound1, bound2, valid_ratio;
   long long survivors, flagged;
   int max_tile, nonempty, flag_exp;
+  int ne_base;                              // non-empty tiles of the instances before this one
   unsigned int ticket;                      // prep CTAs of this instance that have finished
   double bin_sum[kFlagBins];                // surviving products per relative binade
   unsigned long long bin_cnt[kFlagBins];
@@ -41,7 +42,13 @@ struct BatchDevice {
   int cursor[kMaxBd + 2];   // next slot of each count's bucket in `order`
   int nonempty;             // non-empty tiles over all instances
   unsigned int ticket;      // finalize CTAs that have finished
+  int mul_ticket;           // next slot of `order` to hand out (dynamic multiply schedule)
+  int need_count;           // entries of the needed-block list
 };
+
+// Multiply schedules: CTAs walk the longest-first order with a fixed
+// interleave (static) or take 32-slot chunks from a global counter (dynamic).
+enum Schedule { kScheduleStatic = 0, kScheduleDynamic = 1 };
 
 // Extended-range FP32 sum: value = m * 2^e with an integer exponent.
 struct ExtSum {
@@ -59,6 +66,7 @@ struct Inst {
   int64_t n;
   int bd;
   int split;            // 1: BF16/FP16 split mode (dominant triples get hi+lo)
+  int quant;            // 1: the multiply rounds operands (build the needed-block list)
   int64_t tile0;        // first global tile / block index
   int64_t kidx0;        // first k_idx slot
   int prep0;            // first CTA of this instance in the prep grid
@@ -111,15 +119,24 @@ struct PlanBuffers {
   ExtSum* part_b1;     // sums of skipped relative products
   ExtSum* part_b2;     // sums of their per-tile squares
   int* cta_base;       // [count_ctas] first k_idx slot of the CTA's tiles
+  int* ne_cta_base;    // [count_ctas] non-empty tiles of the instance's earlier CTAs
   int* cnt;            // [tiles] survivors per tile
   int* tile_beg;       // [tiles] absolute first k_idx slot of the tile
-  int* order;          // [tiles] global ids of the non-empty tiles, most survivors first
+  int* order;          // [tiles] global ids: the non-empty tiles, most survivors first, then
+                       // the empty tiles in increasing order
   uint16_t* k_idx;     // [kslots] surviving k per tile, increasing (bit 15: split triple)
-  uint8_t* needA;      // [tiles] 1 if block A[i,k] takes part in some surviving triple
-  uint8_t* needB;      // [tiles] 1 if block B[k,j] takes part in some surviving triple
-  PlanDevice* pd;      // [instances]
+  int* tile_inst;      // [tiles] instance of each global tile / block
+  uint32_t* need_bits; // [2 * words] bit g: block g of A (first half) / B (second half) is used
+  uint32_t* need_list; // [2 * tiles] used blocks, each once: g (A) or g | 2^31 (B)
+  int64_t need_words;  // 32-bit words per operand in need_bits
+  PlanDevice* pd;      // [instances]; pd, bdev and need_bits are contiguous (one memset)
   BatchDevice* bdev;
 };
+
+// Instance of a global tile (or leaf block) number.
+__device__ __forceinline__ int inst_of(const InstRef& r, const PlanBuffers& b, int64_t g) {
+  return r.count <= 1 ? 0 : b.tile_inst[g];
+}
 
 // Grid sizes of the plan kernels for one instance of bd x bd tiles.
 int prep_ctas_of(int bd);
@@ -152,7 +169,7 @@ cudaError_t launch_normmap_jobs(const NormJob* dev_jobs, int njobs, int total_ct
                                 cudaStream_t s);
 
 cudaError_t launch_multiply_simt(const InstRef& ref, const PlanBuffers& b, int leaf,
-                                 cudaStream_t s);
+                                 int schedule, cudaStream_t s);
 
 cudaError_t launch_frobenius_diff(const float* X, const float* Y, int64_t count, double* partials,
                                   int nparts, double* out, cudaStream_t s);

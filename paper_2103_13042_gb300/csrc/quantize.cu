@@ -1,11 +1,10 @@
 // Operand rounding for the tensor-core multiply (spec mixed precision on
 // top of the paper's FP16 tensor-core kernel, Section 3.3 / Algorithm 3).
 //
-// For every leaf block that some surviving triple uses (the plan's need flags)
-// one CTA stages the FP32 block in shared memory, finds e = frexp exponent of
-// its largest magnitude, scales by 2^-e (exact), rounds to nearest-even in the
-// operand format (hi) and, in split modes, rounds the exact residual scaled by
-// 2^s_lo (lo).  The result is written directly as the K-major, 128-byte
+// For every leaf block that some surviving triple uses (the plan's list of
+// needed blocks) one warp finds e = frexp exponent of its largest magnitude,
+// scales by 2^-e (exact), rounds to nearest-even in the operand format (hi)
+// and, in split modes, rounds the exact residual scaled by 2^s_lo (lo).  The result is written directly as the K-major, 128-byte
 // swizzled image the MMA reads: chunk c of a block holds K elements
 // [c*kc, (c+1)*kc) (kc = 128 bytes / element size) for every row, 128 bytes
 // per row, 16-byte pieces XOR-swizzled by (row mod 8).  A blocks keep their
@@ -20,7 +19,6 @@ namespace spamm {
 namespace {
 
 constexpr int kThreads = 256;
-constexpr int kChunk = 64;   // candidate blocks per need-flag scan (two warps)
 
 // Round to nearest even, keeping 10 explicit significand bits (TF32), on the
 // IEEE bit pattern; NaN/Inf pass through unchanged.
@@ -51,93 +49,98 @@ __device__ __forceinline__ uint32_t pack2(float a, float b) {
   }
 }
 
+// Loads X[r][c] of an n x n matrix, 0 outside it.
+__device__ __forceinline__ float ld_or_zero(const float* X, int64_t n, int64_t r, int64_t c) {
+  return (r < n && c < n) ? __ldg(X + r * n + c) : 0.0f;
+}
+
+// One warp per used leaf block (the plan's needed-block list).  Pass 1 reads
+// the block row-major (coalesced float4) for its largest magnitude; pass 2
+// re-reads it (now from L2) in the order of the image: lane l takes 16-byte
+// piece l % 8 of image row 4m + l / 8 (fewer rows per step when a row spans
+// several 128-byte chunks), so each warp store covers whole 128-byte rows.
 template <uint32_t FMT, int LEAF, bool SPLIT>
 __global__ void __launch_bounds__(kThreads)
     quantize_kernel(InstRef R, PlanBuffers Bf, OperandImages img) {
   using L = TcLayout<FMT, LEAF>;
-  constexpr int ELT = L::kElt, KC = L::kKc, NCH = L::kNch;
-  constexpr int PER16 = 16 / ELT;                 // elements per 16-byte piece
-  constexpr int UNITS = NCH * LEAF * 8;           // 16-byte pieces per block image
-  extern __shared__ float tile[];                 // [LEAF][LEAF + 1]
-  __shared__ float warp_max[kThreads / 32];
-  __shared__ int s_list[kChunk];
-  const int64_t tiles = Bf.tiles;      // global blocks of A (and of B)
-  const uint8_t* __restrict__ needA = Bf.needA;
-  const uint8_t* __restrict__ needB = Bf.needB;
+  constexpr int KC = L::kKc;                 // K elements per 128-byte chunk row
+  constexpr int PER16 = 16 / L::kElt;        // elements per 16-byte piece
+  constexpr int PPR = LEAF / PER16;          // pieces per image row
+  constexpr int UNITS = LEAF * PPR;          // pieces per block image
+  static_assert(UNITS % 32 == 0, "whole warps of pieces");
+  const int lane = threadIdx.x & 31;
+  const int64_t gw = ((int64_t)blockIdx.x * kThreads + threadIdx.x) / 32;
+  const int64_t nw = (int64_t)gridDim.x * (kThreads / 32);
+  const int count = Bf.bdev->need_count;
   const float lo_scale = (float)(1 << L::kLoShift);
 
-  // Candidates (A blocks, then B blocks) in chunks of kChunk: the first two
-  // warps read one need flag each, thread 0 lists the needed ones in order,
-  // then the CTA rounds them one block at a time.
-  const int64_t nchunks = (2 * tiles + kChunk - 1) / kChunk;
-  for (int64_t chunk = blockIdx.x; chunk < nchunks; chunk += gridDim.x) {
-    if (threadIdx.x < kChunk) {
-      const int64_t cand = chunk * kChunk + threadIdx.x;
-      bool need = false;
-      if (cand < 2 * tiles) need = cand >= tiles ? needB[cand - tiles] != 0 : needA[cand] != 0;
-      s_list[threadIdx.x] = need ? 1 : 0;
-    }
-    __syncthreads();
-    // compact (kChunk entries; thread 0 is enough and keeps the order)
-    __shared__ int s_total;
-    if (threadIdx.x == 0) {
-      int tot = 0;
-      for (int q = 0; q < kChunk; ++q)
-        if (s_list[q]) s_list[tot++] = q;
-      s_total = tot;
-    }
-    __syncthreads();
-    const int total = s_total;
-  for (int li = 0; li < total; ++li) {
-    const int64_t w = chunk * kChunk + s_list[li];
-    const bool isB = w >= tiles;
-    const int64_t blk = isB ? w - tiles : w;      // global block number
-    const Inst& in = R.at(inst_of_tile(R, blk));
+  for (int64_t idx = gw; idx < count; idx += nw) {
+    const uint32_t ent = Bf.need_list[idx];
+    const bool isB = (ent >> 31) != 0;
+    const int64_t blk = (int64_t)(ent & 0x7fffffffu);   // global block number
+    const Inst& in = R.at(inst_of(R, Bf, blk));
     const int64_t n = in.n, lb = blk - in.tile0;
-    const int bd = in.bd;
-    const float* X = isB ? in.B : in.A;
-    const int64_t r0 = (lb / bd) * LEAF, c0 = (lb % bd) * LEAF;
+    const float* __restrict__ X = isB ? in.B : in.A;
+    const int64_t r0 = (lb / in.bd) * LEAF, c0 = (lb % in.bd) * LEAF;
+    const bool full = (n & 3) == 0 && r0 + LEAF <= n && c0 + LEAF <= n;
 
-    // stage the block (zero outside the matrix) and its largest magnitude;
-    // all loads are issued before the first shared-memory store
-    constexpr int PER_T = LEAF * LEAF / kThreads;
-    float vals[PER_T];
-#pragma unroll
-    for (int q = 0; q < PER_T; ++q) {
-      const int e = threadIdx.x + q * kThreads;
-      const int64_t gr = r0 + e / LEAF, gc = c0 + e % LEAF;
-      vals[q] = (gr < n && gc < n) ? __ldg(X + gr * n + gc) : 0.0f;
-    }
+    // pass 1: largest magnitude (NaN ignored, as fmaxf does)
     float mx = 0.0f;
-#pragma unroll
-    for (int q = 0; q < PER_T; ++q) {
-      const int e = threadIdx.x + q * kThreads;
-      tile[(e / LEAF) * (LEAF + 1) + e % LEAF] = vals[q];
-      mx = fmaxf(mx, fabsf(vals[q]));
+    if (full) {
+      constexpr int kIters = LEAF * LEAF / 128;   // float4 per lane
+#pragma unroll 8
+      for (int it = 0; it < kIters; ++it) {
+        const int e = (it * 32 + lane) * 4;
+        const float4 v = __ldg(reinterpret_cast<const float4*>(X + (r0 + e / LEAF) * n + c0 + e % LEAF));
+        mx = fmaxf(mx, fmaxf(fmaxf(fabsf(v.x), fabsf(v.y)), fmaxf(fabsf(v.z), fabsf(v.w))));
+      }
+    } else {
+      for (int e = lane; e < LEAF * LEAF; e += 32)
+        mx = fmaxf(mx, fabsf(ld_or_zero(X, n, r0 + e / LEAF, c0 + e % LEAF)));
     }
-    for (int off = 16; off > 0; off >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, off));
-    if ((threadIdx.x & 31) == 0) warp_max[threadIdx.x / 32] = mx;
-    __syncthreads();
-    mx = 0.0f;
 #pragma unroll
-    for (int q = 0; q < kThreads / 32; ++q) mx = fmaxf(mx, warp_max[q]);
-    int e = 0;
-    if (mx > 0.0f && mx <= 3.402823466e38f) frexpf(mx, &e);
-    if (threadIdx.x == 0) (isB ? img.eb : img.ea)[blk] = e;
+    for (int off = 16; off > 0; off >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+    int ex = 0;
+    if (mx > 0.0f && mx <= 3.402823466e38f) frexpf(mx, &ex);
+    if (lane == 0) (isB ? img.eb : img.ea)[blk] = ex;
+    // 2^-ex as a float when it is a normal number (the usual case), else ldexpf
+    const bool pow2_ok = ex >= -126 && ex <= 126;
+    const float scale = pow2_ok ? __int_as_float((127 - ex) << 23) : 1.0f;
 
     uint8_t* hi_img = (isB ? img.b_hi : img.a_hi) + blk * (int64_t)L::kBlockBytes;
     uint8_t* lo_img = SPLIT ? (isB ? img.b_lo : img.a_lo) + blk * (int64_t)L::kBlockBytes : nullptr;
-    for (int u = threadIdx.x; u < UNITS; u += kThreads) {
-      const int piece = u % 8, row = (u / 8) % LEAF, ch = u / (8 * LEAF);
+#pragma unroll 2
+    for (int u = lane; u < UNITS; u += 32) {
+      const int row = u / PPR, kp = u % PPR;
+      const int k0 = kp * PER16;
+      float x[PER16];
+      if (!isB) {   // image row = block row, K along the block's columns
+        if (full) {
+#pragma unroll
+          for (int q = 0; q < PER16; q += 4) {
+            const float4 v = __ldg(reinterpret_cast<const float4*>(X + (r0 + row) * n + c0 + k0 + q));
+            x[q] = v.x; x[q + 1] = v.y; x[q + 2] = v.z; x[q + 3] = v.w;
+          }
+        } else {
+#pragma unroll
+          for (int q = 0; q < PER16; ++q) x[q] = ld_or_zero(X, n, r0 + row, c0 + k0 + q);
+        }
+      } else {      // image row = block column, K along the block's rows
+        if (full) {
+#pragma unroll
+          for (int q = 0; q < PER16; ++q) x[q] = __ldg(X + (r0 + k0 + q) * n + c0 + row);
+        } else {
+#pragma unroll
+          for (int q = 0; q < PER16; ++q) x[q] = ld_or_zero(X, n, r0 + k0 + q, c0 + row);
+        }
+      }
       float hv[PER16], lv[PER16];
 #pragma unroll
       for (int q = 0; q < PER16; ++q) {
-        const int k = ch * KC + piece * PER16 + q;
-        const float x = isB ? tile[k * (LEAF + 1) + row] : tile[row * (LEAF + 1) + k];
-        const float s = ldexpf(x, -e);
-        const float h = round_op<FMT>(s);
+        const float sc = pow2_ok ? __fmul_rn(x[q], scale) : ldexpf(x[q], -ex);
+        const float h = round_op<FMT>(sc);
         hv[q] = h;
-        if constexpr (SPLIT) lv[q] = round_op<FMT>(__fmul_rn(__fsub_rn(s, h), lo_scale));
+        if constexpr (SPLIT) lv[q] = round_op<FMT>(__fmul_rn(__fsub_rn(sc, h), lo_scale));
       }
       uint4 ph, pl;
       if constexpr (FMT == tc::kFmtTF32) {
@@ -153,31 +156,25 @@ __global__ void __launch_bounds__(kThreads)
           pl = make_uint4(pack2<FMT>(lv[0], lv[1]), pack2<FMT>(lv[2], lv[3]),
                           pack2<FMT>(lv[4], lv[5]), pack2<FMT>(lv[6], lv[7]));
       }
-      const uint32_t off = ch * (LEAF * 128) + tc::sw128_offset(row, piece);
+      const uint32_t off = (uint32_t)(k0 / KC) * (LEAF * 128) + tc::sw128_offset(row, (k0 % KC) / PER16);
       *reinterpret_cast<uint4*>(hi_img + off) = ph;
       if constexpr (SPLIT) *reinterpret_cast<uint4*>(lo_img + off) = pl;
     }
-    __syncthreads();   // the tile is reused by the next block
-  }
-    __syncthreads();   // s_list / s_total are rewritten by the next chunk
   }
 }
 
 template <uint32_t FMT, int LEAF, bool SPLIT>
 cudaError_t launch_q(const InstRef& ref, const PlanBuffers& b, const OperandImages& img,
                      cudaStream_t s) {
-  const size_t smem = (size_t)LEAF * (LEAF + 1) * sizeof(float);
-  cudaFuncSetAttribute(quantize_kernel<FMT, LEAF, SPLIT>,
-                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   int dev = 0, sms = 0, per_sm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, quantize_kernel<FMT, LEAF, SPLIT>,
-                                                kThreads, smem);
-  const int64_t chunks = (2 * b.tiles + kChunk - 1) / kChunk;
-  const int grid =
-      (int)std::max<int64_t>(1, std::min<int64_t>(chunks, (int64_t)sms * std::max(1, per_sm)));
-  quantize_kernel<FMT, LEAF, SPLIT><<<grid, kThreads, smem, s>>>(ref, b, img);
+                                                kThreads, 0);
+  // the list length is known on the device only: one full wave of warps
+  const int64_t cap = (2 * b.tiles + kThreads / 32 - 1) / (kThreads / 32);
+  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(cap, (int64_t)sms * std::max(1, per_sm)));
+  quantize_kernel<FMT, LEAF, SPLIT><<<grid, kThreads, 0, s>>>(ref, b, img);
   return cudaPeekAtLastError();
 }
 

@@ -33,7 +33,7 @@ cudaError_t launch_quantize(spamm_precision_t prec, int leaf, const InstRef& ref
 
 cudaError_t launch_multiply_tc(spamm_precision_t prec, int leaf, const InstRef& ref,
                                const PlanBuffers& b, const OperandImages& img, int32_t* status,
-                               cudaStream_t s);
+                               int schedule, cudaStream_t s);
 
 // Writes zeros to every tile without survivors, of every instance.
 cudaError_t launch_zero_empty_tiles(const InstRef& ref, const PlanBuffers& b, int leaf,

@@ -193,3 +193,46 @@ def test_batch_rejects_bad_problems():
         batch.run([A, A], [B, B], [C, torch.zeros_like(C)], [0.0, float("nan")])
     assert e.value.code == 1
     batch.close()
+
+
+@pytest.mark.parametrize("prec", [P.FP32, P.BF16_SPLIT])
+def test_dynamic_schedule_and_timings(prec):
+    """The dynamic multiply schedule gives the same C as the static one; phase timings exist."""
+    leaf = 64
+    specs, pairs = _instances(6, 31337, 64, 800, 0.5)
+    taus = _taus(pairs, leaf, 0.5)
+    ns = [a.shape[0] for a, _ in pairs]
+    As = [dev(a) for a, _ in pairs]
+    Bs = [dev(b) for _, b in pairs]
+    Cs = [torch.full_like(A, float("nan")) for A in As]
+    Cd = [torch.full_like(A, float("nan")) for A in As]
+    st = P.Batch(ns, leaf, prec, graph=False)
+    dy = P.Batch(ns, leaf, prec, graph=True, dynamic=True)
+    tm = P.Batch(ns, leaf, prec, graph=True, dynamic=True, timing=True)
+    st.run(As, Bs, Cs, taus, 1e-6)
+    for _ in range(2):   # a second run re-uses the counter: it must be reset
+        dy.run(As, Bs, Cd, taus, 1e-6)
+        torch.cuda.synchronize()
+        for i in range(len(As)):
+            assert torch.equal(Cs[i], Cd[i]), i
+    Ct = [torch.full_like(A, float("nan")) for A in As]
+    tm.run(As, Bs, Ct, taus, 1e-6)
+    t = tm.timings()
+    assert all(v > 0 for v in t.values()), t
+    for i in range(len(As)):
+        assert torch.equal(Cs[i], Ct[i]), i
+    for b in (st, dy, tm):
+        b.close()
+
+
+def test_autotune_returns_a_measured_candidate():
+    specs, pairs = _instances(5, 2718, 128, 700, 0.5)
+    As = [dev(a) for a, _ in pairs]
+    Bs = [dev(b) for _, b in pairs]
+    Cs = [torch.zeros_like(A) for A in As]
+    taus = _taus(pairs, 64, 0.5)
+    best, allc = P.spamm_batch_autotune(As, Bs, Cs, taus, P.BF16, reps=2)
+    assert len(allc) == 4
+    assert {(c["leaf"], c["schedule"]) for c in allc} == {(64, "static"), (64, "dynamic"),
+                                                          (128, "static"), (128, "dynamic")}
+    assert best["ms"] == min(c["ms"] for c in allc if c["ms"] >= 0)
