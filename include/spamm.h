@@ -293,6 +293,76 @@ spamm_status_t spamm_multiply_batched(const spamm_problem_t* problems, int32_t c
 spamm_status_t spamm_batch_destroy(spamm_batch_t batch);
 
 /* ---------------------------------------------------------------------------
+ * Band plans -- the error measurement behind tau selection.
+ * spamm_plan_band: as spamm_plan (FP32 precision only in meaning, any plan
+ *   accepted), but lists the triples with tau_lo <= p < tau_hi (p the norm
+ *   product, both tests exact in FP64; a NaN product is left out).  With C
+ *   the product over that band, AB - SpAMM(A, B, tau_hi) = C + (AB -
+ *   SpAMM(A, B, tau_lo)): against a reference tau_lo whose skipped bound is
+ *   negligible, ||C||_F is the pruning error at tau_hi without forming AB.
+ *   Only survivors, nonempty_tiles and max_tile_survivors of the statistics
+ *   are meaningful for a band plan.  tau_hi >= tau_lo >= 0, not NaN.
+ * ------------------------------------------------------------------------- */
+spamm_status_t spamm_plan_band(spamm_plan_t plan, const double* normA, const double* normB,
+                               double tau_lo, double tau_hi, void* stream);
+
+/* ---------------------------------------------------------------------------
+ * Learned tau.  The paper picks tau by a search for a target valid ratio
+ * (Section 3.5.2); here a small network maps the distribution of the norm
+ * products and a target relative error ||C - AB||_F / (||A||_F ||B||_F) to
+ * tau in one forward pass.
+ *
+ * Features: the 64-bin histogram of r = p / (||A||_F ||B||_F) over all bd^3
+ * triples (p = normA[i,k] normB[k,j] in FP64, ||.||_F from the norm maps),
+ * bin t = min(63, max(0, floor(-log2 r))), r = 0 or NaN in bin 63, +Inf in
+ * bin 0, each bin divided by bd^3; then log10(target).  Network: FP32,
+ * Linear(65,64) - GELU - Linear(64,64) - GELU - Linear(64,1) with exact
+ * GELU 0.5 z (1 + erf(z / sqrt 2)); output y = log10(tau / (||A|| ||B||)).
+ * Parameters: one device FP32 array of 8449 values: W1 (64 x 65, row-major,
+ * y = W x + b), b1 (64), W2 (64 x 64), b2 (64), W3 (1 x 64), b3 (1).
+ *
+ * spamm_norm_histogram: the raw bin counts (host int64[64]) for the plan's
+ *   shape; blocks.
+ * spamm_tau_predict: the predicted tau (host) for a target in (0, inf);
+ *   blocks.  It uses the plan's buffers: plan again (spamm_plan) afterwards.
+ * spamm_batch_tau_predict: per instance of a batch (norm maps of the given
+ *   A and B computed on the way; C and tau of the problems are not read),
+ *   targets and taus host arrays of `count`; blocks.
+ * spamm_mlp_param_count: 8449.
+ * spamm_mlp_forward: y[count] = network(X[count][65]); all device pointers.
+ * spamm_mlp_grad: gradient (device [8449]) and value (device [1]) of the
+ *   pinball loss mean_s rho_q(y_true[s] - y[s]), rho_q(r) = max(q r,
+ *   (q - 1) r), over count samples; 0 < quantile < 1.
+ * spamm_mlp_adam: one Adam step (beta 0.9 / 0.999, eps 1e-8, bias-corrected
+ *   with step number t >= 1) on device weights with device moments m, v.
+ * spamm_mlp_train: `steps` Adam steps (numbers t0 + 1 ...); step s uses the
+ *   samples idx[s * batch .. (s + 1) * batch) (device int32) of X / y_true;
+ *   loss_hist (device [steps], may be NULL) receives each step's loss.  One
+ *   CTA runs the whole loop with the weights on chip.
+ * All are asynchronous unless stated.
+ * ------------------------------------------------------------------------- */
+spamm_status_t spamm_norm_histogram(spamm_plan_t plan, const double* normA, const double* normB,
+                                    int64_t* counts, void* stream);
+spamm_status_t spamm_tau_predict(spamm_plan_t plan, const double* normA, const double* normB,
+                                 double target_rel_err, const float* weights, double* tau,
+                                 void* stream);
+spamm_status_t spamm_batch_tau_predict(spamm_batch_t batch, const spamm_problem_t* problems,
+                                       const double* targets, const float* weights,
+                                       double* taus, void* stream);
+spamm_status_t spamm_mlp_param_count(int32_t* count);
+spamm_status_t spamm_mlp_forward(const float* weights, const float* X, int32_t count, float* y,
+                                 void* stream);
+spamm_status_t spamm_mlp_grad(const float* weights, const float* X, const float* y_true,
+                              int32_t count, float quantile, float* grad, float* loss,
+                              void* stream);
+spamm_status_t spamm_mlp_adam(float* weights, const float* grad, float* m, float* v, int32_t t,
+                              float lr, void* stream);
+spamm_status_t spamm_mlp_train(float* weights, float* m, float* v, int32_t t0, const float* X,
+                               const float* y_true, const int32_t* idx, int32_t steps,
+                               int32_t batch, float lr, float quantile, float* loss_hist,
+                               void* stream);
+
+/* ---------------------------------------------------------------------------
  * Status helpers.
  * spamm_status_string: static description of a status code.
  * spamm_last_device_status: reads and clears the library's device status word

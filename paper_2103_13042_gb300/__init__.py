@@ -81,6 +81,16 @@ _SIGS = {
     "spamm_multiply_batched": [_VP, _I32, _I32, _I32, _D, _VP, _VP],
     "spamm_batch_destroy": [_VP],
     "spamm_batch_timings": [_VP, _VP],
+    "spamm_plan_band": [_VP, _VP, _VP, _D, _D, _VP],
+    "spamm_norm_histogram": [_VP, _VP, _VP, _VP, _VP],
+    "spamm_tau_predict": [_VP, _VP, _VP, _D, _VP, ctypes.POINTER(_D), _VP],
+    "spamm_batch_tau_predict": [_VP, _VP, _VP, _VP, _VP, _VP],
+    "spamm_mlp_param_count": [ctypes.POINTER(_I32)],
+    "spamm_mlp_forward": [_VP, _VP, _I32, _VP, _VP],
+    "spamm_mlp_grad": [_VP, _VP, _VP, _I32, ctypes.c_float, _VP, _VP, _VP],
+    "spamm_mlp_adam": [_VP, _VP, _VP, _VP, _I32, ctypes.c_float, _VP],
+    "spamm_mlp_train": [_VP, _VP, _VP, _I32, _VP, _VP, _VP, _I32, _I32, ctypes.c_float,
+                        ctypes.c_float, _VP, _VP],
     "spamm_batch_autotune": [_VP, _I32, _I32, _D, _I32, _VP, ctypes.POINTER(Tune), _VP,
                              ctypes.POINTER(_I32)],
 }
@@ -198,6 +208,29 @@ class Plan:
                "spamm_multiply")
         return C
 
+    def band(self, normA, normB, tau_lo: float, tau_hi: float, stream=None):
+        """Plan the triples with tau_lo <= p < tau_hi (error measurement)."""
+        _check(lib().spamm_plan_band(self.handle, _ptr(normA), _ptr(normB), float(tau_lo),
+                                     float(tau_hi), _stream(stream)), "spamm_plan_band")
+        return self
+
+    def histogram(self, normA, normB, stream=None):
+        """Raw counts of the 64-bin log2 histogram of relative norm products."""
+        import numpy as np
+        out = np.zeros(64, dtype=np.int64)
+        _check(lib().spamm_norm_histogram(self.handle, _ptr(normA), _ptr(normB),
+                                          out.ctypes.data_as(ctypes.c_void_p), _stream(stream)),
+               "spamm_norm_histogram")
+        return out
+
+    def tau_predict(self, normA, normB, target_rel_err: float, weights, stream=None) -> float:
+        """The network's tau for this plan's shape (weights: device float32 [8449])."""
+        t = ctypes.c_double()
+        _check(lib().spamm_tau_predict(self.handle, _ptr(normA), _ptr(normB),
+                                       float(target_rel_err), _ptr(weights), ctypes.byref(t),
+                                       _stream(stream)), "spamm_tau_predict")
+        return t.value
+
 
 def spamm_plan(normA, normB, n: int, leaf: int, tau: float, precision: int = FP32,
                target_rel_err: float = 1e-5, stream=None) -> Plan:
@@ -292,6 +325,20 @@ class Batch:
                                         _stream(stream)), "spamm_batch_export")
         return nA, nB, tp, kk[:int(tp[-1])]
 
+    def tau_predict(self, As, Bs, targets, weights, stream=None):
+        """Predicted tau per instance (the norm maps of As / Bs are computed on the way)."""
+        import numpy as np
+        probs = (Problem * len(As))()
+        for i, (A, B) in enumerate(zip(As, Bs)):   # no output: C stays NULL
+            probs[i] = Problem(A.data_ptr(), B.data_ptr(), None, A.shape[0], 0.0)
+        tg = np.ascontiguousarray(targets, dtype=np.float64)
+        out = np.zeros(self.count, dtype=np.float64)
+        _check(lib().spamm_batch_tau_predict(self.handle, ctypes.cast(probs, ctypes.c_void_p),
+                                             tg.ctypes.data_as(ctypes.c_void_p), _ptr(weights),
+                                             out.ctypes.data_as(ctypes.c_void_p),
+                                             _stream(stream)), "spamm_batch_tau_predict")
+        return out
+
     def timings(self):
         """{"normmap", "plan", "multiply"} device ms of the last run (timing batches only)."""
         ms = (ctypes.c_float * 3)()
@@ -335,6 +382,51 @@ def spamm_multiply_batched(As, Bs, Cs, taus, leaf: int, precision: int = FP32,
                                         ctypes.cast(arr, ctypes.c_void_p), _stream(stream)),
            "spamm_multiply_batched")
     return [a.as_dict() for a in arr]
+
+
+# ---------------------------------------------------------------------------
+# Learned-tau network (device float32 tensors)
+# ---------------------------------------------------------------------------
+
+def spamm_mlp_param_count() -> int:
+    c = ctypes.c_int32()
+    _check(lib().spamm_mlp_param_count(ctypes.byref(c)), "spamm_mlp_param_count")
+    return c.value
+
+
+def spamm_mlp_forward(weights, X, stream=None):
+    import torch
+    y = torch.empty(X.shape[0], dtype=torch.float32, device=X.device)
+    _check(lib().spamm_mlp_forward(_ptr(weights), _ptr(X), X.shape[0], _ptr(y), _stream(stream)),
+           "spamm_mlp_forward")
+    return y
+
+
+def spamm_mlp_grad(weights, X, y_true, quantile: float, stream=None):
+    """(gradient [8449], loss tensor [1]) of the mean pinball loss."""
+    import torch
+    g = torch.empty_like(weights)
+    loss = torch.empty(1, dtype=torch.float32, device=X.device)
+    _check(lib().spamm_mlp_grad(_ptr(weights), _ptr(X), _ptr(y_true), X.shape[0],
+                                float(quantile), _ptr(g), _ptr(loss), _stream(stream)),
+           "spamm_mlp_grad")
+    return g, loss
+
+
+def spamm_mlp_adam(weights, grad, m, v, t: int, lr: float, stream=None):
+    _check(lib().spamm_mlp_adam(_ptr(weights), _ptr(grad), _ptr(m), _ptr(v), int(t), float(lr),
+                                _stream(stream)), "spamm_mlp_adam")
+
+
+def spamm_mlp_train(weights, m, v, t0: int, X, y_true, idx, steps: int, batch: int, lr: float,
+                    quantile: float, stream=None):
+    """Runs `steps` Adam steps in one launch; returns the per-step losses (device tensor)."""
+    import torch
+    hist = torch.empty(max(1, steps), dtype=torch.float32, device=X.device)
+    _check(lib().spamm_mlp_train(_ptr(weights), _ptr(m), _ptr(v), int(t0), _ptr(X), _ptr(y_true),
+                                 _ptr(idx), int(steps), int(batch), float(lr), float(quantile),
+                                 _ptr(hist), _stream(stream)), "spamm_mlp_train")
+    return hist[:steps]
 
 
 def spamm_last_device_status(stream=None) -> int:

@@ -74,7 +74,8 @@ double hi_unit(spamm_precision_t p) {
 }
 
 size_t engine_layout(std::vector<Inst>& insts, int leaf, spamm_precision_t prec, size_t extra,
-                     PlanBuffers* buf, OperandImages* img, char* base) {
+                     PlanBuffers* buf, OperandImages* img, char* base, double** tau,
+                     float** feat) {
   size_t off = align_up(extra, 256);
   PlanBuffers b{};
   const size_t plan_bytes =
@@ -98,6 +99,14 @@ size_t engine_layout(std::vector<Inst>& insts, int leaf, spamm_precision_t prec,
     }
     t.ea = reinterpret_cast<int32_t*>(take(tiles * sizeof(int32_t)));
     t.eb = reinterpret_cast<int32_t*>(take(tiles * sizeof(int32_t)));
+  }
+  {
+    off = align_up(off, 256);
+    if (tau) *tau = base ? reinterpret_cast<double*>(base + off) : nullptr;
+    off += insts.size() * sizeof(double);
+    off = align_up(off, 256);
+    if (feat) *feat = base ? reinterpret_cast<float*>(base + off) : nullptr;
+    off += insts.size() * 65 * sizeof(float);
   }
   if (buf) *buf = b;
   if (img) *img = t;
@@ -124,7 +133,8 @@ spamm_status_t engine_init(Engine& e, std::vector<Inst> insts, int leaf, spamm_p
     }
     e.owns = true;
   }
-  engine_layout(e.insts, leaf, prec, extra, &e.buf, &e.img, static_cast<char*>(e.base));
+  engine_layout(e.insts, leaf, prec, extra, &e.buf, &e.img, static_cast<char*>(e.base), &e.tau_dev,
+                &e.feat_dev);
   if (cudaStreamCreateWithFlags(&e.side, cudaStreamNonBlocking) != cudaSuccess ||
       cudaEventCreateWithFlags(&e.fork, cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&e.join, cudaEventDisableTiming) != cudaSuccess) {
@@ -363,6 +373,137 @@ spamm_status_t spamm_multiply(spamm_plan_t plan, const float* A, const float* B,
   in.C = C;
   cudaError_t err = engine_multiply(e, make_ref(e.insts.data(), nullptr, 1), status,
                                     (cudaStream_t)stream);
+  if (err != cudaSuccess) {
+    (void)cudaGetLastError();
+    return SPAMM_ERR_CUDA;
+  }
+  return SPAMM_OK;
+}
+
+spamm_status_t spamm_plan_band(spamm_plan_t plan, const double* normA, const double* normB,
+                               double tau_lo, double tau_hi, void* stream) {
+  if (!plan || !normA || !normB) return SPAMM_ERR_INVALID_ARG;
+  if (!aligned16(normA) || !aligned16(normB)) return SPAMM_ERR_INVALID_ARG;
+  if (std::isnan(tau_lo) || tau_lo < 0.0 || std::isnan(tau_hi) || !(tau_hi >= tau_lo))
+    return SPAMM_ERR_INVALID_ARG;
+  Engine& e = plan->eng;
+  Inst& in = e.insts[0];
+  in.nA = normA;
+  in.nB = normB;
+  in.T = make_tau_screen(tau_lo);
+  in.T_hi = make_tau_screen(tau_hi);
+  in.band = 1;
+  in.split = 0;
+  in.quant = is_tensor_mode(e.precision) ? 1 : 0;
+  in.target_rel = 0.0;
+  in.c1 = 0.0;
+  cudaError_t err = run_plan(make_ref(e.insts.data(), nullptr, 1), e.buf, (cudaStream_t)stream);
+  in.band = 0;
+  if (err != cudaSuccess) {
+    (void)cudaGetLastError();
+    return SPAMM_ERR_CUDA;
+  }
+  return SPAMM_OK;
+}
+
+spamm_status_t spamm_norm_histogram(spamm_plan_t plan, const double* normA, const double* normB,
+                                    int64_t* counts, void* stream) {
+  if (!plan || !normA || !normB || !counts) return SPAMM_ERR_INVALID_ARG;
+  if (!aligned16(normA) || !aligned16(normB)) return SPAMM_ERR_INVALID_ARG;
+  Engine& e = plan->eng;
+  Inst& in = e.insts[0];
+  in.nA = normA;
+  in.nB = normB;
+  const cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t err = run_histogram(make_ref(e.insts.data(), nullptr, 1), e.buf, s);
+  if (err != cudaSuccess) {
+    (void)cudaGetLastError();
+    return SPAMM_ERR_CUDA;
+  }
+  PlanDevice h;
+  SPAMM_CUDA_TRY(cudaMemcpyAsync(&h, e.buf.pd, sizeof(PlanDevice), cudaMemcpyDeviceToHost, s));
+  SPAMM_CUDA_TRY(cudaStreamSynchronize(s));
+  for (int b = 0; b < kHistBins; ++b) counts[b] = (int64_t)h.hist[b];
+  return SPAMM_OK;
+}
+
+spamm_status_t spamm_tau_predict(spamm_plan_t plan, const double* normA, const double* normB,
+                                 double target_rel_err, const float* weights, double* tau,
+                                 void* stream) {
+  if (!plan || !normA || !normB || !weights || !tau) return SPAMM_ERR_INVALID_ARG;
+  if (!aligned16(normA) || !aligned16(normB)) return SPAMM_ERR_INVALID_ARG;
+  if (!(target_rel_err > 0.0) || std::isinf(target_rel_err)) return SPAMM_ERR_INVALID_ARG;
+  Engine& e = plan->eng;
+  Inst& in = e.insts[0];
+  in.nA = normA;
+  in.nB = normB;
+  const double keep = in.target_rel;
+  in.target_rel = target_rel_err;
+  const cudaStream_t s = (cudaStream_t)stream;
+  const InstRef ref = make_ref(e.insts.data(), nullptr, 1);
+  cudaError_t err = run_histogram(ref, e.buf, s);
+  if (err == cudaSuccess) err = launch_tau_from_hist(ref, weights, e.feat_dev, e.tau_dev, s);
+  in.target_rel = keep;
+  if (err != cudaSuccess) {
+    (void)cudaGetLastError();
+    return SPAMM_ERR_CUDA;
+  }
+  SPAMM_CUDA_TRY(cudaMemcpyAsync(tau, e.tau_dev, sizeof(double), cudaMemcpyDeviceToHost, s));
+  SPAMM_CUDA_TRY(cudaStreamSynchronize(s));
+  return SPAMM_OK;
+}
+
+spamm_status_t spamm_mlp_param_count(int32_t* count) {
+  if (!count) return SPAMM_ERR_INVALID_ARG;
+  *count = mlp_param_count();
+  return SPAMM_OK;
+}
+
+spamm_status_t spamm_mlp_forward(const float* weights, const float* X, int32_t count, float* y,
+                                 void* stream) {
+  if (!weights || count < 0 || (count > 0 && (!X || !y))) return SPAMM_ERR_INVALID_ARG;
+  cudaError_t err = launch_mlp_forward(weights, X, count, y, (cudaStream_t)stream);
+  if (err != cudaSuccess) {
+    (void)cudaGetLastError();
+    return SPAMM_ERR_CUDA;
+  }
+  return SPAMM_OK;
+}
+
+spamm_status_t spamm_mlp_grad(const float* weights, const float* X, const float* y_true,
+                              int32_t count, float quantile, float* grad, float* loss,
+                              void* stream) {
+  if (!weights || !X || !y_true || !grad || !loss || count < 1) return SPAMM_ERR_INVALID_ARG;
+  if (!(quantile > 0.0f && quantile < 1.0f)) return SPAMM_ERR_INVALID_ARG;
+  cudaError_t err = launch_mlp_grad(weights, X, y_true, count, quantile, grad, loss,
+                                    (cudaStream_t)stream);
+  if (err != cudaSuccess) {
+    (void)cudaGetLastError();
+    return SPAMM_ERR_CUDA;
+  }
+  return SPAMM_OK;
+}
+
+spamm_status_t spamm_mlp_adam(float* weights, const float* grad, float* m, float* v, int32_t t,
+                              float lr, void* stream) {
+  if (!weights || !grad || !m || !v || t < 1 || !(lr > 0.0f)) return SPAMM_ERR_INVALID_ARG;
+  cudaError_t err = launch_mlp_adam(weights, grad, m, v, t, lr, (cudaStream_t)stream);
+  if (err != cudaSuccess) {
+    (void)cudaGetLastError();
+    return SPAMM_ERR_CUDA;
+  }
+  return SPAMM_OK;
+}
+
+spamm_status_t spamm_mlp_train(float* weights, float* m, float* v, int32_t t0, const float* X,
+                               const float* y_true, const int32_t* idx, int32_t steps,
+                               int32_t batch, float lr, float quantile, float* loss_hist,
+                               void* stream) {
+  if (!weights || !m || !v || !X || !y_true || !idx || t0 < 0 || steps < 0 || batch < 1)
+    return SPAMM_ERR_INVALID_ARG;
+  if (!(quantile > 0.0f && quantile < 1.0f) || !(lr > 0.0f)) return SPAMM_ERR_INVALID_ARG;
+  cudaError_t err = launch_mlp_train(weights, m, v, t0, X, y_true, idx, steps, batch, lr,
+                                     quantile, loss_hist, (cudaStream_t)stream);
   if (err != cudaSuccess) {
     (void)cudaGetLastError();
     return SPAMM_ERR_CUDA;

@@ -263,18 +263,18 @@ spamm_status_t spamm_batch_destroy(spamm_batch_t batch) {
   return st;
 }
 
-spamm_status_t spamm_batch_run(spamm_batch_t b, const spamm_problem_t* problems,
-                               double target_rel_err, void* stream) {
-  if (!b) return SPAMM_ERR_INVALID_ARG;
-  spamm_status_t st = check_problems(b, problems);
-  if (st != SPAMM_OK) return st;
+}  // extern "C"
+
+namespace {
+
+// Fills the instance and norm-map job tables for `problems` and uploads them
+// when they changed.  targets (per instance, may be null) overrides
+// target_rel_err for tau prediction.
+spamm_status_t upload_tables(spamm_batch_s* b, const spamm_problem_t* problems,
+                             double target_rel_err, const double* targets, cudaStream_t s) {
   Engine& e = b->eng;
   const bool split = uses_split_flags(e.precision);
-  if (split && !(target_rel_err >= 0.0)) return SPAMM_ERR_INVALID_ARG;
   const double u = hi_unit(e.precision);
-  const cudaStream_t s = (cudaStream_t)stream;
-
-  // tables of this run, in their device layout
   std::vector<char> tab(b->table_bytes, 0);
   NormJob* jobs = reinterpret_cast<NormJob*>(tab.data());
   for (int32_t i = 0; i < b->count; ++i) {
@@ -284,10 +284,11 @@ spamm_status_t spamm_batch_run(spamm_batch_t b, const spamm_problem_t* problems,
     in.C = problems[i].C;
     in.nA = b->normA + in.tile0;
     in.nB = b->normB + in.tile0;
-    in.T = make_tau_screen(problems[i].tau);
+    in.T = make_tau_screen(targets ? 0.0 : problems[i].tau);
+    in.band = 0;
     in.split = split ? 1 : 0;
     in.quant = is_tensor_mode(e.precision) ? 1 : 0;
-    in.target_rel = split ? target_rel_err : 0.0;
+    in.target_rel = targets ? targets[i] : (split ? target_rel_err : 0.0);
     in.c1 = split ? 2.0 * u + u * u : 0.0;
     for (int op = 0; op < 2; ++op) {
       NormJob& j = jobs[2 * i + op];
@@ -300,7 +301,6 @@ spamm_status_t spamm_batch_run(spamm_batch_t b, const spamm_problem_t* problems,
     }
   }
   std::memcpy(tab.data() + b->insts_offset, e.insts.data(), (size_t)b->count * sizeof(Inst));
-
   // upload only what changed since the last run (the staging buffer is reused
   // once the previous copy has read it)
   if (!b->uploaded_once || std::memcmp(tab.data(), b->last.data(), b->table_bytes) != 0) {
@@ -312,6 +312,23 @@ spamm_status_t spamm_batch_run(spamm_batch_t b, const spamm_problem_t* problems,
     b->last.swap(tab);
     b->uploaded_once = true;
   }
+  return SPAMM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+spamm_status_t spamm_batch_run(spamm_batch_t b, const spamm_problem_t* problems,
+                               double target_rel_err, void* stream) {
+  if (!b) return SPAMM_ERR_INVALID_ARG;
+  spamm_status_t st = check_problems(b, problems);
+  if (st != SPAMM_OK) return st;
+  Engine& e = b->eng;
+  if (uses_split_flags(e.precision) && !(target_rel_err >= 0.0)) return SPAMM_ERR_INVALID_ARG;
+  const cudaStream_t s = (cudaStream_t)stream;
+  st = upload_tables(b, problems, target_rel_err, nullptr, s);
+  if (st != SPAMM_OK) return st;
 
   cudaError_t err = cudaSuccess;
   const bool timing = (b->flags & SPAMM_BATCH_TIMING) != 0;
@@ -347,6 +364,35 @@ spamm_status_t spamm_batch_run(spamm_batch_t b, const spamm_problem_t* problems,
     (void)cudaGetLastError();
     return SPAMM_ERR_CUDA;
   }
+  return SPAMM_OK;
+}
+
+spamm_status_t spamm_batch_tau_predict(spamm_batch_t b, const spamm_problem_t* problems,
+                                       const double* targets, const float* weights,
+                                       double* taus, void* stream) {
+  if (!b || !problems || !targets || !weights || !taus) return SPAMM_ERR_INVALID_ARG;
+  for (int32_t i = 0; i < b->count; ++i) {   // only A, B and n are read
+    const spamm_problem_t& q = problems[i];
+    if (q.n != b->n[i] || !q.A || !q.B || !aligned16(q.A) || !aligned16(q.B))
+      return SPAMM_ERR_INVALID_ARG;
+  }
+  spamm_status_t st = SPAMM_OK;
+  for (int32_t i = 0; i < b->count; ++i)
+    if (!(targets[i] > 0.0) || std::isinf(targets[i])) return SPAMM_ERR_INVALID_ARG;
+  const cudaStream_t s = (cudaStream_t)stream;
+  st = upload_tables(b, problems, 0.0, targets, s);
+  if (st != SPAMM_OK) return st;
+  const InstRef ref = batch_ref(b);
+  cudaError_t err = launch_normmap_jobs(b->jobs_dev, 2 * b->count, b->norm_ctas, b->eng.leaf, s);
+  if (err == cudaSuccess) err = run_histogram(ref, b->eng.buf, s);
+  if (err == cudaSuccess) err = launch_tau_from_hist(ref, weights, b->eng.feat_dev, b->eng.tau_dev, s);
+  if (err != cudaSuccess) {
+    (void)cudaGetLastError();
+    return SPAMM_ERR_CUDA;
+  }
+  SPAMM_CUDA_TRY(cudaMemcpyAsync(taus, b->eng.tau_dev, (size_t)b->count * sizeof(double),
+                                 cudaMemcpyDeviceToHost, s));
+  SPAMM_CUDA_TRY(cudaStreamSynchronize(s));
   return SPAMM_OK;
 }
 

@@ -19,6 +19,8 @@ struct Engine {
   std::vector<Inst> insts;     // host copy of the instance table (layout fields filled)
   PlanBuffers buf{};
   OperandImages img{};         // tensor-core modes only
+  double* tau_dev = nullptr;   // [instances] predicted tau
+  float* feat_dev = nullptr;   // [instances * 65] network inputs of the last prediction
   size_t extra_bytes = 0;      // caller-defined area at the start of the workspace
   int schedule = kScheduleStatic;
   cudaStream_t side = nullptr; // zero-fill of empty tiles runs here, overlapped
@@ -33,7 +35,8 @@ double hi_unit(spamm_precision_t p);
 // Bytes of the workspace for `insts` (bd fields set) with `extra` bytes in
 // front; fills the layout of `insts`, `buf` and `img` when `base` is non-null.
 size_t engine_layout(std::vector<Inst>& insts, int leaf, spamm_precision_t prec, size_t extra,
-                     PlanBuffers* buf, OperandImages* img, char* base);
+                     PlanBuffers* buf, OperandImages* img, char* base, double** tau = nullptr,
+                     float** feat = nullptr);
 
 // Sets up `e` for `insts` (only n and bd read): allocates the workspace when
 // `workspace` is null, creates the side stream and events.

@@ -228,8 +228,9 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32)
   const int warp = threadIdx.x / 32, lane = threadIdx.x & 31;
   const int ii = inst_of_count_cta(R, blockIdx.x);
   const Inst& in = R.at(ii);
-  const int bd = in.bd, split = in.split;
+  const int bd = in.bd, split = in.split, band = in.band;
   const TauScreen T = in.T;
+  const TauScreen Thi = in.T_hi;
   const double* nA = in.nA;
   const double* nB = in.nB;
   PlanDevice* pd = in.pd;
@@ -265,6 +266,7 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32)
       if (k < bd) {
         const Screen a = ra[k], b = rb[k];
         s = survives(a, b, nA + (int64_t)i * bd + k, nB + (int64_t)k * bd + j, T);
+        if (s && band) s = !survives(a, b, nA + (int64_t)i * bd + k, nB + (int64_t)k * bd + j, Thi);
         if (!s) {
           ext_add_rel(sk, a, b, inv_m, inv_e);
         } else if (split) {
@@ -335,6 +337,76 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32)
       }
     }
   }
+}
+
+// Histogram bin of r = fl(fl(na nb) * inv) (FP64, as the oracle defines it):
+// floor(-log2 r) clamped to [0, 63]; r = 0 or NaN goes to bin 63, +Inf to 0.
+__device__ __forceinline__ int hist_bin_exact(double p, double inv) {
+  const double r = __dmul_rn(p, inv);
+  if (!(r > 0.0)) return kHistBins - 1;
+  if (isinf(r)) return 0;
+  int e;
+  const double m = frexp(r, &e);          // r = m 2^e, m in [0.5, 1)
+  const int t = -e + (m == 0.5 ? 1 : 0);
+  return t < 0 ? 0 : (t > kHistBins - 1 ? kHistBins - 1 : t);
+}
+
+// The same bin from the screen forms in FP32; the FP64 form decides whenever
+// the FP32 product lies within 2^-20 of a power of two.
+__device__ __forceinline__ int hist_bin_screened(Screen a, Screen b, float inv_m, int inv_e,
+                                                 const double* pa, const double* pb, double inv) {
+  if ((a.e == kZeroExp || b.e == kZeroExp) && inv > 0.0 && !isinf(inv)) return kHistBins - 1;
+  if (a.e == kNonFiniteExp || b.e == kNonFiniteExp || a.e == kZeroExp || b.e == kZeroExp ||
+      !(inv > 0.0) || isinf(inv))
+    return hist_bin_exact(__dmul_rn(*pa, *pb), inv);
+  const float q = __fmul_rn(__fmul_rn(a.m, b.m), inv_m);   // in [0.125, 1]
+  const uint32_t frac = __float_as_uint(q) & 0x7fffffu;
+  if (frac < 8u || frac > 0x7fffffu - 8u) return hist_bin_exact(__dmul_rn(*pa, *pb), inv);
+  // r = q' 2^(b0) with q' in (1, 2) not a power of two: floor(-log2 r) = -b0 - 1
+  const int b0 = a.e + b.e + inv_e + ((int)((__float_as_uint(q) >> 23) & 0xffu) - 127);
+  const int t = -b0 - 1;
+  return t < 0 ? 0 : (t > kHistBins - 1 ? kHistBins - 1 : t);
+}
+
+// Histogram of every triple of every instance: one warp per output tile,
+// lanes over k; equal bins of a warp are merged with match_any before the
+// shared-memory atomics, CTA totals go to the instance's global bins.
+__global__ void __launch_bounds__(kWarpsPerCta * 32)
+    hist_kernel(InstRef R, PlanBuffers Bf) {
+  __shared__ unsigned int s_hist[kHistBins];
+  const int warp = threadIdx.x / 32, lane = threadIdx.x & 31;
+  const int ii = inst_of_count_cta(R, blockIdx.x);
+  const Inst& in = R.at(ii);
+  const int bd = in.bd;
+  const double* nA = in.nA;
+  const double* nB = in.nB;
+  for (int q = threadIdx.x; q < kHistBins; q += blockDim.x) s_hist[q] = 0u;
+  __syncthreads();
+  const double inv = in.pd->inv_ab;   // written by the prep kernel
+  int inv_e;
+  const float inv_m = (float)frexp(inv, &inv_e);
+  const int64_t tiles = (int64_t)bd * bd;
+  const int64_t lt0 = (int64_t)(blockIdx.x - in.count0) * kTilesPerCta;
+  for (int r = 0; r < kTileRounds; ++r) {
+    const int64_t t = lt0 + warp + (int64_t)r * kWarpsPerCta;
+    if (t >= tiles) break;
+    const int i = (int)(t / bd), j = (int)(t % bd);
+    const Screen* ra = Bf.sA + in.tile0 + (int64_t)i * bd;
+    const Screen* rb = Bf.sBT + in.tile0 + (int64_t)j * bd;
+    for (int k0 = 0; k0 < bd; k0 += 32) {
+      const int k = k0 + lane;
+      const bool act = k < bd;
+      int bin = kHistBins;   // inactive lanes: a bin of their own
+      if (act)
+        bin = hist_bin_screened(ra[k], rb[k], inv_m, inv_e, nA + (int64_t)i * bd + k,
+                                nB + (int64_t)k * bd + j, inv);
+      const unsigned same = __match_any_sync(0xffffffffu, bin);
+      if (act && lane == __ffs(same) - 1) atomicAdd(&s_hist[bin], (unsigned)__popc(same));
+    }
+  }
+  __syncthreads();
+  for (int q = threadIdx.x; q < kHistBins; q += blockDim.x)
+    if (s_hist[q]) atomicAdd(&in.pd->hist[q], s_hist[q]);
 }
 
 // Block-wide exclusive scan of one value per thread (Hillis-Steele in smem).
@@ -505,8 +577,9 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32)
   const int warp = threadIdx.x / 32, lane = threadIdx.x & 31;
   const int ii = inst_of_count_cta(R, blockIdx.x);
   const Inst& in = R.at(ii);
-  const int bd = in.bd, split = in.split, quant = in.quant;
+  const int bd = in.bd, split = in.split, quant = in.quant, band = in.band;
   const TauScreen T = in.T;
+  const TauScreen Thi = in.T_hi;
   const double* nA = in.nA;
   const double* nB = in.nB;
   const int64_t tiles = (int64_t)bd * bd;
@@ -559,6 +632,7 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32)
         a = ra[k];
         b = rb[k];
         s = survives(a, b, nA + (int64_t)i * bd + k, nB + (int64_t)k * bd + j, T);
+        if (s && band) s = !survives(a, b, nA + (int64_t)i * bd + k, nB + (int64_t)k * bd + j, Thi);
       }
       const unsigned ball = __ballot_sync(0xffffffffu, s);
       if (s) {
@@ -668,6 +742,16 @@ cudaError_t run_plan(const InstRef& ref, const PlanBuffers& b, cudaStream_t s) {
   count_kernel<<<b.count_ctas, kWarpsPerCta * 32, 0, s>>>(ref, b);
   finalize_kernel<<<ref.count, kFinThreads, 0, s>>>(ref, b);
   fill_kernel<<<b.count_ctas, kWarpsPerCta * 32, 0, s>>>(ref, b);
+  return cudaPeekAtLastError();
+}
+
+cudaError_t run_histogram(const InstRef& ref, const PlanBuffers& b, cudaStream_t s) {
+  const size_t clear = reinterpret_cast<const char*>(b.need_bits + 2 * b.need_words) -
+                       reinterpret_cast<const char*>(b.pd);
+  cudaError_t e = cudaMemsetAsync(b.pd, 0, clear, s);
+  if (e != cudaSuccess) return e;
+  prep_kernel<<<b.prep_ctas, kPrepThreads, 0, s>>>(ref, b);
+  hist_kernel<<<b.count_ctas, kWarpsPerCta * 32, 0, s>>>(ref, b);
   return cudaPeekAtLastError();
 }
 

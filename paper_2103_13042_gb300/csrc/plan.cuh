@@ -24,6 +24,9 @@ struct TauScreen {
 
 TauScreen make_tau_screen(double tau);
 
+// Bins of the log2 histogram of relative norm products (tau prediction).
+constexpr int kHistBins = 64;
+
 // Per-instance statistics; `ticket` and the bins are cleared before each plan.
 struct PlanDevice {
   double norm_a, norm_b, inv_ab;
@@ -31,6 +34,7 @@ struct PlanDevice {
   long long survivors, flagged;
   int max_tile, nonempty, flag_exp;
   int ne_base;                              // non-empty tiles of the instances before this one
+  unsigned int hist[kHistBins];             // norm-product histogram (tau prediction)
   unsigned int ticket;                      // prep CTAs of this instance that have finished
   double bin_sum[kFlagBins];                // surviving products per relative binade
   unsigned long long bin_cnt[kFlagBins];
@@ -74,6 +78,9 @@ struct Inst {
   double target_rel;    // split modes: relative error target
   double c1;            // split modes: hi-only error coefficient 2u + u^2
   TauScreen T;
+  TauScreen T_hi;       // band plans: triples with p >= T_hi.tau are left out too
+  int band;             // 1: multiply only tau <= p < T_hi.tau
+  int pad_;
   PlanDevice* pd;
 };
 
@@ -152,6 +159,10 @@ InstRef make_ref(const Inst* host_insts, const Inst* dev_table, int count);
 
 cudaError_t run_plan(const InstRef& ref, const PlanBuffers& b, cudaStream_t s);
 
+// Clears the statistics, builds the screen forms and norms (as run_plan's
+// first step) and the per-instance norm-product histograms (pd[i].hist).
+cudaError_t run_histogram(const InstRef& ref, const PlanBuffers& b, cudaStream_t s);
+
 cudaError_t launch_normmap(const float* X, int64_t n, int32_t leaf, double* out, cudaStream_t s);
 
 // Batched norm maps: one job per operand of an instance.
@@ -170,6 +181,22 @@ cudaError_t launch_normmap_jobs(const NormJob* dev_jobs, int njobs, int total_ct
 
 cudaError_t launch_multiply_simt(const InstRef& ref, const PlanBuffers& b, int leaf,
                                  int schedule, cudaStream_t s);
+
+// Learned tau (FP32 network, 8449 parameters).
+int mlp_param_count();
+cudaError_t launch_mlp_forward(const float* W, const float* X, int count, float* Y,
+                               cudaStream_t s);
+cudaError_t launch_mlp_grad(const float* W, const float* X, const float* Y, int count, float q,
+                            float* grad, float* loss, cudaStream_t s);
+cudaError_t launch_mlp_adam(float* W, const float* grad, float* m, float* v, int t, float lr,
+                            cudaStream_t s);
+cudaError_t launch_mlp_train(float* W, float* m, float* v, int t0, const float* X, const float* Y,
+                             const int* idx, int steps, int batch, float lr, float q,
+                             float* loss_hist, cudaStream_t s);
+// tau[i] (and the 65 features, when feats is non-null) of every instance
+// from pd[i].hist, pd[i].norm_a/b and Inst::target_rel.
+cudaError_t launch_tau_from_hist(const InstRef& ref, const float* W, float* feats, double* tau,
+                                 cudaStream_t s);
 
 cudaError_t launch_frobenius_diff(const float* X, const float* Y, int64_t count, double* partials,
                                   int nparts, double* out, cudaStream_t s);

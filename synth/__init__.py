@@ -176,3 +176,33 @@ def mlp_init(seed: int, sizes=(65, 64, 64, 1)) -> np.ndarray:
         parts.append(g.uniform(-bound, bound, size=fo * fi))
         parts.append(g.uniform(-bound, bound, size=fo))
     return np.concatenate(parts).astype(np.float32)
+
+
+# ---------------------------------------------------------------------------
+# Device-side draws of the same families (training data for the learned-tau
+# network, where thousands of large matrices are needed and host generation
+# would dominate).  Seeded with torch's device generator: deterministic for a
+# given seed and device, but NOT the same bits as the numpy generators above,
+# so nothing here feeds a parity test against the oracle.
+# ---------------------------------------------------------------------------
+
+def spec_matrices_device(spec, device):
+    """(A, B) float32 device tensors of a spec from :func:`training_specs` / :func:`batch_specs`."""
+    import torch
+    n, rate = int(spec["n"]), float(spec["rate"])
+    idx = torch.arange(n, device=device, dtype=torch.float32)
+    dist = (idx[:, None] - idx[None, :]).abs()
+    if spec["kind"] == "exp":
+        mag = torch.exp(-rate * dist)
+    else:
+        mag = (dist + 1.0).pow(-rate)
+    out = []
+    for seed in (spec["seed_a"], spec["seed_b"]):
+        g = torch.Generator(device=device)
+        g.manual_seed(int(seed))
+        if spec["kind"] == "exp":
+            z = torch.randn(n, n, generator=g, device=device, dtype=torch.float32)
+        else:
+            z = torch.randint(0, 2, (n, n), generator=g, device=device).to(torch.float32) * 2.0 - 1.0
+        out.append((mag * z).contiguous())
+    return out[0], out[1]
