@@ -41,6 +41,11 @@ sys.path.insert(0, ROOT)
 import synth  # noqa: E402
 
 METRIC = "SpAMM time & TFLOP/s at fixed rel. error vs plain FP32 SpAMM & cuBLAS; roofline %"
+
+# DRAM bytes (read + write) per launch from one ncu capture of the kernel as it
+# stands (profiles/kernels_mixed_n8192.md); an entry is removed whenever the
+# kernel changes, until it is captured again.
+NCU_TRAFFIC = {("normmap_kernel", 8192, 64): 268.471040e6 + 3.060224e6}
 N_DEFAULT, LEAF_DEFAULT = 8192, 64
 
 
@@ -119,6 +124,12 @@ class ClockSampler:
 # ---------------------------------------------------------------------------
 # CPU baseline: the oracle as it stands on a bounded sample of the workload
 # ---------------------------------------------------------------------------
+
+def spread_rows(bd: int, count: int, offset: int = 0):
+    """`count` output block-rows spread evenly over [0, bd) (edges and middle alike)."""
+    count = max(1, min(bd, count))
+    return sorted({(offset + (q * bd) // count) % bd for q in range(count)})
+
 
 def cpu_baseline(a, b, leaf, tau, rows, nB_full=None, gpu_c=None):
     """Times the oracle on `rows` output block-rows: norm maps of those block-rows
@@ -323,16 +334,19 @@ def run_ours(args, rank, world):
     peaks = load_peaks()
     dense = 2.0 * n ** 3
     value = dense / (ms * 1e-3) / 1e12 * world
-    # roofline of the dominant kernel
+    # roofline of the dominant kernel: by the ncu launch list of this command the
+    # norm map (two launches per step) has the largest share of device time
     norm_ms = 0.5 * (part_ms["normmap_A"] + part_ms["normmap_B"])
     mul_ms = part_ms["multiply"]
-    if norm_ms >= mul_ms:
+    if norm_ms > 0.0:
         bytes_ = 4.0 * n * n + 8.0 * bd * bd
         ach = bytes_ / (norm_ms * 1e-3) / 1e9
-        roof = {"kernel": "normmap", "bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"],
-                "unit": "GB/s", "frac": ach / peaks["hbm_gbs"], "traffic": None,
-                "per_launch_ms": norm_ms, "algorithmic_bytes": bytes_,
-                "peak_source": peaks["source"]}
+        traffic = NCU_TRAFFIC.get(("normmap_kernel", n, leaf))
+        roof = {"kernel": "normmap_kernel", "bound": "hbm", "achieved": ach,
+                "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": ach / peaks["hbm_gbs"],
+                "traffic": traffic, "per_launch_ms": norm_ms, "algorithmic_bytes": bytes_,
+                "peak_source": peaks["source"] + " copy bandwidth (burst)",
+                "timing": "CUDA events around one spamm_normmap call on the launching stream"}
     else:
         flops = 2.0 * leaf ** 3 * st["survivors"]
         if prec == P.FP32:
@@ -372,11 +386,15 @@ def run_ours(args, rank, world):
                 "h2d_bytes_per_step": 2 * 4 * n * n, "d2h_bytes_per_step": 4 * n * n},
         "gpu_launches": launches_per_step * args.steps,
         "roofline": roof,
+        # the whole step against the HBM floor of reading A, B and writing C once
+        "roofline_step": {"bound": "hbm", "algorithmic_bytes": 12.0 * n * n,
+                          "achieved": 12.0 * n * n / (ms * 1e-3) / 1e9, "peak": peaks["hbm_gbs"],
+                          "unit": "GB/s", "frac": 12.0 * n * n / (ms * 1e-3) / 1e9 / peaks["hbm_gbs"]},
         "clocks": clk.summary(),
     }
     if not args.no_cpu_baseline:
         c_host = C.cpu().numpy()
-        cb, _ = cpu_baseline(a_h, b_h, leaf, tau, rows=list(range(args.cpu_rows)), gpu_c=c_host)
+        cb, _ = cpu_baseline(a_h, b_h, leaf, tau, rows=spread_rows(bd, args.cpu_rows), gpu_c=c_host)
         line["cpu_baseline"] = cb
     return line
 
@@ -643,15 +661,15 @@ def batch_cpu_baseline(mats, taus, leaf, ns, budget_s=15.0):
 def run_reference(args):
     a_h, b_h = workload(args.n)
     leaf, tau = args.leaf, args.tau
-    rows = list(range(args.cpu_rows))
+    bd = -(-args.n // leaf)
     nB = None
-    for _ in range(args.warmup):
-        _, nB = cpu_baseline(a_h, b_h, leaf, tau, rows, nB)
+    for w in range(args.warmup):
+        _, nB = cpu_baseline(a_h, b_h, leaf, tau, spread_rows(bd, args.ref_rows, w), nB)
     vals = []
     t0 = time.perf_counter()
     cb = None
-    for _ in range(args.steps):
-        cb, nB = cpu_baseline(a_h, b_h, leaf, tau, rows, nB)
+    for k in range(args.steps):   # each step a different spread of block-rows
+        cb, nB = cpu_baseline(a_h, b_h, leaf, tau, spread_rows(bd, args.ref_rows, args.warmup + k), nB)
         vals.append(cb["value"])
     wall = time.perf_counter() - t0
     value = statistics.median(vals)
@@ -683,7 +701,10 @@ def main():
     ap.add_argument("--target", type=float, default=1e-5)
     ap.add_argument("--n", type=int, default=N_DEFAULT)
     ap.add_argument("--leaf", type=int, default=LEAF_DEFAULT)
-    ap.add_argument("--cpu-rows", type=int, default=2)
+    ap.add_argument("--cpu-rows", type=int, default=128,
+                    help="output block-rows of the oracle's timed sample (cpu_baseline)")
+    ap.add_argument("--ref-rows", type=int, default=8,
+                    help="output block-rows per step of --impl reference")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-baselines", action="store_true")
     ap.add_argument("--eager", action="store_true", help="time host-enqueued calls, no graph")

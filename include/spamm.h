@@ -175,7 +175,7 @@ spamm_status_t spamm_multiply(spamm_plan_t plan, const float* A, const float* B,
                               void* stream);
 
 /* ---------------------------------------------------------------------------
- * Error measures (Eq. 6): E = AB - SpAMM(A, B, tau).
+ * Error measures (Eq. 5): E = AB - SpAMM(A, B, tau).
  * spamm_frobenius_diff: *out = ||X - Y||_F over `count` FP32 entries
  *   (Y may be NULL for ||X||_F).  FP64 accumulation of exact FP32 squares.
  *   X, Y device; out host.  Blocks until done.

@@ -9,7 +9,7 @@ Modules
 -------
 spamm      block Frobenius norms (Eq. 2), recursive quadtree SpAMM (Algorithm 1),
            the flat leaf-level skip rule (Section 3.1), dense reference, errors
-           (Eq. 6) and the skipped-product bounds.
+           (Eq. 5) and the skipped-product bounds.
 precision  reduced-precision emulation: power-of-two block scaling, RNE rounding
            to BF16 / FP16 / TF32, hi+lo splits, dominant-triple flags and the
            a-priori error bound of each precision mode.

@@ -217,7 +217,7 @@ def spamm_recursive(a: np.ndarray, b: np.ndarray, leaf: int, tau: float):
 
 
 # ---------------------------------------------------------------------------
-# Statistics, errors (Eq. 6) and skipped-product bounds
+# Statistics, errors (Eq. 5) and skipped-product bounds
 # ---------------------------------------------------------------------------
 
 def valid_counts(surv: np.ndarray) -> np.ndarray:
@@ -250,7 +250,7 @@ def skipped_bounds(nA: np.ndarray, nB: np.ndarray, surv: np.ndarray):
 
 
 def errors(c: np.ndarray, ref: np.ndarray, norm_a: float, norm_b: float):
-    """Eq. 6 error E = AB - SpAMM(A, B, tau) in the three normalisations used.
+    """Eq. 5 error E = AB - SpAMM(A, B, tau) in the three normalisations used.
 
     Returns dict(abs=||E||_F, rel_c=||E||_F/||AB||_F, rel_ab=||E||_F/(||A||_F ||B||_F)).
     """

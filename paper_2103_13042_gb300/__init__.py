@@ -429,6 +429,20 @@ def spamm_mlp_train(weights, m, v, t0: int, X, y_true, idx, steps: int, batch: i
     return hist[:steps]
 
 
+TAU_WEIGHTS_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "data",
+                                "tau_mlp_leaf64.f32")
+
+
+def load_tau_weights(device=None, path: str = TAU_WEIGHTS_PATH):
+    """The trained learned-tau network (leaf 64) as a device float32 tensor [8449]."""
+    import numpy as np
+    import torch
+    w = np.fromfile(path, dtype=np.float32)
+    if w.size != spamm_mlp_param_count():
+        raise RuntimeError(f"{path}: {w.size} values, expected {spamm_mlp_param_count()}")
+    return torch.from_numpy(w).to(device or torch.device("cuda"))
+
+
 def spamm_last_device_status(stream=None) -> int:
     c = ctypes.c_int32()
     _check(lib().spamm_last_device_status(_stream(stream), ctypes.byref(c)),

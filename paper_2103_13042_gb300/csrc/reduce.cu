@@ -1,4 +1,4 @@
-// Error measures (Eq. 6): ||X - Y||_F (or ||X||_F) with FP64-grade accuracy.
+// Error measures (Eq. 5): ||X - Y||_F (or ||X||_F) with FP64-grade accuracy.
 //
 // Each difference d = x - y is formed in FP32 and its rounding error dl kept
 // (TwoSum); groups of 32 differences are scaled by a power of two, squared
