@@ -174,7 +174,7 @@ def run_ours(args, rank, world):
     local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    n, leaf, tau = args.n, args.leaf, args.tau
+    n, leaf, tau = args.n or N_DEFAULT, args.leaf, args.tau
     prec = P.PRECISIONS[args.precision]
     a_h, b_h = workload(n)
     A = torch.from_numpy(a_h).to(dev)
@@ -481,7 +481,7 @@ def run_batch(args, rank, world):
 
     # phase breakdown (same configuration, events between phases, no graph)
     tb = P.Batch(ns, leaf, prec, graph=False, dynamic=best["schedule"] == "dynamic", timing=True)
-    ph = {"normmap": [], "plan": [], "multiply": []}
+    ph = {"normmap": [], "plan": [], "round": [], "multiply": []}
     for _ in range(max(3, args.steps // 4)):
         tb.run(As, Bs, Cs, taus, args.target)
         for k, v in tb.timings().items():
@@ -655,10 +655,152 @@ def batch_cpu_baseline(mats, taus, leaf, ns, budget_s=15.0):
 
 
 # ---------------------------------------------------------------------------
+# Near-sparse workload: tensor-core bound (most block products survive)
+# ---------------------------------------------------------------------------
+
+def run_sparse(args, rank, world):
+    import torch
+    import paper_2103_13042_gb300 as P
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    n = args.n or 32768
+    prec = P.PRECISIONS[args.precision if args.precision != "bf16_split" else "bf16"]
+    prec_name = [k for k, v in P.PRECISIONS.items() if v == prec][0]
+    A = synth.near_sparse_device(n, synth.config_seed(2, operand="A"), dev)
+    B = synth.near_sparse_device(n, synth.config_seed(2, operand="B"), dev)
+    C = torch.empty_like(A)
+    stream = torch.cuda.current_stream()
+    dense = 2.0 * n ** 3
+
+    # tau by the paper's valid-ratio search (Section 3.5.2), per candidate leaf
+    taus = {}
+    for leaf in (64, 128):
+        nA, nB = P.spamm_normmap(A, leaf), P.spamm_normmap(B, leaf)
+        pl = P.Plan(n, leaf, P.FP32)
+        taus[leaf] = pl.tau_for_valid_ratio(nA, nB, args.ratio, 0.01, 30)
+        del pl, nA, nB
+    # autotuner on this instance: leaf x schedule (each leaf with its own tau)
+    cands = []
+    for leaf in (64, 128):
+        best, allc = P.spamm_batch_autotune([A], [B], [C], [taus[leaf][0]], prec, args.target, reps=2)
+        cands += [c for c in allc if c["leaf"] == leaf]
+    best = min((c for c in cands if c["ms"] >= 0), key=lambda c: c["ms"])
+    leaf = best["leaf"]
+    tau, ratio, probes = taus[leaf]
+    batch = P.Batch([n], leaf, prec, graph=True, dynamic=best["schedule"] == "dynamic")
+    tb = P.Batch([n], leaf, prec, graph=False, dynamic=best["schedule"] == "dynamic", timing=True)
+
+    def step():
+        batch.run([A], [B], [C], [tau], args.target)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    st = batch.stats()[0]
+    assert P.spamm_last_device_status() == 0
+    ph = {"normmap": [], "plan": [], "round": [], "multiply": []}
+    for _ in range(3):
+        tb.run([A], [B], [C], [tau], args.target)
+        for k, v in tb.timings().items():
+            ph[k].append(v)
+    tb.close()
+    part_ms = {k: statistics.median(v) for k, v in ph.items()}
+
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        time.sleep(0.3)
+        e0.record(stream)
+        for _ in range(args.steps):
+            step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        time.sleep(0.3)
+    ms = e0.elapsed_time(e1) / args.steps
+
+    # accuracy on sampled output tiles against FP64 products on the GPU
+    g = np.random.default_rng(5)
+    bd = P.num_blocks(n, leaf)
+    errs, refs = 0.0, 0.0
+    for _ in range(16):
+        i, j = int(g.integers(0, bd)), int(g.integers(0, bd))
+        r = slice(i * leaf, min(n, (i + 1) * leaf))
+        c = slice(j * leaf, min(n, (j + 1) * leaf))
+        ref = torch.matmul(A[r].double(), B[:, c].double())
+        errs += float(((C[r, c].double() - ref) ** 2).sum())
+        refs += float((ref ** 2).sum())
+    rel_tiles = (errs / refs) ** 0.5
+
+    base = {}
+    if not args.no_baselines:
+        def timed(fn, reps):
+            fn()
+            g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            g0.record(stream)
+            for _ in range(reps):
+                fn()
+            g1.record(stream)
+            torch.cuda.synchronize()
+            return g0.elapsed_time(g1) / reps
+        prev = torch.backends.cuda.matmul.allow_tf32
+        torch.backends.cuda.matmul.allow_tf32 = False
+        base["cublas_sgemm_ms"] = timed(lambda: torch.matmul(A, B, out=C), 1)
+        torch.backends.cuda.matmul.allow_tf32 = prev
+        Ab, Bb = A.to(torch.bfloat16), B.to(torch.bfloat16)
+        Cb = torch.empty_like(Ab)
+        base["cublas_bf16_gemm_ms"] = timed(lambda: torch.matmul(Ab, Bb, out=Cb), 3)
+        del Ab, Bb, Cb
+        f32 = P.Batch([n], leaf, P.FP32, graph=True)
+        base["fp32_spamm_ms"] = timed(lambda: f32.run([A], [B], [C], [tau]), 1)
+        f32.close()
+        for k in ("cublas_sgemm_ms", "cublas_bf16_gemm_ms", "fp32_spamm_ms"):
+            base["speedup_vs_" + k[:-3]] = base[k] / ms
+    if rank != 0:
+        return None
+    peaks = load_peaks()
+    useful = 2.0 * leaf ** 3 * st["survivors"]
+    mul_ms = part_ms["multiply"]
+    ach = useful / (mul_ms * 1e-3) / 1e12
+    peak = peaks["bf16_tflops"]
+    line = {
+        "metric": METRIC, "value": dense / (ms * 1e-3) / 1e12 * world,
+        "unit": "TFLOP/s (dense-equivalent, 2N^3/t)", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": {"bf16": "bf16", "fp16": "f16", "tf32x3": "tf32",
+                                       "fp32": "f32"}.get(prec_name, prec_name),
+        "data": "synthetic (seeded near-sparse ReLU(N(0,1)) with 70% of the rest zeroed, drawn on the GPU)",
+        "config": {"workload": f"near-sparse N={n}, leaf {leaf}, {prec_name}, tau for valid ratio "
+                               f"{args.ratio:g} (valid-ratio search)",
+                   "n": n, "leaf": leaf, "tau": tau, "valid_ratio": st["valid_ratio"],
+                   "search_probes": probes, "survivors": st["survivors"],
+                   "schedule": best["schedule"], "autotune": cands,
+                   "rel_err_sampled_tiles_vs_fp64": rel_tiles,
+                   "useful_tflops": useful / (ms * 1e-3) / 1e12,
+                   "l2": f"inputs larger than L2 ({4 * n * n / 1e9:.1f} GB each)",
+                   "parallelism": f"replicas x{world}", "launch": "cuda-graph replay"},
+        "breakdown_ms": part_ms,
+        "baselines_same_gpu": base,
+        "gpu_launches": 8 * args.steps,
+        "roofline": {"kernel": "multiply phase (tcgen05 multiply; rounding excluded)",
+                     "bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+                     "frac": ach / peak, "traffic": None, "per_launch_ms": mul_ms,
+                     "algorithmic_flops": useful,
+                     "peak_source": peaks["source"] + " bf16 dense (burst)"},
+        "clocks": clk.summary(),
+    }
+    batch.close()
+    return line
+
+
+# ---------------------------------------------------------------------------
 # Reference arm: the oracle as it stands, on the host cores
 # ---------------------------------------------------------------------------
 
 def run_reference(args):
+    args.n = args.n or N_DEFAULT
     a_h, b_h = workload(args.n)
     leaf, tau = args.leaf, args.tau
     bd = -(-args.n // leaf)
@@ -699,7 +841,8 @@ def main():
     ap.add_argument("--precision", default="bf16_split")
     ap.add_argument("--tau", type=float, default=1e-2)
     ap.add_argument("--target", type=float, default=1e-5)
-    ap.add_argument("--n", type=int, default=N_DEFAULT)
+    ap.add_argument("--n", type=int, default=None,
+                    help="matrix size (default 8192; sparse workload 32768)")
     ap.add_argument("--leaf", type=int, default=LEAF_DEFAULT)
     ap.add_argument("--cpu-rows", type=int, default=128,
                     help="output block-rows of the oracle's timed sample (cpu_baseline)")
@@ -708,8 +851,10 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-baselines", action="store_true")
     ap.add_argument("--eager", action="store_true", help="time host-enqueued calls, no graph")
-    ap.add_argument("--workload", default="single", choices=["single", "batch"],
-                    help="single: one N=8192 product; batch: 256 uneven instances")
+    ap.add_argument("--workload", default="single", choices=["single", "batch", "sparse"],
+                    help="single: one N=8192 product; batch: 256 uneven instances; "
+                         "sparse: near-sparse N=32768 at a target valid ratio")
+    ap.add_argument("--ratio", type=float, default=0.5, help="sparse: target valid ratio")
     ap.add_argument("--count", type=int, default=BATCH_COUNT)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
@@ -725,7 +870,8 @@ def main():
         import torch
         import torch.distributed as dist
         dist.init_process_group("nccl")
-    line = run_batch(args, rank, world) if args.workload == "batch" else run_ours(args, rank, world)
+    runner = {"batch": run_batch, "sparse": run_sparse}.get(args.workload, run_ours)
+    line = runner(args, rank, world)
     if line is not None:
         print(json.dumps(line), flush=True)
     if world > 1:

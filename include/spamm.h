@@ -236,8 +236,10 @@ spamm_status_t spamm_multiply_fp32_noalloc(const float* A, const float* B, float
  * spamm_batch_export: host copies of one instance's norm maps (FP64
  *   [bd*bd] each) and work queues (as spamm_plan_export); every pointer may
  *   be NULL; blocks.
- * spamm_batch_timings: ms[3] = device time of the norm maps, the plan and
- *   the multiply of the last run (SPAMM_BATCH_TIMING only); blocks.
+ * spamm_batch_timings: ms[4] = device time of the norm maps, the plan, the
+ *   operand rounding (0 for FP32) and the multiply (with the zero-fill of
+ *   empty tiles, overlapped) of the last run (SPAMM_BATCH_TIMING only);
+ *   blocks.
  * spamm_batch_autotune: times every candidate configuration on the given
  *   problems and returns the fastest in *best: leaf 64 and 128 (32, 64 and
  *   128 for FP32) times the static and dynamic multiply schedules, each
@@ -305,6 +307,22 @@ spamm_status_t spamm_batch_destroy(spamm_batch_t batch);
  * ------------------------------------------------------------------------- */
 spamm_status_t spamm_plan_band(spamm_plan_t plan, const double* normA, const double* normB,
                                double tau_lo, double tau_hi, void* stream);
+
+/* ---------------------------------------------------------------------------
+ * spamm_tau_for_valid_ratio -- the paper's search for a customised accuracy
+ * (Section 3.5.2): tau whose valid ratio S / bd^3 is within `tol` of
+ * `target_ratio`.  ave = mean norm product over all bd^3 triples (closed
+ * form sum_k colsum_A(k) rowsum_B(k) / bd^3); the interval [0, k ave] is
+ * widened (k = 1, 2, ...) until its end gives a ratio <= target, the first
+ * probe is min(ave, k ave), then bisection until within tol or max_probes
+ * probes.  Each probe is the counting half of a plan (no queues).  Outputs
+ * (host): *tau, and *ratio / *probes when non-NULL.  Blocks.  The plan's
+ * buffers are used: plan again (spamm_plan) afterwards.
+ * ------------------------------------------------------------------------- */
+spamm_status_t spamm_tau_for_valid_ratio(spamm_plan_t plan, const double* normA,
+                                         const double* normB, double target_ratio, double tol,
+                                         int32_t max_probes, double* tau, double* ratio,
+                                         int32_t* probes, void* stream);
 
 /* ---------------------------------------------------------------------------
  * Learned tau.  The paper picks tau by a search for a target valid ratio

@@ -82,6 +82,8 @@ _SIGS = {
     "spamm_batch_destroy": [_VP],
     "spamm_batch_timings": [_VP, _VP],
     "spamm_plan_band": [_VP, _VP, _VP, _D, _D, _VP],
+    "spamm_tau_for_valid_ratio": [_VP, _VP, _VP, _D, _D, _I32, ctypes.POINTER(_D),
+                                  ctypes.POINTER(_D), ctypes.POINTER(_I32), _VP],
     "spamm_norm_histogram": [_VP, _VP, _VP, _VP, _VP],
     "spamm_tau_predict": [_VP, _VP, _VP, _D, _VP, ctypes.POINTER(_D), _VP],
     "spamm_batch_tau_predict": [_VP, _VP, _VP, _VP, _VP, _VP],
@@ -214,6 +216,16 @@ class Plan:
                                      float(tau_hi), _stream(stream)), "spamm_plan_band")
         return self
 
+    def tau_for_valid_ratio(self, normA, normB, target: float, tol: float = 0.01,
+                            max_probes: int = 20, stream=None):
+        """(tau, valid ratio, probes) of the valid-ratio search (Section 3.5.2)."""
+        t, r, k = ctypes.c_double(), ctypes.c_double(), ctypes.c_int32()
+        _check(lib().spamm_tau_for_valid_ratio(self.handle, _ptr(normA), _ptr(normB),
+                                               float(target), float(tol), int(max_probes),
+                                               ctypes.byref(t), ctypes.byref(r), ctypes.byref(k),
+                                               _stream(stream)), "spamm_tau_for_valid_ratio")
+        return t.value, r.value, k.value
+
     def histogram(self, normA, normB, stream=None):
         """Raw counts of the 64-bin log2 histogram of relative norm products."""
         import numpy as np
@@ -340,11 +352,11 @@ class Batch:
         return out
 
     def timings(self):
-        """{"normmap", "plan", "multiply"} device ms of the last run (timing batches only)."""
-        ms = (ctypes.c_float * 3)()
+        """{"normmap", "plan", "round", "multiply"} device ms of the last run (timing batches only)."""
+        ms = (ctypes.c_float * 4)()
         _check(lib().spamm_batch_timings(self.handle, ctypes.cast(ms, ctypes.c_void_p)),
                "spamm_batch_timings")
-        return {"normmap": ms[0], "plan": ms[1], "multiply": ms[2]}
+        return {"normmap": ms[0], "plan": ms[1], "round": ms[2], "multiply": ms[3]}
 
     def close(self):
         if self.handle:

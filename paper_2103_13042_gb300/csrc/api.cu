@@ -160,7 +160,8 @@ spamm_status_t engine_free(Engine& e) {
   return st;
 }
 
-cudaError_t engine_multiply(Engine& e, const InstRef& ref, int32_t* status, cudaStream_t s) {
+cudaError_t engine_multiply(Engine& e, const InstRef& ref, int32_t* status, cudaStream_t s,
+                            cudaEvent_t after_round) {
   // empty tiles (zeros, HBM-write bound) on the side stream, overlapped with
   // the rounding and multiply of the non-empty tiles (disjoint parts of C)
   cudaError_t err = cudaEventRecord(e.fork, s);
@@ -171,9 +172,11 @@ cudaError_t engine_multiply(Engine& e, const InstRef& ref, int32_t* status, cuda
     err = cudaMemsetAsync(&e.buf.bdev->mul_ticket, 0, sizeof(int), s);
   if (err == cudaSuccess) {
     if (e.precision == SPAMM_FP32) {
-      err = launch_multiply_simt(ref, e.buf, e.leaf, e.schedule, s);
+      if (after_round) err = cudaEventRecord(after_round, s);
+      if (err == cudaSuccess) err = launch_multiply_simt(ref, e.buf, e.leaf, e.schedule, s);
     } else {
       err = launch_quantize(e.precision, e.leaf, ref, e.buf, e.img, s);
+      if (err == cudaSuccess && after_round) err = cudaEventRecord(after_round, s);
       if (err == cudaSuccess)
         err = launch_multiply_tc(e.precision, e.leaf, ref, e.buf, e.img, status, e.schedule, s);
     }
@@ -196,6 +199,41 @@ void fill_stats(const PlanDevice& h, int leaf, int bd, spamm_stats_t* stats) {
   stats->bd = bd;
   stats->max_tile_survivors = h.max_tile;
   stats->flag_exponent = h.flag_exp;
+}
+
+spamm_status_t export_queues(const PlanBuffers& b, const Inst& in, int32_t* tile_ptr,
+                             uint16_t* k_idx, int64_t cap, cudaStream_t s) {
+  const int64_t tiles = (int64_t)in.bd * in.bd;
+  // per tile: count and absolute first slot (tiles are stored in the plan's
+  // enumeration order, not row-major)
+  std::vector<int32_t> cnt((size_t)tiles), beg((size_t)tiles);
+  SPAMM_CUDA_TRY(cudaMemcpyAsync(cnt.data(), b.cnt + in.tile0, (size_t)tiles * sizeof(int32_t),
+                                 cudaMemcpyDeviceToHost, s));
+  SPAMM_CUDA_TRY(cudaMemcpyAsync(beg.data(), b.tile_beg + in.tile0,
+                                 (size_t)tiles * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  SPAMM_CUDA_TRY(cudaStreamSynchronize(s));
+  int64_t total = 0;
+  for (int64_t t = 0; t < tiles; ++t) {
+    if (tile_ptr) tile_ptr[t] = (int32_t)total;
+    total += cnt[(size_t)t];
+  }
+  if (tile_ptr) tile_ptr[tiles] = (int32_t)total;
+  if (k_idx) {
+    if (cap < total) return SPAMM_ERR_NO_MEMORY;
+    if (total > 0) {
+      // the instance's slots are one contiguous range from its first slot
+      std::vector<uint16_t> raw((size_t)total);
+      SPAMM_CUDA_TRY(cudaMemcpyAsync(raw.data(), b.k_idx + in.kidx0,
+                                     (size_t)total * sizeof(uint16_t), cudaMemcpyDeviceToHost, s));
+      SPAMM_CUDA_TRY(cudaStreamSynchronize(s));
+      int64_t o = 0;
+      for (int64_t t = 0; t < tiles; ++t) {
+        const int64_t src = (int64_t)beg[(size_t)t] - in.kidx0;
+        for (int32_t q = 0; q < cnt[(size_t)t]; ++q) k_idx[o++] = raw[(size_t)(src + q)];
+      }
+    }
+  }
+  return SPAMM_OK;
 }
 
 }  // namespace spamm
@@ -332,28 +370,8 @@ spamm_status_t spamm_plan_stats(spamm_plan_t plan, spamm_stats_t* stats, void* s
 spamm_status_t spamm_plan_export(spamm_plan_t plan, int32_t* tile_ptr, uint16_t* k_idx,
                                  int64_t cap, void* stream) {
   if (!plan) return SPAMM_ERR_INVALID_ARG;
-  cudaStream_t s = (cudaStream_t)stream;
-  const PlanBuffers& b = plan->eng.buf;
-  const int64_t tiles = b.tiles;
-  // a single instance's queues are one contiguous CSR in tile order
-  std::vector<int32_t> cnt((size_t)tiles);
-  SPAMM_CUDA_TRY(cudaMemcpyAsync(cnt.data(), b.cnt, (size_t)tiles * sizeof(int32_t),
-                                 cudaMemcpyDeviceToHost, s));
-  SPAMM_CUDA_TRY(cudaStreamSynchronize(s));
-  int64_t total = 0;
-  for (int64_t t = 0; t < tiles; ++t) {
-    if (tile_ptr) tile_ptr[t] = (int32_t)total;
-    total += cnt[(size_t)t];
-  }
-  if (tile_ptr) tile_ptr[tiles] = (int32_t)total;
-  if (k_idx) {
-    if (cap < total) return SPAMM_ERR_NO_MEMORY;
-    if (total > 0)
-      SPAMM_CUDA_TRY(cudaMemcpyAsync(k_idx, b.k_idx, (size_t)total * sizeof(uint16_t),
-                                     cudaMemcpyDeviceToHost, s));
-  }
-  SPAMM_CUDA_TRY(cudaStreamSynchronize(s));
-  return SPAMM_OK;
+  return export_queues(plan->eng.buf, plan->eng.insts[0], tile_ptr, k_idx, cap,
+                       (cudaStream_t)stream);
 }
 
 spamm_status_t spamm_multiply(spamm_plan_t plan, const float* A, const float* B, float* C,
@@ -403,6 +421,82 @@ spamm_status_t spamm_plan_band(spamm_plan_t plan, const double* normA, const dou
     (void)cudaGetLastError();
     return SPAMM_ERR_CUDA;
   }
+  return SPAMM_OK;
+}
+
+spamm_status_t spamm_tau_for_valid_ratio(spamm_plan_t plan, const double* normA,
+                                         const double* normB, double target_ratio, double tol,
+                                         int32_t max_probes, double* tau, double* ratio,
+                                         int32_t* probes, void* stream) {
+  if (!plan || !normA || !normB || !tau) return SPAMM_ERR_INVALID_ARG;
+  if (!aligned16(normA) || !aligned16(normB)) return SPAMM_ERR_INVALID_ARG;
+  if (!(target_ratio >= 0.0 && target_ratio <= 1.0) || !(tol >= 0.0) || max_probes < 1)
+    return SPAMM_ERR_INVALID_ARG;
+  Engine& e = plan->eng;
+  const int bd = plan->bd;
+  const cudaStream_t s = (cudaStream_t)stream;
+  // ave = mean of nA[i,k] nB[k,j] over all bd^3 triples = sum_k colsum_A(k) rowsum_B(k) / bd^3
+  std::vector<double> ha((size_t)bd * bd), hb((size_t)bd * bd);
+  SPAMM_CUDA_TRY(cudaMemcpyAsync(ha.data(), normA, ha.size() * sizeof(double),
+                                 cudaMemcpyDeviceToHost, s));
+  SPAMM_CUDA_TRY(cudaMemcpyAsync(hb.data(), normB, hb.size() * sizeof(double),
+                                 cudaMemcpyDeviceToHost, s));
+  SPAMM_CUDA_TRY(cudaStreamSynchronize(s));
+  double acc = 0.0;
+  for (int k = 0; k < bd; ++k) {
+    double col = 0.0, row = 0.0;
+    for (int i = 0; i < bd; ++i) col += ha[(size_t)i * bd + k];
+    for (int j = 0; j < bd; ++j) row += hb[(size_t)k * bd + j];
+    acc += col * row;
+  }
+  const double cube = (double)bd * bd * bd;
+  const double ave = acc / cube;
+  Inst& in = e.insts[0];
+  in.nA = normA;
+  in.nB = normB;
+  in.band = 0;
+  in.split = 0;
+  in.quant = 0;
+  auto valid_ratio = [&](double t, double* out) -> spamm_status_t {
+    in.T = make_tau_screen(t);
+    cudaError_t err = run_plan_count(make_ref(e.insts.data(), nullptr, 1), e.buf, s);
+    if (err != cudaSuccess) {
+      (void)cudaGetLastError();
+      return SPAMM_ERR_CUDA;
+    }
+    long long surv = 0;
+    SPAMM_CUDA_TRY(cudaMemcpyAsync(&surv, &e.buf.pd->survivors, sizeof(long long),
+                                   cudaMemcpyDeviceToHost, s));
+    SPAMM_CUDA_TRY(cudaStreamSynchronize(s));
+    *out = (double)surv / cube;
+    return SPAMM_OK;
+  };
+  // Section 3.5.2: widen [0, k ave] until its upper end gives at most the
+  // target ratio, probe ave, then bisect until within tol
+  double vr = 0.0;
+  int k = 1;
+  for (;;) {
+    spamm_status_t st = valid_ratio(k * ave, &vr);
+    if (st != SPAMM_OK) return st;
+    if (!(vr > target_ratio) || k >= 1000000) break;
+    ++k;
+  }
+  double lo = 0.0, hi = k * ave;
+  double t = ave < hi ? ave : hi;
+  spamm_status_t st = valid_ratio(t, &vr);
+  if (st != SPAMM_OK) return st;
+  int n = 1;
+  while (std::fabs(vr - target_ratio) > tol && n < max_probes) {
+    if (vr > target_ratio) lo = t;
+    else hi = t;
+    t = 0.5 * (lo + hi);
+    st = valid_ratio(t, &vr);
+    if (st != SPAMM_OK) return st;
+    ++n;
+  }
+  *tau = t;
+  if (ratio) *ratio = vr;
+  if (probes) *probes = n;
   return SPAMM_OK;
 }
 

@@ -39,7 +39,7 @@ struct spamm_batch_s {
   cudaEvent_t ev_in = nullptr, ev_out = nullptr;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
-  cudaEvent_t phase[4] = {};     // SPAMM_BATCH_TIMING: before norms, after norms, plan, multiply
+  cudaEvent_t phase[5] = {};     // SPAMM_BATCH_TIMING: start, after norms, plan, rounding, multiply
   bool timed = false;            // a timed run has been enqueued
 };
 
@@ -134,8 +134,8 @@ cudaError_t enqueue(spamm_batch_s* b, cudaStream_t s, bool timing) {
   if (e == cudaSuccess && timing) e = cudaEventRecord(b->phase[1], s);
   if (e == cudaSuccess) e = run_plan(ref, b->eng.buf, s);
   if (e == cudaSuccess && timing) e = cudaEventRecord(b->phase[2], s);
-  if (e == cudaSuccess) e = engine_multiply(b->eng, ref, b->status, s);
-  if (e == cudaSuccess && timing) e = cudaEventRecord(b->phase[3], s);
+  if (e == cudaSuccess) e = engine_multiply(b->eng, ref, b->status, s, timing ? b->phase[3] : nullptr);
+  if (e == cudaSuccess && timing) e = cudaEventRecord(b->phase[4], s);
   return e;
 }
 
@@ -420,32 +420,15 @@ spamm_status_t spamm_batch_export(spamm_batch_t b, int32_t index, double* normA,
   if (normB)
     SPAMM_CUDA_TRY(cudaMemcpyAsync(normB, b->normB + in.tile0, (size_t)tiles * sizeof(double),
                                    cudaMemcpyDeviceToHost, s));
-  // an instance's queues are one contiguous CSR from its first k_idx slot
-  std::vector<int32_t> cnt((size_t)tiles);
-  SPAMM_CUDA_TRY(cudaMemcpyAsync(cnt.data(), pb.cnt + in.tile0, (size_t)tiles * sizeof(int32_t),
-                                 cudaMemcpyDeviceToHost, s));
   SPAMM_CUDA_TRY(cudaStreamSynchronize(s));
-  int64_t total = 0;
-  for (int64_t t = 0; t < tiles; ++t) {
-    if (tile_ptr) tile_ptr[t] = (int32_t)total;
-    total += cnt[(size_t)t];
-  }
-  if (tile_ptr) tile_ptr[tiles] = (int32_t)total;
-  if (k_idx) {
-    if (cap < total) return SPAMM_ERR_NO_MEMORY;
-    if (total > 0)
-      SPAMM_CUDA_TRY(cudaMemcpyAsync(k_idx, pb.k_idx + in.kidx0, (size_t)total * sizeof(uint16_t),
-                                     cudaMemcpyDeviceToHost, s));
-  }
-  SPAMM_CUDA_TRY(cudaStreamSynchronize(s));
-  return SPAMM_OK;
+  return export_queues(pb, in, tile_ptr, k_idx, cap, s);
 }
 
 spamm_status_t spamm_batch_timings(spamm_batch_t b, float* ms) {
   if (!b || !ms) return SPAMM_ERR_INVALID_ARG;
   if (!(b->flags & SPAMM_BATCH_TIMING) || !b->timed) return SPAMM_ERR_INVALID_ARG;
-  SPAMM_CUDA_TRY(cudaEventSynchronize(b->phase[3]));
-  for (int q = 0; q < 3; ++q)
+  SPAMM_CUDA_TRY(cudaEventSynchronize(b->phase[4]));
+  for (int q = 0; q < 4; ++q)
     SPAMM_CUDA_TRY(cudaEventElapsedTime(&ms[q], b->phase[q], b->phase[q + 1]));
   return SPAMM_OK;
 }

@@ -118,6 +118,14 @@ __device__ __forceinline__ void sumsq_merge(SumSq& acc, float hi, float lo, int 
 }
 
 // Exact-squares sum of one group of N entries into acc.
+//
+// The running pair starts at B = 2 fl((scaled max)^2), so every square p
+// satisfies p < hi (also after a renormalisation, which moves hi by far less
+// than B / 2) and Fast2Sum gives the exact error of hi + p in 3 operations;
+// the errors and the low halves of the squares go into lo, and (hi, lo) is
+// renormalised every 8 entries.  B is removed with one TwoSum at the end.  Groups whose largest magnitude lies in
+// [2^-30, 2^61) are not scaled: squares of entries below 2^-63 may then lose
+// bits, but they are below 2^-66 of the largest square.
 template <int N>
 __device__ __forceinline__ void sumsq_group(SumSq& acc, const float (&v)[N]) {
   float mx = 0.0f;
@@ -133,11 +141,34 @@ __device__ __forceinline__ void sumsq_group(SumSq& acc, const float (&v)[N]) {
     }
     return;
   }
-  const int g = group_exponent(mx);
-  const float sc = pow2f(-g);
-  float hi = 0.0f, lo = 0.0f;
+  const int g0 = group_exponent(mx);
+  const bool scaled = g0 < -30 || g0 > 60;
+  const int g = scaled ? g0 : 0;
+  const float sc = scaled ? pow2f(-g0) : 1.0f;
+  const float ms = __fmul_rn(mx, sc);
+  const float pB = 2.0f * __fmul_rn(ms, ms);   // the starting value B (a float)
+  float hi = pB, lo = 0.0f;
 #pragma unroll
-  for (int q = 0; q < N; ++q) dw_add_square(__fmul_rn(v[q], sc), hi, lo);
+  for (int q = 0; q < N; ++q) {
+    const float x = __fmul_rn(v[q], sc);
+    const float p = __fmul_rn(x, x);
+    const float pe = __fmaf_rn(x, x, -p);
+    const float s = __fadd_rn(hi, p);
+    const float e = __fsub_rn(p, __fsub_rn(s, hi));   // exact: hi >= p
+    hi = s;
+    lo = __fadd_rn(lo, __fadd_rn(e, pe));
+    if ((q & 7) == 7) {   // renormalise: |hi| >= |lo|
+      const float t = __fadd_rn(hi, lo);
+      lo = __fsub_rn(lo, __fsub_rn(t, hi));
+      hi = t;
+    }
+  }
+  // remove the starting value B
+  float s, e;
+  two_sum(hi, -pB, s, e);
+  lo = __fadd_rn(lo, e);
+  hi = __fadd_rn(s, lo);
+  lo = __fsub_rn(lo, __fsub_rn(hi, s));
   sumsq_merge(acc, hi, lo, g);
 }
 

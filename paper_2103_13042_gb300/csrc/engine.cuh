@@ -46,9 +46,17 @@ spamm_status_t engine_free(Engine& e);
 
 // Enqueues the multiply of every instance of `ref` on `s` (zero-fill of the
 // empty tiles forked to the side stream and joined back).
-cudaError_t engine_multiply(Engine& e, const InstRef& ref, int32_t* status, cudaStream_t s);
+// `after_round` (optional) is recorded on `s` once the operands are rounded
+// (tensor modes) or right away (FP32).
+cudaError_t engine_multiply(Engine& e, const InstRef& ref, int32_t* status, cudaStream_t s,
+                            cudaEvent_t after_round = nullptr);
 
 void fill_stats(const PlanDevice& h, int leaf, int bd, spamm_stats_t* out);
+
+// Host copy of one instance's work queues as a row-major CSR (tile t = i*bd + j):
+// tile_ptr[bd*bd + 1] and k_idx[cap] may be null.  Blocks.
+spamm_status_t export_queues(const PlanBuffers& b, const Inst& in, int32_t* tile_ptr,
+                             uint16_t* k_idx, int64_t cap, cudaStream_t s);
 
 // Lazily allocated device status word of the current device (tensor-core
 // kernels latch timeouts there).

@@ -6,19 +6,24 @@
 //   prep      FP64 norm maps -> FP32 mantissa/exponent "screen" forms (B transposed
 //             so a tile's k-run is contiguous) and per-CTA sums of squared norms;
 //             the last CTA of each instance forms ||A||_F, ||B||_F.
-//   count     each CTA owns 32 consecutive tiles of one instance, one warp per
-//             tile at a time: lanes test k = lane, lane+32, ...; ballot + popc
-//             count the survivors; skipped products are summed for the bounds;
-//             split modes bin the surviving products by binade; per-CTA totals
-//             and a batch-wide histogram of the per-tile counts.
-//   finalize  one CTA per instance over its CTAs' totals: their exclusive scan
-//             (the first k_idx slot of each CTA's tiles), statistics and the
-//             split-flag binade; the last of these CTAs turns the histogram into
-//             the bucket starts of the batch-wide longest-first order.
-//   fill      same tile partition: first slots from the CTA base plus a warp
-//             scan; the same test again, ballot ranks place the surviving k
-//             (increasing) at tile_beg[t] + rank; non-empty tiles take their
-//             longest-first slot from a per-count cursor.
+//   count     each CTA owns 32 tiles of one instance (consecutive in a grouped
+//             raster enumeration: bands of 8 block rows, column by column), one
+//             warp per tile at a time: lanes test k = lane, lane+32, ...; the
+//             ballot words are kept as the tile's survivor bitmask; skipped
+//             products are summed for the bounds; split modes bin the surviving
+//             products by binade; per-CTA totals and per-CTA counts of the
+//             longest-first buckets (floor(log2 survivors) + 1).
+//   finalize  one CTA per instance: one vector scan over its CTAs' totals gives
+//             each CTA's first k_idx slot, non-empty rank and bucket slots;
+//             statistics and the split-flag binade; the last of these CTAs lays
+//             out the batch-wide buckets (largest first) and each instance's
+//             place in them.
+//   fill      same partition: first slots from the CTA base plus a warp scan;
+//             the bitmask words are expanded (ballot ranks place the surviving
+//             k, increasing, at tile_beg[t] + rank); each non-empty tile takes
+//             its slot in the longest-first order (bucket base + CTA base +
+//             rank among the CTA's tiles of the bucket, enumeration order), each
+//             empty tile its slot after all non-empty ones.
 #include <cstddef>
 #include <cstring>
 #include <vector>
@@ -50,7 +55,28 @@ constexpr int kWarpsPerCta = 8;
 constexpr int kTilesPerCta = 32;   // count and fill: 8 warps x 4 tiles
 constexpr int kTileRounds = kTilesPerCta / kWarpsPerCta;
 constexpr int kPrepThreads = 256;
-constexpr int kFinThreads = 1024;
+constexpr int kFinThreads = 512;
+constexpr int kGroupRows = 8;      // block rows per band of the tile enumeration
+static_assert(kOrderKeys <= kMaxBd + 2 && kOrderKeys <= 32, "order buckets");
+
+// Output tile (i, j) at enumeration position `pos` of an instance: bands of
+// kGroupRows block rows, column by column inside a band, so that tiles close
+// in the enumeration (and so in the multiply's order, which keeps it inside
+// a bucket) share block rows of A and block columns of B in L2.
+__device__ __forceinline__ void tile_at(int64_t pos64, int bd, int& i, int& j) {
+  const int pos = (int)pos64;              // bd <= 1024: pos < 2^20
+  const int band_tiles = kGroupRows * bd;
+  const int band = pos / band_tiles;
+  const int r0 = band * kGroupRows;
+  const int rows = min(kGroupRows, bd - r0);
+  const int w = pos - band * band_tiles;
+  j = w / rows;
+  i = r0 + (w - j * rows);
+}
+
+// Longest-first bucket of a survivor count c >= 1: floor(log2 c) + 1.  Near-
+// equal counts share a bucket, so the order keeps the enumeration's locality.
+__device__ __forceinline__ int order_key(int c) { return 32 - __clz(c); }
 
 // Exactly !(na * nb < tau) in FP64, decided in FP32 whenever that is safe.
 __device__ __forceinline__ bool survives(Screen a, Screen b, const double* nA_ptr,
@@ -107,6 +133,26 @@ __device__ __forceinline__ void ext_add(ExtSum& s, float q, int E) {
 __device__ __forceinline__ void ext_add_rel(ExtSum& s, Screen a, Screen b, float inv_m, int inv_e) {
   if (a.e == kZeroExp || b.e == kZeroExp) return;
   ext_add(s, __fmul_rn(__fmul_rn(a.m, b.m), inv_m), a.e + b.e + inv_e);
+}
+
+// Warp total of ExtSums in one pass: every lane rescales its sum to 2^-40 of
+// the warp's largest binade (smaller terms dropped, as ext_add does) and the
+// FP32 values are added with xor shuffles (a fixed order).
+__device__ __forceinline__ ExtSum ext_warp_sum_fast(ExtSum s) {
+  constexpr int kNone = -(1 << 29);
+  const int eb = s.m > 0.0f ? s.e + fexp(s.m) : kNone;   // true binade of the lane's sum
+  int emax = eb;
+  for (int off = 16; off > 0; off >>= 1) emax = max(emax, __shfl_xor_sync(0xffffffffu, emax, off));
+  if (emax == kNone) return ExtSum{0.0f, 0};
+  float v = 0.0f;
+  if (eb >= emax - 40) v = s.m * pow2f(s.e - (emax - 40));   // exponent in [-80, 40]
+  for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+  ExtSum r{v, emax - 40};
+  while (r.m >= 1099511627776.0f) {   // keep the mantissa below 2^40 (v < 2^89)
+    r.m *= pow2f(-40);
+    r.e += 40;
+  }
+  return r;
 }
 
 __device__ __forceinline__ ExtSum ext_warp_sum(ExtSum s) {
@@ -218,14 +264,16 @@ __global__ void __launch_bounds__(kPrepThreads)
   }
 }
 
-__global__ void __launch_bounds__(kWarpsPerCta * 32)
+__global__ void __launch_bounds__(kWarpsPerCta * 32, 3)
     count_kernel(InstRef R, PlanBuffers Bf) {
   __shared__ double s_bin_sum[kFlagBins];
   __shared__ int s_bin_cnt[kFlagBins];
   __shared__ long long s_S[kWarpsPerCta];
   __shared__ int s_kmax[kWarpsPerCta], s_ne[kWarpsPerCta];
   __shared__ ExtSum s_b1[kWarpsPerCta], s_b2[kWarpsPerCta];
+  __shared__ int s_keys[kOrderKeys];
   const int warp = threadIdx.x / 32, lane = threadIdx.x & 31;
+  if (threadIdx.x < kOrderKeys) s_keys[threadIdx.x] = 0;
   const int ii = inst_of_count_cta(R, blockIdx.x);
   const Inst& in = R.at(ii);
   const int bd = in.bd, split = in.split, band = in.band;
@@ -245,26 +293,43 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32)
   int inv_e;
   const float inv_m = (float)frexp(inv, &inv_e);
   const int64_t tiles = (int64_t)bd * bd;
+  const int nch = (bd + 31) >> 5;
   const int64_t lt0 = (int64_t)(blockIdx.x - in.count0) * kTilesPerCta;
   long long wS = 0;
   int wkmax = 0, wne = 0;
   ExtSum wb1{0.0f, 0}, wb2{0.0f, 0};
   for (int r = 0; r < kTileRounds; ++r) {
-    const int64_t t = lt0 + warp + (int64_t)r * kWarpsPerCta;
-    if (t >= tiles) break;
-    const int i = (int)(t / bd), j = (int)(t % bd);
+    const int64_t pos = lt0 + warp + (int64_t)r * kWarpsPerCta;
+    if (pos >= tiles) break;
+    int i, j;
+    tile_at(pos, bd, i, j);
+    const int64_t t = (int64_t)i * bd + j;
     const Screen* ra = Bf.sA + in.tile0 + (int64_t)i * bd;
     const Screen* rb = Bf.sBT + in.tile0 + (int64_t)j * bd;
     ExtSum sk{0.0f, 0};
     int count = 0;
     int run_bin = kFlagBinMin - 1, run_cnt = 0;
     double run_sum = 0.0;
-#pragma unroll 4
-    for (int k0 = 0; k0 < bd; k0 += 32) {
+    // the screens of up to four 32-wide chunks of k are loaded together (one
+    // memory latency per group instead of one per chunk)
+    for (int kg = 0; kg < bd; kg += 128) {
+      Screen av[4], bv[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int k = kg + 32 * q + lane;
+        if (k < bd) {
+          av[q] = ra[k];
+          bv[q] = rb[k];
+        }
+      }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int k0 = kg + 32 * q;
+      if (k0 >= bd) break;   // uniform over the warp
       const int k = k0 + lane;
       bool s = false;
       if (k < bd) {
-        const Screen a = ra[k], b = rb[k];
+        const Screen a = av[q], b = bv[q];
         s = survives(a, b, nA + (int64_t)i * bd + k, nB + (int64_t)k * bd + j, T);
         if (s && band) s = !survives(a, b, nA + (int64_t)i * bd + k, nB + (int64_t)k * bd + j, Thi);
         if (!s) {
@@ -286,17 +351,20 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32)
           ++run_cnt;
         }
       }
-      count += __popc(__ballot_sync(0xffffffffu, s));
+      const unsigned bal = __ballot_sync(0xffffffffu, s);
+      count += __popc(bal);
+      if (lane == 0) Bf.surv_mask[in.mask0 + t * nch + (k0 >> 5)] = bal;
+    }
     }
     if (split && run_cnt) {
       atomicAdd(&s_bin_sum[run_bin - kFlagBinMin], run_sum);
       atomicAdd(&s_bin_cnt[run_bin - kFlagBinMin], run_cnt);
     }
-    const ExtSum tot = ext_warp_sum(sk);   // no FP64: the FP64 pipe is narrow here
+    const ExtSum tot = ext_warp_sum_fast(sk);   // no FP64: the FP64 pipe is narrow here
     if (lane == 0) {
       const int64_t g = in.tile0 + t;
       Bf.cnt[g] = count;
-      if (count > 0) atomicAdd(&Bf.bdev->hist[count], 1);
+      if (count > 0) atomicAdd(&s_keys[order_key(count)], 1);
       ext_add(wb1, tot.m, tot.e);
       ext_add(wb2, __fmul_rn(tot.m, tot.m), 2 * tot.e);
     }
@@ -325,6 +393,7 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32)
     }
     Bf.part_S[blockIdx.x] = S;
     Bf.part_kmax[blockIdx.x] = km;
+    for (int q = 0; q < kOrderKeys; ++q) Bf.part_keys[(int64_t)blockIdx.x * kOrderKeys + q] = s_keys[q];
     Bf.part_ne[blockIdx.x] = ne;
     Bf.part_b1[blockIdx.x] = b1;
     Bf.part_b2[blockIdx.x] = b2;
@@ -409,94 +478,131 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32)
     if (s_hist[q]) atomicAdd(&in.pd->hist[q], s_hist[q]);
 }
 
-// Block-wide exclusive scan of one value per thread (Hillis-Steele in smem).
-template <typename V>
-__device__ V block_exclusive_scan(V x, V* sh, V& total) {
-  const int tid = threadIdx.x;
-  sh[tid] = x;
-  __syncthreads();
-  for (int off = 1; off < kFinThreads; off <<= 1) {
-    const V y = tid >= off ? sh[tid - off] : V(0);
-    __syncthreads();
-    sh[tid] += y;
-    __syncthreads();
+// Block-wide exclusive scan of K values per thread at once (one shuffle scan
+// per warp, one warp over the warp totals): ex[k] = prefix, total[k] = sum.
+// `sh` holds 33 * K ints; every thread of the block calls it.
+template <int K>
+__device__ void block_scan_vec(const int (&x)[K], int (&ex)[K], int (&total)[K], int* sh) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int nwarps = (int)(blockDim.x >> 5);
+  int incl[K];
+#pragma unroll
+  for (int k = 0; k < K; ++k) incl[k] = x[k];
+#pragma unroll
+  for (int off = 1; off < 32; off <<= 1) {
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      const int y = __shfl_up_sync(0xffffffffu, incl[k], off);
+      if (lane >= off) incl[k] += y;
+    }
   }
-  const V incl = sh[tid];
-  total = sh[kFinThreads - 1];
+  if (lane == 31)
+#pragma unroll
+    for (int k = 0; k < K; ++k) sh[warp * K + k] = incl[k];
   __syncthreads();
-  return incl - x;
+  if (warp == 0) {
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      const int w = lane < nwarps ? sh[lane * K + k] : 0;
+      int wi = w;
+#pragma unroll
+      for (int off = 1; off < 32; off <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, wi, off);
+        if (lane >= off) wi += y;
+      }
+      sh[lane * K + k] = wi - w;
+      if (lane == 31) sh[32 * K + k] = wi;
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    ex[k] = sh[warp * K + k] + incl[k] - x[k];
+    total[k] = sh[32 * K + k];
+  }
+  __syncthreads();   // sh is reused by the next scan
 }
 
+// One CTA per instance: per-CTA slot bases (survivors, non-empty tiles, order
+// buckets) by one vector scan, statistics, skipped bounds and the split-flag
+// binade; the last CTA to finish lays out the batch-wide longest-first order.
 __global__ void __launch_bounds__(kFinThreads)
     finalize_kernel(InstRef R, PlanBuffers Bf) {
-  __shared__ long long s_ll[kFinThreads];
-  __shared__ ExtSum s_x[kFinThreads];
-  __shared__ int s_i[kFinThreads];
-  const int tid = threadIdx.x;
+  constexpr int K = 2 + (kOrderKeys - 1);   // survivors, non-empty, buckets 1 .. kOrderKeys-1
+  __shared__ int s_sh[33 * K];
+  __shared__ int s_kmax[kFinThreads / 32];
+  __shared__ ExtSum s_b1[kFinThreads / 32], s_b2[kFinThreads / 32];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const Inst& in = R.at(blockIdx.x);
   const int bd = in.bd;
-  const int64_t tiles = (int64_t)bd * bd;
   const int nparts = (int)(((int64_t)bd * bd + kTilesPerCta - 1) / kTilesPerCta);
   PlanDevice* pd = in.pd;
 
-  // per-CTA first k_idx slots: each thread scans a contiguous chunk
+  // each thread takes a contiguous chunk of the instance's count CTAs
   const int chunk = (nparts + kFinThreads - 1) / kFinThreads;
   const int p0 = min(nparts, chunk * tid), p1 = min(nparts, p0 + chunk);
-  long long locS = 0;
-  int locK = 0, locNE = 0;
+  int loc[K];
+#pragma unroll
+  for (int k = 0; k < K; ++k) loc[k] = 0;
+  int locK = 0;
   ExtSum locB1{0.0f, 0}, locB2{0.0f, 0};
   for (int q = p0; q < p1; ++q) {
     const int cq = in.count0 + q;
-    locS += Bf.part_S[cq];
-    locNE += Bf.part_ne[cq];
+    loc[0] += (int)Bf.part_S[cq];   // at most 32 * bd per CTA
+    loc[1] += Bf.part_ne[cq];
+#pragma unroll
+    for (int key = 1; key < kOrderKeys; ++key)
+      loc[1 + key] += Bf.part_keys[(int64_t)cq * kOrderKeys + key];
     locK = max(locK, Bf.part_kmax[cq]);
     ext_add(locB1, Bf.part_b1[cq].m, Bf.part_b1[cq].e);
     ext_add(locB2, Bf.part_b2[cq].m, Bf.part_b2[cq].e);
   }
-  long long totS;
-  long long baseS = block_exclusive_scan<long long>(locS, s_ll, totS) + in.kidx0;
-  for (int q = p0; q < p1; ++q) {
-    Bf.cta_base[in.count0 + q] = (int)baseS;
-    baseS += Bf.part_S[in.count0 + q];
-  }
-  long long totNE;
-  long long baseNE = block_exclusive_scan<long long>((long long)locNE, s_ll, totNE);
-  for (int q = p0; q < p1; ++q) {
-    Bf.ne_cta_base[in.count0 + q] = (int)baseNE;
-    baseNE += Bf.part_ne[in.count0 + q];
-  }
-  // max and the extended-range sums (FP32 only)
-  s_i[tid] = locK;
-  s_x[tid] = locB1;
-  __syncthreads();
-  for (int s = kFinThreads / 2; s > 0; s >>= 1) {
-    if (tid < s) {
-      s_i[tid] = max(s_i[tid], s_i[tid + s]);
-      ext_add(s_x[tid], s_x[tid + s].m, s_x[tid + s].e);
+  int ex[K], tot[K];
+  block_scan_vec<K>(loc, ex, tot, s_sh);
+  {
+    int base[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) base[k] = ex[k];
+    for (int q = p0; q < p1; ++q) {
+      const int cq = in.count0 + q;
+      Bf.cta_base[cq] = (int)in.kidx0 + base[0];
+      base[0] += (int)Bf.part_S[cq];
+      Bf.ne_cta_base[cq] = base[1];
+      base[1] += Bf.part_ne[cq];
+#pragma unroll
+      for (int key = 1; key < kOrderKeys; ++key) {
+        const int64_t o = (int64_t)cq * kOrderKeys + key;
+        Bf.key_cta_base[o] = base[1 + key];
+        base[1 + key] += Bf.part_keys[o];
+      }
     }
-    __syncthreads();
   }
-  const int kmax = s_i[0];
-  const ExtSum b1x = s_x[0];
-  __syncthreads();
-  s_x[tid] = locB2;
-  __syncthreads();
-  for (int s = kFinThreads / 2; s > 0; s >>= 1) {
-    if (tid < s) ext_add(s_x[tid], s_x[tid + s].m, s_x[tid + s].e);
-    __syncthreads();
+  // max and the extended-range sums (FP32 only): warp shuffles, then warp 0
+  for (int off = 16; off > 0; off >>= 1) locK = max(locK, __shfl_xor_sync(0xffffffffu, locK, off));
+  locB1 = ext_warp_sum(locB1);
+  locB2 = ext_warp_sum(locB2);
+  if (lane == 0) {
+    s_kmax[warp] = locK;
+    s_b1[warp] = locB1;
+    s_b2[warp] = locB2;
   }
-  const ExtSum b2x = s_x[0];
   __syncthreads();
 
-  // split flag binade (one warp): m = the largest mm in [kFlagBinMin - 1, 1]
-  // with c1 * sum_{bins < mm} p <= budget; bins are prefix-summed in a fixed
-  // order (7 consecutive bins per lane, then a warp scan of the lane totals).
-  if (tid < 32) {
+  // warp 0: totals and the split flag binade m = the largest mm in
+  // [kFlagBinMin - 1, 1] with c1 * sum_{bins < mm} p <= budget; bins are
+  // prefix-summed in a fixed order (7 consecutive bins per lane, then a warp
+  // scan of the lane totals).
+  if (warp == 0) {
+    int kmax = lane < kFinThreads / 32 ? s_kmax[lane] : 0;
+    ExtSum b1x = lane < kFinThreads / 32 ? s_b1[lane] : ExtSum{0.0f, 0};
+    ExtSum b2x = lane < kFinThreads / 32 ? s_b2[lane] : ExtSum{0.0f, 0};
+    for (int off = 16; off > 0; off >>= 1) kmax = max(kmax, __shfl_xor_sync(0xffffffffu, kmax, off));
+    b1x = ext_warp_sum(b1x);
+    b2x = ext_warp_sum(b2x);
     const double ab = pd->norm_a * pd->norm_b;
     const double b1 = ext_value(b1x);
     const double bound2 = sqrt(ext_value(b2x)) * ab;
     constexpr int PER = (kFlagBins + 31) / 32;   // 7
-    const int lane = tid;
     int m = kFlagBinMin - 1;
     long long flagged = 0;
     if (in.split) {
@@ -533,18 +639,20 @@ __global__ void __launch_bounds__(kFinThreads)
       flagged = f;
     }
     if (lane == 0) {
-      pd->survivors = totS;
+      pd->survivors = tot[0];
       pd->max_tile = kmax;
-      pd->nonempty = (int)totNE;
+      pd->nonempty = tot[1];
+      for (int key = 1; key < kOrderKeys; ++key) pd->key_tot[key] = tot[1 + key];
       pd->bound1 = b1 * ab;
       pd->bound2 = bound2;
-      pd->valid_ratio = (double)totS / ((double)bd * (double)bd * (double)bd);
+      pd->valid_ratio = (double)tot[0] / ((double)bd * (double)bd * (double)bd);
       pd->flag_exp = m;
       pd->flagged = flagged;
     }
   }
 
-  // the last finalize CTA: bucket starts of the batch-wide longest-first order
+  // the last finalize CTA: bucket starts of the batch-wide longest-first
+  // order, each instance's first slot in each bucket and its non-empty base
   __shared__ bool s_last;
   __threadfence();
   __syncthreads();
@@ -552,21 +660,61 @@ __global__ void __launch_bounds__(kFinThreads)
   __syncthreads();
   if (s_last) {
     __threadfence();
-    const int c = kMaxBd - tid;      // thread tid owns count c (counts 1 .. kMaxBd)
-    const long long h = (c >= 1) ? __ldcg(&Bf.bdev->hist[c]) : 0;
-    long long tot_ne;
-    const long long start = block_exclusive_scan<long long>(h, s_ll, tot_ne);
-    if (c >= 1) Bf.bdev->cursor[c] = (int)start;
-    if (tid == 0) Bf.bdev->nonempty = (int)tot_ne;
-    // non-empty tiles before each instance (the empty-tile ranks of the fill kernel)
-    long long carry = 0;
-    for (int i0 = 0; i0 < R.count; i0 += kFinThreads) {
+    constexpr int KB = kOrderKeys;   // buckets 1 .. kOrderKeys-1 and (slot 0) non-empty
+    int sum[KB];
+#pragma unroll
+    for (int k = 0; k < KB; ++k) sum[k] = 0;
+    for (int i0 = 0; i0 < R.count; i0 += kFinThreads) {   // pass 1: totals over instances
       const int i = i0 + tid;
-      const long long v = i < R.count ? (long long)__ldcg(&R.at(i).pd->nonempty) : 0;
-      long long tot;
-      const long long ex = block_exclusive_scan<long long>(v, s_ll, tot);
-      if (i < R.count) R.at(i).pd->ne_base = (int)(carry + ex);
-      carry += tot;
+      int v[KB], e[KB], t[KB];
+#pragma unroll
+      for (int k = 0; k < KB; ++k) v[k] = 0;
+      if (i < R.count) {
+        const PlanDevice* q = R.at(i).pd;
+        v[0] = __ldcg(&q->nonempty);
+#pragma unroll
+        for (int key = 1; key < kOrderKeys; ++key) v[key] = __ldcg(&q->key_tot[key]);
+      }
+      block_scan_vec<KB>(v, e, t, s_sh);
+#pragma unroll
+      for (int k = 0; k < KB; ++k) sum[k] += t[k];
+    }
+    int start[KB];   // start[key]: first slot of the bucket (largest key first)
+    {
+      int acc = 0;
+#pragma unroll
+      for (int key = kOrderKeys - 1; key >= 1; --key) {
+        start[key] = acc;
+        acc += sum[key];
+      }
+      start[0] = 0;
+      if (tid == 0) {
+        for (int key = 1; key < kOrderKeys; ++key) Bf.bdev->cursor[key] = start[key];
+        Bf.bdev->nonempty = acc;
+      }
+    }
+    int carry[KB];
+#pragma unroll
+    for (int k = 0; k < KB; ++k) carry[k] = 0;
+    for (int i0 = 0; i0 < R.count; i0 += kFinThreads) {   // pass 2: per-instance bases
+      const int i = i0 + tid;
+      int v[KB], e[KB], t[KB];
+#pragma unroll
+      for (int k = 0; k < KB; ++k) v[k] = 0;
+      if (i < R.count) {
+        const PlanDevice* q = R.at(i).pd;
+        v[0] = __ldcg(&q->nonempty);
+#pragma unroll
+        for (int key = 1; key < kOrderKeys; ++key) v[key] = __ldcg(&q->key_tot[key]);
+      }
+      block_scan_vec<KB>(v, e, t, s_sh);
+      if (i < R.count) {
+        PlanDevice* q = R.at(i).pd;
+        q->ne_base = carry[0] + e[0];
+        for (int key = 1; key < kOrderKeys; ++key) q->key_base[key] = start[key] + carry[key] + e[key];
+      }
+#pragma unroll
+      for (int k = 0; k < KB; ++k) carry[k] += t[k];
     }
   }
 }
@@ -577,18 +725,28 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32)
   const int warp = threadIdx.x / 32, lane = threadIdx.x & 31;
   const int ii = inst_of_count_cta(R, blockIdx.x);
   const Inst& in = R.at(ii);
-  const int bd = in.bd, split = in.split, quant = in.quant, band = in.band;
-  const TauScreen T = in.T;
-  const TauScreen Thi = in.T_hi;
+  const int bd = in.bd, split = in.split, quant = in.quant;
   const double* nA = in.nA;
   const double* nB = in.nB;
   const int64_t tiles = (int64_t)bd * bd;
+  const int nch = (bd + 31) >> 5;
   const int64_t lt0 = (int64_t)(blockIdx.x - in.count0) * kTilesPerCta;
   uint32_t* bitsA = Bf.need_bits;
   uint32_t* bitsB = Bf.need_bits + Bf.need_words;
   if (warp == 0) {   // first k_idx slot of each of the CTA's tiles (kTilesPerCta == 32 lanes)
-    const int64_t t = lt0 + lane;
-    const int c = t < tiles ? Bf.cnt[in.tile0 + t] : 0;
+    const int64_t pos = lt0 + lane;
+    // lane q < kOrderKeys: this CTA's first slot in bucket q (loaded with the counts)
+    int key_slot = 0;
+    if (lane > 0 && lane < kOrderKeys)
+      key_slot = in.pd->key_base[lane] + Bf.key_cta_base[(int64_t)blockIdx.x * kOrderKeys + lane];
+    int64_t g = 0;
+    int c = 0;
+    if (pos < tiles) {
+      int i, j;
+      tile_at(pos, bd, i, j);
+      g = in.tile0 + (int64_t)i * bd + j;
+      c = Bf.cnt[g];
+    }
     int incl = c;
     for (int off = 1; off < 32; off <<= 1) {
       const int y = __shfl_up_sync(0xffffffffu, incl, off);
@@ -596,15 +754,20 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32)
     }
     const int beg = Bf.cta_base[blockIdx.x] + incl - c;
     s_beg[lane] = beg;
-    if (t < tiles) Bf.tile_beg[in.tile0 + t] = beg;
-    // empty tiles go after all non-empty ones, in increasing global order: the
-    // rank of an empty tile is its number minus the non-empty tiles before it
+    if (pos < tiles) Bf.tile_beg[g] = beg;
+    // empty tiles go after all non-empty ones, in enumeration order: the rank
+    // of an empty tile is its position minus the non-empty tiles before it
+    // non-empty tiles: bucket slot = instance base + earlier CTAs + rank among
+    // the CTA's lanes of the same bucket (enumeration order inside a bucket)
+    const int key = c > 0 ? order_key(c) : 0;
+    const unsigned same = __match_any_sync(0xffffffffu, key);
+    const int first = __shfl_sync(0xffffffffu, key_slot, key);
+    if (c > 0) Bf.order[first + __popc(same & ((1u << lane) - 1u))] = (int)g;
     const unsigned ne_mask = __ballot_sync(0xffffffffu, c > 0);
-    if (t < tiles && c == 0) {
-      const int64_t g = in.tile0 + t;
+    if (pos < tiles && c == 0) {
       const int64_t ne_before = (int64_t)in.pd->ne_base + Bf.ne_cta_base[blockIdx.x] +
                                 __popc(ne_mask & ((1u << lane) - 1u));
-      Bf.order[Bf.bdev->nonempty + (g - ne_before)] = (int)g;
+      Bf.order[Bf.bdev->nonempty + (in.tile0 + pos - ne_before)] = (int)g;
     }
   }
   __syncthreads();
@@ -614,52 +777,54 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32)
   const int m = in.pd->flag_exp;
   for (int r = 0; r < kTileRounds; ++r) {
     const int lt = warp + r * kWarpsPerCta;
-    const int64_t t = lt0 + lt;
-    if (t >= tiles) break;
-    const int64_t g = in.tile0 + t;
+    const int64_t pos = lt0 + lt;
+    if (pos >= tiles) break;
+    int i, j;
+    tile_at(pos, bd, i, j);
+    const int64_t g = in.tile0 + (int64_t)i * bd + j;
     const int c = Bf.cnt[g];
     if (c == 0) continue;
-    if (lane == 0) Bf.order[atomicAdd(&Bf.bdev->cursor[c], 1)] = (int)g;
-    const int i = (int)(t / bd), j = (int)(t % bd);
     const Screen* ra = Bf.sA + in.tile0 + (int64_t)i * bd;
     const Screen* rb = Bf.sBT + in.tile0 + (int64_t)j * bd;
     int base = s_beg[lt];
-    for (int k0 = 0; k0 < bd; k0 += 32) {
-      const int k = k0 + lane;
-      bool s = false;
-      Screen a{}, b{};
-      if (k < bd) {
-        a = ra[k];
-        b = rb[k];
-        s = survives(a, b, nA + (int64_t)i * bd + k, nB + (int64_t)k * bd + j, T);
-        if (s && band) s = !survives(a, b, nA + (int64_t)i * bd + k, nB + (int64_t)k * bd + j, Thi);
-      }
-      const unsigned ball = __ballot_sync(0xffffffffu, s);
-      if (s) {
-        uint16_t v = (uint16_t)k;
-        if (split && rel_bin_screened(a, b, inv_m, inv_e, nA + (int64_t)i * bd + k,
-                                      nB + (int64_t)k * bd + j, inv) >= m)
-          v |= kSplitFlag;
-        Bf.k_idx[base + __popc(ball & ((1u << lane) - 1u))] = v;
-      }
-      base += __popc(ball);
-      if (quant && ball) {
-        // list the A and B blocks of surviving triples, each once over the plan
-        const int64_t ga = in.tile0 + (int64_t)i * bd + k, gb = in.tile0 + (int64_t)k * bd + j;
-        bool newA = false, newB = false;
+    // the count kernel's ballots: one word per 32 k, expanded in increasing k
+    const uint32_t* mrow = Bf.surv_mask + in.mask0 + ((int64_t)i * bd + j) * nch;
+    for (int qg = 0; qg < nch; qg += 4) {
+      unsigned words[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) words[q] = qg + q < nch ? __ldg(mrow + qg + q) : 0u;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const unsigned ball = words[q];
+        if (ball == 0u) continue;   // uniform over the warp
+        const int k = (qg + q) * 32 + lane;
+        const bool s = (ball >> lane) & 1u;
         if (s) {
-          const uint32_t bitA = 1u << (ga & 31), bitB = 1u << (gb & 31);
-          newA = (atomicOr(&bitsA[ga >> 5], bitA) & bitA) == 0u;
-          newB = (atomicOr(&bitsB[gb >> 5], bitB) & bitB) == 0u;
+          uint16_t v = (uint16_t)k;
+          if (split && rel_bin_screened(ra[k], rb[k], inv_m, inv_e, nA + (int64_t)i * bd + k,
+                                        nB + (int64_t)k * bd + j, inv) >= m)
+            v |= kSplitFlag;
+          Bf.k_idx[base + __popc(ball & ((1u << lane) - 1u))] = v;
         }
-        const unsigned ma = __ballot_sync(0xffffffffu, newA), mb = __ballot_sync(0xffffffffu, newB);
-        if (ma | mb) {
-          int nb = 0;
-          if (lane == 0) nb = atomicAdd(&Bf.bdev->need_count, __popc(ma) + __popc(mb));
-          nb = __shfl_sync(0xffffffffu, nb, 0);
-          const unsigned lt = (1u << lane) - 1u;
-          if (newA) Bf.need_list[nb + __popc(ma & lt)] = (uint32_t)ga;
-          if (newB) Bf.need_list[nb + __popc(ma) + __popc(mb & lt)] = (uint32_t)gb | 0x80000000u;
+        base += __popc(ball);
+        if (quant) {
+          // list the A and B blocks of surviving triples, each once over the plan
+          const int64_t ga = in.tile0 + (int64_t)i * bd + k, gb = in.tile0 + (int64_t)k * bd + j;
+          bool newA = false, newB = false;
+          if (s) {
+            const uint32_t bitA = 1u << (ga & 31), bitB = 1u << (gb & 31);
+            newA = (atomicOr(&bitsA[ga >> 5], bitA) & bitA) == 0u;
+            newB = (atomicOr(&bitsB[gb >> 5], bitB) & bitB) == 0u;
+          }
+          const unsigned ma = __ballot_sync(0xffffffffu, newA), mb = __ballot_sync(0xffffffffu, newB);
+          if (ma | mb) {
+            int nb = 0;
+            if (lane == 0) nb = atomicAdd(&Bf.bdev->need_count, __popc(ma) + __popc(mb));
+            nb = __shfl_sync(0xffffffffu, nb, 0);
+            const unsigned lt = (1u << lane) - 1u;
+            if (newA) Bf.need_list[nb + __popc(ma & lt)] = (uint32_t)ga;
+            if (newB) Bf.need_list[nb + __popc(ma) + __popc(mb & lt)] = (uint32_t)gb | 0x80000000u;
+          }
         }
       }
     }
@@ -672,16 +837,18 @@ int prep_ctas_of(int bd) { return (int)(((int64_t)bd * bd + kPrepThreads - 1) / 
 int count_ctas_of(int bd) { return (int)(((int64_t)bd * bd + kTilesPerCta - 1) / kTilesPerCta); }
 
 size_t plan_layout(Inst* insts, int count, PlanBuffers* b, char* base) {
-  int64_t tiles = 0, kslots = 0;
+  int64_t tiles = 0, kslots = 0, mwords = 0;
   int prep = 0, cnt = 0;
   for (int i = 0; i < count; ++i) {
     const int64_t bd = insts[i].bd;
     insts[i].tile0 = tiles;
     insts[i].kidx0 = kslots;
+    insts[i].mask0 = mwords;
     insts[i].prep0 = prep;
     insts[i].count0 = cnt;
     tiles += bd * bd;
     kslots += bd * bd * bd;
+    mwords += bd * bd * ((bd + 31) / 32);
     prep += prep_ctas_of((int)bd);
     cnt += count_ctas_of((int)bd);
   }
@@ -712,11 +879,14 @@ size_t plan_layout(Inst* insts, int count, PlanBuffers* b, char* base) {
   t.part_b2 = reinterpret_cast<ExtSum*>(take((size_t)cnt * sizeof(ExtSum)));
   t.cta_base = reinterpret_cast<int*>(take((size_t)cnt * sizeof(int)));
   t.ne_cta_base = reinterpret_cast<int*>(take((size_t)cnt * sizeof(int)));
+  t.part_keys = reinterpret_cast<int*>(take((size_t)cnt * kOrderKeys * sizeof(int)));
+  t.key_cta_base = reinterpret_cast<int*>(take((size_t)cnt * kOrderKeys * sizeof(int)));
   t.cnt = reinterpret_cast<int*>(take((size_t)tiles * sizeof(int)));
   t.tile_beg = reinterpret_cast<int*>(take((size_t)tiles * sizeof(int)));
   t.order = reinterpret_cast<int*>(take((size_t)tiles * sizeof(int)));
   t.k_idx = reinterpret_cast<uint16_t*>(take((size_t)kslots * sizeof(uint16_t)));
   t.tile_inst = reinterpret_cast<int*>(take((size_t)tiles * sizeof(int)));
+  t.surv_mask = reinterpret_cast<uint32_t*>(take((size_t)mwords * sizeof(uint32_t)));
   t.need_list = reinterpret_cast<uint32_t*>(take((size_t)(2 * tiles) * sizeof(uint32_t)));
   for (int i = 0; i < count; ++i) insts[i].pd = t.pd ? t.pd + i : nullptr;
   if (b) *b = t;
@@ -742,6 +912,17 @@ cudaError_t run_plan(const InstRef& ref, const PlanBuffers& b, cudaStream_t s) {
   count_kernel<<<b.count_ctas, kWarpsPerCta * 32, 0, s>>>(ref, b);
   finalize_kernel<<<ref.count, kFinThreads, 0, s>>>(ref, b);
   fill_kernel<<<b.count_ctas, kWarpsPerCta * 32, 0, s>>>(ref, b);
+  return cudaPeekAtLastError();
+}
+
+cudaError_t run_plan_count(const InstRef& ref, const PlanBuffers& b, cudaStream_t s) {
+  const size_t clear = reinterpret_cast<const char*>(b.need_bits + 2 * b.need_words) -
+                       reinterpret_cast<const char*>(b.pd);
+  cudaError_t e = cudaMemsetAsync(b.pd, 0, clear, s);
+  if (e != cudaSuccess) return e;
+  prep_kernel<<<b.prep_ctas, kPrepThreads, 0, s>>>(ref, b);
+  count_kernel<<<b.count_ctas, kWarpsPerCta * 32, 0, s>>>(ref, b);
+  finalize_kernel<<<ref.count, kFinThreads, 0, s>>>(ref, b);
   return cudaPeekAtLastError();
 }
 

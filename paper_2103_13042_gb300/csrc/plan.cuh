@@ -27,6 +27,11 @@ TauScreen make_tau_screen(double tau);
 // Bins of the log2 histogram of relative norm products (tau prediction).
 constexpr int kHistBins = 64;
 
+// Longest-first buckets of the multiply's tile order: key = floor(log2 c) + 1
+// for a tile with c >= 1 survivors (c <= 1024: keys 1 .. 11), largest first;
+// inside a bucket the tiles keep the plan's enumeration order.
+constexpr int kOrderKeys = 12;
+
 // Per-instance statistics; `ticket` and the bins are cleared before each plan.
 struct PlanDevice {
   double norm_a, norm_b, inv_ab;
@@ -35,6 +40,8 @@ struct PlanDevice {
   int max_tile, nonempty, flag_exp;
   int ne_base;                              // non-empty tiles of the instances before this one
   unsigned int hist[kHistBins];             // norm-product histogram (tau prediction)
+  int key_tot[kOrderKeys];                  // non-empty tiles per order bucket
+  int key_base[kOrderKeys];                 // first slot of this instance in each bucket
   unsigned int ticket;                      // prep CTAs of this instance that have finished
   double bin_sum[kFlagBins];                // surviving products per relative binade
   unsigned long long bin_cnt[kFlagBins];
@@ -73,6 +80,7 @@ struct Inst {
   int quant;            // 1: the multiply rounds operands (build the needed-block list)
   int64_t tile0;        // first global tile / block index
   int64_t kidx0;        // first k_idx slot
+  int64_t mask0;        // first word of the survivor bitmask (bd * bd * ceil(bd / 32) words)
   int prep0;            // first CTA of this instance in the prep grid
   int count0;           // first CTA of this instance in the count and fill grids
   double target_rel;    // split modes: relative error target
@@ -127,12 +135,15 @@ struct PlanBuffers {
   ExtSum* part_b2;     // sums of their per-tile squares
   int* cta_base;       // [count_ctas] first k_idx slot of the CTA's tiles
   int* ne_cta_base;    // [count_ctas] non-empty tiles of the instance's earlier CTAs
+  int* part_keys;      // [count_ctas * kOrderKeys] non-empty tiles of the CTA per bucket
+  int* key_cta_base;   // [count_ctas * kOrderKeys] the instance's earlier CTAs' tiles per bucket
   int* cnt;            // [tiles] survivors per tile
   int* tile_beg;       // [tiles] absolute first k_idx slot of the tile
   int* order;          // [tiles] global ids: the non-empty tiles, most survivors first, then
                        // the empty tiles in increasing order
   uint16_t* k_idx;     // [kslots] surviving k per tile, increasing (bit 15: split triple)
   int* tile_inst;      // [tiles] instance of each global tile / block
+  uint32_t* surv_mask; // survivors of each tile, 32 k per word (tile t = i*bd + j of an instance)
   uint32_t* need_bits; // [2 * words] bit g: block g of A (first half) / B (second half) is used
   uint32_t* need_list; // [2 * tiles] used blocks, each once: g (A) or g | 2^31 (B)
   int64_t need_words;  // 32-bit words per operand in need_bits
@@ -158,6 +169,9 @@ size_t plan_layout(Inst* insts, int count, PlanBuffers* b, char* base);
 InstRef make_ref(const Inst* host_insts, const Inst* dev_table, int count);
 
 cudaError_t run_plan(const InstRef& ref, const PlanBuffers& b, cudaStream_t s);
+
+// The plan's counting half (statistics, survivors per tile; no queues).
+cudaError_t run_plan_count(const InstRef& ref, const PlanBuffers& b, cudaStream_t s);
 
 // Clears the statistics, builds the screen forms and norms (as run_plan's
 // first step) and the per-instance norm-product histograms (pd[i].hist).

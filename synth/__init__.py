@@ -206,3 +206,19 @@ def spec_matrices_device(spec, device):
             z = torch.randint(0, 2, (n, n), generator=g, device=device).to(torch.float32) * 2.0 - 1.0
         out.append((mag * z).contiguous())
     return out[0], out[1]
+
+
+def near_sparse_device(n: int, seed: int, device, drop: float = 0.7):
+    """ReLU(N(0,1)) with each remaining entry zeroed with probability ``drop``, drawn on the
+    device (torch's seeded generator; the large near-sparse workload, never an oracle input)."""
+    import torch
+    g = torch.Generator(device=device)
+    g.manual_seed(int(seed))
+    out = torch.empty(n, n, device=device, dtype=torch.float32)
+    rows = max(1, (1 << 26) // n)          # bounded temporaries
+    for r0 in range(0, n, rows):
+        r1 = min(n, r0 + rows)
+        z = torch.randn(r1 - r0, n, generator=g, device=device, dtype=torch.float32)
+        keep = torch.rand(r1 - r0, n, generator=g, device=device) >= drop
+        out[r0:r1] = torch.where((z > 0) & keep, z, torch.zeros((), device=device))
+    return out

@@ -218,7 +218,9 @@ def test_dynamic_schedule_and_timings(prec):
     Ct = [torch.full_like(A, float("nan")) for A in As]
     tm.run(As, Bs, Ct, taus, 1e-6)
     t = tm.timings()
-    assert all(v > 0 for v in t.values()), t
+    assert t["normmap"] > 0 and t["plan"] > 0 and t["multiply"] > 0 and t["round"] >= 0, t
+    if prec != P.FP32:
+        assert t["round"] > 0, t
     for i in range(len(As)):
         assert torch.equal(Cs[i], Ct[i]), i
     for b in (st, dy, tm):

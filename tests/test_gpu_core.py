@@ -64,6 +64,23 @@ def test_normmap_special_values():
     assert np.allclose(got[fin], ref[fin], rtol=NORM_REL_TOL, atol=0)
 
 
+@pytest.mark.parametrize("leaf", [32, 64, 128])
+def test_normmap_wide_dynamic_range(leaf):
+    """Entries spread over 2^-100 .. 2^20 (log-uniform, random signs), blocks dominated by one
+    entry, and blocks of tiny entries only: the exact-square sums keep the 3e-13 accuracy."""
+    g = np.random.default_rng(leaf)
+    n = 4 * leaf + 3
+    a = (np.exp2(g.uniform(-100, 20, size=(n, n))) * g.choice([-1.0, 1.0], size=(n, n))).astype(np.float32)
+    a[:leaf, :leaf] = np.float32(1e-30)            # tiny entries only
+    a[0, 0] = np.float32(3.0e5)                     # then one dominant entry elsewhere
+    a[leaf:2 * leaf, leaf:2 * leaf] *= np.float32(1e-12)
+    a[leaf + 1, leaf + 2] = np.float32(7.0e9)
+    got = host(P.spamm_normmap(dev(a), leaf))
+    ref = S.normmap(a, leaf)
+    rel = np.abs(got - ref) / ref
+    assert rel.max() <= NORM_REL_TOL, rel.max()
+
+
 def test_normmap_c2_full_size():
     a, _ = synth.workload_c2()
     got = host(P.spamm_normmap(dev(a), 64))

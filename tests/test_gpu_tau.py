@@ -184,3 +184,40 @@ def test_band_plan_matches_oracle(leaf):
     c_hi = S.multiply_with_skipset(a, b, leaf, S.flat_survivors(nA, nB, t_hi))
     # (FP64 cancellation in c_lo - c_hi is relative to ||c_lo||)
     assert np.linalg.norm((c_lo - c_hi) - cref) <= 1e-13 * np.linalg.norm(c_lo)
+
+
+# --------------------------------------------------------------------------- Table 1 on the GPU
+
+def _golden(name):
+    import json
+    import os
+    with open(os.path.join(os.path.dirname(__file__), "golden", name)) as f:
+        return json.load(f)
+
+
+@pytest.mark.parametrize("n", [1024, 2048, 4096])
+def test_table1_valid_ratios_on_gpu(n):
+    """The paper's printed tau values give the printed valid ratios (+-1.5 points) through the
+    GPU norm map and plan (Section 4.1, Table 1; leaf 32)."""
+    t = _golden("table1.json")
+    col = t["n"].index(n)
+    A = dev(synth.table1_matrix(n))
+    nA = P.spamm_normmap(A, 32)
+    plan = P.Plan(n, 32, P.FP32)
+    for label, taus in t["rows"].items():
+        st = plan.plan(nA, nA, taus[col]).stats()
+        assert abs(st["valid_ratio"] - float(label)) <= 0.015, (n, label, st["valid_ratio"])
+
+
+@pytest.mark.parametrize("target", [0.3, 0.1, 0.05])
+def test_valid_ratio_search_matches_oracle(target):
+    n, leaf = 1024, 32
+    a = synth.table1_matrix(n)
+    nA = S.normmap(a, leaf)
+    plan = P.Plan(n, leaf, P.FP32)
+    tau, ratio, probes = plan.tau_for_valid_ratio(dev(nA), dev(nA), target, 0.01, 20)
+    ref_tau, ref_ratio, ref_probes = OT.tau_for_valid_ratio(nA, nA, target, iters=20, tol=0.01)
+    assert abs(ratio - target) <= 0.01 or probes == 20
+    assert ratio == pytest.approx(OT.valid_ratio_at(nA, nA, tau), abs=0)
+    assert probes == ref_probes
+    assert tau == pytest.approx(ref_tau, rel=1e-12)
