@@ -68,6 +68,27 @@ def workload(n: int):
 
 
 # ---------------------------------------------------------------------------
+# Replicas (one process per GPU, no data exchange): the job's time is the
+# slowest rank's, its throughput the sum over ranks
+# ---------------------------------------------------------------------------
+
+def slowest_rank_ms(ms: float, world: int, device) -> float:
+    """Max of the per-rank times over the process group (identity for one rank)."""
+    if world <= 1:
+        return ms
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(per_rank_work: float, ms: float, world: int) -> float:
+    """Units per second of the whole job: every rank does per_rank_work units in ms (max)."""
+    return per_rank_work * world / (ms * 1e-3)
+
+
+# ---------------------------------------------------------------------------
 # Clock sampling during the timed region
 # ---------------------------------------------------------------------------
 
@@ -263,11 +284,7 @@ def run_ours(args, rank, world):
         torch.cuda.synchronize()
         time.sleep(0.3)
     barrier()
-    ms = e0.elapsed_time(e1) / args.steps
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = slowest_rank_ms(e0.elapsed_time(e1) / args.steps, world, dev)
 
     # end to end through the public API with host buffers (pinned)
     a_pin = torch.from_numpy(a_h).pin_memory()
@@ -290,11 +307,7 @@ def run_ours(args, rank, world):
         e2e_step()
     f1.record(stream)
     torch.cuda.synchronize()
-    e2e_ms = f0.elapsed_time(f1) / e2e_steps
-    if world > 1:
-        t = torch.tensor([e2e_ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_ms = float(t.item())
+    e2e_ms = slowest_rank_ms(f0.elapsed_time(f1) / e2e_steps, world, dev)
 
     # baselines on the same GPU: plain FP32 SpAMM (same tau) and cuBLAS SGEMM
     base = {}
@@ -333,7 +346,7 @@ def run_ours(args, rank, world):
         return None
     peaks = load_peaks()
     dense = 2.0 * n ** 3
-    value = dense / (ms * 1e-3) / 1e12 * world
+    value = job_throughput(dense, ms, world) / 1e12
     # roofline of the dominant kernel: by the ncu launch list of this command the
     # norm map (two launches per step) has the largest share of device time
     norm_ms = 0.5 * (part_ms["normmap_A"] + part_ms["normmap_B"])
@@ -500,11 +513,7 @@ def run_batch(args, rank, world):
         e1.record(stream)
         torch.cuda.synchronize()
         time.sleep(0.3)
-    ms = e0.elapsed_time(e1) / args.steps
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = slowest_rank_ms(e0.elapsed_time(e1) / args.steps, world, dev)
 
     # accuracy on a sample of instances against an FP64 product on the GPU
     errs = []
@@ -718,7 +727,7 @@ def run_sparse(args, rank, world):
         e1.record(stream)
         torch.cuda.synchronize()
         time.sleep(0.3)
-    ms = e0.elapsed_time(e1) / args.steps
+    ms = slowest_rank_ms(e0.elapsed_time(e1) / args.steps, world, dev)
 
     # accuracy on sampled output tiles against FP64 products on the GPU
     g = np.random.default_rng(5)

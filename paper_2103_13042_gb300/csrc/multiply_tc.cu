@@ -73,7 +73,7 @@ struct TcCfg {
   static constexpr int kThreads = 32 * kFirstEpiWarp + 32 * kEpiWarps;
   static constexpr uint32_t kStageBytes = L::kChunkBytes * 2 * (kHasLo ? 2 : 1);
   static constexpr int kStagesFit =
-      (200 * 1024 - kEpiWarps * (M == 128 ? 32 : 16) * (64 * 4 + 16)) / kStageBytes;
+      (216 * 1024 - kEpiWarps * (M == 64 ? 16 : 0) * (64 * 4 + 16)) / kStageBytes;
   static constexpr int kStages = kStagesFit > 16 ? 16 : kStagesFit;
   static constexpr int kAccCols = N * (kHasLo ? 2 : 1);
   // as many run accumulators as the 512 TMEM columns hold (2 to 8): the MMA
@@ -88,9 +88,11 @@ struct TcCfg {
   static constexpr size_t kMetaOffset = up16(kBarOffset + (size_t)kNumBars * 8);
   static constexpr size_t kRunOffset = up16(kMetaOffset + (size_t)kStages * sizeof(StageMeta));
   static constexpr size_t kEntOffset = up16(kRunOffset + (size_t)kRunRing * sizeof(RunRec));
-  // epilogue staging for the bulk stores of C: per epilogue warp its rows
-  // (16 of M = 64, 32 of M = 128) of 64 columns, rows 272 bytes apart
-  static constexpr int kEpiRows = M == 128 ? 32 : 16;
+  // epilogue staging for the bulk stores of C (M = 64): per epilogue warp its
+  // 16 rows of 64 columns, rows 272 bytes apart.  At M = 128 the shared
+  // memory goes to pipeline stages instead and rows are stored directly.
+  static constexpr bool kBulkEpilogue = M == 64;
+  static constexpr int kEpiRows = kBulkEpilogue ? 16 : 0;
   static constexpr int kEpiRowBytes = 64 * 4 + 16;
   static constexpr size_t kEpiOffset =
       up16(kEntOffset + (size_t)kGroups * 32 * sizeof(int4) + kGroups * sizeof(int));
@@ -386,7 +388,8 @@ __global__ void __launch_bounds__(TcCfg<FMT, LEAF, SPLITMODE>::kThreads, 1)
         }
         const StageMeta m = meta[stage];
         if (m.flags & 8) break;
-        fence_after_sync();
+        // (the operands were written by bulk copies whose completion the
+        // mbarrier reported: no tcgen05 fence is needed before reading them)
         if (m.flags & 1) {
           if (open && !close_run(0)) {
             ok = false;
@@ -408,19 +411,20 @@ __global__ void __launch_bounds__(TcCfg<FMT, LEAF, SPLITMODE>::kThreads, 1)
           run_s = m.s;
           run_tile = m.tile;
         }
+        // descriptors of the stage's chunks; a 32-byte K step adds 2 to the
+        // start-address field (addresses stay below 256 KB: no carry)
         const uint32_t a0 = smem_u32(smem + (size_t)stage * Cfg::kStageBytes);
-        const uint32_t b0 = a0 + CH, al = a0 + 2 * CH, bl = a0 + 3 * CH;
+        const uint64_t da = sdesc_k_sw128(a0), db = sdesc_k_sw128(a0 + CH);
 #pragma unroll
         for (int ks = 0; ks < 4; ++ks) {
-          const uint64_t ad = sdesc_k_sw128(a0 + 32 * ks);
-          const uint64_t bdsc = sdesc_k_sw128(b0 + 32 * ks);
+          const uint64_t ad = da + 2u * ks, bdsc = db + 2u * ks;
           mma<FMT>(d_hh, ad, bdsc, Cfg::kIdesc, acc_hh);
           acc_hh = 1;
           if constexpr (Cfg::kHasLo) {
             if (split_run) {
-              mma<FMT>(d_x, ad, sdesc_k_sw128(bl + 32 * ks), Cfg::kIdesc, acc_x);
+              mma<FMT>(d_x, ad, db + (uint64_t)(2 * CH >> 4) + 2u * ks, Cfg::kIdesc, acc_x);
               acc_x = 1;
-              mma<FMT>(d_x, sdesc_k_sw128(al + 32 * ks), bdsc, Cfg::kIdesc, 1);
+              mma<FMT>(d_x, da + (uint64_t)(2 * CH >> 4) + 2u * ks, bdsc, Cfg::kIdesc, 1);
             }
           }
         }
@@ -500,7 +504,7 @@ __global__ void __launch_bounds__(TcCfg<FMT, LEAF, SPLITMODE>::kThreads, 1)
         if (lane_has_row && gr < n) {
           float* dst = in.C + gr * n + (int64_t)j * LEAF + col0;
           const int64_t cols = n - (int64_t)j * LEAF - col0;
-          if ((n & 3) == 0) {
+          if (Cfg::kBulkEpilogue && (n & 3) == 0) {
             // the row goes through shared memory and leaves as one bulk copy
             // (n % 4 == 0: 16-byte aligned, cols % 4 == 0)
             if (cols > 0) {
@@ -513,6 +517,11 @@ __global__ void __launch_bounds__(TcCfg<FMT, LEAF, SPLITMODE>::kThreads, 1)
               bulk_s2g(dst, smem_u32(stage_row), (uint32_t)(cols < NC ? cols : NC) * 4u);
               bulk_commit();
             }
+          } else if ((n & 3) == 0 && cols >= NC) {
+#pragma unroll
+            for (int c = 0; c < NC; c += 4)
+              *reinterpret_cast<float4*>(dst + c) =
+                  make_float4(acc[c], acc[c + 1], acc[c + 2], acc[c + 3]);
           } else {
 #pragma unroll
             for (int c = 0; c < NC; ++c)

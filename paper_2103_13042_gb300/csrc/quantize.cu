@@ -2,7 +2,7 @@
 // top of the paper's FP16 tensor-core kernel, Section 3.3 / Algorithm 3).
 //
 // For every leaf block that some surviving triple uses (the plan's list of
-// needed blocks) one warp finds e = frexp exponent of its largest magnitude,
+// needed blocks) one CTA finds e = frexp exponent of its largest magnitude,
 // scales by 2^-e (exact), rounds to nearest-even in the operand format (hi)
 // and, in split modes, rounds the exact residual scaled by 2^s_lo (lo).  The result is written directly as the K-major, 128-byte
 // swizzled image the MMA reads: chunk c of a block holds K elements
@@ -18,7 +18,6 @@
 namespace spamm {
 namespace {
 
-constexpr int kThreads = 256;
 
 // Round to nearest even, keeping 10 explicit significand bits (TF32), on the
 // IEEE bit pattern; NaN/Inf pass through unchanged.
@@ -54,27 +53,33 @@ __device__ __forceinline__ float ld_or_zero(const float* X, int64_t n, int64_t r
   return (r < n && c < n) ? __ldg(X + r * n + c) : 0.0f;
 }
 
-// One warp per used leaf block (the plan's needed-block list).  Pass 1 reads
-// the block row-major (coalesced float4) for its largest magnitude; pass 2
-// re-reads it (now from L2) in the order of the image: lane l takes 16-byte
-// piece l % 8 of image row 4m + l / 8 (fewer rows per step when a row spans
-// several 128-byte chunks), so each warp store covers whole 128-byte rows.
+// One CTA per used leaf block (the plan's needed-block list), one pass: each
+// thread owns UNITS / kThreads 16-byte pieces of the image (unit u = image
+// row u / PPR, piece u % PPR; consecutive threads take consecutive pieces, so
+// a warp's stores cover whole 128-byte rows), loads their source values into
+// registers (all loads of a thread issued before any use), the CTA reduces the
+// block's largest magnitude, then every thread scales, rounds and stores.
+// Threads per CTA: 256 at leaf 64, 512 at leaf 128 (32 values per thread at most).
+template <int LEAF>
+constexpr int q_threads() { return LEAF == 128 ? 512 : 256; }
+
 template <uint32_t FMT, int LEAF, bool SPLIT>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(q_threads<LEAF>())
     quantize_kernel(InstRef R, PlanBuffers Bf, OperandImages img) {
+  constexpr int kThreads = q_threads<LEAF>();
   using L = TcLayout<FMT, LEAF>;
   constexpr int KC = L::kKc;                 // K elements per 128-byte chunk row
   constexpr int PER16 = 16 / L::kElt;        // elements per 16-byte piece
   constexpr int PPR = LEAF / PER16;          // pieces per image row
   constexpr int UNITS = LEAF * PPR;          // pieces per block image
-  static_assert(UNITS % 32 == 0, "whole warps of pieces");
-  const int lane = threadIdx.x & 31;
-  const int64_t gw = ((int64_t)blockIdx.x * kThreads + threadIdx.x) / 32;
-  const int64_t nw = (int64_t)gridDim.x * (kThreads / 32);
+  constexpr int U = UNITS / kThreads;        // pieces per thread
+  static_assert(UNITS % kThreads == 0, "whole pieces per thread");
+  __shared__ float s_max[kThreads / 32];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int count = Bf.bdev->need_count;
   const float lo_scale = (float)(1 << L::kLoShift);
 
-  for (int64_t idx = gw; idx < count; idx += nw) {
+  for (int idx = blockIdx.x; idx < count; idx += gridDim.x) {
     const uint32_t ent = Bf.need_list[idx];
     const bool isB = (ent >> 31) != 0;
     const int64_t blk = (int64_t)(ent & 0x7fffffffu);   // global block number
@@ -82,62 +87,69 @@ __global__ void __launch_bounds__(kThreads)
     const int64_t n = in.n, lb = blk - in.tile0;
     const float* __restrict__ X = isB ? in.B : in.A;
     const int64_t r0 = (lb / in.bd) * LEAF, c0 = (lb % in.bd) * LEAF;
-    const bool full = (n & 3) == 0 && r0 + LEAF <= n && c0 + LEAF <= n;
+    const bool full = r0 + LEAF <= n && c0 + LEAF <= n;
+    const bool vec = full && (n & 3) == 0;
 
-    // pass 1: largest magnitude (NaN ignored, as fmaxf does)
-    float mx = 0.0f;
-    if (full) {
-      constexpr int kIters = LEAF * LEAF / 128;   // float4 per lane
-#pragma unroll 8
-      for (int it = 0; it < kIters; ++it) {
-        const int e = (it * 32 + lane) * 4;
-        const float4 v = __ldg(reinterpret_cast<const float4*>(X + (r0 + e / LEAF) * n + c0 + e % LEAF));
-        mx = fmaxf(mx, fmaxf(fmaxf(fabsf(v.x), fabsf(v.y)), fmaxf(fabsf(v.z), fabsf(v.w))));
+    float x[U][PER16];
+#pragma unroll
+    for (int r = 0; r < U; ++r) {
+      const int u = tid + r * kThreads;
+      const int row = u / PPR, k0 = (u % PPR) * PER16;
+      if (!isB) {   // image row = block row, K along the block's columns
+        const float* src = X + (r0 + row) * n + c0 + k0;
+        if (vec) {
+#pragma unroll
+          for (int q = 0; q < PER16; q += 4) {
+            const float4 v = __ldg(reinterpret_cast<const float4*>(src + q));
+            x[r][q] = v.x; x[r][q + 1] = v.y; x[r][q + 2] = v.z; x[r][q + 3] = v.w;
+          }
+        } else if (full) {
+#pragma unroll
+          for (int q = 0; q < PER16; ++q) x[r][q] = __ldg(src + q);
+        } else {
+#pragma unroll
+          for (int q = 0; q < PER16; ++q) x[r][q] = ld_or_zero(X, n, r0 + row, c0 + k0 + q);
+        }
+      } else {      // image row = block column, K along the block's rows
+        if (full) {
+#pragma unroll
+          for (int q = 0; q < PER16; ++q) x[r][q] = __ldg(X + (r0 + k0 + q) * n + c0 + row);
+        } else {
+#pragma unroll
+          for (int q = 0; q < PER16; ++q) x[r][q] = ld_or_zero(X, n, r0 + k0 + q, c0 + row);
+        }
       }
-    } else {
-      for (int e = lane; e < LEAF * LEAF; e += 32)
-        mx = fmaxf(mx, fabsf(ld_or_zero(X, n, r0 + e / LEAF, c0 + e % LEAF)));
     }
+    // largest magnitude of the block (NaN ignored, as fmaxf does)
+    float mx = 0.0f;
+#pragma unroll
+    for (int r = 0; r < U; ++r)
+#pragma unroll
+      for (int q = 0; q < PER16; ++q) mx = fmaxf(mx, fabsf(x[r][q]));
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+    if (lane == 0) s_max[warp] = mx;
+    __syncthreads();
+    mx = 0.0f;
+#pragma unroll
+    for (int w = 0; w < kThreads / 32; ++w) mx = fmaxf(mx, s_max[w]);
     int ex = 0;
     if (mx > 0.0f && mx <= 3.402823466e38f) frexpf(mx, &ex);
-    if (lane == 0) (isB ? img.eb : img.ea)[blk] = ex;
+    if (tid == 0) (isB ? img.eb : img.ea)[blk] = ex;
     // 2^-ex as a float when it is a normal number (the usual case), else ldexpf
     const bool pow2_ok = ex >= -126 && ex <= 126;
     const float scale = pow2_ok ? __int_as_float((127 - ex) << 23) : 1.0f;
 
     uint8_t* hi_img = (isB ? img.b_hi : img.a_hi) + blk * (int64_t)L::kBlockBytes;
     uint8_t* lo_img = SPLIT ? (isB ? img.b_lo : img.a_lo) + blk * (int64_t)L::kBlockBytes : nullptr;
-#pragma unroll 2
-    for (int u = lane; u < UNITS; u += 32) {
-      const int row = u / PPR, kp = u % PPR;
-      const int k0 = kp * PER16;
-      float x[PER16];
-      if (!isB) {   // image row = block row, K along the block's columns
-        if (full) {
 #pragma unroll
-          for (int q = 0; q < PER16; q += 4) {
-            const float4 v = __ldg(reinterpret_cast<const float4*>(X + (r0 + row) * n + c0 + k0 + q));
-            x[q] = v.x; x[q + 1] = v.y; x[q + 2] = v.z; x[q + 3] = v.w;
-          }
-        } else {
-#pragma unroll
-          for (int q = 0; q < PER16; ++q) x[q] = ld_or_zero(X, n, r0 + row, c0 + k0 + q);
-        }
-      } else {      // image row = block column, K along the block's rows
-        if (full) {
-#pragma unroll
-          for (int q = 0; q < PER16; ++q) x[q] = __ldg(X + (r0 + k0 + q) * n + c0 + row);
-        } else {
-#pragma unroll
-          for (int q = 0; q < PER16; ++q) x[q] = ld_or_zero(X, n, r0 + k0 + q, c0 + row);
-        }
-      }
+    for (int r = 0; r < U; ++r) {
+      const int u = tid + r * kThreads;
+      const int row = u / PPR, k0 = (u % PPR) * PER16;
       float hv[PER16], lv[PER16];
 #pragma unroll
       for (int q = 0; q < PER16; ++q) {
-        const float sc = pow2_ok ? __fmul_rn(x[q], scale) : ldexpf(x[q], -ex);
+        const float sc = pow2_ok ? __fmul_rn(x[r][q], scale) : ldexpf(x[r][q], -ex);
         const float h = round_op<FMT>(sc);
         hv[q] = h;
         if constexpr (SPLIT) lv[q] = round_op<FMT>(__fmul_rn(__fsub_rn(sc, h), lo_scale));
@@ -160,6 +172,7 @@ __global__ void __launch_bounds__(kThreads)
       *reinterpret_cast<uint4*>(hi_img + off) = ph;
       if constexpr (SPLIT) *reinterpret_cast<uint4*>(lo_img + off) = pl;
     }
+    __syncthreads();   // s_max is rewritten for the next block
   }
 }
 
@@ -170,11 +183,11 @@ cudaError_t launch_q(const InstRef& ref, const PlanBuffers& b, const OperandImag
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, quantize_kernel<FMT, LEAF, SPLIT>,
-                                                kThreads, 0);
-  // the list length is known on the device only: one full wave of warps
-  const int64_t cap = (2 * b.tiles + kThreads / 32 - 1) / (kThreads / 32);
+                                                q_threads<LEAF>(), 0);
+  // the list length is known on the device only: one full wave of CTAs
+  const int64_t cap = 2 * b.tiles;
   const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(cap, (int64_t)sms * std::max(1, per_sm)));
-  quantize_kernel<FMT, LEAF, SPLIT><<<grid, kThreads, 0, s>>>(ref, b, img);
+  quantize_kernel<FMT, LEAF, SPLIT><<<grid, q_threads<LEAF>(), 0, s>>>(ref, b, img);
   return cudaPeekAtLastError();
 }
 
