@@ -211,12 +211,11 @@ def run_ours(args, rank, world):
         st = st if st is not None else torch.cuda.current_stream()
         P.spamm_normmap(A, leaf, nA, st)
         P.spamm_normmap(B, leaf, nB, st)
-        plan.plan(nA, nB, tau, args.target, st)
-        plan.multiply(A, B, C, st)
+        plan.plan_multiply(nA, nB, tau, A, B, C, args.target, st)
 
-    # our kernels per step: 2 norm maps, 4 plan kernels, multiply (SIMT: multiply +
-    # zero-fill; tensor cores: quantize + zero-fill + multiply)
-    launches_per_step = 2 + 4 + (2 if prec == P.FP32 else 3)
+    # our kernels per step: 2 norm maps, 4 plan kernels, zero-fill, multiply
+    # (tensor cores: + operand rounding)
+    launches_per_step = 2 + 4 + 1 + (1 if prec == P.FP32 else 2)
 
     def barrier():
         if world > 1:
@@ -228,18 +227,21 @@ def run_ours(args, rank, world):
     st = plan.stats()
 
     # per-call breakdown (events on the launching stream)
-    ev = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
-    parts = {"normmap_A": [], "normmap_B": [], "plan": [], "multiply": []}
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(6)]
+    parts = {"normmap_A": [], "normmap_B": [], "plan_multiply": [], "plan_alone": [],
+             "multiply_alone": []}
     for _ in range(max(3, args.steps // 2)):
         ev[0].record(stream)
         P.spamm_normmap(A, leaf, nA, stream)
         ev[1].record(stream)
         P.spamm_normmap(B, leaf, nB, stream)
         ev[2].record(stream)
-        plan.plan(nA, nB, tau, args.target, stream)
+        plan.plan_multiply(nA, nB, tau, A, B, C, args.target, stream)
         ev[3].record(stream)
-        plan.multiply(A, B, C, stream)
+        plan.plan(nA, nB, tau, args.target, stream)     # the two halves, for the breakdown
         ev[4].record(stream)
+        plan.multiply(A, B, C, stream)
+        ev[5].record(stream)
         torch.cuda.synchronize()
         for k, name in enumerate(parts):
             parts[name].append(ev[k].elapsed_time(ev[k + 1]))
@@ -318,8 +320,7 @@ def run_ours(args, rank, world):
         def step32():
             P.spamm_normmap(A, leaf, nA, stream)
             P.spamm_normmap(B, leaf, nB, stream)
-            plan32.plan(nA, nB, tau, args.target, stream)
-            plan32.multiply(A, B, C32, stream)
+            plan32.plan_multiply(nA, nB, tau, A, B, C32, args.target, stream)
 
         def timed(fn, reps):
             for _ in range(3):
@@ -350,7 +351,7 @@ def run_ours(args, rank, world):
     # roofline of the dominant kernel: by the ncu launch list of this command the
     # norm map (two launches per step) has the largest share of device time
     norm_ms = 0.5 * (part_ms["normmap_A"] + part_ms["normmap_B"])
-    mul_ms = part_ms["multiply"]
+    mul_ms = part_ms["multiply_alone"]
     if norm_ms > 0.0:
         bytes_ = 4.0 * n * n + 8.0 * bd * bd
         ach = bytes_ / (norm_ms * 1e-3) / 1e9

@@ -175,6 +175,17 @@ spamm_status_t spamm_multiply(spamm_plan_t plan, const float* A, const float* B,
                               void* stream);
 
 /* ---------------------------------------------------------------------------
+ * spamm_plan_multiply -- spamm_plan followed by spamm_multiply in one call
+ * (same arguments, same results).  Knowing C while planning lets the zeros of
+ * the tiles without survivors be written as soon as the survivor counts are
+ * known, overlapped with the rest of the plan and the multiply.
+ * Asynchronous.
+ * ------------------------------------------------------------------------- */
+spamm_status_t spamm_plan_multiply(spamm_plan_t plan, const double* normA, const double* normB,
+                                   double tau, double target_rel_err, const float* A,
+                                   const float* B, float* C, void* stream);
+
+/* ---------------------------------------------------------------------------
  * Error measures (Eq. 5): E = AB - SpAMM(A, B, tau).
  * spamm_frobenius_diff: *out = ||X - Y||_F over `count` FP32 entries
  *   (Y may be NULL for ||X||_F).  FP64 accumulation of exact FP32 squares.
@@ -237,9 +248,9 @@ spamm_status_t spamm_multiply_fp32_noalloc(const float* A, const float* B, float
  *   [bd*bd] each) and work queues (as spamm_plan_export); every pointer may
  *   be NULL; blocks.
  * spamm_batch_timings: ms[4] = device time of the norm maps, the plan, the
- *   operand rounding (0 for FP32) and the multiply (with the zero-fill of
- *   empty tiles, overlapped) of the last run (SPAMM_BATCH_TIMING only);
- *   blocks.
+ *   operand rounding (0 for FP32) and the multiply of the last run
+ *   (SPAMM_BATCH_TIMING only; the zero-fill of empty tiles runs beside the
+ *   last three); blocks.
  * spamm_batch_autotune: times every candidate configuration on the given
  *   problems and returns the fastest in *best: leaf 64 and 128 (32, 64 and
  *   128 for FP32) times the static and dynamic multiply schedules, each

@@ -69,6 +69,7 @@ _SIGS = {
     "spamm_plan_stats": [_VP, ctypes.POINTER(Stats), _VP],
     "spamm_plan_export": [_VP, _VP, _VP, _I64, _VP],
     "spamm_multiply": [_VP, _VP, _VP, _VP, _VP],
+    "spamm_plan_multiply": [_VP, _VP, _VP, _D, _D, _VP, _VP, _VP, _VP],
     "spamm_frobenius_diff": [_VP, _VP, _I64, ctypes.POINTER(_D), _VP],
     "spamm_last_device_status": [_VP, ctypes.POINTER(_I32)],
     "spamm_multiply_fp32_noalloc": [_VP, _VP, _VP, _I64, _I32, _D, _VP],
@@ -208,6 +209,14 @@ class Plan:
     def multiply(self, A, B, C, stream=None):
         _check(lib().spamm_multiply(self.handle, _ptr(A), _ptr(B), _ptr(C), _stream(stream)),
                "spamm_multiply")
+        return C
+
+    def plan_multiply(self, normA, normB, tau: float, A, B, C, target_rel_err: float = 1e-5,
+                      stream=None):
+        """plan() then multiply() in one call (zero-fill of empty tiles overlapped)."""
+        _check(lib().spamm_plan_multiply(self.handle, _ptr(normA), _ptr(normB), float(tau),
+                                         float(target_rel_err), _ptr(A), _ptr(B), _ptr(C),
+                                         _stream(stream)), "spamm_plan_multiply")
         return C
 
     def band(self, normA, normB, tau_lo: float, tau_hi: float, stream=None):

@@ -160,6 +160,29 @@ spamm_status_t engine_free(Engine& e) {
   return st;
 }
 
+namespace {
+
+// The multiply of the non-empty tiles (operand rounding first in tensor modes).
+cudaError_t multiply_nonempty(Engine& e, const InstRef& ref, int32_t* status, cudaStream_t s,
+                              cudaEvent_t after_round) {
+  cudaError_t err = cudaSuccess;
+  if (e.schedule == kScheduleDynamic)
+    err = cudaMemsetAsync(&e.buf.bdev->mul_ticket, 0, sizeof(int), s);
+  if (err != cudaSuccess) return err;
+  if (e.precision == SPAMM_FP32) {
+    if (after_round) err = cudaEventRecord(after_round, s);
+    if (err == cudaSuccess) err = launch_multiply_simt(ref, e.buf, e.leaf, e.schedule, s);
+  } else {
+    err = launch_quantize(e.precision, e.leaf, ref, e.buf, e.img, s);
+    if (err == cudaSuccess && after_round) err = cudaEventRecord(after_round, s);
+    if (err == cudaSuccess)
+      err = launch_multiply_tc(e.precision, e.leaf, ref, e.buf, e.img, status, e.schedule, s);
+  }
+  return err;
+}
+
+}  // namespace
+
 cudaError_t engine_multiply(Engine& e, const InstRef& ref, int32_t* status, cudaStream_t s,
                             cudaEvent_t after_round) {
   // empty tiles (zeros, HBM-write bound) on the side stream, overlapped with
@@ -168,19 +191,24 @@ cudaError_t engine_multiply(Engine& e, const InstRef& ref, int32_t* status, cuda
   if (err == cudaSuccess) err = cudaStreamWaitEvent(e.side, e.fork, 0);
   if (err == cudaSuccess) err = launch_zero_empty_tiles(ref, e.buf, e.leaf, e.side);
   if (err == cudaSuccess) err = cudaEventRecord(e.join, e.side);
-  if (err == cudaSuccess && e.schedule == kScheduleDynamic)
-    err = cudaMemsetAsync(&e.buf.bdev->mul_ticket, 0, sizeof(int), s);
-  if (err == cudaSuccess) {
-    if (e.precision == SPAMM_FP32) {
-      if (after_round) err = cudaEventRecord(after_round, s);
-      if (err == cudaSuccess) err = launch_multiply_simt(ref, e.buf, e.leaf, e.schedule, s);
-    } else {
-      err = launch_quantize(e.precision, e.leaf, ref, e.buf, e.img, s);
-      if (err == cudaSuccess && after_round) err = cudaEventRecord(after_round, s);
-      if (err == cudaSuccess)
-        err = launch_multiply_tc(e.precision, e.leaf, ref, e.buf, e.img, status, e.schedule, s);
-    }
-  }
+  if (err == cudaSuccess) err = multiply_nonempty(e, ref, status, s, after_round);
+  if (err == cudaSuccess) err = cudaStreamWaitEvent(s, e.join, 0);
+  return err;
+}
+
+cudaError_t engine_plan_multiply(Engine& e, const InstRef& ref, int32_t* status, cudaStream_t s,
+                                 cudaEvent_t after_plan, cudaEvent_t after_round) {
+  // the empty tiles are known once the counting half of the plan is done: their
+  // zeros (HBM-write bound) overlap the latency-bound rest of the plan, the
+  // rounding and the multiply
+  cudaError_t err = run_plan_count_half(ref, e.buf, s);
+  if (err == cudaSuccess) err = cudaEventRecord(e.fork, s);
+  if (err == cudaSuccess) err = cudaStreamWaitEvent(e.side, e.fork, 0);
+  if (err == cudaSuccess) err = launch_zero_empty_tiles_scan(ref, e.buf, e.leaf, e.side);
+  if (err == cudaSuccess) err = cudaEventRecord(e.join, e.side);
+  if (err == cudaSuccess) err = run_plan_queue_half(ref, e.buf, s);
+  if (err == cudaSuccess && after_plan) err = cudaEventRecord(after_plan, s);
+  if (err == cudaSuccess) err = multiply_nonempty(e, ref, status, s, after_round);
   if (err == cudaSuccess) err = cudaStreamWaitEvent(s, e.join, 0);
   return err;
 }
@@ -391,6 +419,44 @@ spamm_status_t spamm_multiply(spamm_plan_t plan, const float* A, const float* B,
   in.C = C;
   cudaError_t err = engine_multiply(e, make_ref(e.insts.data(), nullptr, 1), status,
                                     (cudaStream_t)stream);
+  if (err != cudaSuccess) {
+    (void)cudaGetLastError();
+    return SPAMM_ERR_CUDA;
+  }
+  return SPAMM_OK;
+}
+
+spamm_status_t spamm_plan_multiply(spamm_plan_t plan, const double* normA, const double* normB,
+                                   double tau, double target_rel_err, const float* A,
+                                   const float* B, float* C, void* stream) {
+  if (!plan || !normA || !normB || !A || !B || !C) return SPAMM_ERR_INVALID_ARG;
+  if (!aligned16(normA) || !aligned16(normB)) return SPAMM_ERR_INVALID_ARG;
+  if (!aligned16(A) || !aligned16(B) || !aligned16(C)) return SPAMM_ERR_INVALID_ARG;
+  if (A == C || B == C) return SPAMM_ERR_INVALID_ARG;
+  if (std::isnan(tau) || tau < 0.0) return SPAMM_ERR_INVALID_ARG;
+  Engine& e = plan->eng;
+  const bool split = uses_split_flags(e.precision);
+  if (split && !(target_rel_err >= 0.0)) return SPAMM_ERR_INVALID_ARG;
+  int32_t* status = nullptr;
+  if (e.precision != SPAMM_FP32) {
+    status = device_status_word();
+    if (!status) return SPAMM_ERR_NO_MEMORY;
+  }
+  const double u = hi_unit(e.precision);
+  Inst& in = e.insts[0];
+  in.nA = normA;
+  in.nB = normB;
+  in.T = make_tau_screen(tau);
+  in.band = 0;
+  in.split = split ? 1 : 0;
+  in.quant = is_tensor_mode(e.precision) ? 1 : 0;
+  in.target_rel = split ? target_rel_err : 0.0;
+  in.c1 = split ? 2.0 * u + u * u : 0.0;
+  in.A = A;
+  in.B = B;
+  in.C = C;
+  cudaError_t err = engine_plan_multiply(e, make_ref(e.insts.data(), nullptr, 1), status,
+                                         (cudaStream_t)stream);
   if (err != cudaSuccess) {
     (void)cudaGetLastError();
     return SPAMM_ERR_CUDA;

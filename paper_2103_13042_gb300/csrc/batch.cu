@@ -132,9 +132,9 @@ cudaError_t enqueue(spamm_batch_s* b, cudaStream_t s, bool timing) {
   if (e == cudaSuccess)
     e = launch_normmap_jobs(b->jobs_dev, 2 * b->count, b->norm_ctas, b->eng.leaf, s);
   if (e == cudaSuccess && timing) e = cudaEventRecord(b->phase[1], s);
-  if (e == cudaSuccess) e = run_plan(ref, b->eng.buf, s);
-  if (e == cudaSuccess && timing) e = cudaEventRecord(b->phase[2], s);
-  if (e == cudaSuccess) e = engine_multiply(b->eng, ref, b->status, s, timing ? b->phase[3] : nullptr);
+  if (e == cudaSuccess)
+    e = engine_plan_multiply(b->eng, ref, b->status, s, timing ? b->phase[2] : nullptr,
+                             timing ? b->phase[3] : nullptr);
   if (e == cudaSuccess && timing) e = cudaEventRecord(b->phase[4], s);
   return e;
 }

@@ -51,6 +51,13 @@ spamm_status_t engine_free(Engine& e);
 cudaError_t engine_multiply(Engine& e, const InstRef& ref, int32_t* status, cudaStream_t s,
                             cudaEvent_t after_round = nullptr);
 
+// Plan and multiply in one sequence; the zero-fill of empty tiles starts as
+// soon as the plan's counting half is done.  Optional events after the plan
+// and after the rounding.
+cudaError_t engine_plan_multiply(Engine& e, const InstRef& ref, int32_t* status, cudaStream_t s,
+                                 cudaEvent_t after_plan = nullptr,
+                                 cudaEvent_t after_round = nullptr);
+
 void fill_stats(const PlanDevice& h, int leaf, int bd, spamm_stats_t* out);
 
 // Host copy of one instance's work queues as a row-major CSR (tile t = i*bd + j):

@@ -584,6 +584,56 @@ __global__ void __launch_bounds__(256)
   }
 }
 
+// Zeros for the tiles without survivors found from the counts: a CTA takes
+// 32 consecutive global tiles, warp 0 lists the empty ones (coalesced count
+// loads, ballot), then the CTA writes each of them with the same per-thread
+// column / row-step pattern (whole row segments per warp, 16-byte streaming
+// stores).
+template <int LEAF>
+__global__ void __launch_bounds__(256)
+    zero_scan_kernel(InstRef R, PlanBuffers Bf) {
+  constexpr int kPerRow = LEAF / 4;                 // float4 per tile row
+  constexpr int kRowStep = 256 / kPerRow;           // rows per CTA pass
+  __shared__ int s_list[32];
+  __shared__ int s_count;
+  const int tid = threadIdx.x, lane = tid & 31;
+  const int my_c4 = tid % kPerRow, my_r = tid / kPerRow;
+  for (int64_t g0 = (int64_t)blockIdx.x * 32; g0 < Bf.tiles; g0 += (int64_t)gridDim.x * 32) {
+    if (tid < 32) {
+      const int64_t gl = g0 + lane;
+      const bool empty = gl < Bf.tiles && Bf.cnt[gl] == 0;
+      const unsigned mask = __ballot_sync(0xffffffffu, empty);
+      if (empty) s_list[__popc(mask & ((1u << lane) - 1u))] = lane;
+      if (lane == 0) s_count = __popc(mask);
+    }
+    __syncthreads();
+    const int count = s_count;
+    for (int e = 0; e < count; ++e) {
+      const int64_t g = g0 + s_list[e];
+      const Inst& in = R.at(inst_of(R, Bf, g));
+      const int64_t n = in.n;
+      const int lt = (int)(g - in.tile0), bd = in.bd;   // lt < 2^20
+      const int ti = lt / bd, tj = lt - ti * bd;
+      const int64_t r0 = (int64_t)ti * LEAF, c0 = (int64_t)tj * LEAF;
+      const int rows = (int)min((int64_t)LEAF, n - r0), cols = (int)min((int64_t)LEAF, n - c0);
+      float* C = in.C;
+      if ((n & 3) == 0) {   // then cols % 4 == 0 and every float4 is aligned
+        if (4 * my_c4 < cols) {
+          float4* p = reinterpret_cast<float4*>(C + (r0 + my_r) * n + c0 + 4 * my_c4);
+          const int64_t step = (int64_t)kRowStep * n / 4;
+          for (int r = my_r; r < rows; r += kRowStep, p += step) __stcs(p, make_float4(0.f, 0.f, 0.f, 0.f));
+        }
+      } else {
+        for (int u = tid; u < rows * cols; u += 256) {
+          const int r = u / cols, c = u - r * cols;
+          C[(r0 + r) * n + c0 + c] = 0.f;
+        }
+      }
+    }
+    __syncthreads();   // s_list / s_count are rewritten by the next chunk
+  }
+}
+
 template <uint32_t FMT, int LEAF, int SPLITMODE>
 cudaError_t launch_tc(const TcParams& prm, cudaStream_t s) {
   using Cfg = TcCfg<FMT, LEAF, SPLITMODE>;
@@ -611,6 +661,22 @@ cudaError_t launch_zero_empty_tiles(const InstRef& ref, const PlanBuffers& b, in
     case 32: zero_tiles_kernel<32><<<grid, 256, 0, s>>>(ref, b); break;
     case 64: zero_tiles_kernel<64><<<grid, 256, 0, s>>>(ref, b); break;
     case 128: zero_tiles_kernel<128><<<grid, 256, 0, s>>>(ref, b); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaPeekAtLastError();
+}
+
+cudaError_t launch_zero_empty_tiles_scan(const InstRef& ref, const PlanBuffers& b, int leaf,
+                                         cudaStream_t s) {
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int64_t chunks = (b.tiles + 31) / 32;
+  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(chunks, (int64_t)sms * 8));
+  switch (leaf) {
+    case 32: zero_scan_kernel<32><<<grid, 256, 0, s>>>(ref, b); break;
+    case 64: zero_scan_kernel<64><<<grid, 256, 0, s>>>(ref, b); break;
+    case 128: zero_scan_kernel<128><<<grid, 256, 0, s>>>(ref, b); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaPeekAtLastError();

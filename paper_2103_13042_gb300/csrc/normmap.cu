@@ -98,7 +98,7 @@ __device__ __forceinline__ void norm_strip(const float* __restrict__ X, int64_t 
 }
 
 template <int VEC, int LEAF>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kThreads, 4)
     normmap_kernel(const float* __restrict__ X, int64_t n, int bd, double* __restrict__ out) {
   norm_strip<VEC, LEAF>(X, n, bd, out, blockIdx.y, blockIdx.x);
 }

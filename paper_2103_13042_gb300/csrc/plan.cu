@@ -901,18 +901,28 @@ InstRef make_ref(const Inst* host_insts, const Inst* dev_table, int count) {
   return r;
 }
 
-cudaError_t run_plan(const InstRef& ref, const PlanBuffers& b, cudaStream_t s) {
-  // clear the per-instance statistics and the batch-wide order state (laid
-  // out back to back, one memset)
+cudaError_t run_plan_count_half(const InstRef& ref, const PlanBuffers& b, cudaStream_t s) {
+  // clear the per-instance statistics, the batch-wide order state and the
+  // needed-block bits (laid out back to back, one memset)
   const size_t clear = reinterpret_cast<const char*>(b.need_bits + 2 * b.need_words) -
                        reinterpret_cast<const char*>(b.pd);
   cudaError_t e = cudaMemsetAsync(b.pd, 0, clear, s);
   if (e != cudaSuccess) return e;
   prep_kernel<<<b.prep_ctas, kPrepThreads, 0, s>>>(ref, b);
   count_kernel<<<b.count_ctas, kWarpsPerCta * 32, 0, s>>>(ref, b);
+  return cudaPeekAtLastError();
+}
+
+cudaError_t run_plan_queue_half(const InstRef& ref, const PlanBuffers& b, cudaStream_t s) {
   finalize_kernel<<<ref.count, kFinThreads, 0, s>>>(ref, b);
   fill_kernel<<<b.count_ctas, kWarpsPerCta * 32, 0, s>>>(ref, b);
   return cudaPeekAtLastError();
+}
+
+cudaError_t run_plan(const InstRef& ref, const PlanBuffers& b, cudaStream_t s) {
+  cudaError_t e = run_plan_count_half(ref, b, s);
+  if (e == cudaSuccess) e = run_plan_queue_half(ref, b, s);
+  return e;
 }
 
 cudaError_t run_plan_count(const InstRef& ref, const PlanBuffers& b, cudaStream_t s) {

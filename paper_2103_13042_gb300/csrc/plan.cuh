@@ -170,6 +170,11 @@ InstRef make_ref(const Inst* host_insts, const Inst* dev_table, int count);
 
 cudaError_t run_plan(const InstRef& ref, const PlanBuffers& b, cudaStream_t s);
 
+// run_plan in two halves: the first ends once every tile's survivor count is
+// known (cnt), the second builds the queues and the order.
+cudaError_t run_plan_count_half(const InstRef& ref, const PlanBuffers& b, cudaStream_t s);
+cudaError_t run_plan_queue_half(const InstRef& ref, const PlanBuffers& b, cudaStream_t s);
+
 // The plan's counting half (statistics, survivors per tile; no queues).
 cudaError_t run_plan_count(const InstRef& ref, const PlanBuffers& b, cudaStream_t s);
 

@@ -35,8 +35,14 @@ cudaError_t launch_multiply_tc(spamm_precision_t prec, int leaf, const InstRef& 
                                const PlanBuffers& b, const OperandImages& img, int32_t* status,
                                int schedule, cudaStream_t s);
 
-// Writes zeros to every tile without survivors, of every instance.
+// Writes zeros to every tile without survivors, of every instance (reads the
+// plan's empty-tile list: after the whole plan).
 cudaError_t launch_zero_empty_tiles(const InstRef& ref, const PlanBuffers& b, int leaf,
                                     cudaStream_t s);
+
+// The same from the per-tile counts alone: may run as soon as the plan's
+// counting half has finished.
+cudaError_t launch_zero_empty_tiles_scan(const InstRef& ref, const PlanBuffers& b, int leaf,
+                                         cudaStream_t s);
 
 }  // namespace spamm

@@ -139,3 +139,23 @@ def test_bf16_split_c2_full_size_sampled():
         assert S.frobenius(blk - emu) <= 1e-5 * scale + 1e-30
     # whole-matrix relative error against the FP64 pruned product stays near the target
     assert st["skipped_bound2"] / (st["norm_a"] * st["norm_b"]) <= 1e-5
+
+
+@pytest.mark.parametrize("name,mode", [("fp32", OP.FP32), ("bf16_split", OP.BF16_SPLIT),
+                                       ("tf32x3", OP.TF32X3)])
+def test_plan_multiply_equals_plan_then_multiply(name, mode):
+    """The one-call form (zero-fill started after the counting half) gives the same bits."""
+    n, leaf = 777, 64
+    a, b = _pair("alg", n, 4321)
+    A, B = dev(a), dev(b)
+    nA, nB = P.spamm_normmap(A, leaf), P.spamm_normmap(B, leaf)
+    p = S.triple_products(S.normmap(a, leaf), S.normmap(b, leaf))
+    tau = float(np.quantile(p[p > 0], 0.7))
+    C1 = torch.full_like(A, float("nan"))
+    C2 = torch.full_like(A, float("nan"))
+    pl = P.Plan(n, leaf, mode)
+    pl.plan(nA, nB, tau, 1e-6).multiply(A, B, C1)
+    pl.plan_multiply(nA, nB, tau, A, B, C2, 1e-6)
+    torch.cuda.synchronize()
+    assert torch.equal(C1, C2)
+    assert torch.isfinite(C2).all()
