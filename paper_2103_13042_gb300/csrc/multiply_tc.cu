@@ -71,7 +71,12 @@ struct TcCfg {
   static constexpr int M = LEAF, N = LEAF;
   static constexpr int kEpiWarps = 4 * (N / 64);          // 64 columns per epilogue warp
   static constexpr int kThreads = 32 * kFirstEpiWarp + 32 * kEpiWarps;
-  static constexpr uint32_t kStageBytes = L::kChunkBytes * 2 * (kHasLo ? 2 : 1);
+  // chunks of K per pipeline stage: without lo parts a whole block pair (when
+  // it fits in 72 KB), so one barrier wait serves 4 * kNch MMAs; split modes
+  // already issue 3 MMAs per K step and keep one chunk per stage
+  static constexpr int kCPS =
+      (!kHasLo && L::kNch > 1 && L::kChunkBytes * 2 * L::kNch <= 72 * 1024) ? L::kNch : 1;
+  static constexpr uint32_t kStageBytes = L::kChunkBytes * 2 * (kHasLo ? 2 : 1) * kCPS;
   static constexpr int kStagesFit =
       (216 * 1024 - kEpiWarps * (M == 64 ? 16 : 0) * (64 * 4 + 16)) / kStageBytes;
   static constexpr int kStages = kStagesFit > 16 ? 16 : kStagesFit;
@@ -104,6 +109,7 @@ struct TcCfg {
                 "shared-memory regions aligned");
   static constexpr size_t kSmemBytes = kMiscOffset + 64 + 1024;     // + alignment slack
   static_assert(kStages >= 2, "at least two pipeline stages");
+  static_assert(!kHasLo || kCPS == 1, "lo parts are staged one chunk at a time");
   static_assert(kTmemCols >= 32 && kTmemCols <= 512 && kNumAcc >= 2, "TMEM columns");
   static_assert(kSmemBytes <= 227 * 1024, "shared memory");
 };
@@ -316,22 +322,24 @@ __global__ void __launch_bounds__(TcCfg<FMT, LEAF, SPLITMODE>::kThreads, 1)
           const bool split = (flags & kEntSplit) != 0;
           const int64_t oa = (int64_t)rec.x * L::kBlockBytes;
           const int64_t ob = (int64_t)rec.y * L::kBlockBytes;
-          for (int c = 0; c < L::kNch; ++c) {
+          constexpr int CPS = Cfg::kCPS;
+          for (int c = 0; c < L::kNch; c += CPS) {
             if (!wait_ab(&empty[stage], phase ^ 1u, abort_flag, p.status)) {
               ok = false;
               break;
             }
             StageMeta m;
             m.flags = ((flags & kEntFirst) && c == 0 ? 1 : 0) |
-                      ((flags & kEntLast) && c == L::kNch - 1 ? 2 : 0) | (split ? 4 : 0);
+                      ((flags & kEntLast) && c + CPS == L::kNch ? 2 : 0) | (split ? 4 : 0);
             m.s = sexp;
             m.tile = rec.w;
             m.pad = 0;
             meta[stage] = m;
-            mbar_arrive_expect_tx(&full[stage], CH * 2 * (split ? 2 : 1));
+            mbar_arrive_expect_tx(&full[stage], CH * CPS * 2 * (split ? 2 : 1));
             uint8_t* sb = smem + (size_t)stage * Cfg::kStageBytes;
-            bulk_g2s(sb, p.img.a_hi + oa + c * CH, CH, &full[stage]);
-            bulk_g2s(sb + CH, p.img.b_hi + ob + c * CH, CH, &full[stage]);
+            // the image's chunks are consecutive: CPS chunks are one copy
+            bulk_g2s(sb, p.img.a_hi + oa + c * CH, CH * CPS, &full[stage]);
+            bulk_g2s(sb + CH * CPS, p.img.b_hi + ob + c * CH, CH * CPS, &full[stage]);
             if constexpr (Cfg::kHasLo) {
               if (split) {
                 bulk_g2s(sb + 2 * CH, p.img.a_lo + oa + c * CH, CH, &full[stage]);
@@ -413,18 +421,23 @@ __global__ void __launch_bounds__(TcCfg<FMT, LEAF, SPLITMODE>::kThreads, 1)
         }
         // descriptors of the stage's chunks; a 32-byte K step adds 2 to the
         // start-address field (addresses stay below 256 KB: no carry)
+        constexpr int CPS = Cfg::kCPS;
         const uint32_t a0 = smem_u32(smem + (size_t)stage * Cfg::kStageBytes);
-        const uint64_t da = sdesc_k_sw128(a0), db = sdesc_k_sw128(a0 + CH);
+        const uint64_t da = sdesc_k_sw128(a0), db = sdesc_k_sw128(a0 + CPS * CH);
 #pragma unroll
-        for (int ks = 0; ks < 4; ++ks) {
-          const uint64_t ad = da + 2u * ks, bdsc = db + 2u * ks;
-          mma<FMT>(d_hh, ad, bdsc, Cfg::kIdesc, acc_hh);
-          acc_hh = 1;
-          if constexpr (Cfg::kHasLo) {
-            if (split_run) {
-              mma<FMT>(d_x, ad, db + (uint64_t)(2 * CH >> 4) + 2u * ks, Cfg::kIdesc, acc_x);
-              acc_x = 1;
-              mma<FMT>(d_x, da + (uint64_t)(2 * CH >> 4) + 2u * ks, bdsc, Cfg::kIdesc, 1);
+        for (int cc = 0; cc < CPS; ++cc) {
+#pragma unroll
+          for (int ks = 0; ks < 4; ++ks) {
+            const uint64_t step = (uint64_t)(cc * CH >> 4) + 2u * ks;
+            const uint64_t ad = da + step, bdsc = db + step;
+            mma<FMT>(d_hh, ad, bdsc, Cfg::kIdesc, acc_hh);
+            acc_hh = 1;
+            if constexpr (Cfg::kHasLo) {   // CPS == 1 here: lo parts at 2 CH and 3 CH
+              if (split_run) {
+                mma<FMT>(d_x, ad, db + (uint64_t)(2 * CH >> 4) + 2u * ks, Cfg::kIdesc, acc_x);
+                acc_x = 1;
+                mma<FMT>(d_x, da + (uint64_t)(2 * CH >> 4) + 2u * ks, bdsc, Cfg::kIdesc, 1);
+              }
             }
           }
         }
