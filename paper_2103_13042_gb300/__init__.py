@@ -73,6 +73,7 @@ _SIGS = {
     "spamm_frobenius_diff": [_VP, _VP, _I64, ctypes.POINTER(_D), _VP],
     "spamm_last_device_status": [_VP, ctypes.POINTER(_I32)],
     "spamm_multiply_fp32_noalloc": [_VP, _VP, _VP, _I64, _I32, _D, _VP],
+    "spamm_selftest_bounded_wait": [_I64, ctypes.POINTER(_I64), _VP],
     "spamm_batch_workspace_size": [_VP, _I32, _I32, _I32, ctypes.POINTER(ctypes.c_size_t)],
     "spamm_batch_create": [ctypes.POINTER(_VP), _VP, _I32, _I32, _I32, _I32, _VP,
                            ctypes.c_size_t],
@@ -462,6 +463,14 @@ def load_tau_weights(device=None, path: str = TAU_WEIGHTS_PATH):
     if w.size != spamm_mlp_param_count():
         raise RuntimeError(f"{path}: {w.size} values, expected {spamm_mlp_param_count()}")
     return torch.from_numpy(w).to(device or torch.device("cuda"))
+
+
+def spamm_selftest_bounded_wait(limit_ns: int = 20_000_000, stream=None) -> int:
+    """Bounded-wait self-test; returns the nanoseconds the wait took before giving up."""
+    e = ctypes.c_int64()
+    _check(lib().spamm_selftest_bounded_wait(int(limit_ns), ctypes.byref(e), _stream(stream)),
+           "spamm_selftest_bounded_wait")
+    return e.value
 
 
 def spamm_last_device_status(stream=None) -> int:

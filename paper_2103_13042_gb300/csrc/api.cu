@@ -689,6 +689,31 @@ spamm_status_t spamm_frobenius_diff(const float* X, const float* Y, int64_t coun
   return SPAMM_OK;
 }
 
+spamm_status_t spamm_selftest_bounded_wait(int64_t limit_ns, int64_t* elapsed_ns,
+                                           void* stream) {
+  if (limit_ns < 1000 || limit_ns > 1000000000LL) return SPAMM_ERR_INVALID_ARG;
+  int32_t* status = device_status_word();
+  if (!status) return SPAMM_ERR_NO_MEMORY;
+  const cudaStream_t s = (cudaStream_t)stream;
+  long long* out = nullptr;
+  if (cudaMalloc(&out, 3 * sizeof(long long)) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return SPAMM_ERR_NO_MEMORY;
+  }
+  long long h[3] = {0, 0, 0};
+  cudaError_t err = launch_wait_selftest(status, (uint64_t)limit_ns, out, s);
+  if (err == cudaSuccess) err = cudaMemcpyAsync(h, out, sizeof(h), cudaMemcpyDeviceToHost, s);
+  if (err == cudaSuccess) err = cudaStreamSynchronize(s);
+  cudaFree(out);
+  if (err != cudaSuccess) {
+    (void)cudaGetLastError();
+    return SPAMM_ERR_CUDA;
+  }
+  if (elapsed_ns) *elapsed_ns = h[2];
+  // the wait must have given up and raised the abort flag
+  return (h[0] == 1 && h[1] == 1) ? SPAMM_OK : SPAMM_ERR_DEVICE_FAULT;
+}
+
 spamm_status_t spamm_last_device_status(void* stream, int32_t* code) {
   if (!code) return SPAMM_ERR_INVALID_ARG;
   int32_t* w = device_status_word();

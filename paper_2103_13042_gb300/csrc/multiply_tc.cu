@@ -116,14 +116,14 @@ struct TcCfg {
 
 // Bounded wait that also returns when another role raised the abort flag.
 __device__ __forceinline__ bool wait_ab(uint64_t* bar, uint32_t parity, volatile int* abort_flag,
-                                        int32_t* status) {
+                                        int32_t* status, uint64_t limit_ns = kWaitLimitNs) {
   if (mbar_try_wait(bar, parity)) return true;
   const uint64_t t0 = globaltimer_ns();
   for (uint32_t it = 1;; ++it) {
     if (mbar_try_wait(bar, parity)) return true;
     if ((it & 63u) == 0) {
       if (*abort_flag) return false;
-      if (globaltimer_ns() - t0 > kWaitLimitNs) {
+      if (globaltimer_ns() - t0 > limit_ns) {
         *abort_flag = 1;
         atomicExch(status, (int32_t)SPAMM_ERR_TIMEOUT);
         return false;
@@ -647,6 +647,29 @@ __global__ void __launch_bounds__(256)
   }
 }
 
+// Self-test of the bounded wait: one CTA waits, with the multiply's own wait
+// routine and a short limit, on an mbarrier phase that nothing completes; the
+// wait must give up, raise the abort flag and latch SPAMM_ERR_TIMEOUT.
+// out[0] = 1 if the wait returned false, out[1] = the abort flag, out[2] =
+// elapsed nanoseconds.
+__global__ void wait_selftest_kernel(int32_t* status, uint64_t limit_ns, long long* out) {
+  __shared__ __align__(8) uint64_t bar;
+  __shared__ int abort_flag;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);   // phase 0 completes only on an arrival, which never comes
+    abort_flag = 0;
+    fence_mbarrier_init();
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const uint64_t t0 = globaltimer_ns();
+    const bool ok = wait_ab(&bar, 0u, &abort_flag, status, limit_ns);
+    out[0] = ok ? 0 : 1;
+    out[1] = abort_flag;
+    out[2] = (long long)(globaltimer_ns() - t0);
+  }
+}
+
 template <uint32_t FMT, int LEAF, int SPLITMODE>
 cudaError_t launch_tc(const TcParams& prm, cudaStream_t s) {
   using Cfg = TcCfg<FMT, LEAF, SPLITMODE>;
@@ -676,6 +699,12 @@ cudaError_t launch_zero_empty_tiles(const InstRef& ref, const PlanBuffers& b, in
     case 128: zero_tiles_kernel<128><<<grid, 256, 0, s>>>(ref, b); break;
     default: return cudaErrorInvalidValue;
   }
+  return cudaPeekAtLastError();
+}
+
+cudaError_t launch_wait_selftest(int32_t* status, uint64_t limit_ns, long long* out,
+                                 cudaStream_t s) {
+  wait_selftest_kernel<<<1, 32, 0, s>>>(status, limit_ns, out);
   return cudaPeekAtLastError();
 }
 

@@ -40,6 +40,10 @@ cudaError_t launch_multiply_tc(spamm_precision_t prec, int leaf, const InstRef& 
 cudaError_t launch_zero_empty_tiles(const InstRef& ref, const PlanBuffers& b, int leaf,
                                     cudaStream_t s);
 
+// Self-test of the multiply's bounded wait on a phase that never completes.
+cudaError_t launch_wait_selftest(int32_t* status, uint64_t limit_ns, long long* out,
+                                 cudaStream_t s);
+
 // The same from the per-tile counts alone: may run as soon as the plan's
 // counting half has finished.
 cudaError_t launch_zero_empty_tiles_scan(const InstRef& ref, const PlanBuffers& b, int leaf,
