@@ -310,7 +310,9 @@ spamm_status_t spamm_normmap(const float* X, int64_t n, int32_t leaf, double* no
   spamm_status_t st = check_shape(n, leaf);
   if (st != SPAMM_OK) return st;
   if (!X || !normmap || !aligned16(X) || !aligned16(normmap)) return SPAMM_ERR_INVALID_ARG;
-  cudaError_t e = launch_normmap(X, n, leaf, normmap, (cudaStream_t)stream);
+  int32_t* status = device_status_word();
+  if (!status) return SPAMM_ERR_NO_MEMORY;
+  cudaError_t e = launch_normmap(X, n, leaf, normmap, status, (cudaStream_t)stream);
   if (e != cudaSuccess) {
     (void)cudaGetLastError();
     return SPAMM_ERR_CUDA;

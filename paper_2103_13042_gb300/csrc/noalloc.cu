@@ -103,8 +103,8 @@ extern "C" spamm_status_t spamm_multiply_fp32_noalloc(const float* A, const floa
   const InstRef ref = make_ref(&inst, nullptr, 1);
 
   const cudaStream_t s = (cudaStream_t)stream;
-  cudaError_t e = launch_normmap(A, n, leaf, nA, s);
-  if (e == cudaSuccess) e = launch_normmap(B, n, leaf, nB, s);
+  cudaError_t e = launch_normmap(A, n, leaf, nA, nullptr, s);
+  if (e == cudaSuccess) e = launch_normmap(B, n, leaf, nB, nullptr, s);
   if (e == cudaSuccess) e = run_plan(ref, buf, s);
   if (e == cudaSuccess) e = launch_multiply_simt(ref, buf, leaf, kScheduleStatic, s);
   if (e == cudaSuccess) e = launch_zero_empty_tiles(ref, buf, leaf, s);

@@ -58,6 +58,7 @@ constexpr int kPrepThreads = 256;
 constexpr int kFinThreads = 512;
 constexpr int kGroupRows = 8;      // block rows per band of the tile enumeration
 static_assert(kOrderKeys <= kMaxBd + 2 && kOrderKeys <= 32, "order buckets");
+static_assert(kTilesPerCta % kGroupRows == 0, "a CTA of a full band covers whole columns");
 
 // Output tile (i, j) at enumeration position `pos` of an instance: bands of
 // kGroupRows block rows, column by column inside a band, so that tiles close
@@ -129,10 +130,36 @@ __device__ __forceinline__ void ext_add(ExtSum& s, float q, int E) {
   }
 }
 
-// The sum of the relative product p / (||A|| ||B||) = (mA mB mI) 2^(eA + eB + eI).
-__device__ __forceinline__ void ext_add_rel(ExtSum& s, Screen a, Screen b, float inv_m, int inv_e) {
-  if (a.e == kZeroExp || b.e == kZeroExp) return;
-  ext_add(s, __fmul_rn(__fmul_rn(a.m, b.m), inv_m), a.e + b.e + inv_e);
+// Per-lane sum of a tile's skipped products q 2^E (q = mA mB in [0.25, 1],
+// E = eA + eB), held as S 2^Emax with Emax the largest exponent seen so far;
+// terms more than 126 binades below Emax are dropped.  Zero products (m = 0)
+// add nothing.  A few FP32/integer operations per term and no branch in the
+// common case (E <= Emax).
+struct SkipSum {
+  float S;
+  int Emax;
+};
+constexpr int kSkipNone = -(1 << 29);
+
+// 2^k for -126 <= k <= 0, and 0 for k < -126.
+__device__ __forceinline__ float pow2f_or_zero(int k) {
+  return __int_as_float(max(k + 127, 0) << 23);
+}
+
+__device__ __forceinline__ void skip_add(SkipSum& s, Screen a, Screen b) {
+  const int E = a.e + b.e;
+  const float q = __fmul_rn(a.m, b.m);
+  const int d = E - s.Emax;
+  if (d > 0) {   // a new largest exponent: rescale the running sum
+    s.S = __fmul_rn(s.S, pow2f_or_zero(-d));
+    s.Emax = E;
+  }
+  s.S = __fmaf_rn(q, pow2f_or_zero(min(d, 0)), s.S);
+}
+
+// The lane's sum as an ExtSum (value m 2^e).
+__device__ __forceinline__ ExtSum skip_ext(const SkipSum& s) {
+  return s.S > 0.0f ? ExtSum{s.S, s.Emax} : ExtSum{0.0f, 0};
 }
 
 // Warp total of ExtSums in one pass: every lane rescales its sum to 2^-40 of
@@ -264,7 +291,21 @@ __global__ void __launch_bounds__(kPrepThreads)
   }
 }
 
-__global__ void __launch_bounds__(kWarpsPerCta * 32, 3)
+// Split modes: adds a surviving product to its binade's shared-memory bin
+// (rare: the scale of ||A|| ||B|| is reloaded here rather than kept live).
+__device__ __forceinline__ void bin_survivor(Screen a, Screen b, const double* pa, const double* pb,
+                                          const PlanDevice* pd, double* bin_sum, int* bin_cnt) {
+  const double inv = pd->inv_ab;
+  int inv_e;
+  const float inv_m = (float)frexp(inv, &inv_e);
+  const double p = __dmul_rn(*pa, *pb);
+  const int bin = rel_bin_screened(a, b, inv_m, inv_e, pa, pb, inv);
+  atomicAdd(&bin_sum[bin - kFlagBinMin], p);
+  atomicAdd(&bin_cnt[bin - kFlagBinMin], 1);
+}
+
+template <bool SPLIT, bool BAND>
+__global__ void __launch_bounds__(kWarpsPerCta * 32, 4)
     count_kernel(InstRef R, PlanBuffers Bf) {
   __shared__ double s_bin_sum[kFlagBins];
   __shared__ int s_bin_cnt[kFlagBins];
@@ -276,9 +317,9 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, 3)
   if (threadIdx.x < kOrderKeys) s_keys[threadIdx.x] = 0;
   const int ii = inst_of_count_cta(R, blockIdx.x);
   const Inst& in = R.at(ii);
-  const int bd = in.bd, split = in.split, band = in.band;
+  const int bd = in.bd;
+  const bool split = SPLIT && in.split, band = BAND && in.band;
   const TauScreen T = in.T;
-  const TauScreen Thi = in.T_hi;
   const double* nA = in.nA;
   const double* nB = in.nB;
   PlanDevice* pd = in.pd;
@@ -295,6 +336,27 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, 3)
   const int64_t tiles = (int64_t)bd * bd;
   const int nch = (bd + 31) >> 5;
   const int64_t lt0 = (int64_t)(blockIdx.x - in.count0) * kTilesPerCta;
+  // When the CTA's 32 positions lie in one full band they are 8 block rows x
+  // 4 block columns (warp w: row r0 + w, columns j0 .. j0 + 3): those 8 rows
+  // of A's screens and 4 columns of B's are staged in shared memory with one
+  // coalesced load, so each warp meets one memory latency instead of one per
+  // tile.  Other CTAs (a ragged last band) read the screens from global memory.
+  extern __shared__ Screen s_scr[];   // [8 * bd] A rows, then [4 * bd] B columns
+  const int64_t band_tiles = (int64_t)kGroupRows * bd;
+  const int64_t band0 = lt0 / band_tiles;
+  const int r0 = (int)band0 * kGroupRows;
+  const bool staged = band0 == (lt0 + kTilesPerCta - 1) / band_tiles && r0 + kGroupRows <= bd &&
+                      lt0 + kTilesPerCta <= tiles;
+  const int j0 = (int)((lt0 - band0 * band_tiles) / kGroupRows);
+  if (staged) {
+    const int na = kGroupRows * bd, nb = kTilesPerCta / kGroupRows * bd;
+    const Screen* ga = Bf.sA + in.tile0 + (int64_t)r0 * bd;
+    const Screen* gb = Bf.sBT + in.tile0 + (int64_t)j0 * bd;
+#pragma unroll 4
+    for (int x = threadIdx.x; x < na + nb; x += blockDim.x)
+      s_scr[x] = x < na ? ga[x] : gb[x - na];
+    __syncthreads();
+  }
   long long wS = 0;
   int wkmax = 0, wne = 0;
   ExtSum wb1{0.0f, 0}, wb2{0.0f, 0};
@@ -304,18 +366,17 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, 3)
     int i, j;
     tile_at(pos, bd, i, j);
     const int64_t t = (int64_t)i * bd + j;
-    const Screen* ra = Bf.sA + in.tile0 + (int64_t)i * bd;
-    const Screen* rb = Bf.sBT + in.tile0 + (int64_t)j * bd;
-    ExtSum sk{0.0f, 0};
+    const Screen* ra = staged ? s_scr + (i - r0) * bd : Bf.sA + in.tile0 + (int64_t)i * bd;
+    const Screen* rb = staged ? s_scr + (kGroupRows + j - j0) * bd : Bf.sBT + in.tile0 + (int64_t)j * bd;
+    SkipSum sk{0.0f, kSkipNone};
     int count = 0;
-    int run_bin = kFlagBinMin - 1, run_cnt = 0;
-    double run_sum = 0.0;
-    // the screens of up to four 32-wide chunks of k are loaded together (one
-    // memory latency per group instead of one per chunk)
-    for (int kg = 0; kg < bd; kg += 128) {
-      Screen av[4], bv[4];
+    // the screens of up to kChunks 32-wide chunks of k are loaded together
+    // (one latency per group instead of one per chunk)
+    constexpr int kChunks = 2;
+    for (int kg = 0; kg < bd; kg += 32 * kChunks) {
+      Screen av[kChunks], bv[kChunks];
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
+      for (int q = 0; q < kChunks; ++q) {
         const int k = kg + 32 * q + lane;
         if (k < bd) {
           av[q] = ra[k];
@@ -323,7 +384,7 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, 3)
         }
       }
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
+    for (int q = 0; q < kChunks; ++q) {
       const int k0 = kg + 32 * q;
       if (k0 >= bd) break;   // uniform over the warp
       const int k = k0 + lane;
@@ -331,24 +392,13 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, 3)
       if (k < bd) {
         const Screen a = av[q], b = bv[q];
         s = survives(a, b, nA + (int64_t)i * bd + k, nB + (int64_t)k * bd + j, T);
-        if (s && band) s = !survives(a, b, nA + (int64_t)i * bd + k, nB + (int64_t)k * bd + j, Thi);
+        if (BAND && s && band)
+          s = !survives(a, b, nA + (int64_t)i * bd + k, nB + (int64_t)k * bd + j, in.T_hi);
         if (!s) {
-          ext_add_rel(sk, a, b, inv_m, inv_e);
+          skip_add(sk, a, b);
         } else if (split) {
-          const double p = __dmul_rn(nA[(int64_t)i * bd + k], nB[(int64_t)k * bd + j]);
-          const int bin = rel_bin_screened(a, b, inv_m, inv_e, nA + (int64_t)i * bd + k,
-                                           nB + (int64_t)k * bd + j, inv);
-          if (bin != run_bin) {
-            if (run_cnt) {
-              atomicAdd(&s_bin_sum[run_bin - kFlagBinMin], run_sum);
-              atomicAdd(&s_bin_cnt[run_bin - kFlagBinMin], run_cnt);
-            }
-            run_bin = bin;
-            run_cnt = 0;
-            run_sum = 0.0;
-          }
-          run_sum += p;
-          ++run_cnt;
+          bin_survivor(a, b, nA + (int64_t)i * bd + k, nB + (int64_t)k * bd + j, pd, s_bin_sum,
+                       s_bin_cnt);
         }
       }
       const unsigned bal = __ballot_sync(0xffffffffu, s);
@@ -356,11 +406,13 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, 3)
       if (lane == 0) Bf.surv_mask[in.mask0 + t * nch + (k0 >> 5)] = bal;
     }
     }
-    if (split && run_cnt) {
-      atomicAdd(&s_bin_sum[run_bin - kFlagBinMin], run_sum);
-      atomicAdd(&s_bin_cnt[run_bin - kFlagBinMin], run_cnt);
+    // the tile's skipped sum relative to ||A|| ||B|| (times inv = inv_m 2^inv_e);
+    // no FP64: the FP64 pipe is narrow here
+    ExtSum tot = ext_warp_sum_fast(skip_ext(sk));
+    if (tot.m > 0.0f) {
+      tot.m = __fmul_rn(tot.m, inv_m);
+      tot.e += inv_e;
     }
-    const ExtSum tot = ext_warp_sum_fast(sk);   // no FP64: the FP64 pipe is narrow here
     if (lane == 0) {
       const int64_t g = in.tile0 + t;
       Bf.cnt[g] = count;
@@ -838,9 +890,10 @@ int count_ctas_of(int bd) { return (int)(((int64_t)bd * bd + kTilesPerCta - 1) /
 
 size_t plan_layout(Inst* insts, int count, PlanBuffers* b, char* base) {
   int64_t tiles = 0, kslots = 0, mwords = 0;
-  int prep = 0, cnt = 0;
+  int prep = 0, cnt = 0, max_bd = 0;
   for (int i = 0; i < count; ++i) {
     const int64_t bd = insts[i].bd;
+    max_bd = max_bd > (int)bd ? max_bd : (int)bd;
     insts[i].tile0 = tiles;
     insts[i].kidx0 = kslots;
     insts[i].mask0 = mwords;
@@ -864,6 +917,7 @@ size_t plan_layout(Inst* insts, int count, PlanBuffers* b, char* base) {
   t.kslots = kslots;
   t.prep_ctas = prep;
   t.count_ctas = cnt;
+  t.max_bd = max_bd;
   t.need_words = (tiles + 31) / 32;
   t.pd = reinterpret_cast<PlanDevice*>(take((size_t)count * sizeof(PlanDevice)));
   t.bdev = reinterpret_cast<BatchDevice*>(take(sizeof(BatchDevice)));
@@ -898,7 +952,33 @@ InstRef make_ref(const Inst* host_insts, const Inst* dev_table, int count) {
   r.count = count;
   r.table = dev_table;
   if (!dev_table) r.one = host_insts[0];
+  for (int i = 0; i < count; ++i) {
+    r.any_split |= host_insts[i].split != 0;
+    r.any_band |= host_insts[i].band != 0;
+  }
   return r;
+}
+
+// The count kernel with its staged screens: 12 * max_bd screens of shared memory.
+cudaError_t launch_count(const InstRef& ref, const PlanBuffers& b, cudaStream_t s) {
+  const size_t smem = (size_t)(kGroupRows + kTilesPerCta / kGroupRows) * b.max_bd * sizeof(Screen);
+  auto* kern = ref.any_band ? (ref.any_split ? count_kernel<true, true> : count_kernel<false, true>)
+                            : (ref.any_split ? count_kernel<true, false> : count_kernel<false, false>);
+  if (smem > 48 * 1024) {
+    static bool opted[64][4] = {};
+    const int v = (ref.any_band ? 2 : 0) + (ref.any_split ? 1 : 0);
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev >= 0 && dev < 64 && !opted[dev][v]) {
+      e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)((kGroupRows + kTilesPerCta / kGroupRows) * kMaxBd * sizeof(Screen)));
+      if (e != cudaSuccess) return e;
+      opted[dev][v] = true;
+    }
+  }
+  kern<<<b.count_ctas, kWarpsPerCta * 32, smem, s>>>(ref, b);
+  return cudaPeekAtLastError();
 }
 
 cudaError_t run_plan_count_half(const InstRef& ref, const PlanBuffers& b, cudaStream_t s) {
@@ -909,7 +989,8 @@ cudaError_t run_plan_count_half(const InstRef& ref, const PlanBuffers& b, cudaSt
   cudaError_t e = cudaMemsetAsync(b.pd, 0, clear, s);
   if (e != cudaSuccess) return e;
   prep_kernel<<<b.prep_ctas, kPrepThreads, 0, s>>>(ref, b);
-  count_kernel<<<b.count_ctas, kWarpsPerCta * 32, 0, s>>>(ref, b);
+  e = launch_count(ref, b, s);
+  if (e != cudaSuccess) return e;
   return cudaPeekAtLastError();
 }
 
@@ -931,7 +1012,8 @@ cudaError_t run_plan_count(const InstRef& ref, const PlanBuffers& b, cudaStream_
   cudaError_t e = cudaMemsetAsync(b.pd, 0, clear, s);
   if (e != cudaSuccess) return e;
   prep_kernel<<<b.prep_ctas, kPrepThreads, 0, s>>>(ref, b);
-  count_kernel<<<b.count_ctas, kWarpsPerCta * 32, 0, s>>>(ref, b);
+  e = launch_count(ref, b, s);
+  if (e != cudaSuccess) return e;
   finalize_kernel<<<ref.count, kFinThreads, 0, s>>>(ref, b);
   return cudaPeekAtLastError();
 }

@@ -98,6 +98,7 @@ struct InstRef {
   const Inst* table;
   Inst one;
   int count;
+  int any_split, any_band;   // some instance uses split flags / a band (host-side dispatch)
   __device__ __forceinline__ const Inst& at(int i) const { return table ? table[i] : one; }
 };
 
@@ -124,6 +125,7 @@ struct PlanBuffers {
   int64_t kslots;      // sum of bd^3
   int prep_ctas;       // prep grid
   int count_ctas;      // count and fill grids
+  int max_bd;          // largest bd of the table (the count kernel's shared-memory size)
   Screen* sA;          // [tiles] screen form of normA, row-major per instance
   Screen* sBT;         // [tiles] screen form of normB, transposed per instance
   double* part_a;      // [prep_ctas] partial sums of squared norms
@@ -182,7 +184,11 @@ cudaError_t run_plan_count(const InstRef& ref, const PlanBuffers& b, cudaStream_
 // first step) and the per-instance norm-product histograms (pd[i].hist).
 cudaError_t run_histogram(const InstRef& ref, const PlanBuffers& b, cudaStream_t s);
 
-cudaError_t launch_normmap(const float* X, int64_t n, int32_t leaf, double* out, cudaStream_t s);
+// Norm map of one n x n operand.  `status` (may be null) receives
+// SPAMM_ERR_TIMEOUT if a bounded wait of the staged form expires; the norms
+// that were not finished are then NaN.
+cudaError_t launch_normmap(const float* X, int64_t n, int32_t leaf, double* out, int32_t* status,
+                           cudaStream_t s);
 
 // Batched norm maps: one job per operand of an instance.
 struct NormJob {
