@@ -33,6 +33,35 @@ inline int64_t num_blocks(int64_t n, int32_t leaf) { return (n + leaf - 1) / lea
 int32_t* device_status_word();
 
 // ---------------------------------------------------------------------------
+// Programmatic dependent launch: a kernel of the plan -> rounding -> multiply
+// chain is launched while its predecessor in the stream still runs (its CTAs
+// are placed and set up early); it calls pdl_wait() before anything else, which
+// returns once the predecessor grid has completed and its writes are visible.
+// Every kernel so launched waits unconditionally at its top, so completion
+// stays transitive along the chain.  pdl_trigger() lets the successor launch.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                       Args&&... args) {
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, static_cast<Args&&>(args)...);
+}
+
+// ---------------------------------------------------------------------------
 // Error-free transformations (Knuth TwoSum, FMA-based TwoProd) in FP32.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {

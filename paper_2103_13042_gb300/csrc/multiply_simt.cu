@@ -67,6 +67,7 @@ __device__ __forceinline__ void write_row(float* p, const float* v) {
 
 template <int LEAF>
 __global__ void __launch_bounds__(kThreads) simt_kernel(InstRef R, PlanBuffers Bf, int dynamic) {
+  pdl_wait();
   using T = SimtTile<LEAF>;
   constexpr int TM = T::TM;
   constexpr int kLoads = T::kLoadsA;
@@ -188,7 +189,9 @@ cudaError_t launch(const InstRef& ref, const PlanBuffers& b, int schedule, cudaS
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, simt_kernel<LEAF>, kThreads, smem);
   const int grid = (int)std::max<int64_t>(
       1, std::min<int64_t>(b.tiles, (int64_t)sms * std::max(1, per_sm)));
-  simt_kernel<LEAF><<<grid, kThreads, smem, s>>>(ref, b, schedule == kScheduleDynamic);
+  cudaError_t e = launch_pdl(simt_kernel<LEAF>, dim3(grid), dim3(kThreads), smem, s, ref, b,
+                             (int)(schedule == kScheduleDynamic));
+  if (e != cudaSuccess) return e;
   return cudaPeekAtLastError();
 }
 

@@ -142,6 +142,7 @@ __device__ __forceinline__ void mma(uint32_t d, uint64_t a, uint64_t b, uint32_t
 template <uint32_t FMT, int LEAF, int SPLITMODE>
 __global__ void __launch_bounds__(TcCfg<FMT, LEAF, SPLITMODE>::kThreads, 1)
     tc_multiply_kernel(TcParams p) {
+  pdl_wait();
   using Cfg = TcCfg<FMT, LEAF, SPLITMODE>;
   using L = typename Cfg::L;
   constexpr int S = Cfg::kStages, N = Cfg::N;
@@ -680,8 +681,7 @@ cudaError_t launch_tc(const TcParams& prm, cudaStream_t s) {
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  kern<<<sms, Cfg::kThreads, Cfg::kSmemBytes, s>>>(prm);
-  return cudaPeekAtLastError();
+  return launch_pdl(kern, dim3(sms), dim3(Cfg::kThreads), Cfg::kSmemBytes, s, prm);
 }
 
 }  // namespace

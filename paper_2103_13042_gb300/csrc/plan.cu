@@ -228,6 +228,7 @@ __device__ __forceinline__ int inst_of_count_cta(const InstRef& r, int cta) {
 
 __global__ void __launch_bounds__(kPrepThreads)
     prep_kernel(InstRef R, PlanBuffers Bf) {
+  pdl_trigger();
   const int ii = inst_of_prep_cta(R, blockIdx.x);
   const Inst& in = R.at(ii);
   const int bd = in.bd;
@@ -307,6 +308,8 @@ __device__ __forceinline__ void bin_survivor(Screen a, Screen b, const double* p
 template <bool SPLIT, bool BAND>
 __global__ void __launch_bounds__(kWarpsPerCta * 32, 4)
     count_kernel(InstRef R, PlanBuffers Bf) {
+  pdl_wait();
+  pdl_trigger();
   __shared__ double s_bin_sum[kFlagBins];
   __shared__ int s_bin_cnt[kFlagBins];
   __shared__ long long s_S[kWarpsPerCta];
@@ -580,6 +583,8 @@ __device__ void block_scan_vec(const int (&x)[K], int (&ex)[K], int (&total)[K],
 // binade; the last CTA to finish lays out the batch-wide longest-first order.
 __global__ void __launch_bounds__(kFinThreads)
     finalize_kernel(InstRef R, PlanBuffers Bf) {
+  pdl_wait();
+  pdl_trigger();
   constexpr int K = 2 + (kOrderKeys - 1);   // survivors, non-empty, buckets 1 .. kOrderKeys-1
   __shared__ int s_sh[33 * K];
   __shared__ int s_kmax[kFinThreads / 32];
@@ -703,6 +708,21 @@ __global__ void __launch_bounds__(kFinThreads)
     }
   }
 
+  // one instance: its own totals lay out the order (no other CTA to wait for)
+  if (gridDim.x == 1) {
+    if (tid == 0) {
+      int acc = 0;
+      for (int key = kOrderKeys - 1; key >= 1; --key) {   // largest key first
+        Bf.bdev->cursor[key] = acc;
+        pd->key_base[key] = acc;
+        acc += tot[1 + key];
+      }
+      Bf.bdev->nonempty = acc;
+      pd->ne_base = 0;
+    }
+    return;
+  }
+
   // the last finalize CTA: bucket starts of the batch-wide longest-first
   // order, each instance's first slot in each bucket and its non-empty base
   __shared__ bool s_last;
@@ -773,6 +793,8 @@ __global__ void __launch_bounds__(kFinThreads)
 
 __global__ void __launch_bounds__(kWarpsPerCta * 32)
     fill_kernel(InstRef R, PlanBuffers Bf) {
+  pdl_wait();
+  pdl_trigger();
   __shared__ int s_beg[kTilesPerCta];
   const int warp = threadIdx.x / 32, lane = threadIdx.x & 31;
   const int ii = inst_of_count_cta(R, blockIdx.x);
@@ -977,8 +999,7 @@ cudaError_t launch_count(const InstRef& ref, const PlanBuffers& b, cudaStream_t 
       opted[dev][v] = true;
     }
   }
-  kern<<<b.count_ctas, kWarpsPerCta * 32, smem, s>>>(ref, b);
-  return cudaPeekAtLastError();
+  return launch_pdl(kern, dim3(b.count_ctas), dim3(kWarpsPerCta * 32), smem, s, ref, b);
 }
 
 cudaError_t run_plan_count_half(const InstRef& ref, const PlanBuffers& b, cudaStream_t s) {
@@ -995,9 +1016,10 @@ cudaError_t run_plan_count_half(const InstRef& ref, const PlanBuffers& b, cudaSt
 }
 
 cudaError_t run_plan_queue_half(const InstRef& ref, const PlanBuffers& b, cudaStream_t s) {
-  finalize_kernel<<<ref.count, kFinThreads, 0, s>>>(ref, b);
-  fill_kernel<<<b.count_ctas, kWarpsPerCta * 32, 0, s>>>(ref, b);
-  return cudaPeekAtLastError();
+  cudaError_t e = launch_pdl(finalize_kernel, dim3(ref.count), dim3(kFinThreads), 0, s, ref, b);
+  if (e == cudaSuccess)
+    e = launch_pdl(fill_kernel, dim3(b.count_ctas), dim3(kWarpsPerCta * 32), 0, s, ref, b);
+  return e;
 }
 
 cudaError_t run_plan(const InstRef& ref, const PlanBuffers& b, cudaStream_t s) {
@@ -1014,7 +1036,8 @@ cudaError_t run_plan_count(const InstRef& ref, const PlanBuffers& b, cudaStream_
   prep_kernel<<<b.prep_ctas, kPrepThreads, 0, s>>>(ref, b);
   e = launch_count(ref, b, s);
   if (e != cudaSuccess) return e;
-  finalize_kernel<<<ref.count, kFinThreads, 0, s>>>(ref, b);
+  e = launch_pdl(finalize_kernel, dim3(ref.count), dim3(kFinThreads), 0, s, ref, b);
+  if (e != cudaSuccess) return e;
   return cudaPeekAtLastError();
 }
 

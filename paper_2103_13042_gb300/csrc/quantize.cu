@@ -75,6 +75,8 @@ __global__ void __launch_bounds__(q_threads<LEAF>())
   constexpr int U = UNITS / kThreads;        // pieces per thread
   static_assert(UNITS % kThreads == 0, "whole pieces per thread");
   __shared__ float s_max[kThreads / 32];
+  pdl_wait();
+  pdl_trigger();
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int count = Bf.bdev->need_count;
   const float lo_scale = (float)(1 << L::kLoShift);
@@ -187,8 +189,8 @@ cudaError_t launch_q(const InstRef& ref, const PlanBuffers& b, const OperandImag
   // the list length is known on the device only: one full wave of CTAs
   const int64_t cap = 2 * b.tiles;
   const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(cap, (int64_t)sms * std::max(1, per_sm)));
-  quantize_kernel<FMT, LEAF, SPLIT><<<grid, q_threads<LEAF>(), 0, s>>>(ref, b, img);
-  return cudaPeekAtLastError();
+  return launch_pdl(quantize_kernel<FMT, LEAF, SPLIT>, dim3(grid), dim3(q_threads<LEAF>()), 0, s,
+                    ref, b, img);
 }
 
 }  // namespace
