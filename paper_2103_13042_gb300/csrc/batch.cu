@@ -28,8 +28,10 @@ struct spamm_batch_s {
   Inst* insts_dev = nullptr;     // [count]
   size_t table_bytes = 0;        // jobs + insts (one upload)
   size_t insts_offset = 0;       // offset of the Inst table inside it
-  int norm_ctas = 0;
-  std::vector<int> job_cta0;     // first norm-map CTA of each job
+  int n_vec_jobs = 0;            // norm-map jobs with 16-byte aligned rows (listed first)
+  int units_vec = 0, units_other = 0;
+  std::vector<int> job_slot;     // table slot of job 2 i + op (op 0: A, 1: B)
+  std::vector<int> job_unit0;    // its first unit in its part of the table
   void* staging = nullptr;       // pinned host copy of the tables being uploaded
   std::vector<char> last;        // tables of the previous upload
   bool uploaded_once = false;
@@ -130,7 +132,8 @@ cudaError_t enqueue(spamm_batch_s* b, cudaStream_t s, bool timing) {
   const InstRef ref = batch_ref(b);
   cudaError_t e = timing ? cudaEventRecord(b->phase[0], s) : cudaSuccess;
   if (e == cudaSuccess)
-    e = launch_normmap_jobs(b->jobs_dev, 2 * b->count, b->norm_ctas, b->eng.leaf, s);
+    e = launch_normmap_jobs(b->jobs_dev, b->n_vec_jobs, b->units_vec, 2 * b->count - b->n_vec_jobs,
+                            b->units_other, b->eng.leaf, b->status, s);
   if (e == cudaSuccess && timing) e = cudaEventRecord(b->phase[1], s);
   if (e == cudaSuccess)
     e = engine_plan_multiply(b->eng, ref, b->status, s, timing ? b->phase[2] : nullptr,
@@ -202,32 +205,41 @@ spamm_status_t spamm_batch_create(spamm_batch_t* batch, const int64_t* n, int32_
   b->normB = reinterpret_cast<double*>(base + norm_bytes);
   b->jobs_dev = reinterpret_cast<NormJob*>(base + 2 * norm_bytes);
   b->insts_dev = reinterpret_cast<Inst*>(base + 2 * norm_bytes + b->insts_offset);
-  // norm-map grid: operands are 16-byte aligned, so float4 loads iff n % 4 == 0
-  b->job_cta0.resize(2 * (size_t)count);
-  int cta = 0;
-  for (int32_t i = 0; i < count; ++i) {
-    for (int op = 0; op < 2; ++op) {
-      NormJob j{};
-      j.n = n[i];
-      j.bd = b->eng.insts[i].bd;
-      j.vec = (n[i] % 4) == 0;
-      b->job_cta0[2 * i + op] = cta;
-      const int64_t c = (int64_t)cta + normjob_ctas(j);
-      if (c >= ((int64_t)1 << 31)) {
-        release(b);
-        return SPAMM_ERR_UNSUPPORTED;
+  // norm-map jobs: operands are 16-byte aligned, so rows are iff n % 4 == 0;
+  // those jobs come first in the table, each part with its own unit count
+  b->job_slot.resize(2 * (size_t)count);
+  b->job_unit0.resize(2 * (size_t)count);
+  int slot = 0;
+  for (int pass = 0; pass < 2; ++pass) {
+    const bool vec_pass = pass == 0;
+    int64_t units = 0;
+    for (int32_t i = 0; i < count; ++i) {
+      if (((n[i] % 4) == 0) != vec_pass) continue;
+      for (int op = 0; op < 2; ++op) {
+        NormJob j{};
+        j.n = n[i];
+        j.vec = vec_pass ? 1 : 0;
+        b->job_slot[2 * i + op] = slot++;
+        b->job_unit0[2 * i + op] = (int)units;
+        units += normjob_shape(j, leaf);
+        if (units >= ((int64_t)1 << 31)) {
+          release(b);
+          return SPAMM_ERR_UNSUPPORTED;
+        }
       }
-      cta = (int)c;
+    }
+    if (vec_pass) {
+      b->n_vec_jobs = slot;
+      b->units_vec = (int)units;
+    } else {
+      b->units_other = (int)units;
     }
   }
-  b->norm_ctas = cta;
   b->last.assign(b->table_bytes, 0);
-  if (precision != SPAMM_FP32) {
-    b->status = device_status_word();
-    if (!b->status) {
-      release(b);
-      return SPAMM_ERR_NO_MEMORY;
-    }
+  b->status = device_status_word();   // bounded waits of the norm map and the multiply
+  if (!b->status) {
+    release(b);
+    return SPAMM_ERR_NO_MEMORY;
   }
   if (flags & SPAMM_BATCH_TIMING) {
     for (cudaEvent_t& ev : b->phase) {
@@ -291,13 +303,13 @@ spamm_status_t upload_tables(spamm_batch_s* b, const spamm_problem_t* problems,
     in.target_rel = targets ? targets[i] : (split ? target_rel_err : 0.0);
     in.c1 = split ? 2.0 * u + u * u : 0.0;
     for (int op = 0; op < 2; ++op) {
-      NormJob& j = jobs[2 * i + op];
+      NormJob& j = jobs[b->job_slot[2 * i + op]];
       j.X = op ? in.B : in.A;
       j.out = op ? b->normB + in.tile0 : b->normA + in.tile0;
       j.n = in.n;
-      j.bd = in.bd;
-      j.vec = (in.n % 4) == 0;
-      j.cta0 = b->job_cta0[2 * i + op];
+      j.vec = (in.n % 4) == 0 ? 1 : 0;
+      (void)normjob_shape(j, e.leaf);
+      j.unit0 = b->job_unit0[2 * i + op];
     }
   }
   std::memcpy(tab.data() + b->insts_offset, e.insts.data(), (size_t)b->count * sizeof(Inst));
@@ -383,7 +395,9 @@ spamm_status_t spamm_batch_tau_predict(spamm_batch_t b, const spamm_problem_t* p
   st = upload_tables(b, problems, 0.0, targets, s);
   if (st != SPAMM_OK) return st;
   const InstRef ref = batch_ref(b);
-  cudaError_t err = launch_normmap_jobs(b->jobs_dev, 2 * b->count, b->norm_ctas, b->eng.leaf, s);
+  cudaError_t err = launch_normmap_jobs(b->jobs_dev, b->n_vec_jobs, b->units_vec,
+                                        2 * b->count - b->n_vec_jobs, b->units_other, b->eng.leaf,
+                                        b->status, s);
   if (err == cudaSuccess) err = run_histogram(ref, b->eng.buf, s);
   if (err == cudaSuccess) err = launch_tau_from_hist(ref, weights, b->eng.feat_dev, b->eng.tau_dev, s);
   if (err != cudaSuccess) {

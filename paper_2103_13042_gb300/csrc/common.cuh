@@ -152,9 +152,13 @@ __device__ __forceinline__ void sumsq_merge(SumSq& acc, float hi, float lo, int 
 // satisfies p < hi (also after a renormalisation, which moves hi by far less
 // than B / 2) and Fast2Sum gives the exact error of hi + p in 3 operations;
 // the errors and the low halves of the squares go into lo, and (hi, lo) is
-// renormalised every 8 entries.  B is removed with one TwoSum at the end.  Groups whose largest magnitude lies in
-// [2^-30, 2^61) are not scaled: squares of entries below 2^-63 may then lose
-// bits, but they are below 2^-66 of the largest square.
+// renormalised every 8 entries.  B is removed with one TwoSum at the end.
+// Every group is scaled (its largest magnitude to [1, 2)), so a group's pair
+// lies in [1, 34) of its unit 4^g and an accumulator's hi stays within a few
+// binades of its unit: sumsq_merge's exponent test then drops only terms far
+// below 2^-43 of the sum.  (Leaving groups of moderate magnitude unscaled would
+// break that: an unscaled pair may be as small as 2^-60, and a scaled group
+// 2^-98 below its unit would be dropped at a relative size of 2^-38.)
 template <int N>
 __device__ __forceinline__ void sumsq_group(SumSq& acc, const float (&v)[N]) {
   float mx = 0.0f;
@@ -170,10 +174,8 @@ __device__ __forceinline__ void sumsq_group(SumSq& acc, const float (&v)[N]) {
     }
     return;
   }
-  const int g0 = group_exponent(mx);
-  const bool scaled = g0 < -30 || g0 > 60;
-  const int g = scaled ? g0 : 0;
-  const float sc = scaled ? pow2f(-g0) : 1.0f;
+  const int g = group_exponent(mx);
+  const float sc = pow2f(-g);
   const float ms = __fmul_rn(mx, sc);
   const float pB = 2.0f * __fmul_rn(ms, ms);   // the starting value B (a float)
   float hi = pB, lo = 0.0f;

@@ -598,53 +598,77 @@ __global__ void __launch_bounds__(256)
   }
 }
 
-// Zeros for the tiles without survivors found from the counts: a CTA takes
-// 32 consecutive global tiles, warp 0 lists the empty ones (coalesced count
-// loads, ballot), then the CTA writes each of them with the same per-thread
-// column / row-step pattern (whole row segments per warp, 16-byte streaming
-// stores).
+// Zeros for the tiles without survivors found from the counts.  Every CTA
+// takes an equal contiguous range of global tiles (so every SM writes about
+// the same number of bytes); warp 0 lists the range's empty tiles in shared
+// memory (coalesced count loads, ballots), then each warp writes whole empty
+// tiles (list entries warp, warp + 8, ...): lane l owns float4 column
+// l % (leaf/4) and every (32 / (leaf/4))-th row, so a warp store covers whole
+// 128-byte row segments, and the tile's address arithmetic is paid once per
+// leaf*leaf*4 bytes.  16-byte streaming stores.
+constexpr int kZeroThreads = 256;
+constexpr int kZeroMaxRange = 64;   // tiles per CTA at most (the grid grows beyond that)
+
 template <int LEAF>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(kZeroThreads)
     zero_scan_kernel(InstRef R, PlanBuffers Bf) {
-  constexpr int kPerRow = LEAF / 4;                 // float4 per tile row
-  constexpr int kRowStep = 256 / kPerRow;           // rows per CTA pass
-  __shared__ int s_list[32];
+  constexpr int kPerRow = LEAF / 4;                          // float4 per tile row
+  constexpr int kRowsPerStore = kPerRow >= 32 ? 1 : 32 / kPerRow;
+  constexpr int kColSteps = kPerRow >= 32 ? kPerRow / 32 : 1;
+  constexpr int kWarps = kZeroThreads / 32;
+  __shared__ int s_list[kZeroMaxRange];
   __shared__ int s_count;
-  const int tid = threadIdx.x, lane = tid & 31;
-  const int my_c4 = tid % kPerRow, my_r = tid / kPerRow;
-  for (int64_t g0 = (int64_t)blockIdx.x * 32; g0 < Bf.tiles; g0 += (int64_t)gridDim.x * 32) {
-    if (tid < 32) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t lo = Bf.tiles * blockIdx.x / gridDim.x;
+  const int64_t hi = Bf.tiles * (blockIdx.x + 1) / gridDim.x;   // hi - lo <= kZeroMaxRange
+  if (warp == 0) {
+    int count = 0;
+    for (int64_t g0 = lo; g0 < hi; g0 += 32) {
       const int64_t gl = g0 + lane;
-      const bool empty = gl < Bf.tiles && Bf.cnt[gl] == 0;
+      const bool empty = gl < hi && Bf.cnt[gl] == 0;
       const unsigned mask = __ballot_sync(0xffffffffu, empty);
-      if (empty) s_list[__popc(mask & ((1u << lane) - 1u))] = lane;
-      if (lane == 0) s_count = __popc(mask);
+      if (empty) s_list[count + __popc(mask & ((1u << lane) - 1u))] = (int)(gl - lo);
+      count += __popc(mask);
     }
-    __syncthreads();
-    const int count = s_count;
-    for (int e = 0; e < count; ++e) {
-      const int64_t g = g0 + s_list[e];
-      const Inst& in = R.at(inst_of(R, Bf, g));
-      const int64_t n = in.n;
-      const int lt = (int)(g - in.tile0), bd = in.bd;   // lt < 2^20
-      const int ti = lt / bd, tj = lt - ti * bd;
-      const int64_t r0 = (int64_t)ti * LEAF, c0 = (int64_t)tj * LEAF;
-      const int rows = (int)min((int64_t)LEAF, n - r0), cols = (int)min((int64_t)LEAF, n - c0);
-      float* C = in.C;
-      if ((n & 3) == 0) {   // then cols % 4 == 0 and every float4 is aligned
-        if (4 * my_c4 < cols) {
-          float4* p = reinterpret_cast<float4*>(C + (r0 + my_r) * n + c0 + 4 * my_c4);
-          const int64_t step = (int64_t)kRowStep * n / 4;
-          for (int r = my_r; r < rows; r += kRowStep, p += step) __stcs(p, make_float4(0.f, 0.f, 0.f, 0.f));
-        }
-      } else {
-        for (int u = tid; u < rows * cols; u += 256) {
-          const int r = u / cols, c = u - r * cols;
-          C[(r0 + r) * n + c0 + c] = 0.f;
-        }
+    if (lane == 0) s_count = count;
+  }
+  __syncthreads();
+  const int count = s_count;
+  const int my_c4 = kPerRow >= 32 ? lane : lane % kPerRow;
+  const int my_r = kPerRow >= 32 ? 0 : lane / kPerRow;
+  for (int e = warp; e < count; e += kWarps) {
+    const int64_t g = lo + s_list[e];
+    const Inst& in = R.at(inst_of(R, Bf, g));
+    const int64_t n = in.n;
+    const int lt = (int)(g - in.tile0), bd = in.bd;   // lt < 2^20
+    const int ti = lt / bd, tj = lt - ti * bd;
+    const int64_t r0 = (int64_t)ti * LEAF, c0 = (int64_t)tj * LEAF;
+    const int rows = (int)min((int64_t)LEAF, n - r0), cols = (int)min((int64_t)LEAF, n - c0);
+    float* C = in.C;
+    if ((n & 3) == 0 && rows == LEAF && cols == LEAF) {   // aligned full tile: unrolled stores
+      const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+      for (int cs = 0; cs < kColSteps; ++cs) {
+        float4* p = reinterpret_cast<float4*>(C + (r0 + my_r) * n + c0) + my_c4 + 32 * cs;
+        const int64_t step = (int64_t)kRowsPerStore * n / 4;
+#pragma unroll 8
+        for (int r = 0; r < LEAF / kRowsPerStore; ++r) __stcs(p + r * step, z);
+      }
+    } else if ((n & 3) == 0) {   // aligned ragged tile: cols % 4 == 0
+      for (int cs = 0; cs < kColSteps; ++cs) {
+        const int c4 = my_c4 + 32 * cs;
+        if (4 * c4 >= cols) continue;
+        float4* p = reinterpret_cast<float4*>(C + (r0 + my_r) * n + c0 + 4 * c4);
+        const int64_t step = (int64_t)kRowsPerStore * n / 4;
+        for (int r = my_r; r < rows; r += kRowsPerStore, p += step)
+          __stcs(p, make_float4(0.f, 0.f, 0.f, 0.f));
+      }
+    } else {
+      for (int u = lane; u < rows * cols; u += 32) {
+        const int r = u / cols, c = u - r * cols;
+        C[(r0 + r) * n + c0 + c] = 0.f;
       }
     }
-    __syncthreads();   // s_list / s_count are rewritten by the next chunk
   }
 }
 
@@ -713,12 +737,13 @@ cudaError_t launch_zero_empty_tiles_scan(const InstRef& ref, const PlanBuffers& 
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const int64_t chunks = (b.tiles + 31) / 32;
-  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(chunks, (int64_t)sms * 8));
+  // four CTAs per SM, each an equal range of at most kZeroMaxRange tiles
+  const int64_t want = std::max<int64_t>((int64_t)sms * 4, (b.tiles + kZeroMaxRange - 1) / kZeroMaxRange);
+  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(b.tiles, want));
   switch (leaf) {
-    case 32: zero_scan_kernel<32><<<grid, 256, 0, s>>>(ref, b); break;
-    case 64: zero_scan_kernel<64><<<grid, 256, 0, s>>>(ref, b); break;
-    case 128: zero_scan_kernel<128><<<grid, 256, 0, s>>>(ref, b); break;
+    case 32: zero_scan_kernel<32><<<grid, kZeroThreads, 0, s>>>(ref, b); break;
+    case 64: zero_scan_kernel<64><<<grid, kZeroThreads, 0, s>>>(ref, b); break;
+    case 128: zero_scan_kernel<128><<<grid, kZeroThreads, 0, s>>>(ref, b); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaPeekAtLastError();

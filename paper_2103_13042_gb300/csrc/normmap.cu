@@ -3,37 +3,41 @@
 // GB300 design.  FP64 arithmetic runs at 1/72 of the FP32 rate on this part,
 // so every group of 32 entries is scaled by a power of two (no FP32 underflow
 // of tiny squares), squared exactly with FMA and accumulated as an unevaluated
-// FP32 pair with an explicit scale exponent; the threads of a block column are
+// FP32 pair with an explicit scale exponent; the lanes of a block column are
 // combined in that FP32 form (warp shuffles, and shared memory when a block
 // column spans several warps), and the square root is taken with an FP32
 // Newton step on the exact residual, so a block costs three FP64
 // instructions.
 //
-// Two ways of reading X, both a single pass:
-//  - TMA-staged (rows 16-byte aligned: n % 4 == 0 and X 16-byte aligned):
-//    persistent CTAs, two per SM.  A unit is one block-row strip (leaf rows)
-//    times a window of 1024 columns; the units are dealt round-robin, and the
-//    grid is the smallest that keeps the number of rounds, so every CTA takes
-//    the same number of units (no partial last wave).  One warp streams each
-//    unit's rows into a ring of three 32 KiB shared-memory stages (eight rows
-//    per stage, one bulk copy per row, completion counted in bytes on the
-//    stage's mbarrier); eight consumer warps each own 128 columns (a float4
-//    per lane) of every staged row.  Up to 96 KiB per CTA are in flight
-//    without holding registers.  Every wait is bounded; on expiry the CTA
-//    raises SPAMM_ERR_TIMEOUT, writes NaN to the norms it did not finish and
-//    lets its copies land before it exits.
-//  - streaming (any n and alignment; also the batched form): a CTA covers one
-//    block-row strip and a window of columns; each thread owns a fixed column
-//    slot (a float4 when aligned, else one float) and walks the strip's rows
-//    with streamed (evict-first) loads, eight rows of loads in flight per
-//    group.
+// One streaming pass over X, staged through shared memory by the TMA engine.
+// Persistent CTAs, two per SM.  A unit is one block-row strip (leaf rows)
+// times a window of columns; the units (of one operand, or of every operand
+// of a batch) are dealt round-robin, and the grid is the smallest that keeps
+// the number of rounds, so every CTA takes the same number of units (no
+// partial last wave).  One producer warp streams each unit's rows into a ring
+// of three shared-memory stages (one bulk copy per row, completion counted in
+// bytes on the stage's mbarrier); eight consumer warps read the staged rows
+// and accumulate, each lane one column slot over the strip's rows in groups
+// of 32 entries.  Up to ~100 KiB per CTA are in flight without holding
+// registers.  A lane owns 4 adjacent columns and takes 8 rows per group;
+// windows of 1024 columns.  A row segment's bulk copy starts at the 128-byte
+// boundary at or below its first entry (never before X) and ends at the one
+// at or above its last (never past the last 16-byte boundary inside X), so
+// every copy moves whole cache lines even when rows are not line-aligned (a
+// copy at an odd offset ran at about 60% of the line-aligned rate); the
+// producer records each row's offset into its copy, and the entries the copy
+// carries from neighbouring rows are not read.  Rows 16-byte aligned
+// (n % 4 == 0): float4 reads.  Any other n: scalar reads, each lane taking its
+// 4 columns in a lane-dependent rotation so that the warp's reads hit 32
+// different banks, and the matrix's last few entries past the last 16-byte
+// boundary inside X read from global memory directly.
+// Every wait is bounded; on expiry the CTA raises SPAMM_ERR_TIMEOUT, writes
+// NaN to the norms it did not finish and lets its copies land before it exits.
 #include "plan.cuh"
 #include "tc.cuh"
 
 namespace spamm {
 namespace {
-
-constexpr int kThreads = 256;
 
 __device__ __forceinline__ void merge_from(SumSq& a, float h, float l, int e) {
   if (e == kSumSqEmpty) {
@@ -43,155 +47,58 @@ __device__ __forceinline__ void merge_from(SumSq& a, float h, float l, int e) {
   }
 }
 
-// One CTA: block row I, column window wx of X (kThreads * VEC columns).
-template <int VEC, int LEAF>
-__device__ __forceinline__ void norm_strip(const float* __restrict__ X, int64_t n, int bd,
-                                           double* __restrict__ out, int I, int64_t wx) {
-  constexpr int kCols = kThreads * VEC;               // columns per CTA window
-  constexpr int kThreadsPerBlockCol = LEAF / VEC;     // threads sharing one output
-  constexpr int kRowsPerGroup = 32 / VEC;             // rows per 32-entry group
-  const int64_t col0 = wx * kCols + (int64_t)threadIdx.x * VEC;
-  const int64_t row0 = (int64_t)I * LEAF;
-  const int64_t row1 = (n < row0 + LEAF) ? n : row0 + LEAF;
-  const bool active = col0 < n;
-
-  SumSq ss = sumsq_empty();
-  if (active) {
-    const float* p = X + row0 * n + col0;
-    for (int64_t r = row0; r < row1; r += kRowsPerGroup) {
-      const int rows = (int)((row1 - r) < kRowsPerGroup ? (row1 - r) : kRowsPerGroup);
-      float v[32];
-#pragma unroll
-      for (int q = 0; q < kRowsPerGroup; ++q) {
-        if (q < rows) {
-          if constexpr (VEC == 4) {
-            const float4 t = __ldcs(reinterpret_cast<const float4*>(p + (int64_t)q * n));
-            v[4 * q] = t.x;
-            v[4 * q + 1] = t.y;
-            v[4 * q + 2] = t.z;
-            v[4 * q + 3] = t.w;
-          } else {
-            v[q] = __ldcs(p + (int64_t)q * n);
-          }
-        } else {
-#pragma unroll
-          for (int c = 0; c < VEC; ++c) v[VEC * q + c] = 0.0f;
-        }
-      }
-      sumsq_group<32>(ss, v);
-      p += (int64_t)kRowsPerGroup * n;
-    }
-  }
-
-  // combine the threads of a block column in the FP32-pair form
-  if constexpr (kThreadsPerBlockCol <= 32) {
-#pragma unroll
-    for (int off = kThreadsPerBlockCol / 2; off > 0; off >>= 1) {
-      const float h = __shfl_xor_sync(0xffffffffu, ss.hi, off);
-      const float l = __shfl_xor_sync(0xffffffffu, ss.lo, off);
-      const int e = __shfl_xor_sync(0xffffffffu, ss.e, off);
-      merge_from(ss, h, l, e);
-    }
-    if ((threadIdx.x % kThreadsPerBlockCol) == 0 && active)
-      out[(int64_t)I * bd + col0 / LEAF] = sumsq_sqrt(ss);
-  } else {
-    __shared__ SumSq warp_sum[kThreads / 32];
-    ss = sumsq_warp_sum(ss);
-    if ((threadIdx.x & 31) == 0) warp_sum[threadIdx.x / 32] = ss;
-    __syncthreads();
-    constexpr int kWarpsPerBlockCol = kThreadsPerBlockCol / 32;
-    if ((threadIdx.x % kThreadsPerBlockCol) == 0 && active) {
-      SumSq s = warp_sum[threadIdx.x / 32];
-#pragma unroll
-      for (int w = 1; w < kWarpsPerBlockCol; ++w) {
-        const SumSq o = warp_sum[threadIdx.x / 32 + w];
-        merge_from(s, o.hi, o.lo, o.e);
-      }
-      out[(int64_t)I * bd + col0 / LEAF] = sumsq_sqrt(s);
-    }
-  }
-}
-
-template <int VEC, int LEAF>
-__global__ void __launch_bounds__(kThreads, 4)
-    normmap_kernel(const float* __restrict__ X, int64_t n, int bd, double* __restrict__ out) {
-  norm_strip<VEC, LEAF>(X, n, bd, out, blockIdx.y, blockIdx.x);
-}
-
-// Batched form: one CTA per (job, block row, window); a job is one operand of
-// one instance, aligned (float4) or not.
-template <int LEAF>
-__global__ void __launch_bounds__(kThreads)
-    normmap_batched_kernel(const NormJob* __restrict__ jobs, int njobs) {
-  int lo = 0, hi = njobs - 1;
-  while (lo < hi) {
-    const int mid = (lo + hi + 1) / 2;
-    if (jobs[mid].cta0 <= (int)blockIdx.x) lo = mid;
-    else hi = mid - 1;
-  }
-  const NormJob jb = jobs[lo];
-  const int64_t local = (int64_t)blockIdx.x - jb.cta0;
-  const int64_t windows = (jb.n + kThreads * (jb.vec ? 4 : 1) - 1) / (kThreads * (jb.vec ? 4 : 1));
-  const int I = (int)(local / windows);
-  const int64_t wx = local % windows;
-  if (jb.vec) norm_strip<4, LEAF>(jb.X, jb.n, jb.bd, jb.out, I, wx);
-  else norm_strip<1, LEAF>(jb.X, jb.n, jb.bd, jb.out, I, wx);
-}
-
-// ---------------------------------------------------------------------------
-// TMA-staged form.
-// ---------------------------------------------------------------------------
-// Shape: CW warps across a unit window of CW * 128 columns (a float4 per
-// lane), RP 8-row parts per stage (consumer warp w takes column slice w % CW
-// and rows 8 (w / CW) .. 8 (w / CW) + 7 of every stage), STAGES ring stages,
-// CPS CTAs per SM.  The RP partial sums of a column are merged in part order
-// at the end of each unit.
-template <int CW, int RP, int STAGES, int CPS>
+// Shape of the staged kernel: ALIGNED (rows 16-byte aligned) or not, CW
+// consumer warps across a window of CW * 128 columns (4 per lane), RP parts of
+// 8 rows per stage (consumer warp w takes column slice w % CW and part w / CW
+// of every stage; the parts' sums of a column are merged in part order at the
+// end of a unit), STAGES ring stages, CPS CTAs per SM.
+template <bool ALIGNED, int CW, int RP, int STAGES, int CPS>
 struct StagedCfg {
+  static constexpr bool kAligned = ALIGNED;
   static constexpr int kColWarps = CW;
   static constexpr int kRowParts = RP;
   static constexpr int kConsumers = CW * RP;
   static constexpr int kThreads = (kConsumers + 1) * 32;     // + one producer warp
   static constexpr int kWinCols = CW * 128;
-  static constexpr int kRows = 8 * RP;                       // rows per stage
+  static constexpr int kRowsPerPart = 8;                     // one 32-entry group per lane
+  static constexpr int kRows = kRowsPerPart * RP;            // rows per stage
   static constexpr int kStages = STAGES;
   static constexpr int kCtasPerSm = CPS;
-  static constexpr uint32_t kRowBytes = kWinCols * 4;
+  // a row copy spans up to 31 extra entries on each side (128-byte lines)
+  static constexpr int kRowFloats = kWinCols + 64;
+  static constexpr uint32_t kRowBytes = kRowFloats * 4;
   static constexpr uint32_t kStageBytes = kRows * kRowBytes;
-  // partial sums of parts 1 .. RP-1, double-buffered by unit parity
+  // partial sums of the other row parts, double-buffered by unit parity
   static constexpr size_t kMergeOff = (size_t)STAGES * kStageBytes;
-  static constexpr size_t kMergeBytes = RP > 1 ? 2 * (RP - 1) * CW * 32 * sizeof(SumSq) : 0;
+  static constexpr size_t kMergeBytes = RP > 1 ? 2 * (size_t)kConsumers * 32 * sizeof(SumSq) : 0;
   static constexpr size_t kBarOff = (kMergeOff + kMergeBytes + 15) / 16 * 16;
-  static constexpr size_t kSmem = kBarOff + 2 * STAGES * sizeof(uint64_t) + 16;
+  // per stage and row: the row's first entry's offset (in floats) into its copy
+  static constexpr size_t kOffOff = kBarOff + 2 * STAGES * sizeof(uint64_t) + 16;
+  static constexpr size_t kSmem = kOffOff + (size_t)STAGES * kRows * sizeof(int);
   static_assert(kSmem * CPS <= 227 * 1024, "shared memory");
   static_assert(kRows <= 32, "one producer lane per staged row");
+  static_assert(kRowBytes % 16 == 0, "bulk-copy destinations 16-byte aligned");
 };
-// two CTAs per SM, 8 consumer warps each, 32 KiB stages (8 rows x 1024
-// columns).  Each lane then sums its column slot in the same order as the
-// streaming form (bitwise-equal norm maps).  Measured on N = 8192 (back to
-// back, per operand): 46.9 us, the same as the streaming form and within 3%
-// of the same pipeline with the arithmetic removed; 16 consumer warps with
-// two row parts (StagedCfg<8, 2, 3, 1>) took 49.2 us.
-using StagedDefault = StagedCfg<8, 1, 3, 2>;
+// Two CTAs per SM, 8 consumer warps each, three stages of ~32 KiB.  Measured on
+// N = 8192 (back to back, per operand): 46.9 us, the same as a plain float4
+// streaming kernel and within 3% of the same pipeline with the arithmetic
+// removed; 16 consumer warps with two row parts (StagedCfg<true, 8, 2, 3, 1>)
+// took 49.2 us.  For rows not 16-byte aligned a plain streaming kernel with one
+// column per thread took 74 us on N = 8191, a staged one-column-per-lane
+// mapping 64-86 us (its per-block lane merges cost as much as the sums).
+using StagedAligned = StagedCfg<true, 8, 1, 3, 2>;
+using StagedUnaligned = StagedCfg<false, 8, 1, 3, 2>;
 constexpr uint64_t kStagedWaitNs = 2000000000ull;   // 2 s: a safety net, never hit normally
 constexpr uint64_t kStagedDrainNs = 100000000ull;   // 100 ms for the abort drain
 
-// One operand of a staged launch; its units are unit0 .. unit0 + bd * nwin - 1
-// (block row I = local / nwin, window local % nwin).
-struct StagedJob {
-  const float* X;
-  double* out;
-  int64_t n;
-  int bd, nwin, unit0, pad_;
-};
 // Up to two jobs by value, or a device table (sorted by unit0).
 struct StagedJobs {
-  const StagedJob* table;
+  const NormJob* table;
   int count, units;
-  StagedJob one[2];
+  NormJob one[2];
 };
 
-__device__ __forceinline__ StagedJob job_of(const StagedJobs& J, int u) {
+__device__ __forceinline__ NormJob job_of(const StagedJobs& J, int u) {
   if (J.table == nullptr) {
     if (J.count > 1 && u >= J.one[1].unit0) return J.one[1];
     return J.one[0];
@@ -231,16 +138,39 @@ __device__ __forceinline__ bool warp_wait(uint64_t* bar, uint32_t parity, volati
   }
 }
 
+// Position of one unit: block row I, first row and column, rows in the strip
+// and the window's width in entries.
+struct UnitPos {
+  int I;
+  int64_t row0, col0;
+  int rows, width;
+};
+
+template <int LEAF, class Cfg>
+__device__ __forceinline__ UnitPos unit_pos(const NormJob& jb, int u) {
+  UnitPos p;
+  const int local = u - jb.unit0;
+  p.I = local / jb.nwin;
+  p.col0 = (int64_t)(local - p.I * jb.nwin) * Cfg::kWinCols;
+  p.row0 = (int64_t)p.I * LEAF;
+  p.rows = (int)(jb.n - p.row0 < LEAF ? jb.n - p.row0 : LEAF);
+  p.width = (int)(jb.n - p.col0 < Cfg::kWinCols ? jb.n - p.col0 : Cfg::kWinCols);
+  return p;
+}
+
 template <int LEAF, class Cfg>
 __global__ void __launch_bounds__(Cfg::kThreads, Cfg::kCtasPerSm)
     normmap_staged_kernel(const StagedJobs J, int32_t* status) {
+  constexpr bool ALIGNED = Cfg::kAligned;
   constexpr int kCW = Cfg::kColWarps, kRP = Cfg::kRowParts, kConsumers = Cfg::kConsumers;
-  constexpr int kWinCols = Cfg::kWinCols, kRows = Cfg::kRows, kStages = Cfg::kStages;
+  constexpr int kRows = Cfg::kRows, kRowsPerPart = Cfg::kRowsPerPart, kStages = Cfg::kStages;
+  constexpr int kRowFloats = Cfg::kRowFloats;
   constexpr uint32_t kRowBytes = Cfg::kRowBytes, kStageBytes = Cfg::kStageBytes;
   extern __shared__ __align__(128) uint8_t smem[];
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + Cfg::kBarOff);
   uint64_t* empty = full + kStages;
   volatile int* abort_flag = reinterpret_cast<volatile int*>(empty + kStages);
+  int* offs = reinterpret_cast<int*>(smem + Cfg::kOffOff);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
     for (int s = 0; s < kStages; ++s) {
@@ -257,26 +187,39 @@ __global__ void __launch_bounds__(Cfg::kThreads, Cfg::kCtasPerSm)
     uint32_t stage = 0, phase = 0, issued = 0, issued_phase = 0;
     bool ok = true;
     for (int u = blockIdx.x; u < J.units && ok; u += gridDim.x) {
-      const StagedJob jb = job_of(J, u);
-      const int local = u - jb.unit0;
-      const int I = local / jb.nwin;
+      const NormJob jb = job_of(J, u);
+      const UnitPos p = unit_pos<LEAF, Cfg>(jb, u);
       const int64_t n = jb.n;
-      const int64_t col0 = (int64_t)(local - I * jb.nwin) * kWinCols;
-      const int64_t row0 = (int64_t)I * LEAF;
-      const int rows = (int)(n - row0 < LEAF ? n - row0 : LEAF);
-      const uint32_t width = (uint32_t)((n - col0 < kWinCols ? n - col0 : kWinCols) * 4);
       const float* X = jb.X;
-      for (int r = 0; r < rows; r += kRows) {
-        const int rr = rows - r < kRows ? rows - r : kRows;
+      for (int r = 0; r < p.rows; r += kRows) {
+        const int rr = p.rows - r < kRows ? p.rows - r : kRows;
         if (!warp_wait(&empty[stage], phase ^ 1u, abort_flag, status)) {
           ok = false;
           break;
         }
-        if (lane == 0) tc::mbar_arrive_expect_tx(&full[stage], (uint32_t)rr * width);
+        // lane q < rr copies row row0 + r + q: whole 128-byte lines, clipped
+        // to X's first byte and to its last 16-byte boundary
+        const uintptr_t xb = reinterpret_cast<uintptr_t>(X);
+        const uintptr_t xend = xb + (uintptr_t)(((n * n) & ~(int64_t)3) * 4);
+        uintptr_t a0 = 0, a1 = 0;
+        if (lane < rr) {
+          const uintptr_t b0 = xb + (uintptr_t)(((p.row0 + r + lane) * n + p.col0) * 4);
+          const uintptr_t b1 = b0 + (uintptr_t)p.width * 4u;
+          a0 = b0 & ~(uintptr_t)127;
+          if (a0 < xb) a0 = xb;
+          a1 = (b1 + 127) & ~(uintptr_t)127;
+          if (a1 > xend) a1 = xend;
+          if (a1 < a0) a1 = a0;
+          offs[stage * kRows + lane] = (int)((b0 - a0) >> 2);
+        }
+        const uint32_t bytes = (uint32_t)(a1 - a0);
+        const uint32_t total = __reduce_add_sync(0xffffffffu, bytes);
+        __syncwarp();   // the offsets are written before lane 0's arrive releases them
+        if (lane == 0) tc::mbar_arrive_expect_tx(&full[stage], total);
         __syncwarp();
-        if (lane < rr)
+        if (bytes)
           tc::bulk_g2s(smem + (size_t)stage * kStageBytes + (size_t)lane * kRowBytes,
-                       X + (row0 + r + lane) * n + col0, width, &full[stage]);
+                       reinterpret_cast<const void*>(a0), bytes, &full[stage]);
         issued |= 1u << stage;
         issued_phase = (issued_phase & ~(1u << stage)) | (phase << stage);
         if (++stage == kStages) {
@@ -294,52 +237,107 @@ __global__ void __launch_bounds__(Cfg::kThreads, Cfg::kCtasPerSm)
   }
 
   // -------------------------------------------------------------- consumers
-  constexpr int kLanesPerBlockCol = LEAF / 4;
+  constexpr int kLanesPerBlockCol = LEAF / 4;   // <= 32: a block column is inside a warp
   const int cslice = warp % kCW, part = warp / kCW;
-  const int cw = cslice * 128 + lane * 4;   // this lane's first column inside a window
+  const int cw = (cslice * 32 + lane) * 4;   // this lane's first column inside a window
+  // unaligned rows: this lane reads its 4 columns in the order c0, c1, c2, c3
+  // (rotated by lane / 8), so every scalar read of the warp hits 32 banks
+  const int l8 = lane >> 3;
+  const int c0 = l8 & 3, c1 = (l8 + 1) & 3, c2 = (l8 + 2) & 3, c3 = (l8 + 3) & 3;
   SumSq* merge = reinterpret_cast<SumSq*>(smem + Cfg::kMergeOff);
   uint32_t stage = 0, phase = 0, parity = 0;
   bool ok = true;
   for (int u = blockIdx.x; u < J.units; u += gridDim.x, parity ^= 1u) {
-    const StagedJob jb = job_of(J, u);
-    const int local = u - jb.unit0;
-    const int I = local / jb.nwin;
+    const NormJob jb = job_of(J, u);
+    const UnitPos p = unit_pos<LEAF, Cfg>(jb, u);
     const int64_t n = jb.n;
-    const int64_t col0 = (int64_t)(local - I * jb.nwin) * kWinCols;
-    const int64_t row0 = (int64_t)I * LEAF;
-    const int rows = (int)(n - row0 < LEAF ? n - row0 : LEAF);
-    const bool active = col0 + cw < n;
+    const bool active = p.col0 + cw < n;
     SumSq ss = sumsq_empty();
-    for (int r = 0; r < rows && ok; r += kRows) {
-      const int rr = rows - r < kRows ? rows - r : kRows;
-      const int mine = rr - 8 * part;   // rows of this stage in this warp's part
+    for (int r = 0; r < p.rows && ok; r += kRows) {
+      const int rr = p.rows - r < kRows ? p.rows - r : kRows;
+      const int mine = rr - kRowsPerPart * part;   // rows of this stage in this warp's part
       if (!warp_wait(&full[stage], phase, abort_flag, status)) {
         ok = false;
         break;
       }
       float v[32];
-      const float* src =
-          reinterpret_cast<const float*>(smem + (size_t)stage * kStageBytes) + 8 * part * kWinCols + cw;
-      if (mine >= 8 && active) {
+      const float* src = reinterpret_cast<const float*>(smem + (size_t)stage * kStageBytes) +
+                         kRowsPerPart * part * kRowFloats + cw;
+      const int* so = offs + stage * kRows + kRowsPerPart * part;   // the rows' offsets
+      if constexpr (ALIGNED) {
+        // rows 16-byte aligned: the offsets are multiples of 4 floats (zero
+        // when every row starts on a line)
+        if (mine >= kRowsPerPart && active && jb.lines) {
 #pragma unroll
-        for (int q = 0; q < 8; ++q) {
-          const float4 t = *reinterpret_cast<const float4*>(src + q * kWinCols);
-          v[4 * q] = t.x;
-          v[4 * q + 1] = t.y;
-          v[4 * q + 2] = t.z;
-          v[4 * q + 3] = t.w;
-        }
-      } else {
-#pragma unroll
-        for (int q = 0; q < 8; ++q) {
-          if (q < mine && active) {
-            const float4 t = *reinterpret_cast<const float4*>(src + q * kWinCols);
+          for (int q = 0; q < 8; ++q) {
+            const float4 t = *reinterpret_cast<const float4*>(src + q * kRowFloats);
             v[4 * q] = t.x;
             v[4 * q + 1] = t.y;
             v[4 * q + 2] = t.z;
             v[4 * q + 3] = t.w;
-          } else {
-            v[4 * q] = v[4 * q + 1] = v[4 * q + 2] = v[4 * q + 3] = 0.0f;
+          }
+        } else if (mine >= kRowsPerPart && active) {
+#pragma unroll
+          for (int q = 0; q < 8; ++q) {
+            const float4 t = *reinterpret_cast<const float4*>(src + q * kRowFloats + so[q]);
+            v[4 * q] = t.x;
+            v[4 * q + 1] = t.y;
+            v[4 * q + 2] = t.z;
+            v[4 * q + 3] = t.w;
+          }
+        } else {
+#pragma unroll
+          for (int q = 0; q < 8; ++q) {
+            if (q < mine && active) {
+              const float4 t = *reinterpret_cast<const float4*>(src + q * kRowFloats + so[q]);
+              v[4 * q] = t.x;
+              v[4 * q + 1] = t.y;
+              v[4 * q + 2] = t.z;
+              v[4 * q + 3] = t.w;
+            } else {
+              v[4 * q] = v[4 * q + 1] = v[4 * q + 2] = v[4 * q + 3] = 0.0f;
+            }
+          }
+        }
+      } else {
+        const int64_t row_first = p.row0 + r + kRowsPerPart * part;
+        const int64_t lim = (n * n) & ~(int64_t)3;   // entries past it: read from global
+        const bool tail = p.row0 + r + rr == n && (n - 1) * n + p.col0 + p.width > lim;
+        // columns of this lane inside the matrix (4 except at its right edge)
+        const int64_t left = n - (p.col0 + cw);
+        const int nv = left >= 4 ? 4 : (left > 0 ? (int)left : 0);
+        if (mine >= kRowsPerPart && nv == 4 && !tail) {
+#pragma unroll
+          for (int q = 0; q < 8; ++q) {
+            const float* rp = src + q * kRowFloats + so[q];
+            v[4 * q] = rp[c0];
+            v[4 * q + 1] = rp[c1];
+            v[4 * q + 2] = rp[c2];
+            v[4 * q + 3] = rp[c3];
+          }
+        } else if (!tail) {   // a partial stage or the lane at the right edge: masked reads
+#pragma unroll
+          for (int q = 0; q < 8; ++q) {
+            const float* rp = src + q * kRowFloats + (q < mine ? so[q] : 0);
+            v[4 * q] = (q < mine && c0 < nv) ? rp[c0] : 0.0f;
+            v[4 * q + 1] = (q < mine && c1 < nv) ? rp[c1] : 0.0f;
+            v[4 * q + 2] = (q < mine && c2 < nv) ? rp[c2] : 0.0f;
+            v[4 * q + 3] = (q < mine && c3 < nv) ? rp[c3] : 0.0f;
+          }
+        } else {   // the matrix's last stage: its last entries come from global memory
+#pragma unroll
+          for (int q = 0; q < 8; ++q) {
+            const float* rp = src + q * kRowFloats + (q < mine ? so[q] : 0);
+#pragma unroll
+            for (int jj = 0; jj < 4; ++jj) {
+              const int c = (l8 + jj) & 3;
+              float x = 0.0f;
+              if (q < mine && c < nv) {
+                const int64_t e = (row_first + q) * n + p.col0 + cw + c;
+                x = e < lim ? rp[c] : __ldg(jb.X + e);
+              }
+              v[4 * q + jj] = x;
+            }
           }
         }
       }
@@ -351,18 +349,7 @@ __global__ void __launch_bounds__(Cfg::kThreads, Cfg::kCtasPerSm)
       }
       if (mine > 0) sumsq_group<32>(ss, v);
     }
-    if constexpr (kRP > 1) {
-      // parts 1 .. RP-1 hand their partial sums to part 0 (merged in part order)
-      SumSq* mb = merge + (size_t)parity * (kRP - 1) * kCW * 32;
-      if (part > 0) mb[((part - 1) * kCW + cslice) * 32 + lane] = ss;
-      asm volatile("bar.sync 1, %0;" ::"r"(kConsumers * 32) : "memory");
-      if (part > 0) continue;
-#pragma unroll
-      for (int p = 1; p < kRP; ++p) {
-        const SumSq o = mb[((p - 1) * kCW + cslice) * 32 + lane];
-        merge_from(ss, o.hi, o.lo, o.e);
-      }
-    }
+    // the lanes of a block column (inside this warp)
 #pragma unroll
     for (int off = kLanesPerBlockCol / 2; off > 0; off >>= 1) {
       const float h = __shfl_xor_sync(0xffffffffu, ss.hi, off);
@@ -370,8 +357,20 @@ __global__ void __launch_bounds__(Cfg::kThreads, Cfg::kCtasPerSm)
       const int e = __shfl_xor_sync(0xffffffffu, ss.e, off);
       merge_from(ss, h, l, e);
     }
+    if constexpr (kRP > 1) {
+      // the other row parts hand their sums to part 0 (merged in part order)
+      SumSq* mb = merge + (size_t)parity * kConsumers * 32;
+      mb[warp * 32 + lane] = ss;
+      asm volatile("bar.sync 1, %0;" ::"r"(kConsumers * 32) : "memory");
+      if (part > 0) continue;
+#pragma unroll
+      for (int pp = 1; pp < kRP; ++pp) {
+        const SumSq o = mb[(pp * kCW + cslice) * 32 + lane];
+        merge_from(ss, o.hi, o.lo, o.e);
+      }
+    }
     if ((lane % kLanesPerBlockCol) == 0 && active)
-      jb.out[(int64_t)I * jb.bd + (col0 + cw) / LEAF] =
+      jb.out[(int64_t)p.I * jb.bd + (p.col0 + cw) / LEAF] =
           (ok && !*abort_flag) ? sumsq_sqrt(ss) : __longlong_as_double(0x7ff8000000000000ll);
   }
 }
@@ -402,7 +401,7 @@ cudaError_t staged_capacity(int* cap) {
 
 // The units are dealt round-robin; the grid is the smallest that keeps the
 // number of rounds, so every CTA takes `rounds` or `rounds - 1` units.
-template <int LEAF, class Cfg = StagedDefault>
+template <int LEAF, class Cfg>
 cudaError_t launch_staged_jobs(const StagedJobs& J, int32_t* status, cudaStream_t s) {
   if (J.units <= 0) return cudaSuccess;
   int cap = 0;
@@ -414,73 +413,60 @@ cudaError_t launch_staged_jobs(const StagedJobs& J, int32_t* status, cudaStream_
   return cudaPeekAtLastError();
 }
 
-template <class Cfg = StagedDefault>
-StagedJob staged_job(const float* X, int64_t n, int leaf, double* out, int unit0) {
-  StagedJob j{};
-  j.X = X;
-  j.out = out;
-  j.n = n;
-  j.bd = (int)num_blocks(n, leaf);
-  j.nwin = (int)((n + Cfg::kWinCols - 1) / Cfg::kWinCols);
-  j.unit0 = unit0;
-  return j;
-}
-
-template <int LEAF, class Cfg = StagedDefault>
-cudaError_t launch_staged(const float* X, int64_t n, double* out, int32_t* status,
-                          cudaStream_t s) {
-  StagedJobs J{};
-  J.count = 1;
-  J.one[0] = staged_job<Cfg>(X, n, LEAF, out, 0);
-  J.units = J.one[0].bd * J.one[0].nwin;
-  return launch_staged_jobs<LEAF, Cfg>(J, status, s);
-}
-
-template <int VEC, int LEAF>
-cudaError_t launch(const float* X, int64_t n, int bd, double* out, cudaStream_t s) {
-  constexpr int kCols = kThreads * VEC;
-  dim3 grid((unsigned)((n + kCols - 1) / kCols), (unsigned)bd);
-  normmap_kernel<VEC, LEAF><<<grid, kThreads, 0, s>>>(X, n, bd, out);
-  return cudaPeekAtLastError();
+template <class Cfg>
+cudaError_t launch_leaf(int leaf, const StagedJobs& J, int32_t* status, cudaStream_t s) {
+  switch (leaf) {
+    case 32: return launch_staged_jobs<32, Cfg>(J, status, s);
+    case 64: return launch_staged_jobs<64, Cfg>(J, status, s);
+    case 128: return launch_staged_jobs<128, Cfg>(J, status, s);
+    default: return cudaErrorInvalidValue;
+  }
 }
 
 }  // namespace
 
-cudaError_t launch_normmap(const float* X, int64_t n, int32_t leaf, double* out,
-                           int32_t* status, cudaStream_t s) {
-  const int bd = (int)num_blocks(n, leaf);
-  const bool vec = (n % 4) == 0 && (reinterpret_cast<uintptr_t>(X) % 16) == 0;
-  if (vec) {
-    switch (leaf) {
-      case 32: return launch_staged<32>(X, n, out, status, s);
-      case 64: return launch_staged<64>(X, n, out, status, s);
-      case 128: return launch_staged<128>(X, n, out, status, s);
-      default: return cudaErrorInvalidValue;
-    }
-  }
-  switch (leaf) {
-    case 32: return launch<1, 32>(X, n, bd, out, s);
-    case 64: return launch<1, 64>(X, n, bd, out, s);
-    case 128: return launch<1, 128>(X, n, bd, out, s);
-    default: return cudaErrorInvalidValue;
-  }
+int normjob_shape(NormJob& j, int leaf) {
+  j.bd = (int)num_blocks(j.n, leaf);
+  j.lines = (j.n % 32) == 0 && (reinterpret_cast<uintptr_t>(j.X) % 128) == 0 ? 1 : 0;
+  const int win = j.vec ? StagedAligned::kWinCols : StagedUnaligned::kWinCols;
+  j.nwin = (int)((j.n + win - 1) / win);
+  return j.bd * j.nwin;
 }
 
-int normjob_ctas(const NormJob& j) {
-  const int64_t cols = kThreads * (j.vec ? 4 : 1);
-  return (int)(((j.n + cols - 1) / cols) * j.bd);
+cudaError_t launch_normmap(const float* X, int64_t n, int32_t leaf, double* out, int32_t* status,
+                           cudaStream_t s) {
+  if (reinterpret_cast<uintptr_t>(X) % 16) return cudaErrorMisalignedAddress;   // bulk copies
+  StagedJobs J{};
+  J.count = 1;
+  NormJob& j = J.one[0];
+  j.X = X;
+  j.out = out;
+  j.n = n;
+  j.vec = (n % 4) == 0;
+  j.unit0 = 0;
+  J.units = normjob_shape(j, leaf);
+  return j.vec ? launch_leaf<StagedAligned>(leaf, J, status, s)
+               : launch_leaf<StagedUnaligned>(leaf, J, status, s);
 }
 
-cudaError_t launch_normmap_jobs(const NormJob* dev_jobs, int njobs, int total_ctas, int leaf,
-                                cudaStream_t s) {
-  if (total_ctas <= 0) return cudaSuccess;
-  switch (leaf) {
-    case 32: normmap_batched_kernel<32><<<total_ctas, kThreads, 0, s>>>(dev_jobs, njobs); break;
-    case 64: normmap_batched_kernel<64><<<total_ctas, kThreads, 0, s>>>(dev_jobs, njobs); break;
-    case 128: normmap_batched_kernel<128><<<total_ctas, kThreads, 0, s>>>(dev_jobs, njobs); break;
-    default: return cudaErrorInvalidValue;
+cudaError_t launch_normmap_jobs(const NormJob* dev_jobs, int n_vec, int units_vec, int n_other,
+                                int units_other, int leaf, int32_t* status, cudaStream_t s) {
+  cudaError_t e = cudaSuccess;
+  if (n_vec > 0) {
+    StagedJobs J{};
+    J.table = dev_jobs;
+    J.count = n_vec;
+    J.units = units_vec;
+    e = launch_leaf<StagedAligned>(leaf, J, status, s);
   }
-  return cudaPeekAtLastError();
+  if (e == cudaSuccess && n_other > 0) {
+    StagedJobs J{};
+    J.table = dev_jobs + n_vec;
+    J.count = n_other;
+    J.units = units_other;
+    e = launch_leaf<StagedUnaligned>(leaf, J, status, s);
+  }
+  return e;
 }
 
 }  // namespace spamm

@@ -190,19 +190,23 @@ cudaError_t run_histogram(const InstRef& ref, const PlanBuffers& b, cudaStream_t
 cudaError_t launch_normmap(const float* X, int64_t n, int32_t leaf, double* out, int32_t* status,
                            cudaStream_t s);
 
-// Batched norm maps: one job per operand of an instance.
+// Norm-map jobs (one per operand of an instance) of the staged norm-map
+// kernel.  X must be 16-byte aligned.  A job table lists the jobs whose rows
+// are 16-byte aligned (vec: n % 4 == 0) first, then the others; unit0 counts
+// the kernel's units (block rows x column windows) from the start of the
+// job's part of the table.
 struct NormJob {
   const float* X;
   double* out;
   int64_t n;
-  int bd;
-  int vec;    // n % 4 == 0 and X 16-byte aligned: float4 loads
-  int cta0;   // first CTA of the job
+  int bd, nwin, unit0, vec;
+  int lines;   // every row starts on a 128-byte line (X 128-byte aligned, n % 32 == 0)
   int pad_;
 };
-int normjob_ctas(const NormJob& j);
-cudaError_t launch_normmap_jobs(const NormJob* dev_jobs, int njobs, int total_ctas, int leaf,
-                                cudaStream_t s);
+// Sets bd, nwin and lines from X, n, vec and the leaf; returns the job's units.
+int normjob_shape(NormJob& j, int leaf);
+cudaError_t launch_normmap_jobs(const NormJob* dev_jobs, int n_vec, int units_vec, int n_other,
+                                int units_other, int leaf, int32_t* status, cudaStream_t s);
 
 cudaError_t launch_multiply_simt(const InstRef& ref, const PlanBuffers& b, int leaf,
                                  int schedule, cudaStream_t s);
