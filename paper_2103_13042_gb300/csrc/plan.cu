@@ -986,7 +986,7 @@ cudaError_t launch_count(const InstRef& ref, const PlanBuffers& b, cudaStream_t 
   const size_t smem = (size_t)(kGroupRows + kTilesPerCta / kGroupRows) * b.max_bd * sizeof(Screen);
   auto* kern = ref.any_band ? (ref.any_split ? count_kernel<true, true> : count_kernel<false, true>)
                             : (ref.any_split ? count_kernel<true, false> : count_kernel<false, false>);
-  if (smem > 48 * 1024) {
+  {   // opt in to the largest size once per device and variant (static shared memory counts too)
     static bool opted[64][4] = {};
     const int v = (ref.any_band ? 2 : 0) + (ref.any_split ? 1 : 0);
     int dev = 0;

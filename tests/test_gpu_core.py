@@ -121,6 +121,26 @@ def test_plan_exact_on_oracle_norms(n, leaf, family):
         assert math.isclose(st["norm_a"], OT.frobenius_from_normmap(nA), rel_tol=1e-14)
 
 
+@pytest.mark.parametrize("n,leaf,prec", [(16384, 32, P.FP32), (31000, 64, P.BF16_SPLIT)])
+def test_plan_large_grid_counts(n, leaf, prec):
+    """bd = 512 / 485: the pair-test kernel stages 12 * bd screens of shared memory, which with
+    its static shared memory passes the default 48 KB limit; survivors per tile against numpy
+    on the same maps."""
+    bd = P.num_blocks(n, leaf)
+    rng = np.random.default_rng(500)
+    nA = rng.lognormal(0.0, 2.0, size=(bd, bd))
+    nB = rng.lognormal(0.0, 2.0, size=(bd, bd))
+    tau = float(np.exp(3.0))
+    plan = P.Plan(n, leaf, prec).plan(dev(nA), dev(nB), tau, 1e-5)
+    tp, kk = plan.export()
+    got = np.diff(tp.astype(np.int64)).reshape(bd, bd)
+    ref = np.empty((bd, bd), dtype=np.int64)
+    for i in range(bd):
+        ref[i] = (nA[i, :, None] * nB >= tau).sum(axis=0)   # sum over k of the tile (i, j)
+    assert np.array_equal(got, ref)
+    assert plan.stats()["survivors"] == int(ref.sum())
+
+
 def test_plan_hand_ties_scaled():
     """Hand skip sets of tests/golden/hand_tiny.json at leaf 32: norms are 2^(E+5) exactly."""
     import json, os
