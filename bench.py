@@ -637,7 +637,9 @@ def run_batch(args, rank, world):
         "e2e": {"value": dense / (e2e_ms * 1e-3) / 1e12 * world,
                 "unit": "TFLOP/s (dense-equivalent, sum of 2N^3 / t)", "ms_per_step": e2e_ms,
                 "h2d_bytes_per_step": int(2 * 4 * sum_n2), "d2h_bytes_per_step": int(4 * sum_n2)},
-        "gpu_launches": 8 * args.steps,
+        # norm maps (one launch for the operands with 16-byte aligned rows, one for
+        # the others), 4 plan kernels, zero-fill, rounding, multiply
+        "gpu_launches": (len({int(m[0].shape[0]) % 4 == 0 for m in mats}) + 4 + 1 + 2) * args.steps,
         "roofline": roof,
         "clocks": clk.summary(),
     }
@@ -802,6 +804,8 @@ def run_sparse(args, rank, world):
                    "parallelism": f"replicas x{world}", "launch": "cuda-graph replay"},
         "breakdown_ms": part_ms,
         "baselines_same_gpu": base,
+        # one norm-map launch (both operands alike), 4 plan kernels, zero-fill,
+        # rounding, multiply
         "gpu_launches": 8 * args.steps,
         "roofline": {"kernel": "multiply phase (tcgen05 multiply; rounding excluded)",
                      "bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
