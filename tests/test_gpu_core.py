@@ -81,6 +81,26 @@ def test_normmap_wide_dynamic_range(leaf):
     assert rel.max() <= NORM_REL_TOL, rel.max()
 
 
+@pytest.mark.parametrize("n,leaf,shift", [(1, 32, 0), (2, 32, 4), (3, 32, 12), (5, 32, 28),
+                                           (7, 64, 4), (33, 32, 20), (130, 128, 4), (131, 128, 8),
+                                           (1001, 64, 12), (1027, 64, 28), (2049, 128, 4),
+                                           (1024, 32, 4), (1028, 64, 8)])
+def test_normmap_offset_views(n, leaf, shift):
+    """X 16-byte aligned but not on a 128-byte line (a view `shift` floats into a buffer), tiny
+    and ragged n: the staged copies are clipped to X's first byte and last 16-byte boundary."""
+    a, _ = _pair("normal", n, 900 + n)
+    buf = torch.full((n * n + 64,), float("nan"), dtype=torch.float32, device="cuda")
+    X = buf[shift:shift + n * n].view(n, n)
+    X.copy_(torch.from_numpy(a).cuda())
+    assert X.data_ptr() % 16 == 0
+    got = host(P.spamm_normmap(X, leaf))
+    ref = S.normmap(a, leaf)
+    zero = ref == 0
+    assert np.array_equal(got[zero], ref[zero])
+    assert np.max(np.abs(got[~zero] - ref[~zero]) / ref[~zero], initial=0.0) <= NORM_REL_TOL
+    assert P.spamm_last_device_status() == 0
+
+
 def test_normmap_c2_full_size():
     a, _ = synth.workload_c2()
     got = host(P.spamm_normmap(dev(a), 64))
