@@ -203,93 +203,6 @@ __device__ __forceinline__ void sumsq_group(SumSq& acc, const float (&v)[N]) {
   sumsq_merge(acc, hi, lo, g);
 }
 
-// ---------------------------------------------------------------------------
-// Packed FP32x2 arithmetic (two IEEE round-to-nearest lanes per instruction).
-// ---------------------------------------------------------------------------
-typedef unsigned long long f32x2_t;
-
-__device__ __forceinline__ f32x2_t f2_fma(f32x2_t a, f32x2_t b, f32x2_t c) {
-  f32x2_t d;
-  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
-  return d;
-}
-// add, sub and mul as packed FMAs: rn(a * 1 + b) = rn(a + b), rn(b * -1 + a) =
-// rn(a - b), rn(a * b + 0) = rn(a * b) (up to the sign of an exact zero).
-constexpr f32x2_t kF2One = 0x3f8000003f800000ull;
-constexpr f32x2_t kF2MinusOne = 0xbf800000bf800000ull;
-__device__ __forceinline__ f32x2_t f2_add(f32x2_t a, f32x2_t b) { return f2_fma(a, kF2One, b); }
-__device__ __forceinline__ f32x2_t f2_sub(f32x2_t a, f32x2_t b) {
-  return f2_fma(b, kF2MinusOne, a);
-}
-__device__ __forceinline__ f32x2_t f2_mul(f32x2_t a, f32x2_t b) { return f2_fma(a, b, 0ull); }
-__device__ __forceinline__ float f2_x(f32x2_t a) { return __uint_as_float((uint32_t)a); }
-__device__ __forceinline__ float f2_y(f32x2_t a) { return __uint_as_float((uint32_t)(a >> 32)); }
-__device__ __forceinline__ f32x2_t f2_make(float x, float y) {
-  return (f32x2_t)__float_as_uint(x) | ((f32x2_t)__float_as_uint(y) << 32);
-}
-
-// sumsq_group on NP packed pairs: two independent renormalised FP32-pair
-// accumulators (one per lane of the pair), joined at the end of the group.
-// Per pair: scale, exact square (p = y*y, -e = fma(-y, y, p)), TwoSum, pair
-// update and renormalisation, 15 packed instructions.
-template <int NP>
-__device__ __forceinline__ void sumsq_group2(SumSq& acc, const f32x2_t (&v)[NP]) {
-  float mx = 0.0f;
-#pragma unroll
-  for (int q = 0; q < NP; ++q) mx = fmaxf(mx, fmaxf(fabsf(f2_x(v[q])), fabsf(f2_y(v[q]))));
-  if (mx == 0.0f) {
-    bool nan = false;
-#pragma unroll
-    for (int q = 0; q < NP; ++q) nan |= (f2_x(v[q]) != f2_x(v[q])) | (f2_y(v[q]) != f2_y(v[q]));
-    if (nan) {
-      acc.hi = __int_as_float(0x7fffffff);
-      acc.e = 0;
-    }
-    return;
-  }
-  const int g = group_exponent(mx);
-  const float sc = pow2f(-g);
-  const f32x2_t sc2 = f2_make(sc, sc), zero2 = 0ull;
-  f32x2_t hi = 0ull, lo = 0ull;
-#pragma unroll
-  for (int q = 0; q < NP; ++q) {
-    const f32x2_t y = f2_mul(v[q], sc2);
-    const f32x2_t ny = f2_sub(zero2, y);
-    const f32x2_t p = f2_mul(y, y);
-    const f32x2_t en = f2_fma(ny, y, p);          // p - y*y, exactly
-    const f32x2_t s = f2_add(hi, p);
-    const f32x2_t z = f2_sub(s, hi);
-    const f32x2_t err = f2_add(f2_sub(hi, f2_sub(s, z)), f2_sub(p, z));
-    const f32x2_t t = f2_add(lo, f2_sub(err, en));
-    const f32x2_t h2 = f2_add(s, t);
-    lo = f2_sub(t, f2_sub(h2, s));
-    hi = h2;
-  }
-  float sh, se;
-  two_sum(f2_x(hi), f2_y(hi), sh, se);
-  const float t = __fadd_rn(__fadd_rn(f2_x(lo), f2_y(lo)), se);
-  const float H = __fadd_rn(sh, t);
-  const float L = __fsub_rn(t, __fsub_rn(H, sh));
-  sumsq_merge(acc, H, L, g);
-}
-
-// Warp-wide sum of the lanes' accumulators in the FP32-pair domain (no FP64);
-// every lane ends with the total.
-__device__ __forceinline__ SumSq sumsq_warp_sum(SumSq a) {
-#pragma unroll
-  for (int off = 16; off > 0; off >>= 1) {
-    const float h = __shfl_xor_sync(0xffffffffu, a.hi, off);
-    const float l = __shfl_xor_sync(0xffffffffu, a.lo, off);
-    const int e = __shfl_xor_sync(0xffffffffu, a.e, off);
-    if (e == kSumSqEmpty) {
-      if (h != h) a.hi = h;   // NaN from an otherwise empty lane
-    } else {
-      sumsq_merge(a, h, l, e);
-    }
-  }
-  return a;
-}
-
 // sqrt of the accumulated value, returned in FP64, with FP32 arithmetic and
 // three FP64 instructions (the FP64 pipe is narrow on this part).  With
 // S = (hi + lo) 4^e: r0 = sqrtf(hi); one Newton step on the exact residual
