@@ -400,13 +400,13 @@ spamm_status_t spamm_mlp_train(float* weights, float* m, float* v, int32_t t0, c
 const char* spamm_status_string(spamm_status_t status);
 spamm_status_t spamm_last_device_status(void* stream, int32_t* code);
 
-/* spamm_selftest_bounded_wait: runs the tensor-core multiply's bounded wait
- *   routine on an mbarrier phase that nothing completes, with the given limit
- *   (1 us .. 1 s).  The wait gives up, raises its abort flag and latches
- *   SPAMM_ERR_TIMEOUT in the device status word (read it with
- *   spamm_last_device_status); returns SPAMM_OK when all of that happened,
- *   *elapsed_ns (may be NULL) = the time the wait took.  Blocks.  No part of
- *   the GPU is left waiting. */
+/* spamm_selftest_bounded_wait: runs the bounded wait routines of the
+ *   tensor-core multiply (one thread) and of the norm map (a whole warp) on an
+ *   mbarrier phase that nothing completes, with the given limit (1 us .. 1 s).
+ *   Each wait gives up, raises its abort flag and latches SPAMM_ERR_TIMEOUT in
+ *   the device status word (read it with spamm_last_device_status); returns
+ *   SPAMM_OK when all of that happened for both, *elapsed_ns (may be NULL) =
+ *   the shorter of the two waits.  Blocks.  No part of the GPU is left waiting. */
 spamm_status_t spamm_selftest_bounded_wait(int64_t limit_ns, int64_t* elapsed_ns, void* stream);
 
 #ifdef __cplusplus

@@ -698,12 +698,14 @@ spamm_status_t spamm_selftest_bounded_wait(int64_t limit_ns, int64_t* elapsed_ns
   if (!status) return SPAMM_ERR_NO_MEMORY;
   const cudaStream_t s = (cudaStream_t)stream;
   long long* out = nullptr;
-  if (cudaMalloc(&out, 3 * sizeof(long long)) != cudaSuccess) {
+  if (cudaMalloc(&out, 6 * sizeof(long long)) != cudaSuccess) {
     (void)cudaGetLastError();
     return SPAMM_ERR_NO_MEMORY;
   }
-  long long h[3] = {0, 0, 0};
+  long long h[6] = {0, 0, 0, 0, 0, 0};
+  // the multiply's wait (one thread) and the norm map's warp-wide wait
   cudaError_t err = launch_wait_selftest(status, (uint64_t)limit_ns, out, s);
+  if (err == cudaSuccess) err = launch_normmap_wait_selftest(status, (uint64_t)limit_ns, out + 3, s);
   if (err == cudaSuccess) err = cudaMemcpyAsync(h, out, sizeof(h), cudaMemcpyDeviceToHost, s);
   if (err == cudaSuccess) err = cudaStreamSynchronize(s);
   cudaFree(out);
@@ -711,9 +713,9 @@ spamm_status_t spamm_selftest_bounded_wait(int64_t limit_ns, int64_t* elapsed_ns
     (void)cudaGetLastError();
     return SPAMM_ERR_CUDA;
   }
-  if (elapsed_ns) *elapsed_ns = h[2];
-  // the wait must have given up and raised the abort flag
-  return (h[0] == 1 && h[1] == 1) ? SPAMM_OK : SPAMM_ERR_DEVICE_FAULT;
+  if (elapsed_ns) *elapsed_ns = h[2] < h[5] ? h[2] : h[5];
+  // both waits must have given up and raised their abort flags
+  return (h[0] == 1 && h[1] == 1 && h[3] == 1 && h[4] == 1) ? SPAMM_OK : SPAMM_ERR_DEVICE_FAULT;
 }
 
 spamm_status_t spamm_last_device_status(void* stream, int32_t* code) {

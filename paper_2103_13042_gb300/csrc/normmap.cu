@@ -115,7 +115,7 @@ __device__ __forceinline__ NormJob job_of(const StagedJobs& J, int u) {
 // Bounded wait of a whole warp: returns (uniformly) once every lane has seen
 // the phase complete, or false when the limit passed or the abort flag is up.
 __device__ __forceinline__ bool warp_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag,
-                                          int32_t* status) {
+                                          int32_t* status, uint64_t limit_ns = kStagedWaitNs) {
   bool done = tc::mbar_try_wait(bar, parity);
   if (__all_sync(0xffffffffu, done)) return true;
   const uint64_t t0 = tc::globaltimer_ns();
@@ -127,7 +127,7 @@ __device__ __forceinline__ bool warp_wait(uint64_t* bar, uint32_t parity, volati
       if ((threadIdx.x & 31) == 0) {
         if (*abort_flag) {
           give_up = 1;
-        } else if (tc::globaltimer_ns() - t0 > kStagedWaitNs) {
+        } else if (tc::globaltimer_ns() - t0 > limit_ns) {
           *abort_flag = 1;
           if (status) atomicExch(status, (int32_t)SPAMM_ERR_TIMEOUT);
           give_up = 1;
@@ -423,7 +423,35 @@ cudaError_t launch_leaf(int leaf, const StagedJobs& J, int32_t* status, cudaStre
   }
 }
 
+// Self-test of the norm map's warp-wide bounded wait: one warp waits, with a
+// short limit, on an mbarrier phase that nothing completes.  out[0] = 1 if the
+// wait returned false, out[1] = the abort flag, out[2] = elapsed nanoseconds.
+__global__ void normmap_wait_selftest_kernel(int32_t* status, uint64_t limit_ns, long long* out) {
+  __shared__ __align__(8) uint64_t bar;
+  __shared__ int abort_flag;
+  if (threadIdx.x == 0) {
+    tc::mbar_init(&bar, 1);   // phase 0 completes only on an arrival, which never comes
+    abort_flag = 0;
+    tc::fence_mbarrier_init();
+  }
+  __syncwarp();
+  const uint64_t t0 = tc::globaltimer_ns();
+  const bool ok = warp_wait(&bar, 0u, &abort_flag, status, limit_ns);
+  const uint64_t t1 = tc::globaltimer_ns();
+  if (threadIdx.x == 0) {
+    out[0] = ok ? 0 : 1;
+    out[1] = abort_flag;
+    out[2] = (long long)(t1 - t0);
+  }
+}
+
 }  // namespace
+
+cudaError_t launch_normmap_wait_selftest(int32_t* status, uint64_t limit_ns, long long* out,
+                                         cudaStream_t s) {
+  normmap_wait_selftest_kernel<<<1, 32, 0, s>>>(status, limit_ns, out);
+  return cudaPeekAtLastError();
+}
 
 int normjob_shape(NormJob& j, int leaf) {
   j.bd = (int)num_blocks(j.n, leaf);

@@ -203,6 +203,9 @@ struct NormJob {
   int lines;   // every row starts on a 128-byte line (X 128-byte aligned, n % 32 == 0)
   int pad_;
 };
+// Self-test of the norm map's bounded wait (a phase nothing completes).
+cudaError_t launch_normmap_wait_selftest(int32_t* status, uint64_t limit_ns, long long* out,
+                                         cudaStream_t s);
 // Sets bd, nwin and lines from X, n, vec and the leaf; returns the job's units.
 int normjob_shape(NormJob& j, int leaf);
 cudaError_t launch_normmap_jobs(const NormJob* dev_jobs, int n_vec, int units_vec, int n_other,

@@ -131,8 +131,9 @@ def test_tensor_ragged_unaligned(n, leaf, mode):
 
 
 def test_bounded_wait_gives_up_and_reports():
-    """Failure detection without a fault: the multiply's wait routine on a phase nothing
-    completes gives up after its limit, and the status word reports SPAMM_ERR_TIMEOUT."""
+    """Failure detection without a fault: the multiply's and the norm map's wait routines on
+    a phase nothing completes give up after their limit, and the status word reports
+    SPAMM_ERR_TIMEOUT."""
     assert P.spamm_last_device_status() in (0, 5)  # clear
     elapsed = P.spamm_selftest_bounded_wait(20_000_000)
     assert 20_000_000 <= elapsed < 2_000_000_000
