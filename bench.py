@@ -883,6 +883,103 @@ def run_sparse(args, rank, world):
 
 
 # ---------------------------------------------------------------------------
+# Table-2 analogue: the paper's Table 1 matrix, speedup over cuBLAS
+# ---------------------------------------------------------------------------
+
+# Section 4.2, Table 2: speedup of SpAMM over cuBLAS on one V100 (FP32 vs
+# cublasSgemm / FP16 vs cublasHgemm), Table 1 matrix, rows = target valid ratio.
+TABLE2_V100 = {
+    "0.30": {1024: (5.7, 4.3), 2048: (3.1, 5.2), 4096: (1.0, 2.3), 8192: (0.9, 1.1)},
+    "0.20": {1024: (7.6, 5.2), 2048: (4.3, 6.9), 4096: (1.5, 3.7), 8192: (1.4, 2.0)},
+    "0.10": {1024: (10.8, 6.5), 2048: (7.6, 11.4), 4096: (2.6, 6.8), 8192: (2.6, 3.5)},
+    "0.05": {1024: (13.4, 7.6), 2048: (11.7, 16.1), 4096: (5.0, 11.9), 8192: (5.2, 7.0)},
+}
+
+
+def run_table2(args, rank, world):
+    """One pass of the hot path (norm map, plan, multiply) on the Table 1 matrix
+    a_ij = 0.1 / (|i - j|^0.1 + 1) (A = B), tau from the valid-ratio search at each target
+    ratio, timed against cuBLAS: FP32 SpAMM (SIMT, leaf 32 or 64) vs SGEMM, FP16 SpAMM
+    (tensor cores, leaf 64 or 128) vs cuBLAS FP16 GEMM; the faster leaf is reported."""
+    import torch
+    import paper_2103_13042_gb300 as P
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+    sizes = [int(x) for x in args.table2_sizes.split(",")]
+
+    def timed(fn, reps):
+        for _ in range(max(2, args.warmup)):
+            fn()
+        torch.cuda.synchronize()
+        g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        g0.record(stream)
+        for _ in range(reps):
+            fn()
+        g1.record(stream)
+        torch.cuda.synchronize()
+        return g0.elapsed_time(g1) / reps
+
+    cells = {}
+    prev_tf32 = torch.backends.cuda.matmul.allow_tf32
+    torch.backends.cuda.matmul.allow_tf32 = False   # SGEMM in FP32
+    with ClockSampler(local) as clk:
+        for n in sizes:
+            A = torch.from_numpy(synth.table1_matrix(n)).to(dev)
+            C = torch.empty_like(A)
+            Ah = A.half()
+            sgemm = timed(lambda: torch.matmul(A, A, out=C), args.steps)
+            hgemm = timed(lambda: torch.matmul(Ah, Ah), args.steps)
+            for ratio in TABLE2_V100:
+                row = {}
+                # each precision at its leaf candidates (tau re-searched per leaf, as the
+                # valid ratio is a per-leaf quantity); the faster one is reported
+                for name, prec, leaves, gemm in (("fp32", P.FP32, (32, 64), sgemm),
+                                                 ("fp16", P.FP16, (64, 128), hgemm)):
+                    best = None
+                    for leaf in leaves:
+                        nA = P.spamm_normmap(A, leaf)
+                        plan = P.Plan(n, leaf, prec)
+                        tau, got, _ = plan.tau_for_valid_ratio(nA, nA, float(ratio), 0.01, 30)
+
+                        def step():
+                            P.spamm_normmap(A, leaf, nA, stream)
+                            plan.plan_multiply(nA, nA, tau, A, A, C, args.target, stream)
+
+                        ms = timed(step, args.steps)
+                        if best is None or ms < best["spamm_ms"]:
+                            best = {"leaf": leaf, "tau": tau, "valid_ratio": got, "spamm_ms": ms}
+                        del plan, nA
+                    best.update({"cublas_ms": gemm, "speedup": gemm / best["spamm_ms"],
+                                 "paper_v100_speedup": TABLE2_V100[ratio][n][0 if name == "fp32" else 1]
+                                 if n in TABLE2_V100[ratio] else None})
+                    row[name] = best
+                cells[f"{n}/{ratio}"] = row
+            del A, C, Ah
+            torch.cuda.empty_cache()
+    torch.backends.cuda.matmul.allow_tf32 = prev_tf32
+    assert P.spamm_last_device_status() == 0
+    if rank != 0:
+        return None
+    head = cells[f"{sizes[-1]}/0.05"]["fp16"]
+    paper = head["paper_v100_speedup"]
+    return {
+        "metric": "Table 2 analogue: speedup of SpAMM over cuBLAS (FP32 vs SGEMM, FP16 vs HGEMM)",
+        "value": head["speedup"], "unit": f"x vs cuBLAS HGEMM (N={sizes[-1]}, valid ratio 5%, FP16)",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": head["spamm_ms"], "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": head["speedup"] / paper if paper else None, "dtype": "fp16",
+        "data": "synthetic (the Table 1 matrix, computed)",
+        "config": {"workload": "Table 1 matrix a_ij = 0.1/(|i-j|^0.1+1), A = B, tau by valid-ratio "
+                               "search; one step = norm map (A = B) + plan + multiply",
+                   "cells": cells, "parallelism": f"replicas x{world}"},
+        "clocks": clk.summary(),
+    }
+
+
+# ---------------------------------------------------------------------------
 # Reference arm: the oracle as it stands, on the host cores
 # ---------------------------------------------------------------------------
 
@@ -938,7 +1035,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-baselines", action="store_true")
     ap.add_argument("--eager", action="store_true", help="time host-enqueued calls, no graph")
-    ap.add_argument("--workload", default="single", choices=["single", "batch", "sparse"],
+    ap.add_argument("--table2-sizes", default="1024,2048,4096,8192",
+                    help="table2 workload: matrix sizes")
+    ap.add_argument("--workload", default="single", choices=["single", "batch", "sparse", "table2"],
                     help="single: one N=8192 product; batch: 256 uneven instances; "
                          "sparse: near-sparse N=32768 at a target valid ratio")
     ap.add_argument("--ratio", type=float, default=0.5, help="sparse: target valid ratio")
@@ -957,7 +1056,7 @@ def main():
         import torch
         import torch.distributed as dist
         dist.init_process_group("nccl")
-    runner = {"batch": run_batch, "sparse": run_sparse}.get(args.workload, run_ours)
+    runner = {"batch": run_batch, "sparse": run_sparse, "table2": run_table2}.get(args.workload, run_ours)
     line = runner(args, rank, world)
     if line is not None:
         print(json.dumps(line), flush=True)
