@@ -206,17 +206,25 @@ template <uint32_t FMT, int LEAF, bool SPLIT>
 cudaError_t launch_q(const InstRef& ref, const PlanBuffers& b, const OperandImages& img,
                      cudaStream_t s) {
   constexpr size_t kBlkSmem = (size_t)LEAF * (LEAF + 1) * sizeof(float);
-  int dev = 0, sms = 0, per_sm = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  cudaError_t e = cudaFuncSetAttribute(quantize_kernel<FMT, LEAF, SPLIT>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBlkSmem);
+  static int wave[64] = {};   // resident CTAs per device (occupancy x SMs)
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, quantize_kernel<FMT, LEAF, SPLIT>,
-                                                q_threads<LEAF>(), kBlkSmem);
+  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+  if (wave[dev] == 0) {
+    int sms = 0, per_sm = 0;
+    e = cudaFuncSetAttribute(quantize_kernel<FMT, LEAF, SPLIT>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBlkSmem);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess)
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, quantize_kernel<FMT, LEAF, SPLIT>,
+                                                        q_threads<LEAF>(), kBlkSmem);
+    if (e != cudaSuccess) return e;
+    wave[dev] = sms * std::max(1, per_sm);
+  }
   // the list length is known on the device only: one full wave of CTAs
   const int64_t cap = 2 * b.tiles;
-  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(cap, (int64_t)sms * std::max(1, per_sm)));
+  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(cap, (int64_t)wave[dev]));
   return launch_pdl(quantize_kernel<FMT, LEAF, SPLIT>, dim3(grid), dim3(q_threads<LEAF>()),
                     kBlkSmem, s, ref, b, img);
 }
