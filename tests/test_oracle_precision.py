@@ -151,3 +151,64 @@ def test_relative_bin_is_floor_log2():
     ref = np.where(p > 0, np.maximum(np.floor(np.log2(np.where(p > 0, p, 1.0))), P.FLAG_BIN_MIN),
                    P.FLAG_BIN_MIN)
     assert np.array_equal(b, ref.astype(np.int64))
+
+
+@pytest.mark.parametrize("fmt,split", [("bf16", False), ("bf16", True), ("fp16", False),
+                                       ("fp16", True), ("tf32", True)])
+def test_quantize_matrix_reconstructs_each_block(fmt, split):
+    """Every leaf block of the zero-padded matrix (ragged n) is recovered from its images: the
+    scale exponent puts the block maximum in [0.5, 1), hi * 2^e is within u of each entry (plus
+    FP16's subnormal floor) and hi + lo within about u^2; padding quantises to exact zeros."""
+    n, leaf = 70, 32
+    g = np.random.default_rng(7)
+    x = (g.standard_normal((n, n)) * np.exp2(g.integers(-12, 12, (n, n)))).astype(np.float32)
+    ex, hi, lo = P.quantize_matrix(x, leaf, fmt, split)
+    bd = S.num_blocks(n, leaf)
+    u = {"bf16": P.U_BF16, "fp16": P.U_FP16, "tf32": P.U_TF32}[fmt]
+    pad = np.zeros((bd * leaf, bd * leaf))
+    pad[:n, :n] = x
+    for i in range(bd):
+        for k in range(bd):
+            blk = pad[i * leaf:(i + 1) * leaf, k * leaf:(k + 1) * leaf]
+            mx = np.max(np.abs(blk))
+            if mx > 0:
+                assert 0.5 <= mx * 2.0 ** -float(ex[i, k]) < 1.0
+            scale = 2.0 ** float(ex[i, k])
+            floor = 2.0 ** -24 * scale if fmt == "fp16" else 0.0     # FP16 subnormal spacing
+            h = hi[i, k].astype(np.float64) * scale
+            assert np.all(np.abs(blk - h) <= u * np.abs(blk) + floor)
+            if split:
+                rec = (hi[i, k].astype(np.float64)
+                       + lo[i, k].astype(np.float64) * 2.0 ** -P.lo_shift(fmt)) * scale
+                assert np.all(np.abs(blk - rec) <= 2 * u * u * np.abs(blk) + 2 * floor)
+            outside = np.zeros_like(blk, dtype=bool)
+            outside[max(0, n - i * leaf):, :] = True
+            outside[:, max(0, n - k * leaf):] = True
+            assert np.all(h[outside] == 0.0)
+
+
+@pytest.mark.parametrize("mode", [P.BF16, P.FP16, P.BF16_SPLIT, P.FP16_SPLIT, P.TF32X3])
+def test_triple_error_coeff_bounds_single_products(mode):
+    """The per-triple coefficient bounds the rounding error of single block products measured
+    in FP64 on random blocks spanning several binades: ||AB - Q(A)Q(B)||_F <= c ||A|| ||B||."""
+    leaf = 32
+    fmt, split = P.mode_format(mode), P.mode_is_split(mode)
+    c = P.triple_error_coeff(mode, split, leaf)
+    g = np.random.default_rng(mode)
+    worst = 0.0
+    for _ in range(20):
+        a = (g.standard_normal((leaf, leaf)) * np.exp2(g.integers(-6, 6, (leaf, leaf)))).astype(np.float32)
+        b = (g.standard_normal((leaf, leaf)) * np.exp2(g.integers(-6, 6, (leaf, leaf)))).astype(np.float32)
+        ea, ha, la = P.quantize_block(a, fmt, split)
+        eb, hb, lb = P.quantize_block(b, fmt, split)
+        qa = ha.astype(np.float64) + (la.astype(np.float64) * 2.0 ** -P.lo_shift(fmt) if split else 0)
+        qb = hb.astype(np.float64) + (lb.astype(np.float64) * 2.0 ** -P.lo_shift(fmt) if split else 0)
+        exact = a.astype(np.float64) @ b.astype(np.float64)
+        # the split product omits lo*lo, as the tensor-core mode does
+        got = (qa @ qb if not split else
+               (ha.astype(np.float64) @ qb + la.astype(np.float64) * 2.0 ** -P.lo_shift(fmt)
+                @ hb.astype(np.float64))) * 2.0 ** float(ea + eb)
+        err = np.linalg.norm(exact - got) / (np.linalg.norm(a) * np.linalg.norm(b))
+        worst = max(worst, err)
+    assert worst <= c
+    assert worst >= c * 1e-3   # the bound is not vacuous by orders of magnitude

@@ -287,3 +287,41 @@ def test_table1_oracle_path(n):
     for label, taus in t["rows"].items():
         vr = S.valid_ratio(S.flat_survivors(nA, nA, taus[col]))
         assert abs(vr - float(label)) <= t["tolerance_pp"] / 100.0
+
+
+# ------------------------------------------------ row-sampled forms and errors
+
+@pytest.mark.parametrize("n,leaf,rows", [(300, 32, [0, 4, 9]), (257, 64, [0, 3, 4]),
+                                         (128, 32, [1, 2])])
+def test_row_sampled_forms_equal_full_oracle(n, leaf, rows):
+    """normmap_rows / spamm_rows (the CPU baseline's bounded sample) equal the matching rows of
+    the full norm map, flat survivor set and product, including ragged last block-rows."""
+    a = synth.exp_decay_su(n, 0.3, 11 + n)
+    b = synth.alg_decay_signed(n, 2.0, 12 + n)
+    nA, nB = S.normmap(a, leaf), S.normmap(b, leaf)
+    nA_rows = S.normmap_rows(a, leaf, rows)
+    assert np.array_equal(nA_rows, nA[rows])
+    p = S.triple_products(nA, nB)
+    tau = float(np.quantile(p[p > 0], 0.6))
+    full = S.spamm(a, b, leaf, tau)
+    surv_full = S.flat_survivors(nA, nB, tau)
+    part = S.spamm_rows(a, b, leaf, tau, rows, nA_rows, nB)
+    for i in rows:
+        strip, surv = part[i]
+        lo, hi = i * leaf, min(n, (i + 1) * leaf)
+        assert np.array_equal(surv, surv_full[i])
+        ref = full["C"][lo:hi]
+        assert np.max(np.abs(strip - ref)) <= 1e-13 * max(np.max(np.abs(ref)), 1e-300)
+
+
+def test_errors_three_normalisations():
+    """Eq. 5 errors: a known perturbation gives ||E||_F in absolute and both relative forms."""
+    ref = np.diag([3.0, 4.0])
+    c = ref.copy()
+    c[0, 1] = 1e-3                       # E = ref - c has one entry of magnitude 1e-3
+    e = S.errors(c, ref, 2.0, 5.0)
+    assert e["abs"] == pytest.approx(1e-3, rel=1e-15)
+    assert e["rel_c"] == pytest.approx(1e-3 / 5.0, rel=1e-15)    # ||ref||_F = 5
+    assert e["rel_ab"] == pytest.approx(1e-3 / 10.0, rel=1e-15)
+    z = S.errors(ref, ref, 0.0, 0.0)
+    assert z["abs"] == 0.0 and z["rel_c"] == 0.0 and z["rel_ab"] == 0.0
