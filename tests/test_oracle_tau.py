@@ -76,3 +76,25 @@ def test_bisection_on_real_inputs_meets_target():
         tau, _ = T.bisect_tau(err, eps, T.mean_norm_product(nA, nB))
         assert err(tau) <= eps
         assert err(tau * 1.02) > eps or err(tau * 1.02) <= eps  # bracket ends at <=1% ratio
+
+
+def test_frobenius_from_normmap_equals_matrix_norm():
+    """||X||_F from the leaf norms equals the matrix's own Frobenius norm (ragged n too)."""
+    for n, leaf in ((256, 32), (250, 64), (97, 32)):
+        a, _, _, _ = _norms(n, leaf, 70 + n)
+        nA = S.normmap(a, leaf)
+        assert T.frobenius_from_normmap(nA) == pytest.approx(
+            float(np.linalg.norm(a.astype(np.float64))), rel=1e-14)
+        assert T.inv_norm_product(nA, nA) == pytest.approx(
+            1.0 / float(np.linalg.norm(a.astype(np.float64))) ** 2, rel=1e-14)
+    z = np.zeros((4, 4))
+    assert T.inv_norm_product(z, z) == 0.0
+
+
+def test_mlp_features_layout():
+    """65 features: the 64 bins unchanged, then log10 of the target error."""
+    h = np.arange(64, dtype=np.float64) / 2016.0
+    x = T.mlp_features(h, 1e-5)
+    assert x.shape == (65,)
+    assert np.array_equal(x[:64], h)
+    assert x[64] == pytest.approx(-5.0, abs=1e-15)
