@@ -108,6 +108,11 @@ typedef struct spamm_plan_s* spamm_plan_t;
  * compensated double-FP32 groups and combined in FP64, so the result is
  * within 3e-13 relative of the exactly rounded norm (NaN entries give NaN;
  * an infinite entry gives NaN or +Inf, both of which survive every test).
+ * Asynchronous on `stream`; allocates the device status word on first use.
+ * Errors: SPAMM_ERR_INVALID_ARG (null or misaligned pointer), _UNSUPPORTED
+ * (leaf not 32/64/128, n out of range), _CUDA (launch failure).  Device
+ * waits are bounded: if one expires, SPAMM_ERR_TIMEOUT is latched in the
+ * status word (spamm_last_device_status) and the unfinished norms are NaN.
  * ------------------------------------------------------------------------- */
 spamm_status_t spamm_normmap(const float* X, int64_t n, int32_t leaf, double* normmap,
                              void* stream);
