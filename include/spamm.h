@@ -109,8 +109,9 @@ typedef struct spamm_plan_s* spamm_plan_t;
  * within 3e-13 relative of the exactly rounded norm (NaN entries give NaN;
  * an infinite entry gives NaN or +Inf, both of which survive every test).
  * Asynchronous on `stream`; allocates the device status word on first use.
- * Errors: SPAMM_ERR_INVALID_ARG (null or misaligned pointer), _UNSUPPORTED
- * (leaf not 32/64/128, n out of range), _CUDA (launch failure).  Device
+ * Errors: SPAMM_ERR_INVALID_ARG (n < 1, null or misaligned pointer),
+ * _UNSUPPORTED (leaf not 32/64/128, or ceil(n / leaf) > 1024), _CUDA
+ * (launch failure).  Device
  * waits are bounded: if one expires, SPAMM_ERR_TIMEOUT is latched in the
  * status word (spamm_last_device_status) and the unfinished norms are NaN.
  * ------------------------------------------------------------------------- */
