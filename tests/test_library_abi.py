@@ -73,3 +73,40 @@ def test_batch_validation_without_gpu(lib):
     assert lib.spamm_batch_create(ctypes.byref(h), ns, 3, 64, 0, 8, None, 0) == 1  # flags
     assert lib.spamm_batch_run(None, None, 0.0, None) == 1
     assert lib.spamm_batch_destroy(None) == 1
+
+
+def test_shape_limits_without_gpu(lib):
+    """The block grid is capped at 1024 leaf blocks a side: the largest n for each leaf is
+    accepted, one more element is UNSUPPORTED (2), and n < 1 is INVALID_ARG (1)."""
+    b = ctypes.c_size_t()
+    for leaf in (32, 64, 128):
+        n_max = 1024 * leaf
+        assert lib.spamm_plan_workspace_size(n_max, leaf, 0, ctypes.byref(b)) == 0
+        assert lib.spamm_plan_workspace_size(n_max + 1, leaf, 0, ctypes.byref(b)) == 2
+        assert lib.spamm_normmap(ctypes.c_void_p(16), n_max + 1, leaf,
+                                 ctypes.c_void_p(16), None) == 2
+        assert lib.spamm_plan_workspace_size(-5, leaf, 0, ctypes.byref(b)) == 1
+    assert lib.spamm_plan_workspace_size(1024, 64, 0, None) == 1              # null out
+    assert lib.spamm_plan_workspace_size(1024, 32, 2, ctypes.byref(b)) == 2   # BF16 at leaf 32
+    for prec in (1, 2, 3, 4, 5):                                              # tensor modes
+        assert lib.spamm_plan_workspace_size(1024, 64, prec, ctypes.byref(b)) == 0
+    assert lib.spamm_plan_workspace_size(1024, 64, -1, ctypes.byref(b)) == 1
+
+
+def test_workspace_grows_with_n(lib):
+    """The plan workspace holds the per-triple index lists, so it grows with the block count."""
+    sizes = []
+    for n in (256, 1024, 4096, 16384):
+        b = ctypes.c_size_t()
+        assert lib.spamm_plan_workspace_size(n, 64, 4, ctypes.byref(b)) == 0
+        sizes.append(b.value)
+    assert sizes == sorted(sizes) and len(set(sizes)) == len(sizes)
+    bd = 16384 // 64
+    assert sizes[-1] >= bd ** 3 * 2                                            # k_idx, 2 B each
+
+
+def test_unknown_status_string(lib):
+    lib.spamm_status_string.restype = ctypes.c_char_p
+    assert lib.spamm_status_string(0) == b"ok"
+    assert lib.spamm_status_string(5) == b"a bounded device wait timed out"
+    assert lib.spamm_status_string(99) == b"unknown status"
