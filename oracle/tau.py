@@ -109,7 +109,7 @@ def mlp_features(hist: np.ndarray, target_rel_err: float) -> np.ndarray:
 
 
 # ---------------------------------------------------------------------------
-# Bisection on the achieved error (fallback and judge of learned tau)
+# Bisection on the achieved error (fallback and arbiter of learned tau)
 # ---------------------------------------------------------------------------
 
 def bisect_tau(err_fn, eps: float, tau0: float, max_steps: int = 40, ratio: float = 1.01):

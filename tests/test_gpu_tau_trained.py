@@ -4,7 +4,7 @@ On fresh seeded decay pairs (a seed used neither for training nor for the
 held-out evaluation) the committed network's tau must meet the target error
 in most cases, and the time to an admissible tau (prediction, one error check,
 bisection only on a miss) must need fewer error evaluations than plain
-bisection on the error, which stays the fallback and the judge.
+bisection on the error, which stays the fallback and the arbiter.
 """
 import numpy as np
 import pytest
@@ -34,7 +34,7 @@ def test_trained_network_beats_bisection():
             e_p = m.error(tau_p)
             tau_b, n_b = TT.bisect_on_error(m, eps, tau0=m.ab * eps)
             e_b = m.error(tau_b)
-            assert e_b <= eps                       # the judge's own answer is admissible
+            assert e_b <= eps                       # the arbiter's own answer is admissible
             bis_evals.append(n_b)
             if e_p <= eps:
                 hits += 1
