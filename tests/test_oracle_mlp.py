@@ -92,3 +92,28 @@ def test_adam_matches_torch():
         tt.grad = torch.tensor(g2)
         opt.step()
     assert np.allclose(th, tt.detach().numpy(), rtol=1e-12, atol=1e-14)
+
+
+def test_pinball_loss_by_hand_and_quantile_minimiser():
+    """rho_q(r) = q r for r > 0 and (q - 1) r otherwise, checked on hand values; a constant
+    prediction minimising the mean loss is a q-quantile of the targets (the textbook property
+    the learned tau relies on); the gradient matches central differences away from kinks."""
+    q = 0.8
+    assert M.pinball_loss([0.0, 0.0], [2.0, -1.0], q) == pytest.approx((0.8 * 2 + 0.2 * 1) / 2)
+    g = np.random.Generator(np.random.PCG64(64))
+    y = g.normal(size=101)
+    grid = np.linspace(-3, 3, 6001)
+    losses = [M.pinball_loss(np.full_like(y, c), y, q) for c in grid]
+    best = grid[int(np.argmin(losses))]
+    ys = np.sort(y)
+    assert ys[79] - 1e-3 <= best <= ys[81] + 1e-3          # the 0.8-quantile of 101 values
+    pred = g.normal(size=7)
+    tgt = g.normal(size=7)
+    grad = M.pinball_grad(pred, tgt, q)
+    h = 1e-6
+    for t in range(7):
+        up, dn = pred.copy(), pred.copy()
+        up[t] += h
+        dn[t] -= h
+        fd = (M.pinball_loss(up, tgt, q) - M.pinball_loss(dn, tgt, q)) / (2 * h)
+        assert grad[t] == pytest.approx(fd, rel=1e-6, abs=1e-9)

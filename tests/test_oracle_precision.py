@@ -212,3 +212,131 @@ def test_triple_error_coeff_bounds_single_products(mode):
         worst = max(worst, err)
     assert worst <= c
     assert worst >= c * 1e-3   # the bound is not vacuous by orders of magnitude
+
+
+# ---------------------------------------------------------------------------
+# The accumulation bound against simulated FP32 accumulation chains
+# ---------------------------------------------------------------------------
+
+def _to_f32(x, toward_zero):
+    """FP32 rounding of FP64 values: to nearest, or toward zero (a truncating adder)."""
+    y = x.astype(np.float32)
+    if toward_zero:
+        y = np.where(np.abs(y.astype(np.float64)) > np.abs(x), np.nextafter(y, np.float32(0)), y)
+    return y
+
+
+def _elementwise(blocks, leaf):
+    return np.kron(blocks, np.ones((leaf, leaf), dtype=blocks.dtype))
+
+
+def _fma_chain_fp32(a, b, leaf, surv):
+    """One FP32 FMA chain per output entry over every surviving k and inner index, k ascending
+    (a product of two FP32 values is exact in FP64, so each step rounds once, then to FP32)."""
+    n = a.shape[0]
+    bd = S.num_blocks(n, leaf)
+    m = bd * leaf
+    A = np.zeros((m, m), np.float32)
+    B = np.zeros((m, m), np.float32)
+    A[:n, :n], B[:n, :n] = a, b
+    c = np.zeros((m, m), np.float32)
+    for k in range(bd):
+        keep = _elementwise(surv[:, k, :], leaf)
+        for p in range(k * leaf, (k + 1) * leaf):
+            step = _to_f32(c + np.outer(A[:, p].astype(np.float64), B[p, :]), False)
+            c = np.where(keep, step, c)
+    return c[:n, :n]
+
+
+def _tensor_chain(a, b, leaf, surv, mode, flags, toward_zero):
+    """The tensor-core modes' accumulation model: per surviving k, a fresh FP32 sum of the
+    leaf hi*hi terms (then 2^-s_lo hi*lo and lo*hi on split triples), each add rounded; then
+    one rounded add of 2^(ea+eb) times that sum into C."""
+    n = a.shape[0]
+    bd = S.num_blocks(n, leaf)
+    m = bd * leaf
+    fmt = P.mode_format(mode)
+    split = P.mode_is_split(mode)
+    ea, ha, la = P.quantize_matrix(a, leaf, fmt, split)
+    eb, hb, lb = P.quantize_matrix(b, leaf, fmt, split)
+    sl = 2.0 ** -P.lo_shift(fmt)
+    c = np.zeros((m, m), np.float32)
+    for k in range(bd):
+        keep = _elementwise(surv[:, k, :], leaf)
+        if mode == P.TF32X3:
+            use = np.ones((m, m), bool)
+        elif split:
+            use = _elementwise(flags[:, k, :], leaf)
+        hA = np.concatenate([ha[i, k] for i in range(bd)], 0).astype(np.float64)
+        hB = np.concatenate([hb[k, j] for j in range(bd)], 1).astype(np.float64)
+        terms = [(hA[:, p], hB[p, :], 1.0, None) for p in range(leaf)]
+        if split:
+            lA = np.concatenate([la[i, k] for i in range(bd)], 0).astype(np.float64)
+            lB = np.concatenate([lb[k, j] for j in range(bd)], 1).astype(np.float64)
+            terms += [(hA[:, p], lB[p, :], sl, use) for p in range(leaf)]
+            terms += [(lA[:, p], hB[p, :], sl, use) for p in range(leaf)]
+        s = np.zeros((m, m), np.float32)
+        for x, y, w, mask in terms:
+            step = _to_f32(s + w * np.outer(x, y), toward_zero)
+            s = step if mask is None else np.where(mask, step, s)
+        scale = _elementwise(np.ldexp(1.0, (ea[:, k, None] + eb[None, k, :]).astype(np.int64)),
+                             leaf)
+        c = np.where(keep, _to_f32(c + scale * s, toward_zero), c)
+    return c[:n, :n]
+
+
+def _positive(n, seed):
+    g = np.random.Generator(np.random.PCG64(seed))
+    return g.uniform(0.5, 1.0, (n, n)).astype(np.float32)
+
+
+def test_accumulation_bound_covers_an_fp32_fma_chain():
+    """All-positive inputs make the rounding errors of one long chain add up; the simulated
+    chain stays inside the bound, and the bound is not vacuous (within 100x of it)."""
+    n, leaf = 200, 64
+    a, b = _positive(n, 71), _positive(n, 72)
+    nA, nB = S.normmap(a, leaf), S.normmap(b, leaf)
+    surv = S.flat_survivors(nA, nB, 0.0)
+    ref = S.multiply_with_skipset(a, b, leaf, surv)
+    err = np.linalg.norm(_fma_chain_fp32(a, b, leaf, surv).astype(np.float64) - ref)
+    bound = P.accumulation_bound(nA, nB, surv, P.FP32, leaf)
+    assert 0.01 * bound < err <= bound
+
+
+@pytest.mark.parametrize("mode", [P.FP16, P.BF16_SPLIT, P.TF32X3])
+def test_accumulation_bound_covers_truncating_tensor_chains(mode):
+    """Rounding toward zero on positive data is the worst ordinary case of the model: it stays
+    inside the bound, yet breaks a bound that drops the per-k product length (3 leaf), so that
+    term is needed."""
+    n, leaf = 200, 64
+    a, b = _positive(n, 73), _positive(n, 74)
+    nA, nB = S.normmap(a, leaf), S.normmap(b, leaf)
+    surv = S.flat_survivors(nA, nB, 0.0)
+    flags = surv.copy() if mode == P.BF16_SPLIT else None
+    emu = P.emulated_multiply(a, b, leaf, surv, mode, flags)
+    bound = P.accumulation_bound(nA, nB, surv, mode, leaf)
+    for toward_zero in (False, True):
+        sim = _tensor_chain(a, b, leaf, surv, mode, flags, toward_zero).astype(np.float64)
+        err = np.linalg.norm(sim - emu)
+        assert err <= bound
+    kmax = int(surv.sum(axis=1).max())
+    if P.mode_is_split(mode):
+        assert err > bound * (kmax + 4) / (3 * leaf + kmax + 4)
+
+
+@pytest.mark.parametrize("mode", [P.BF16, P.FP16_SPLIT, P.TF32X3])
+def test_accumulation_bound_on_pruned_signed_inputs(mode):
+    """A decaying signed pair under pruning (uneven survivor counts per tile, ragged edge)."""
+    n, leaf = 150, 64
+    a = synth.exp_decay_normal(n, 0.02, 75)
+    b = synth.exp_decay_normal(n, 0.02, 76)
+    nA, nB = S.normmap(a, leaf), S.normmap(b, leaf)
+    p = np.sort((nA[:, :, None] * nB[None, :, :]).ravel())
+    surv = S.flat_survivors(nA, nB, float(p[p.size // 3]))
+    assert 0 < surv.sum() < surv.size
+    flags = surv.copy() if mode == P.FP16_SPLIT else None
+    emu = P.emulated_multiply(a, b, leaf, surv, mode, flags)
+    bound = P.accumulation_bound(nA, nB, surv, mode, leaf)
+    for toward_zero in (False, True):
+        sim = _tensor_chain(a, b, leaf, surv, mode, flags, toward_zero).astype(np.float64)
+        assert np.linalg.norm(sim - emu) <= bound

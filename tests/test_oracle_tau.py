@@ -98,3 +98,16 @@ def test_mlp_features_layout():
     assert x.shape == (65,)
     assert np.array_equal(x[:64], h)
     assert x[64] == pytest.approx(-5.0, abs=1e-15)
+
+
+def test_valid_ratio_at_counts_triples_one_by_one():
+    """Brute force over every (i, k, j) with the skip rule written out (multiply iff not
+    p < tau), including a tau equal to one product (a tie is multiplied)."""
+    _, _, nA, nB = _norms(n=160, leaf=32)
+    bd = nA.shape[0]
+    p_mid = float(nA[1, 2] * nB[2, 3])
+    for tau in (0.0, p_mid, 1e-3, math.inf):
+        cnt = sum(1 for i in range(bd) for k in range(bd) for j in range(bd)
+                  if not float(nA[i, k]) * float(nB[k, j]) < tau)
+        assert T.valid_ratio_at(nA, nB, tau) == cnt / bd ** 3
+    assert T.valid_ratio_at(nA, nB, 0.0) == 1.0 and T.valid_ratio_at(nA, nB, math.inf) == 0.0
