@@ -134,6 +134,97 @@ def _ptr(t):
     return None if t is None else ctypes.c_void_p(t.data_ptr())
 
 
+# Tensor checks.  The C ABI sees bare pointers, so it cannot tell a CPU tensor, a wrong dtype,
+# a strided view or a short buffer from a valid operand; those are caught here, before any
+# pointer reaches a kernel, and reported as SPAMM_ERR_INVALID_ARG like the library's own
+# argument errors.  Alignment, aliasing and value checks stay in the library.
+
+_DEVICE_TYPE = "cuda"
+MLP_INPUTS = 65
+
+
+def _bad(where: str, what: str):
+    raise SpammError(1, f"{where}: {what}")
+
+
+def _tensor(t, where: str, name: str, dtype, numel=None, square=None, min_numel=None):
+    """Pointer of ``t`` after checking device, dtype, contiguity and size.
+
+    ``numel``: the exact element count; ``min_numel``: the least one; ``square``: the side n
+    of an n x n matrix."""
+    import torch
+    if not isinstance(t, torch.Tensor):
+        _bad(where, f"{name} is not a tensor")
+    if t.device.type != _DEVICE_TYPE:
+        _bad(where, f"{name} is on {t.device}, not on the GPU")
+    if t.dtype != dtype:
+        _bad(where, f"{name} is {t.dtype}, expected {dtype}")
+    if not t.is_contiguous():
+        _bad(where, f"{name} is not contiguous")
+    if square is not None and (t.dim() != 2 or t.shape[0] != square or t.shape[1] != square):
+        _bad(where, f"{name} has shape {tuple(t.shape)}, expected ({square}, {square})")
+    if numel is not None and t.numel() != numel:
+        _bad(where, f"{name} has {t.numel()} elements, expected {numel}")
+    if min_numel is not None and t.numel() < min_numel:
+        _bad(where, f"{name} has {t.numel()} elements, expected at least {min_numel}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+_F32 = None
+
+
+def _mat_ptr(t, where: str, name, n: int) -> int:
+    """Address of an n x n contiguous FP32 GPU tensor (fast path; _tensor names the fault)."""
+    global _F32
+    if _F32 is None:
+        import torch
+        _F32 = torch.float32
+    try:
+        ok = (t.dtype is _F32 and t.shape == (n, n) and t.is_contiguous() and
+              (t.is_cuda if _DEVICE_TYPE == "cuda" else t.device.type == _DEVICE_TYPE))
+    except AttributeError:
+        ok = False
+    if not ok:
+        if not isinstance(name, str):             # ("As", i): formatted only on failure
+            name = "%s[%d]" % name
+        return _tensor(t, where, name, _F32, square=n).value
+    return t.data_ptr()
+
+
+def _mat(t, where: str, name: str, n: int):
+    return ctypes.c_void_p(_mat_ptr(t, where, name, n))
+
+
+def _side(t, where: str, name: str) -> int:
+    """n of an n x n operand (checked to be 2-D and square by the caller's _mat)."""
+    if getattr(t, "dim", lambda: 0)() != 2:
+        _bad(where, f"{name} must be a 2-D n x n tensor")
+    return int(t.shape[0])
+
+
+def _norms(t, where: str, name: str, bd: int):
+    import torch
+    return _tensor(t, where, name, torch.float64, numel=bd * bd)
+
+
+_PARAMS = None
+
+
+def _weights(t, where: str, name: str = "weights"):
+    import torch
+    global _PARAMS
+    if _PARAMS is None:
+        _PARAMS = spamm_mlp_param_count()
+    return _tensor(t, where, name, torch.float32, numel=_PARAMS)
+
+
+def _features_arg(X, where: str):
+    import torch
+    if getattr(X, "dim", lambda: 0)() != 2 or X.shape[1] != MLP_INPUTS:
+        _bad(where, f"X must be [count, {MLP_INPUTS}]")
+    return _tensor(X, where, "X", torch.float32)
+
+
 def num_blocks(n: int, leaf: int) -> int:
     return -(-n // leaf)
 
@@ -145,11 +236,13 @@ def num_blocks(n: int, leaf: int) -> int:
 def spamm_normmap(X, leaf: int, out=None, stream=None):
     """Leaf Frobenius norms of the n x n FP32 device tensor X -> FP64 [bd, bd] tensor."""
     import torch
-    n = X.shape[0]
-    bd = num_blocks(n, leaf)
+    n = _side(X, "spamm_normmap", "X")
+    x = _mat(X, "spamm_normmap", "X", n)
+    bd = num_blocks(n, leaf) if leaf > 0 else 0
     if out is None:
         out = torch.empty((bd, bd), dtype=torch.float64, device=X.device)
-    _check(lib().spamm_normmap(_ptr(X), n, leaf, _ptr(out), _stream(stream)), "spamm_normmap")
+    o = _norms(out, "spamm_normmap", "out", bd)
+    _check(lib().spamm_normmap(x, n, leaf, o, _stream(stream)), "spamm_normmap")
     return out
 
 
@@ -158,10 +251,11 @@ class Plan:
 
     def __init__(self, n: int, leaf: int, precision: int = FP32, workspace=None):
         self.n, self.leaf, self.precision = n, leaf, precision
-        self.bd = num_blocks(n, leaf)
+        self.bd = num_blocks(n, leaf) if leaf > 0 else 0
         h = ctypes.c_void_p()
-        ws_ptr, ws_bytes = (None, 0) if workspace is None else (_ptr(workspace),
-                                                                 workspace.numel() * workspace.element_size())
+        ws_ptr, ws_bytes = (None, 0) if workspace is None else (
+            _tensor(workspace, "spamm_plan_create", "workspace", workspace.dtype),
+            workspace.numel() * workspace.element_size())
         _check(lib().spamm_plan_create(ctypes.byref(h), n, leaf, precision, ws_ptr, ws_bytes),
                "spamm_plan_create")
         self.handle = h
@@ -186,8 +280,10 @@ class Plan:
             pass
 
     def plan(self, normA, normB, tau: float, target_rel_err: float = 1e-5, stream=None):
-        _check(lib().spamm_plan(self.handle, _ptr(normA), _ptr(normB), float(tau),
-                                float(target_rel_err), _stream(stream)), "spamm_plan")
+        w = "spamm_plan"
+        _check(lib().spamm_plan(self.handle, _norms(normA, w, "normA", self.bd),
+                                _norms(normB, w, "normB", self.bd), float(tau),
+                                float(target_rel_err), _stream(stream)), w)
         return self
 
     def stats(self, stream=None) -> dict:
@@ -208,29 +304,37 @@ class Plan:
         return tp, kk[:st["survivors"]]
 
     def multiply(self, A, B, C, stream=None):
-        _check(lib().spamm_multiply(self.handle, _ptr(A), _ptr(B), _ptr(C), _stream(stream)),
-               "spamm_multiply")
+        w, n = "spamm_multiply", self.n
+        _check(lib().spamm_multiply(self.handle, _mat(A, w, "A", n), _mat(B, w, "B", n),
+                                    _mat(C, w, "C", n), _stream(stream)), w)
         return C
 
     def plan_multiply(self, normA, normB, tau: float, A, B, C, target_rel_err: float = 1e-5,
                       stream=None):
         """plan() then multiply() in one call (zero-fill of empty tiles overlapped)."""
-        _check(lib().spamm_plan_multiply(self.handle, _ptr(normA), _ptr(normB), float(tau),
-                                         float(target_rel_err), _ptr(A), _ptr(B), _ptr(C),
-                                         _stream(stream)), "spamm_plan_multiply")
+        w, n, bd = "spamm_plan_multiply", self.n, self.bd
+        _check(lib().spamm_plan_multiply(self.handle, _norms(normA, w, "normA", bd),
+                                         _norms(normB, w, "normB", bd), float(tau),
+                                         float(target_rel_err), _mat(A, w, "A", n),
+                                         _mat(B, w, "B", n), _mat(C, w, "C", n),
+                                         _stream(stream)), w)
         return C
 
     def band(self, normA, normB, tau_lo: float, tau_hi: float, stream=None):
         """Plan the triples with tau_lo <= p < tau_hi (error measurement)."""
-        _check(lib().spamm_plan_band(self.handle, _ptr(normA), _ptr(normB), float(tau_lo),
-                                     float(tau_hi), _stream(stream)), "spamm_plan_band")
+        w = "spamm_plan_band"
+        _check(lib().spamm_plan_band(self.handle, _norms(normA, w, "normA", self.bd),
+                                     _norms(normB, w, "normB", self.bd), float(tau_lo),
+                                     float(tau_hi), _stream(stream)), w)
         return self
 
     def tau_for_valid_ratio(self, normA, normB, target: float, tol: float = 0.01,
                             max_probes: int = 20, stream=None):
         """(tau, valid ratio, probes) of the valid-ratio search (Section 3.5.2)."""
         t, r, k = ctypes.c_double(), ctypes.c_double(), ctypes.c_int32()
-        _check(lib().spamm_tau_for_valid_ratio(self.handle, _ptr(normA), _ptr(normB),
+        w = "spamm_tau_for_valid_ratio"
+        _check(lib().spamm_tau_for_valid_ratio(self.handle, _norms(normA, w, "normA", self.bd),
+                                               _norms(normB, w, "normB", self.bd),
                                                float(target), float(tol), int(max_probes),
                                                ctypes.byref(t), ctypes.byref(r), ctypes.byref(k),
                                                _stream(stream)), "spamm_tau_for_valid_ratio")
@@ -240,17 +344,20 @@ class Plan:
         """Raw counts of the 64-bin log2 histogram of relative norm products."""
         import numpy as np
         out = np.zeros(64, dtype=np.int64)
-        _check(lib().spamm_norm_histogram(self.handle, _ptr(normA), _ptr(normB),
-                                          out.ctypes.data_as(ctypes.c_void_p), _stream(stream)),
-               "spamm_norm_histogram")
+        w = "spamm_norm_histogram"
+        _check(lib().spamm_norm_histogram(self.handle, _norms(normA, w, "normA", self.bd),
+                                          _norms(normB, w, "normB", self.bd),
+                                          out.ctypes.data_as(ctypes.c_void_p), _stream(stream)), w)
         return out
 
     def tau_predict(self, normA, normB, target_rel_err: float, weights, stream=None) -> float:
         """The network's tau for this plan's shape (weights: device float32 [8449])."""
         t = ctypes.c_double()
-        _check(lib().spamm_tau_predict(self.handle, _ptr(normA), _ptr(normB),
-                                       float(target_rel_err), _ptr(weights), ctypes.byref(t),
-                                       _stream(stream)), "spamm_tau_predict")
+        w = "spamm_tau_predict"
+        _check(lib().spamm_tau_predict(self.handle, _norms(normA, w, "normA", self.bd),
+                                       _norms(normB, w, "normB", self.bd),
+                                       float(target_rel_err), _weights(weights, w),
+                                       ctypes.byref(t), _stream(stream)), w)
         return t.value
 
 
@@ -267,24 +374,40 @@ def spamm_multiply(plan: Plan, A, B, C=None, stream=None):
 
 
 def spamm_frobenius_diff(X, Y=None, stream=None) -> float:
+    import torch
+    w = "spamm_frobenius_diff"
+    x = _tensor(X, w, "X", torch.float32)
+    y = None if Y is None else _tensor(Y, w, "Y", torch.float32, numel=X.numel())
     out = ctypes.c_double()
-    _check(lib().spamm_frobenius_diff(_ptr(X), _ptr(Y), X.numel(), ctypes.byref(out),
-                                      _stream(stream)), "spamm_frobenius_diff")
+    _check(lib().spamm_frobenius_diff(x, y, X.numel(), ctypes.byref(out), _stream(stream)), w)
     return out.value
 
 
 def spamm_multiply_fp32_noalloc(A, B, C, leaf: int, tau: float, stream=None):
     """FP32 SpAMM with no device allocation (static library scratch; ceil(n/leaf) <= 64)."""
-    _check(lib().spamm_multiply_fp32_noalloc(_ptr(A), _ptr(B), _ptr(C), A.shape[0], leaf,
-                                             float(tau), _stream(stream)),
-           "spamm_multiply_fp32_noalloc")
+    w = "spamm_multiply_fp32_noalloc"
+    n = _side(A, w, "A")
+    _check(lib().spamm_multiply_fp32_noalloc(_mat(A, w, "A", n), _mat(B, w, "B", n),
+                                             _mat(C, w, "C", n), n, leaf, float(tau),
+                                             _stream(stream)), w)
     return C
 
 
-def _problems(As, Bs, Cs, taus):
-    arr = (Problem * len(As))()
-    for i, (A, B, C, t) in enumerate(zip(As, Bs, Cs, taus)):
-        arr[i] = Problem(A.data_ptr(), B.data_ptr(), C.data_ptr(), A.shape[0], float(t))
+def _problems(As, Bs, Cs, taus, where: str, ns=None):
+    """The problem table; every operand checked (n x n FP32 on the GPU, n = ns[i] if given).
+    Cs may be None (no outputs: C stays NULL)."""
+    count = len(As)
+    if len(Bs) != count or (Cs is not None and len(Cs) != count) or len(taus) != count:
+        _bad(where, "As, Bs, Cs and taus differ in length")
+    if ns is not None and count != len(ns):
+        _bad(where, f"{count} problems for a batch of {len(ns)}")
+    arr = (Problem * count)()
+    for i in range(count):
+        A = As[i]
+        n = _side(A, where, f"As[{i}]") if ns is None else ns[i]
+        arr[i] = Problem(_mat_ptr(A, where, ("As", i), n), _mat_ptr(Bs[i], where, ("Bs", i), n),
+                         None if Cs is None else _mat_ptr(Cs[i], where, ("Cs", i), n),
+                         n, float(taus[i]))
     return arr
 
 
@@ -298,7 +421,8 @@ class Batch:
         self.count = len(self.ns)
         n_arr = (ctypes.c_int64 * self.count)(*self.ns)
         ws_ptr, ws_bytes = (None, 0) if workspace is None else (
-            _ptr(workspace), workspace.numel() * workspace.element_size())
+            _tensor(workspace, "spamm_batch_create", "workspace", workspace.dtype),
+            workspace.numel() * workspace.element_size())
         h = ctypes.c_void_p()
         flags = ((BATCH_GRAPH if graph else 0) | (BATCH_DYNAMIC if dynamic else 0) |
                  (BATCH_TIMING if timing else 0))
@@ -319,7 +443,7 @@ class Batch:
         return b.value
 
     def run(self, As, Bs, Cs, taus, target_rel_err: float = 1e-5, stream=None):
-        probs = _problems(As, Bs, Cs, taus)
+        probs = _problems(As, Bs, Cs, taus, "spamm_batch_run", self.ns)
         self._keep = probs
         _check(lib().spamm_batch_run(self.handle, ctypes.cast(probs, ctypes.c_void_p),
                                      float(target_rel_err), _stream(stream)), "spamm_batch_run")
@@ -350,15 +474,17 @@ class Batch:
     def tau_predict(self, As, Bs, targets, weights, stream=None):
         """Predicted tau per instance (the norm maps of As / Bs are computed on the way)."""
         import numpy as np
-        probs = (Problem * len(As))()
-        for i, (A, B) in enumerate(zip(As, Bs)):   # no output: C stays NULL
-            probs[i] = Problem(A.data_ptr(), B.data_ptr(), None, A.shape[0], 0.0)
+        w = "spamm_batch_tau_predict"
+        probs = _problems(As, Bs, None, [0.0] * len(As), w, self.ns)
         tg = np.ascontiguousarray(targets, dtype=np.float64)
+        if tg.shape != (self.count,):
+            _bad(w, f"{tg.size} targets for a batch of {self.count}")
         out = np.zeros(self.count, dtype=np.float64)
         _check(lib().spamm_batch_tau_predict(self.handle, ctypes.cast(probs, ctypes.c_void_p),
-                                             tg.ctypes.data_as(ctypes.c_void_p), _ptr(weights),
+                                             tg.ctypes.data_as(ctypes.c_void_p),
+                                             _weights(weights, w),
                                              out.ctypes.data_as(ctypes.c_void_p),
-                                             _stream(stream)), "spamm_batch_tau_predict")
+                                             _stream(stream)), w)
         return out
 
     def timings(self):
@@ -383,7 +509,7 @@ class Batch:
 def spamm_batch_autotune(As, Bs, Cs, taus, precision: int = FP32, target_rel_err: float = 1e-5,
                          reps: int = 3, stream=None):
     """Times every (leaf, schedule) candidate on these problems: (best, all) as dicts."""
-    probs = _problems(As, Bs, Cs, taus)
+    probs = _problems(As, Bs, Cs, taus, "spamm_batch_autotune")
     best = Tune()
     res = (Tune * 8)()
     nres = ctypes.c_int32(8)
@@ -397,7 +523,7 @@ def spamm_batch_autotune(As, Bs, Cs, taus, precision: int = FP32, target_rel_err
 def spamm_multiply_batched(As, Bs, Cs, taus, leaf: int, precision: int = FP32,
                            target_rel_err: float = 1e-5, stream=None):
     """One-off batch (allocates and blocks). Returns the per-instance statistics."""
-    probs = _problems(As, Bs, Cs, taus)
+    probs = _problems(As, Bs, Cs, taus, "spamm_multiply_batched")
     arr = (Stats * len(As))()
     _check(lib().spamm_multiply_batched(ctypes.cast(probs, ctypes.c_void_p), len(As), leaf,
                                         precision, float(target_rel_err),
@@ -418,36 +544,47 @@ def spamm_mlp_param_count() -> int:
 
 def spamm_mlp_forward(weights, X, stream=None):
     import torch
+    w = "spamm_mlp_forward"
+    x = _features_arg(X, w)
     y = torch.empty(X.shape[0], dtype=torch.float32, device=X.device)
-    _check(lib().spamm_mlp_forward(_ptr(weights), _ptr(X), X.shape[0], _ptr(y), _stream(stream)),
-           "spamm_mlp_forward")
+    _check(lib().spamm_mlp_forward(_weights(weights, w), x, X.shape[0], _ptr(y),
+                                   _stream(stream)), w)
     return y
 
 
 def spamm_mlp_grad(weights, X, y_true, quantile: float, stream=None):
     """(gradient [8449], loss tensor [1]) of the mean pinball loss."""
     import torch
+    w = "spamm_mlp_grad"
+    wp, x = _weights(weights, w), _features_arg(X, w)
+    y = _tensor(y_true, w, "y_true", torch.float32, numel=X.shape[0])
     g = torch.empty_like(weights)
     loss = torch.empty(1, dtype=torch.float32, device=X.device)
-    _check(lib().spamm_mlp_grad(_ptr(weights), _ptr(X), _ptr(y_true), X.shape[0],
-                                float(quantile), _ptr(g), _ptr(loss), _stream(stream)),
-           "spamm_mlp_grad")
+    _check(lib().spamm_mlp_grad(wp, x, y, X.shape[0], float(quantile), _ptr(g), _ptr(loss),
+                                _stream(stream)), w)
     return g, loss
 
 
 def spamm_mlp_adam(weights, grad, m, v, t: int, lr: float, stream=None):
-    _check(lib().spamm_mlp_adam(_ptr(weights), _ptr(grad), _ptr(m), _ptr(v), int(t), float(lr),
-                                _stream(stream)), "spamm_mlp_adam")
+    w = "spamm_mlp_adam"
+    _check(lib().spamm_mlp_adam(_weights(weights, w), _weights(grad, w, "grad"),
+                                _weights(m, w, "m"), _weights(v, w, "v"), int(t), float(lr),
+                                _stream(stream)), w)
 
 
 def spamm_mlp_train(weights, m, v, t0: int, X, y_true, idx, steps: int, batch: int, lr: float,
                     quantile: float, stream=None):
-    """Runs `steps` Adam steps in one launch; returns the per-step losses (device tensor)."""
+    """Runs `steps` Adam steps in one launch; returns the per-step losses (device tensor).
+
+    idx holds steps * batch sample indices (int32), each in [0, rows of X)."""
     import torch
+    w = "spamm_mlp_train"
+    args = (_weights(weights, w), _weights(m, w, "m"), _weights(v, w, "v"), int(t0),
+            _features_arg(X, w), _tensor(y_true, w, "y_true", torch.float32, numel=X.shape[0]),
+            _tensor(idx, w, "idx", torch.int32, min_numel=max(0, int(steps)) * max(0, int(batch))))
     hist = torch.empty(max(1, steps), dtype=torch.float32, device=X.device)
-    _check(lib().spamm_mlp_train(_ptr(weights), _ptr(m), _ptr(v), int(t0), _ptr(X), _ptr(y_true),
-                                 _ptr(idx), int(steps), int(batch), float(lr), float(quantile),
-                                 _ptr(hist), _stream(stream)), "spamm_mlp_train")
+    _check(lib().spamm_mlp_train(*args, int(steps), int(batch), float(lr), float(quantile),
+                                 _ptr(hist), _stream(stream)), w)
     return hist[:steps]
 
 
