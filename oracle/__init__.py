@@ -17,6 +17,8 @@ tau        valid ratio and its tau search (Section 3.5.2), the log-histogram of
            block-norm products, tau bisection on the achieved error.
 mlp        the 65-64-64-1 GELU network for learned tau: forward, analytic
            backward, pinball loss, Adam, all in FP64 numpy.
+general    the general statement of Section 2, C = alpha*A*B + beta*C on
+           rectangular operands, and chained products for matrix powers.
 
 Every function is pinned by ``tests/test_oracle_*.py`` against values the
 paper prints (Table 1), closed forms, brute force on tiny inputs, invariants
