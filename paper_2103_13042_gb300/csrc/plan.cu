@@ -195,7 +195,8 @@ __device__ __forceinline__ double ext_value(ExtSum s) {
   return s.m == 0.0f ? 0.0 : ldexp((double)s.m, s.e);
 }
 
-// floor(log2(fl(fl(na nb) * inv))) clamped to the flag bins, as the oracle defines it.
+// floor(log2(fl(fl(na nb) * inv))) clamped to the flag bins: the binade of a relative norm
+// product, taken from one FP64 multiply so that every implementation bins it alike.
 __device__ __forceinline__ int rel_bin(double p, double inv) {
   const double r = __dmul_rn(p, inv);
   if (!(r > 0.0)) return kFlagBinMin;
@@ -463,7 +464,7 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, 4)
   }
 }
 
-// Histogram bin of r = fl(fl(na nb) * inv) (FP64, as the oracle defines it):
+// Histogram bin of r = fl(fl(na nb) * inv) (one FP64 multiply, no other rounding):
 // floor(-log2 r) clamped to [0, 63]; r = 0 or NaN goes to bin 63, +Inf to 0.
 __device__ __forceinline__ int hist_bin_exact(double p, double inv) {
   const double r = __dmul_rn(p, inv);
