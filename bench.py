@@ -36,6 +36,19 @@ os.environ.setdefault("MKL_NUM_THREADS", "1")
 import numpy as np
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
+
+
+def blas_threads() -> int:
+    """Threads the oracle's BLAS calls may use: 1 under the pins above, or what the caller's
+    environment set instead (the largest of the three); the oracle's own loops use one."""
+    vals = [1]
+    for k in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS"):
+        try:
+            vals.append(int(os.environ.get(k, "1")))
+        except ValueError:
+            pass
+    return max(vals)
+
 sys.path.insert(0, ROOT)
 
 import synth  # noqa: E402
@@ -169,7 +182,7 @@ def cpu_baseline(a, b, leaf, tau, rows, nB_full=None, gpu_c=None):
     dt = time.perf_counter() - t0
     t_full = dt * bd / len(rows)
     res = {"value": 2.0 * n ** 3 / t_full / 1e12, "unit": "TFLOP/s (dense-equivalent)",
-           "cores": 1, "kind": "oracle",
+           "cores": blas_threads(), "kind": "oracle",
            "sample": f"{len(rows)} of {bd} output block-rows (norm maps of those block-rows of "
                      f"A and B, their pair tests and block products), {dt:.1f} s, "
                      f"extrapolated x{bd / len(rows):.0f}",
@@ -733,7 +746,7 @@ def batch_cpu_baseline(mats, taus, leaf, ns, budget_s=15.0):
     t_full = t_used * total_n2 / n2
     dense = float(sum(2.0 * n ** 3 for n in ns))
     return {"value": dense / t_full / 1e12, "unit": "TFLOP/s (dense-equivalent, sum of 2N^3 / t)",
-            "cores": 1, "kind": "oracle",
+            "cores": blas_threads(), "kind": "oracle",
             "sample": f"{len(done)} whole instances (N = {min(done)}..{max(done)}), "
                       f"{t_used:.1f} s, extrapolated by sum N^2 (x{total_n2 / n2:.1f})",
             "seconds_full_extrapolated": t_full}
@@ -1008,8 +1021,8 @@ def run_reference(args):
         "config": {"workload": f"algebraic decay (|i-j|+1)^-3 * (+-1), N={args.n}, leaf {leaf}, "
                                f"tau={tau:g}, {args.precision}",
                    "n": args.n, "leaf": leaf, "tau": tau, "precision": args.precision},
-        "cpu_baseline": {"value": value, "unit": cb["unit"], "cores": 1, "kind": "oracle",
-                         "sample": cb["sample"]},
+        "cpu_baseline": {"value": value, "unit": cb["unit"], "cores": blas_threads(),
+                         "kind": "oracle", "sample": cb["sample"]},
         "e2e": {"value": value, "unit": "TFLOP/s (dense-equivalent, 2N^3/t)",
                 "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
         "wall_seconds": wall,

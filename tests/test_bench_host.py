@@ -43,3 +43,12 @@ def test_spread_rows_cover_edges_evenly():
 
 def test_job_throughput_sums_ranks():
     assert bench.job_throughput(2.0e12, 1000.0, 4) == 8.0e12
+
+
+def test_blas_threads_reads_the_pins(monkeypatch):
+    for k in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS"):
+        monkeypatch.setenv(k, "1")
+    assert bench.blas_threads() == 1
+    monkeypatch.setenv("OMP_NUM_THREADS", "8")
+    monkeypatch.setenv("MKL_NUM_THREADS", "junk")
+    assert bench.blas_threads() == 8
