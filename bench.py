@@ -1068,6 +1068,7 @@ def main():
     if world > 1:
         import torch
         import torch.distributed as dist
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))   # before NCCL binds
         dist.init_process_group("nccl")
     runner = {"batch": run_batch, "sparse": run_sparse, "table2": run_table2}.get(args.workload, run_ours)
     line = runner(args, rank, world)
