@@ -110,3 +110,15 @@ def test_unknown_status_string(lib):
     assert lib.spamm_status_string(0) == b"ok"
     assert lib.spamm_status_string(5) == b"a bounded device wait timed out"
     assert lib.spamm_status_string(99) == b"unknown status"
+
+
+def test_batch_index_range_limit_without_gpu(lib):
+    """Tile ids and k slots of a batch are 32-bit on the device: one instance at the largest
+    block grid (1024^3 slots) fits, two of them (2^31 slots) are UNSUPPORTED."""
+    b = ctypes.c_size_t()
+    one = (ctypes.c_int64 * 1)(65536)
+    two = (ctypes.c_int64 * 2)(65536, 65536)
+    assert lib.spamm_batch_workspace_size(one, 1, 64, 0, ctypes.byref(b)) == 0
+    assert lib.spamm_batch_workspace_size(two, 2, 64, 0, ctypes.byref(b)) == 2
+    big = (ctypes.c_int64 * 1)((1 << 20) + 1)
+    assert lib.spamm_batch_workspace_size(big, 1, 128, 0, ctypes.byref(b)) == 2
