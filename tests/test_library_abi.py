@@ -122,3 +122,14 @@ def test_batch_index_range_limit_without_gpu(lib):
     assert lib.spamm_batch_workspace_size(two, 2, 64, 0, ctypes.byref(b)) == 2
     big = (ctypes.c_int64 * 1)((1 << 20) + 1)
     assert lib.spamm_batch_workspace_size(big, 1, 128, 0, ctypes.byref(b)) == 2
+
+
+def test_batch_of_one_holds_a_plan_and_its_norm_maps(lib):
+    """A batch of one instance provisions the plan's workspace plus both norm maps."""
+    for n, leaf, prec in ((1000, 64, 4), (4096, 128, 1), (777, 32, 0)):
+        pw, bw = ctypes.c_size_t(), ctypes.c_size_t()
+        assert lib.spamm_plan_workspace_size(n, leaf, prec, ctypes.byref(pw)) == 0
+        ns = (ctypes.c_int64 * 1)(n)
+        assert lib.spamm_batch_workspace_size(ns, 1, leaf, prec, ctypes.byref(bw)) == 0
+        bd = -(-n // leaf)
+        assert bw.value >= pw.value + 2 * 8 * bd * bd
