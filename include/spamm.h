@@ -215,10 +215,18 @@ spamm_status_t spamm_frobenius_diff(const float* X, const float* Y, int64_t coun
  *   tau       as for spamm_plan.
  * Its scratch is a 1 MiB array in the library's device memory (static, one
  * per device, kept until the process exits).  The first call on a device
- * looks that array up with cudaGetSymbolAddress: make it before any stream
- * capture on that device.  Every call on a device shares the array and
- * leaves its contents behind; calls that overlap on the GPU race on it and
- * must be serialised by the caller.  Asynchronous on `stream`.
+ * looks that array up with cudaGetSymbolAddress; under lazy module loading
+ * (the CUDA default) that is also when the library's device code is loaded
+ * onto the device, so that one call may allocate driver memory for the
+ * module and synchronise.  Make it at set-up (n = 1 is enough), before any
+ * stream capture on that device.  The address is kept per CUDA context (by
+ * the context's unique id): after cudaDeviceReset the next call looks it up
+ * again.  Every call on a device shares the array and leaves its contents
+ * behind; calls that overlap on the GPU race on it and must be serialised by
+ * the caller.  A bounded wait of its norm maps that runs out latches
+ * SPAMM_ERR_TIMEOUT in this entry point's own static status word, which
+ * spamm_last_device_status reads and clears along with the library's.
+ * Asynchronous on `stream`.
  * ------------------------------------------------------------------------- */
 spamm_status_t spamm_multiply_fp32_noalloc(const float* A, const float* B, float* C, int64_t n,
                                            int32_t leaf, double tau, void* stream);
@@ -401,7 +409,9 @@ spamm_status_t spamm_mlp_train(float* weights, float* m, float* v, int32_t t0, c
  * Status helpers.
  * spamm_status_string: static description of a status code.
  * spamm_last_device_status: reads and clears the library's device status word
- *   for the current device (0 = clean, else a spamm_status_t).  Blocks.
+ *   for the current device, and the static one of spamm_multiply_fp32_noalloc
+ *   once that entry point has run in the current context (0 = clean, else a
+ *   spamm_status_t; the library's word first when both are set).  Blocks.
  * ------------------------------------------------------------------------- */
 const char* spamm_status_string(spamm_status_t status);
 spamm_status_t spamm_last_device_status(void* stream, int32_t* code);

@@ -327,3 +327,60 @@ def accumulation_bound(nA, nB, surv, mode: int, leaf: int) -> float:
         tot.append(np.where(surv[i], g * p, 0.0).sum(axis=0))
     tot = np.concatenate(tot)
     return math.sqrt(math.fsum((tot * tot).tolist()))
+
+
+# ---------------------------------------------------------------------------
+# The same bounds tile by tile.  Both totals above are tile-orthogonal: each is
+# sqrt(sum over output tiles of t_ij^2) with t_ij a bound on the Frobenius
+# error of tile (i, j) alone.  These return the t_ij themselves ([bd, bd]), so
+# a test can hold every tile to its own share instead of only the total (on a
+# decay matrix the off-diagonal tiles are orders of magnitude below ||C||_F,
+# and a whole-matrix check cannot see an error there).
+# ---------------------------------------------------------------------------
+
+def apriori_tile_bounds(nA, nB, surv, mode: int, leaf: int, flags=None) -> np.ndarray:
+    """t_ij = sum over surviving k of (c_ikj + g) p_ikj: bound on the tile's ||C_mode - C_exact||_F,
+    with c_ikj and g as in :func:`apriori_bound` (g from the largest survivor count)."""
+    bd = nA.shape[0]
+    kmax = int(surv.sum(axis=1).max()) if surv.any() else 0
+    g = accumulation_coeff(mode, leaf, kmax)
+    c_plain = triple_error_coeff(mode, False, leaf)
+    c_split = triple_error_coeff(mode, True, leaf) if mode != FP32 else 0.0
+    out = np.zeros((bd, bd))
+    for i in range(bd):
+        p = nA[i, :, None] * nB                      # [k, j]
+        if mode == TF32X3:
+            coeff = np.full_like(p, c_split)
+        elif flags is not None and mode in (BF16_SPLIT, FP16_SPLIT):
+            coeff = np.where(flags[i], c_split, c_plain)
+        else:
+            coeff = np.full_like(p, c_plain)
+        out[i] = np.where(surv[i], (coeff + g) * p, 0.0).sum(axis=0)
+    return out
+
+
+def accumulation_tile_bounds(nA, nB, surv, mode: int, leaf: int) -> np.ndarray:
+    """t_ij = sum over surviving k of g p_ikj (doubled in split modes, as in
+    :func:`accumulation_bound`): bound on the tile's distance from the FP64 evaluation of
+    the same rounded operands."""
+    bd = nA.shape[0]
+    kmax = int(surv.sum(axis=1).max()) if surv.any() else 0
+    g = accumulation_coeff(mode, leaf, kmax)
+    if mode_is_split(mode):
+        g *= 2.0
+    out = np.zeros((bd, bd))
+    for i in range(bd):
+        p = nA[i, :, None] * nB
+        out[i] = np.where(surv[i], g * p, 0.0).sum(axis=0)
+    return out
+
+
+def tile_errors(x: np.ndarray, y: np.ndarray, leaf: int) -> np.ndarray:
+    """||X[i,j] - Y[i,j]||_F per leaf tile of two n x n matrices ([bd, bd], FP64, the ragged
+    edge tiles cover only their in-range entries)."""
+    d = np.asarray(x, dtype=np.float64) - np.asarray(y, dtype=np.float64)
+    n = d.shape[0]
+    bd = -(-n // leaf)
+    p = np.zeros((bd * leaf, bd * leaf))
+    p[:n, :n] = d * d
+    return np.sqrt(p.reshape(bd, leaf, bd, leaf).sum(axis=(1, 3)))

@@ -147,6 +147,18 @@ def _bad(where: str, what: str):
     raise SpammError(1, f"{where}: {what}")
 
 
+def _current_index() -> int:
+    """Index of the current CUDA device: the library launches every kernel there, so every
+    tensor of a call must live on it (a tensor on another GPU would be read through an
+    address that GPU 0 cannot reach)."""
+    import torch
+    return torch.cuda.current_device()
+
+
+def _index_of(t) -> int:
+    return t.device.index if t.device.index is not None else 0
+
+
 def _tensor(t, where: str, name: str, dtype, numel=None, square=None, min_numel=None):
     """Pointer of ``t`` after checking device, dtype, contiguity and size.
 
@@ -157,6 +169,9 @@ def _tensor(t, where: str, name: str, dtype, numel=None, square=None, min_numel=
         _bad(where, f"{name} is not a tensor")
     if t.device.type != _DEVICE_TYPE:
         _bad(where, f"{name} is on {t.device}, not on the GPU")
+    cur = _current_index()
+    if _index_of(t) != cur:
+        _bad(where, f"{name} is on {t.device}, but the current device is {cur}")
     if t.dtype != dtype:
         _bad(where, f"{name} is {t.dtype}, expected {dtype}")
     if not t.is_contiguous():
@@ -173,15 +188,19 @@ def _tensor(t, where: str, name: str, dtype, numel=None, square=None, min_numel=
 _F32 = None
 
 
-def _mat_ptr(t, where: str, name, n: int) -> int:
-    """Address of an n x n contiguous FP32 GPU tensor (fast path; _tensor names the fault)."""
+def _mat_ptr(t, where: str, name, n: int, dev=None) -> int:
+    """Address of an n x n contiguous FP32 tensor on the current GPU (fast path; _tensor names
+    the fault).  ``dev``: the current device index, when the caller already has it."""
     global _F32
     if _F32 is None:
         import torch
         _F32 = torch.float32
+    if dev is None:
+        dev = _current_index()
     try:
         ok = (t.dtype is _F32 and t.shape == (n, n) and t.is_contiguous() and
-              (t.is_cuda if _DEVICE_TYPE == "cuda" else t.device.type == _DEVICE_TYPE))
+              (t.is_cuda and t.get_device() == dev if _DEVICE_TYPE == "cuda" else
+               t.device.type == _DEVICE_TYPE and _index_of(t) == dev))
     except AttributeError:
         ok = False
     if not ok:
@@ -402,11 +421,13 @@ def _problems(As, Bs, Cs, taus, where: str, ns=None):
     if ns is not None and count != len(ns):
         _bad(where, f"{count} problems for a batch of {len(ns)}")
     arr = (Problem * count)()
+    dev = _current_index()
     for i in range(count):
         A = As[i]
         n = _side(A, where, f"As[{i}]") if ns is None else ns[i]
-        arr[i] = Problem(_mat_ptr(A, where, ("As", i), n), _mat_ptr(Bs[i], where, ("Bs", i), n),
-                         None if Cs is None else _mat_ptr(Cs[i], where, ("Cs", i), n),
+        arr[i] = Problem(_mat_ptr(A, where, ("As", i), n, dev),
+                         _mat_ptr(Bs[i], where, ("Bs", i), n, dev),
+                         None if Cs is None else _mat_ptr(Cs[i], where, ("Cs", i), n, dev),
                          n, float(taus[i]))
     return arr
 

@@ -723,9 +723,12 @@ spamm_status_t spamm_last_device_status(void* stream, int32_t* code) {
   int32_t* w = device_status_word();
   if (!w) return SPAMM_ERR_CUDA;
   cudaStream_t s = (cudaStream_t)stream;
+  int32_t other = 0;
   SPAMM_CUDA_TRY(cudaMemcpyAsync(code, w, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
   SPAMM_CUDA_TRY(cudaMemsetAsync(w, 0, sizeof(int32_t), s));
+  SPAMM_CUDA_TRY(noalloc_take_status(s, &other));   // the no-allocation entry point's word
   SPAMM_CUDA_TRY(cudaStreamSynchronize(s));
+  if (*code == 0) *code = other;
   return SPAMM_OK;
 }
 

@@ -69,4 +69,9 @@ spamm_status_t export_queues(const PlanBuffers& b, const Inst& in, int32_t* tile
 // kernels latch timeouts there).
 int32_t* device_status_word();
 
+// The no-allocation entry point's own status word on the current device:
+// copied to *code (host) and cleared, asynchronously on `s`; *code = 0 when
+// that entry point has not run in the current context.
+cudaError_t noalloc_take_status(cudaStream_t s, int32_t* code);
+
 }  // namespace spamm

@@ -32,6 +32,7 @@ def rec(monkeypatch):
     monkeypatch.setattr(P, "_DEVICE_TYPE", "cpu")
     monkeypatch.setattr(P, "_PARAMS", 8449)
     monkeypatch.setattr(P, "_stream", lambda stream: 0)
+    monkeypatch.setattr(P, "_current_index", lambda: 0)
     return r
 
 
@@ -145,3 +146,31 @@ def test_batch_tables_are_checked(rec):
     assert "As[1]" in _invalid(P.spamm_multiply_batched, [As[0], As[1].t()], Bs, Cs,
                                [0.1, 0.2], 32)
     assert rec.calls == []
+
+
+def test_tensors_on_another_device_are_rejected(rec, monkeypatch):
+    """Every operand must live on the current device, where the library launches: with the
+    current device mocked as 1, tensors of device 0 are refused before any pointer reaches the
+    library, by the general check and by the batch's fast path alike."""
+    n, leaf = 100, 32
+    bd = P.num_blocks(n, leaf)
+    A, B, C = _m(n), _m(n), _m(n)
+    nA = torch.zeros(bd, bd, dtype=torch.float64)
+    pl = _plan(n, leaf)
+    ns = [64, 100]
+    As, Bs, Cs = [_m(k) for k in ns], [_m(k) for k in ns], [_m(k) for k in ns]
+    b = P.Batch(ns, 32, P.FP32, graph=False)
+    rec.calls.clear()
+    monkeypatch.setattr(P, "_current_index", lambda: 1)
+    assert "current device is 1" in _invalid(pl.multiply, A, B, C)
+    assert "current device is 1" in _invalid(pl.plan, nA, nA, 0.1)
+    assert "current device is 1" in _invalid(P.spamm_normmap, A, leaf)
+    assert "current device is 1" in _invalid(P.spamm_frobenius_diff, torch.zeros(7))
+    assert "current device is 1" in _invalid(P.spamm_multiply_fp32_noalloc, A, B, C, leaf, 0.1)
+    assert "current device is 1" in _invalid(b.run, As, Bs, Cs, [0.1, 0.2])
+    assert "current device is 1" in _invalid(P.spamm_multiply_batched, As, Bs, Cs, [0.1, 0.2], 32)
+    assert rec.calls == []
+    monkeypatch.setattr(P, "_current_index", lambda: 0)
+    pl.multiply(A, B, C)
+    b.run(As, Bs, Cs, [0.1, 0.2])
+    assert rec.calls == ["spamm_multiply", "spamm_batch_run"]

@@ -220,6 +220,11 @@ def _fp32_case(a, b, leaf, tau):
     scale = S.frobenius(ref)
     assert err <= FP32_REL_TOL * scale + 1e-30
     assert err <= OP.accumulation_bound(nA, nB, surv, OP.FP32, leaf) + 1e-30
+    # tile by tile: each output tile within its own share of the accumulation bound (a tile
+    # written wrongly or in the wrong place fails here even when it is tiny next to ||C||_F;
+    # tiles without survivors must be exact zeros)
+    t = OP.accumulation_tile_bounds(nA, nB, surv, OP.FP32, leaf)
+    assert np.all(OP.tile_errors(got, ref, leaf) <= t), "a tile exceeds its own bound"
     return got, ref, surv
 
 

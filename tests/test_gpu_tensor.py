@@ -58,14 +58,17 @@ def test_tc_matches_emulation(name, mode, n, leaf, family, q):
     tau = float(np.quantile(p[p > 0], q)) if q > 0 else 0.0
     got, surv, flags, st, gA, gB = _run(a, b, leaf, tau, mode, 1e-6)
     assert np.isfinite(got).all()
-    if mode == OP.TF32X3:
-        assert flags.sum() == 0 or True
     emu = OP.emulated_multiply(a, b, leaf, surv, mode, flags)
     acc_bound = OP.accumulation_bound(nA, nB, surv, mode, leaf)
     assert S.frobenius(got - emu) <= acc_bound + 1e-30, (S.frobenius(got - emu), acc_bound)
     exact = S.multiply_with_skipset(a, b, leaf, surv)
     fl = flags if mode in (OP.BF16_SPLIT, OP.FP16_SPLIT) else None
     assert S.frobenius(got - exact) <= OP.apriori_bound(nA, nB, surv, mode, leaf, fl) + 1e-30
+    # tile by tile: each output tile within its own share of both bounds
+    t_acc = OP.accumulation_tile_bounds(nA, nB, surv, mode, leaf)
+    assert np.all(OP.tile_errors(got, emu, leaf) <= t_acc), "a tile exceeds its accumulation share"
+    t_ap = OP.apriori_tile_bounds(nA, nB, surv, mode, leaf, fl)
+    assert np.all(OP.tile_errors(got, exact, leaf) <= t_ap), "a tile exceeds its a-priori share"
 
 
 @pytest.mark.parametrize("name,mode", [("bf16_split", OP.BF16_SPLIT), ("fp16_split", OP.FP16_SPLIT)])
@@ -102,6 +105,8 @@ def test_tc_all_skipped_and_tau0(name, mode):
     nA, nB = S.normmap(a, leaf), S.normmap(b, leaf)
     fl = flags if mode in (OP.BF16_SPLIT, OP.FP16_SPLIT) else None
     assert S.frobenius(got - dense) <= OP.apriori_bound(nA, nB, surv, mode, leaf, fl) * 1.0001
+    t_ap = OP.apriori_tile_bounds(nA, nB, surv, mode, leaf, fl)
+    assert np.all(OP.tile_errors(got, dense, leaf) <= t_ap * 1.0001)
 
 
 def test_bf16_split_c2_full_size_sampled():

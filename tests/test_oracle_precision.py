@@ -340,3 +340,82 @@ def test_accumulation_bound_on_pruned_signed_inputs(mode):
     for toward_zero in (False, True):
         sim = _tensor_chain(a, b, leaf, surv, mode, flags, toward_zero).astype(np.float64)
         assert np.linalg.norm(sim - emu) <= bound
+
+
+# --------------------------------------------------------------------------- per-tile bounds
+
+def _decay_pair(n=320, seed=81, alpha=0.05):
+    return synth.exp_decay_normal(n, alpha, seed), synth.exp_decay_normal(n, alpha, seed + 1)
+
+
+@pytest.mark.parametrize("mode", [P.BF16, P.FP16_SPLIT, P.TF32X3])
+def test_tile_bounds_are_the_shares_of_the_totals(mode):
+    a, b = _decay_pair()
+    leaf = 64
+    nA, nB = S.normmap(a, leaf), S.normmap(b, leaf)
+    surv = S.flat_survivors(nA, nB, 1e-3)
+    flags = surv.copy() if mode == P.FP16_SPLIT else None
+    t_ap = P.apriori_tile_bounds(nA, nB, surv, mode, leaf, flags)
+    t_ac = P.accumulation_tile_bounds(nA, nB, surv, mode, leaf)
+    assert t_ap.shape == (nA.shape[0],) * 2
+    assert math.isclose(math.sqrt(math.fsum((t_ap * t_ap).ravel().tolist())),
+                        P.apriori_bound(nA, nB, surv, mode, leaf, flags), rel_tol=1e-12)
+    assert math.isclose(math.sqrt(math.fsum((t_ac * t_ac).ravel().tolist())),
+                        P.accumulation_bound(nA, nB, surv, mode, leaf), rel_tol=1e-12)
+    # a tile without survivors has a zero bound, so a check against it demands exact zeros
+    assert np.all(t_ap[~surv.any(axis=1)] == 0.0)
+
+
+@pytest.mark.parametrize("mode", [P.BF16, P.FP16, P.TF32X3, P.BF16_SPLIT])
+def test_apriori_tile_bounds_hold_tile_by_tile(mode):
+    """Every tile of the emulated product (even the off-diagonal ones, many decades below
+    ||C||_F) stays within its own a-priori share."""
+    a, b = _decay_pair(alpha=0.1)
+    leaf = 64
+    nA, nB = S.normmap(a, leaf), S.normmap(b, leaf)
+    surv = S.flat_survivors(nA, nB, 0.0)
+    flags = None
+    if mode == P.BF16_SPLIT:
+        flags = P.flag_mask(nA, nB, surv, -6, S.frobenius(a), S.frobenius(b))
+    emu = P.emulated_multiply(a, b, leaf, surv, mode, flags)
+    exact = S.multiply_with_skipset(a, b, leaf, surv)
+    err = P.tile_errors(emu, exact, leaf)
+    t = P.apriori_tile_bounds(nA, nB, surv, mode, leaf, flags)
+    assert np.all(err <= t)
+    assert t.max() / t.min() > 1e3          # the tiles span several decades
+
+
+@pytest.mark.parametrize("mode", [P.FP16, P.BF16_SPLIT])
+def test_accumulation_tile_bounds_cover_simulated_chains(mode):
+    n, leaf = 200, 64
+    a, b = synth.exp_decay_normal(n, 0.02, 77), synth.exp_decay_normal(n, 0.02, 78)
+    nA, nB = S.normmap(a, leaf), S.normmap(b, leaf)
+    surv = S.flat_survivors(nA, nB, 0.0)
+    flags = surv.copy() if mode == P.BF16_SPLIT else None
+    emu = P.emulated_multiply(a, b, leaf, surv, mode, flags)
+    t = P.accumulation_tile_bounds(nA, nB, surv, mode, leaf)
+    for toward_zero in (False, True):
+        sim = _tensor_chain(a, b, leaf, surv, mode, flags, toward_zero).astype(np.float64)
+        assert np.all(P.tile_errors(sim, emu, leaf) <= t)
+    sim = _fma_chain_fp32(a, b, leaf, surv).astype(np.float64)
+    ref = S.multiply_with_skipset(a, b, leaf, surv)
+    assert np.all(P.tile_errors(sim, ref, leaf) <= P.accumulation_tile_bounds(nA, nB, surv,
+                                                                              P.FP32, leaf))
+
+
+def test_tile_check_catches_an_error_the_total_misses():
+    """A planted mistake in a small off-diagonal tile (its entries written with the wrong sign)
+    keeps the whole-matrix error inside the total bound but breaks that tile's own bound."""
+    a, b = _decay_pair()
+    leaf = 64
+    nA, nB = S.normmap(a, leaf), S.normmap(b, leaf)
+    surv = S.flat_survivors(nA, nB, 0.0)
+    emu = P.emulated_multiply(a, b, leaf, surv, P.BF16)
+    exact = S.multiply_with_skipset(a, b, leaf, surv)
+    bad = emu.copy()
+    bad[0:leaf, 3 * leaf:4 * leaf] *= -1.0            # tile (0, 3): far from the diagonal
+    total = P.apriori_bound(nA, nB, surv, P.BF16, leaf)
+    assert S.frobenius(bad - exact) <= total
+    t = P.apriori_tile_bounds(nA, nB, surv, P.BF16, leaf)
+    assert not np.all(P.tile_errors(bad, exact, leaf) <= t)
+    assert np.all(P.tile_errors(emu, exact, leaf) <= t)
