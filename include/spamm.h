@@ -406,6 +406,45 @@ spamm_status_t spamm_mlp_train(float* weights, float* m, float* v, int32_t t0, c
                                void* stream);
 
 /* ---------------------------------------------------------------------------
+ * Choosing tau for a target error -- the arbiter and fallback of the learned
+ * tau.  The paper searches tau for a valid ratio (Section 3.5.2); these
+ * calls choose it for the pruning error of Eq. 5 relative to the operands,
+ * e(tau) = ||AB - SpAMM(A, B, tau)||_F / (||A||_F ||B||_F), without forming AB.
+ * All use the plan's buffers (plan again with spamm_plan afterwards) and block.
+ *
+ * spamm_tau_certify: *tau_ref = the largest tau = ||A|| ||B|| 10^x, x found
+ *   by 36 bisection steps over [-60, 0], whose skipped bound2 is <=
+ *   ref_rel ||A|| ||B|| (so ||AB - SpAMM(tau_ref)||_F <= ref_rel ||A|| ||B||);
+ *   0 when ||A|| ||B|| is 0 or not finite.  *norm_ab (may be NULL) =
+ *   ||A||_F ||B||_F from the norm maps.  ref_rel in (0, inf).
+ * spamm_tau_error: *err = e(tau) up to ref_rel: 0 when tau <= tau_ref, else
+ *   ||C_band||_F / (||A|| ||B||), C_band the FP32 product over the triples with
+ *   tau_ref <= p < tau (a band plan and the SIMT multiply into `scratch`).
+ *   A, B device FP32 n x n as for spamm_multiply; scratch device FP32 n x n,
+ *   16-byte aligned, aliasing neither, overwritten.
+ * spamm_tau_select: tau for target_rel_err in (0, inf).  tau_ref is
+ *   certified at ref_rel = 1e-11.  With `weights` (device FP32 [8449], the
+ *   network of spamm_tau_predict) the predicted tau is checked once with
+ *   spamm_tau_error and returned if e <= target.  Otherwise (a miss, or
+ *   weights == NULL) bisection on e: lo = 0, hi = target ||A|| ||B||; if e(hi)
+ *   <= target, hi moves up by factors of 10 while admissible, else down by
+ *   factors of 10 until an admissible tau is found; then hi := sqrt(lo hi) or
+ *   lo := sqrt(lo hi) until hi / lo <= 1.01, at most 40 evaluations of e in
+ *   all.  *tau = the largest admissible tau tested (0 if none), *evals
+ *   (may be NULL) = evaluations of e including the network's check,
+ *   *achieved (may be NULL) = e(*tau).
+ * ------------------------------------------------------------------------- */
+spamm_status_t spamm_tau_certify(spamm_plan_t plan, const double* normA, const double* normB,
+                                 double ref_rel, double* tau_ref, double* norm_ab, void* stream);
+spamm_status_t spamm_tau_error(spamm_plan_t plan, const double* normA, const double* normB,
+                               const float* A, const float* B, double tau, double tau_ref,
+                               float* scratch, double* err, void* stream);
+spamm_status_t spamm_tau_select(spamm_plan_t plan, const double* normA, const double* normB,
+                                const float* A, const float* B, double target_rel_err,
+                                const float* weights, float* scratch, double* tau,
+                                int32_t* evals, double* achieved, void* stream);
+
+/* ---------------------------------------------------------------------------
  * Status helpers.
  * spamm_status_string: static description of a status code.
  * spamm_last_device_status: reads and clears the library's device status word

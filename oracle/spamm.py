@@ -291,12 +291,22 @@ def normmap_rows(x: np.ndarray, leaf: int, rows) -> np.ndarray:
     return out
 
 
+def block64(x: np.ndarray, leaf: int, i: int, k: int) -> np.ndarray:
+    """FP64 copy of leaf block X[i, k] of an unpadded n x n matrix, zero padded to leaf x leaf
+    (the same values as ``block(padded64(x), ...)`` without copying the whole matrix)."""
+    n = x.shape[0]
+    out = np.zeros((leaf, leaf))
+    r0, c0 = i * leaf, k * leaf
+    r1, c1 = min(n, r0 + leaf), min(n, c0 + leaf)
+    out[:r1 - r0, :c1 - c0] = x[r0:r1, c0:c1]
+    return out
+
+
 def spamm_rows(a: np.ndarray, b: np.ndarray, leaf: int, tau: float, rows,
                nA_rows: np.ndarray, nB: np.ndarray) -> dict:
     """Block-rows ``rows`` of C by the flat rule: {i: (C strip [leaf, n], surviving (k, j))}."""
     n = a.shape[0]
     bd = num_blocks(n, leaf)
-    pb = padded64(b, leaf)
     out = {}
     for r, i in enumerate(rows):
         lo, hi = i * leaf, min(n, (i + 1) * leaf)
@@ -307,6 +317,35 @@ def spamm_rows(a: np.ndarray, b: np.ndarray, leaf: int, tau: float, rows,
         for j in range(bd):
             for k in np.nonzero(surv[:, j])[0]:
                 c[:, j * leaf:(j + 1) * leaf] += (a_strip[:, k * leaf:(k + 1) * leaf]
-                                                  @ block(pb, leaf, k, j))
+                                                  @ block64(b, leaf, k, j))
         out[i] = (c[:hi - lo, :n], surv)
+    return out
+
+
+def needed_b_rows(nA_rows: np.ndarray, tau: float):
+    """Block rows k of B's norm map that can decide a triple of the given block rows of C.
+
+    For tau > 0, a triple (i, k, j) with nA[i, k] = 0 has p = 0 * nB[k, j] = 0 < tau for
+    every finite nB[k, j], so it is skipped whatever row k of B holds; only the k with a
+    non-zero (or non-finite) nA[i, k] in some sampled row are needed.  Every k is needed
+    for tau = 0.  (With a non-finite entry in row k of B, p would be NaN and survive: the
+    caller checks that B is finite before relying on this.)
+    """
+    if not tau > 0.0:
+        return np.arange(nA_rows.shape[1])
+    return np.nonzero(np.any(nA_rows != 0.0, axis=0))[0]
+
+
+def normmap_needed(b: np.ndarray, leaf: int, nA_rows: np.ndarray, tau: float) -> np.ndarray:
+    """B's [bd, bd] norm map with only the rows :func:`needed_b_rows` computed (Eq. 2, exactly
+    rounded sums) and the others 0.  For the sampled block rows of C, :func:`spamm_rows` makes
+    the same decisions with it as with the full map when tau > 0 and B is finite (checked)."""
+    n = b.shape[0]
+    bd = num_blocks(n, leaf)
+    ks = needed_b_rows(nA_rows, tau)
+    if tau > 0.0 and ks.size < bd and not np.isfinite(b).all():
+        ks = np.arange(bd)
+    out = np.zeros((bd, bd))
+    if ks.size:
+        out[ks] = normmap_rows(b, leaf, ks)
     return out

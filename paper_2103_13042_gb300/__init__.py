@@ -97,6 +97,10 @@ _SIGS = {
                         ctypes.c_float, _VP, _VP],
     "spamm_batch_autotune": [_VP, _I32, _I32, _D, _I32, _VP, ctypes.POINTER(Tune), _VP,
                              ctypes.POINTER(_I32)],
+    "spamm_tau_certify": [_VP, _VP, _VP, _D, ctypes.POINTER(_D), ctypes.POINTER(_D), _VP],
+    "spamm_tau_error": [_VP, _VP, _VP, _VP, _VP, _D, _D, _VP, ctypes.POINTER(_D), _VP],
+    "spamm_tau_select": [_VP, _VP, _VP, _VP, _VP, _D, _VP, _VP, ctypes.POINTER(_D),
+                         ctypes.POINTER(_I32), ctypes.POINTER(_D), _VP],
 }
 
 
@@ -368,6 +372,45 @@ class Plan:
                                           _norms(normB, w, "normB", self.bd),
                                           out.ctypes.data_as(ctypes.c_void_p), _stream(stream)), w)
         return out
+
+    def tau_certify(self, normA, normB, ref_rel: float = 1e-11, stream=None):
+        """(tau_ref, ||A||_F ||B||_F): the largest tau on the certification grid whose skipped
+        bound2 is <= ref_rel ||A|| ||B||."""
+        t, ab = ctypes.c_double(), ctypes.c_double()
+        w = "spamm_tau_certify"
+        _check(lib().spamm_tau_certify(self.handle, _norms(normA, w, "normA", self.bd),
+                                       _norms(normB, w, "normB", self.bd), float(ref_rel),
+                                       ctypes.byref(t), ctypes.byref(ab), _stream(stream)), w)
+        return t.value, ab.value
+
+    def tau_error(self, normA, normB, A, B, tau: float, tau_ref: float, scratch,
+                  stream=None) -> float:
+        """e(tau) = ||AB - SpAMM(tau)||_F / (||A|| ||B||) up to the certified tau_ref's bound."""
+        out = ctypes.c_double()
+        w, n, bd = "spamm_tau_error", self.n, self.bd
+        _check(lib().spamm_tau_error(self.handle, _norms(normA, w, "normA", bd),
+                                     _norms(normB, w, "normB", bd), _mat(A, w, "A", n),
+                                     _mat(B, w, "B", n), float(tau), float(tau_ref),
+                                     _mat(scratch, w, "scratch", n), ctypes.byref(out),
+                                     _stream(stream)), w)
+        return out.value
+
+    def tau_select(self, normA, normB, A, B, target_rel_err: float, weights=None, scratch=None,
+                   stream=None):
+        """(tau, evaluations of e, e(tau)): the network's tau checked once, bisection on the
+        error on a miss (or without weights)."""
+        import torch
+        w, n, bd = "spamm_tau_select", self.n, self.bd
+        if scratch is None:
+            scratch = torch.empty_like(A)
+        t, k, e = ctypes.c_double(), ctypes.c_int32(), ctypes.c_double()
+        _check(lib().spamm_tau_select(self.handle, _norms(normA, w, "normA", bd),
+                                      _norms(normB, w, "normB", bd), _mat(A, w, "A", n),
+                                      _mat(B, w, "B", n), float(target_rel_err),
+                                      None if weights is None else _weights(weights, w),
+                                      _mat(scratch, w, "scratch", n), ctypes.byref(t),
+                                      ctypes.byref(k), ctypes.byref(e), _stream(stream)), w)
+        return t.value, k.value, e.value
 
     def tau_predict(self, normA, normB, target_rel_err: float, weights, stream=None) -> float:
         """The network's tau for this plan's shape (weights: device float32 [8449])."""

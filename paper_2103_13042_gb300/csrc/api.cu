@@ -8,12 +8,6 @@
 
 using namespace spamm;
 
-struct spamm_plan_s {
-  int64_t n = 0;
-  int32_t bd = 0;
-  spamm::Engine eng;
-};
-
 namespace spamm {
 
 namespace {

@@ -75,3 +75,10 @@ int32_t* device_status_word();
 cudaError_t noalloc_take_status(cudaStream_t s, int32_t* code);
 
 }  // namespace spamm
+
+// A single-instance plan (the C ABI's spamm_plan_t).
+struct spamm_plan_s {
+  int64_t n = 0;
+  int32_t bd = 0;
+  spamm::Engine eng;
+};

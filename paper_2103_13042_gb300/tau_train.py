@@ -48,14 +48,14 @@ def _lib():
 
 
 class ErrorMeter:
-    """Achieved relative pruning error of one (A, B) pair at any tau (band products)."""
+    """Achieved relative pruning error of one (A, B) pair at any tau, through the library's
+    spamm_tau_certify (tau_ref) and spamm_tau_error (band products)."""
 
     def __init__(self, n: int, device):
         import torch
         P = _lib()
         self.n = n
         self.plan = P.Plan(n, LEAF, P.FP32)
-        self.band_plan = P.Plan(n, LEAF, P.FP32)
         bd = P.num_blocks(n, LEAF)
         self.nA = torch.empty((bd, bd), dtype=torch.float64, device=device)
         self.nB = torch.empty_like(self.nA)
@@ -67,65 +67,22 @@ class ErrorMeter:
         self.A, self.B = A, B
         P.spamm_normmap(A, LEAF, self.nA)
         P.spamm_normmap(B, LEAF, self.nB)
-        st = self.plan.plan(self.nA, self.nB, 0.0).stats()
-        self.ab = st["norm_a"] * st["norm_b"]
-        # certified reference: largest tau (log bisection) with bound2 <= REF_REL |A||B|
-        lo, hi = -60.0, 0.0
-        for _ in range(36):
-            mid = 0.5 * (lo + hi)
-            s = self.plan.plan(self.nA, self.nB, self.ab * 10.0 ** mid).stats()
-            if s["skipped_bound2"] <= REF_REL * self.ab:
-                lo = mid
-            else:
-                hi = mid
-        self.tau_ref = self.ab * 10.0 ** lo
+        self.tau_ref, self.ab = self.plan.tau_certify(self.nA, self.nB, REF_REL)
         return self
 
     def error(self, tau: float) -> float:
         """e(tau) = ||AB - SpAMM(tau)||_F / (||A|| ||B||) up to the certified REF_REL."""
-        P = _lib()
         self.evals += 1
-        if tau <= self.tau_ref:
-            return 0.0
-        self.band_plan.band(self.nA, self.nB, self.tau_ref, tau)
-        self.band_plan.multiply(self.A, self.B, self.T)
-        return P.spamm_frobenius_diff(self.T) / self.ab
+        return self.plan.tau_error(self.nA, self.nB, self.A, self.B, tau, self.tau_ref, self.T)
+
+    def select(self, eps: float, weights=None):
+        """(tau, evaluations, e(tau)) of spamm_tau_select: the network's tau checked once with
+        bisection on a miss, or plain bisection without weights."""
+        return self.plan.tau_select(self.nA, self.nB, self.A, self.B, eps, weights, self.T)
 
     def histogram(self):
         h = self.plan.histogram(self.nA, self.nB).astype(np.float64)
         return h / h.sum()
-
-
-def bisect_on_error(meter: ErrorMeter, eps: float, tau0: float, max_steps: int = 40,
-                    ratio: float = 1.01):
-    """Largest tested tau with e(tau) <= eps: bracket by factors of 10 from tau0,
-    then geometric bisection until hi / lo <= ratio.  Returns (tau, evaluations)."""
-    e0 = meter.evals
-
-    def ok(t):
-        return meter.error(t) <= eps
-
-    lo, hi = 0.0, float(tau0)
-    if ok(hi):
-        lo, hi = hi, hi * 10.0
-        while meter.evals - e0 < max_steps and ok(hi):
-            lo, hi = hi, hi * 10.0
-    else:
-        t = hi / 10.0
-        while meter.evals - e0 < max_steps and t > meter.tau_ref:
-            if ok(t):
-                lo = t
-                break
-            hi, t = t, t / 10.0
-        if lo == 0.0:
-            return meter.tau_ref, meter.evals - e0
-    while hi / lo > ratio and meter.evals - e0 < max_steps:
-        mid = math.sqrt(lo * hi)
-        if ok(mid):
-            lo = mid
-        else:
-            hi = mid
-    return lo, meter.evals - e0
 
 
 def make_dataset(specs, device, sweep: int, seed: int, log=print):
@@ -199,7 +156,7 @@ def evaluate(W, specs, device, targets=TARGETS, log=print):
             t_check = time.perf_counter() - t0
             hit = e_p <= eps
             t1 = time.perf_counter()
-            tau_b, n_b = bisect_on_error(m, eps, tau0=m.ab * eps)
+            tau_b, n_b, _ = m.select(eps)            # plain bisection (no network)
             t_bis = time.perf_counter() - t1
             rows.append({"n": sp["n"], "kind": sp["kind"], "eps": eps, "tau_pred": tau_p,
                          "err_pred": e_p, "hit": bool(hit), "tau_bisect": tau_b,

@@ -3,8 +3,9 @@
 On fresh seeded decay pairs (a seed used neither for training nor for the
 held-out evaluation) the committed network's tau must meet the target error
 in most cases, and the time to an admissible tau (prediction, one error check,
-bisection only on a miss) must need fewer error evaluations than plain
-bisection on the error, which stays the fallback and the arbiter.
+bisection only on a miss: spamm_tau_select with the network) must need fewer
+error evaluations than plain bisection on the error (spamm_tau_select without
+it), which stays the fallback and the arbiter.
 """
 import numpy as np
 import pytest
@@ -32,16 +33,19 @@ def test_trained_network_beats_bisection():
             total += 1
             tau_p = m.plan.tau_predict(m.nA, m.nB, eps, W)
             e_p = m.error(tau_p)
-            tau_b, n_b = TT.bisect_on_error(m, eps, tau0=m.ab * eps)
-            e_b = m.error(tau_b)
+            tau_b, n_b, e_b = m.select(eps)          # plain bisection: spamm_tau_select
             assert e_b <= eps                       # the arbiter's own answer is admissible
+            assert m.error(tau_b) == e_b
+            tau_n, n_n, e_n = m.select(eps, W)       # network, one check, bisection on a miss
+            assert e_n <= eps
             bis_evals.append(n_b)
+            net_evals.append(n_n)
             if e_p <= eps:
                 hits += 1
-                net_evals.append(1)
+                assert n_n == 1 and tau_n == tau_p
                 ratios.append(tau_p / tau_b)
             else:
-                net_evals.append(1 + n_b)
+                assert n_n == 1 + n_b and tau_n == tau_b
     assert hits / total >= 0.75, hits / total
     assert np.mean(net_evals) < 0.5 * np.mean(bis_evals), (np.mean(net_evals), np.mean(bis_evals))
     # a hit is not an over-cautious tau: within three decades of the largest admissible one

@@ -325,3 +325,27 @@ def test_errors_three_normalisations():
     assert e["rel_ab"] == pytest.approx(1e-3 / 10.0, rel=1e-15)
     z = S.errors(ref, ref, 0.0, 0.0)
     assert z["abs"] == 0.0 and z["rel_c"] == 0.0 and z["rel_ab"] == 0.0
+
+
+def test_needed_b_rows_give_the_same_sampled_rows():
+    """spamm_rows with B's norm map restricted to the needed block rows equals spamm_rows with
+    the full map (decisions and values), on a decay pair whose far blocks are exactly zero."""
+    n, leaf = 600, 32
+    a = synth.exp_decay_normal(n, 2.0, 31)    # |i-j| beyond ~60 underflows to exact zeros
+    b = synth.exp_decay_normal(n, 2.0, 32)
+    bd = S.num_blocks(n, leaf)
+    rows = [0, 7, bd - 1]
+    nA_rows = S.normmap_rows(a, leaf, rows)
+    full = S.normmap(b, leaf)
+    for tau in (1e-30, 1e-6):
+        part = S.normmap_needed(b, leaf, nA_rows, tau)
+        ks = S.needed_b_rows(nA_rows, tau)
+        assert 0 < ks.size < bd
+        assert np.array_equal(part[ks], full[ks])
+        r_full = S.spamm_rows(a, b, leaf, tau, rows, nA_rows, full)
+        r_part = S.spamm_rows(a, b, leaf, tau, rows, nA_rows, part)
+        for i in rows:
+            assert np.array_equal(r_full[i][0], r_part[i][0])
+            assert np.array_equal(r_full[i][1], r_part[i][1])
+    # tau = 0 needs every row (a zero block survives at tau = 0)
+    assert S.needed_b_rows(nA_rows, 0.0).size == bd
