@@ -2,19 +2,21 @@
 
 A step is one pass of the hot path over the workload with inputs resident in
 HBM: norm map of A, norm map of B, the pair test / work-queue plan at tau,
-and the multiply that writes C.  The default workload is the mixed-precision
-decay case: N = 8192, a_ij = (|i-j|+1)^-3 * s_ij (s = +-1, A and B
-independent), leaf 64, BF16 block products with power-of-two block scaling,
-FP32 accumulation and hi+lo products on the dominant blocks, at the fixed
-relative error ||C - AB||_F / (||A||_F ||B||_F) <= 1e-5: tau = 1e-2 is the
-largest tau of the 1e-1..1e-7 sweep whose pruning error stays below it
-(1.4e-7), and the split flags keep the rounding inside the rest of the
-budget.  The metric is dense-equivalent throughput 2 N^3 / t (TFLOP/s);
-ms_per_step gives the time.  The plain FP32 SpAMM and cuBLAS SGEMM (TF32 off)
-are timed on the same GPU as baselines.
+and the multiply that writes C.  The default workload is the largest
+single-GPU configuration: N = 32768, a_ij = exp(-alpha |i-j|) * z_ij with
+z ~ N(0,1) and alpha = 0.5 (A and B independent, seeded numpy draws on the
+host), FP16 tensor-core block products with power-of-two block scaling and
+FP32 accumulation (the paper's tensor-core precision), tau = 1e-6, the leaf
+(64 or 128) and multiply schedule picked by the library's autotuner.  The
+metric is dense-equivalent throughput 2 N^3 / t (TFLOP/s); ms_per_step gives
+the time, and the line states the achieved error against the FP64 oracle on
+sampled block rows.  Plain FP32 SpAMM and cuBLAS SGEMM (TF32 off) are timed on
+the same GPU as baselines; the near-sparse N = 32768 product and the N = 8192
+algebraic-decay product are summarised in the same line (extra_workloads).
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                       [--precision fp32|bf16|...] [--tau T]
+                       [--workload decay|c2|batch|sparse|table2]
+                       [--precision fp32|bf16|...] [--tau T] [--alpha A]
 With N > 1 (torchrun) every rank runs an independent replica (the path does
 not shard); the value is the sum over ranks, timed by the slowest rank.
 """
@@ -28,7 +30,8 @@ import subprocess
 import sys
 import time
 
-# the CPU baseline is timed single-threaded: pin BLAS before numpy loads
+# the oracle's BLAS calls run single-threaded (the all-core timing uses worker
+# processes instead): pin BLAS before numpy loads
 os.environ.setdefault("OPENBLAS_NUM_THREADS", "1")
 os.environ.setdefault("OMP_NUM_THREADS", "1")
 os.environ.setdefault("MKL_NUM_THREADS", "1")
@@ -55,11 +58,19 @@ import synth  # noqa: E402
 
 METRIC = "SpAMM time & TFLOP/s at fixed rel. error vs plain FP32 SpAMM & cuBLAS; roofline %"
 
-# DRAM bytes (read + write) per launch from one ncu capture of the kernel as it
-# stands (profiles/kernels_mixed_n8192.md); an entry is removed whenever the
-# kernel changes, until it is captured again.
+# DRAM bytes (read + write) per launch of a kernel, from one ncu capture of the
+# kernel as it stands; an entry is removed whenever the kernel changes, until it
+# is captured again.
 NCU_TRAFFIC = {("normmap_staged_kernel", 8192, 64): 268.5e6 + 3.669e6}
-N_DEFAULT, LEAF_DEFAULT = 8192, 64
+
+# The synthetic workloads of a single product (one step = norm maps of A and B,
+# plan, multiply).  decay: exp(-alpha |i-j|) N(0,1), N = 32768, A and B
+# independent, the largest single-GPU configuration; c2: the algebraic-decay
+# mixed-precision configuration at N = 8192.
+WORKLOADS = {
+    "decay": {"n": 32768, "leaves": (64, 128), "precision": "fp16", "tau": 1e-6, "config": 2},
+    "c2": {"n": 8192, "leaves": (64,), "precision": "bf16_split", "tau": 1e-2, "config": 1},
+}
 
 
 def load_peaks():
@@ -74,10 +85,20 @@ def load_peaks():
                 "sm_max_mhz": 2070.0, "source": "fallback"}
 
 
-def workload(n: int):
-    a = synth.alg_decay_signed(n, 3.0, synth.config_seed(1, operand="A"))
-    b = synth.alg_decay_signed(n, 3.0, synth.config_seed(1, operand="B"))
-    return a, b
+def workload(name: str, n: int, alpha: float = 0.5):
+    """Host FP32 (A, B) of a single-product workload (seeded numpy PCG64, row-major draws)."""
+    cfg = WORKLOADS[name]["config"]
+    if name == "decay":
+        return (synth.exp_decay_normal(n, alpha, synth.config_seed(cfg, operand="A")),
+                synth.exp_decay_normal(n, alpha, synth.config_seed(cfg, operand="B")))
+    return (synth.alg_decay_signed(n, 3.0, synth.config_seed(cfg, operand="A")),
+            synth.alg_decay_signed(n, 3.0, synth.config_seed(cfg, operand="B")))
+
+
+def workload_desc(name: str, n: int, alpha: float) -> str:
+    if name == "decay":
+        return f"exponential decay exp(-{alpha:g}|i-j|) * N(0,1), N={n}"
+    return f"algebraic decay (|i-j|+1)^-3 * (+-1), N={n}"
 
 
 # ---------------------------------------------------------------------------
@@ -165,28 +186,121 @@ def spread_rows(bd: int, count: int, offset: int = 0):
     return sorted({(offset + (q * bd) // count) % bd for q in range(count)})
 
 
-def cpu_baseline(a, b, leaf, tau, rows, nB_full=None, gpu_c=None):
-    """Times the oracle on `rows` output block-rows: norm maps of those block-rows
-    of A and of B (the per-block-row share of both norm passes), the pair test of
-    those rows against all of B's blocks, and their block products.  The full job
-    is `bd / len(rows)` such shares.  Returns (dict, nB_full)."""
+# Worker processes for the oracle's all-core timing.  They are forked before the
+# first CUDA call of the process (a process forked after it can hang), inherit
+# the host inputs copy-on-write through these globals and never touch the GPU;
+# every worker runs the oracle single-threaded (BLAS pinned to one thread).
+_ORACLE_A = None
+_ORACLE_B = None
+
+
+def host_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+class OraclePool:
+    def __init__(self, a, b, cores=None):
+        import multiprocessing as mp
+        global _ORACLE_A, _ORACLE_B
+        _ORACLE_A, _ORACLE_B = a, b
+        self.cores = cores or host_cores()
+        self.pool = mp.get_context("fork").Pool(self.cores)
+
+    def map(self, fn, items):
+        return self.pool.map(fn, items, chunksize=1)
+
+    def close(self):
+        self.pool.terminate()
+        self.pool.join()
+
+
+def _w_norm_row(task):
+    """One block row of A's (which == 'A') or B's norm map (oracle, Eq. 2)."""
+    from oracle import spamm as OS
+    which, leaf, i = task
+    return OS.normmap_rows(_ORACLE_A if which == "A" else _ORACLE_B, leaf, [i])[0]
+
+
+def _w_share(task):
+    """The oracle's work for one output block row: that row of A's norm map, B's matching
+    share of its norm pass, the row's pair tests and block products.  Returns its seconds."""
+    from oracle import spamm as OS
+    leaf, tau, i, nB = task
+    t0 = time.perf_counter()
+    nA_row = OS.normmap_rows(_ORACLE_A, leaf, [i])
+    OS.normmap_rows(_ORACLE_B, leaf, [i])
+    OS.spamm_rows(_ORACLE_A, _ORACLE_B, leaf, tau, [i], nA_row, nB)
+    return time.perf_counter() - t0
+
+
+def needed_normmap_b(pool, a, b, leaf, tau, rows):
+    """B's norm map restricted to the block rows that can decide a triple of the sampled rows
+    (oracle.spamm.needed_b_rows), computed on the pool (set-up, not timed)."""
+    from oracle import spamm as OS
+    bd = OS.num_blocks(a.shape[0], leaf)
+    if pool is not None:
+        nA_rows = np.array(pool.map(_w_norm_row, [("A", leaf, i) for i in rows]))
+    else:
+        nA_rows = OS.normmap_rows(a, leaf, rows)
+    ks = OS.needed_b_rows(nA_rows, tau)
+    if tau > 0.0 and ks.size < bd and not np.isfinite(b).all():
+        ks = np.arange(bd)
+    nB = np.zeros((bd, bd))
+    if ks.size:
+        if pool is not None:
+            nB[ks] = np.array(pool.map(_w_norm_row, [("B", leaf, int(k)) for k in ks]))
+        else:
+            nB[ks] = OS.normmap_rows(b, leaf, ks)
+    return nB
+
+
+def cpu_baseline(a, b, leaf, tau, pool=None, single_rows=4, nB_full=None, gpu_c=None,
+                 offset=0):
+    """The oracle as it stands, timed on a bounded sample of the job: output block rows, each
+    one share = that block row of A's norm map, B's matching share of its norm pass, the
+    row's pair tests against B's blocks and its block products; the full job is bd such
+    shares.  All cores: one row per worker process at a time (value, cores = workers);
+    single thread: `single_rows` rows in this process.  B's norm map for the pair tests is
+    set-up (its rows that can decide the sampled triples only), not timed.  Also the GPU's
+    error on the single-thread rows against the oracle.  Returns (dict, nB_full)."""
     from oracle import spamm as OS
     n = a.shape[0]
     bd = OS.num_blocks(n, leaf)
+    cores = pool.cores if pool is not None else 1
+    rows_all = spread_rows(bd, max(cores, single_rows), offset)
     if nB_full is None:
-        nB_full = OS.normmap(b, leaf)          # needed by the tests; not timed
+        nB_full = needed_normmap_b(pool, a, b, leaf, tau, rows_all)
+    res = {"unit": "TFLOP/s (dense-equivalent)", "kind": "oracle", "nproc": host_cores()}
+    if pool is not None:
+        t0 = time.perf_counter()
+        secs = pool.map(_w_share, [(leaf, tau, i, nB_full) for i in rows_all])
+        wall = time.perf_counter() - t0
+        t_full = wall * bd / len(rows_all)
+        res.update({"value": 2.0 * n ** 3 / t_full / 1e12, "cores": cores,
+                    "sample": f"{len(rows_all)} of {bd} output block rows on {cores} worker "
+                              f"processes (per row: its norm-map rows of A and B, pair tests "
+                              f"and block products), {wall:.1f} s wall, extrapolated "
+                              f"x{bd / len(rows_all):.1f}",
+                    "seconds_full_extrapolated": t_full,
+                    "row_seconds_median": statistics.median(secs)})
+    rows = rows_all[:single_rows]
     t0 = time.perf_counter()
     nA_rows = OS.normmap_rows(a, leaf, rows)
     _ = OS.normmap_rows(b, leaf, rows)          # B's share of the norm pass
     out = OS.spamm_rows(a, b, leaf, tau, rows, nA_rows, nB_full)
     dt = time.perf_counter() - t0
-    t_full = dt * bd / len(rows)
-    res = {"value": 2.0 * n ** 3 / t_full / 1e12, "unit": "TFLOP/s (dense-equivalent)",
-           "cores": blas_threads(), "kind": "oracle",
-           "sample": f"{len(rows)} of {bd} output block-rows (norm maps of those block-rows of "
-                     f"A and B, their pair tests and block products), {dt:.1f} s, "
-                     f"extrapolated x{bd / len(rows):.0f}",
-           "seconds_full_extrapolated": t_full}
+    t1 = dt * bd / len(rows)
+    single = {"value": 2.0 * n ** 3 / t1 / 1e12, "cores": 1,
+              "sample": f"{len(rows)} of {bd} output block rows in one thread, {dt:.1f} s, "
+                        f"extrapolated x{bd / len(rows):.0f}",
+              "seconds_full_extrapolated": t1}
+    if pool is None:
+        res.update(single)
+    else:
+        res["single_thread"] = single
     if gpu_c is not None:
         errs, refs = 0.0, 0.0
         for i, (c, _) in out.items():
@@ -194,6 +308,7 @@ def cpu_baseline(a, b, leaf, tau, rows, nB_full=None, gpu_c=None):
             errs += float(np.sum((g - c) ** 2))
             refs += float(np.sum(c ** 2))
         res["rel_err_vs_oracle_sampled_rows"] = (errs / refs) ** 0.5 if refs > 0 else 0.0
+        res["sampled_rows"] = [int(i) for i in rows]
     return res, nB_full
 
 
@@ -206,14 +321,34 @@ def run_ours(args, rank, world):
     import paper_2103_13042_gb300 as P
 
     local = int(os.environ.get("LOCAL_RANK", "0"))
+    wl = WORKLOADS[args.workload]
+    n = args.n or wl["n"]
+    tau = wl["tau"] if args.tau is None else args.tau
+    prec_name = args.precision or wl["precision"]
+    prec = P.PRECISIONS[prec_name]
+    t_gen = time.perf_counter()
+    a_h, b_h = workload(args.workload, n, args.alpha)
+    t_gen = time.perf_counter() - t_gen
+    # the oracle's worker processes, forked before this process's first CUDA call
+    pool = OraclePool(a_h, b_h) if (world == 1 and not args.no_cpu_baseline) else None
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    n, leaf, tau = args.n or N_DEFAULT, args.leaf, args.tau
-    prec = P.PRECISIONS[args.precision]
-    a_h, b_h = workload(n)
     A = torch.from_numpy(a_h).to(dev)
     B = torch.from_numpy(b_h).to(dev)
     C = torch.empty_like(A)
+    # leaf: given, or the project's autotuner on this instance (leaf x multiply schedule,
+    # each candidate timed under graph replay); the single-product API then runs the
+    # chosen leaf
+    tune = None
+    if args.leaf:
+        leaf = args.leaf
+    elif len(wl["leaves"]) == 1:
+        leaf = wl["leaves"][0]
+    else:
+        best, allc = P.spamm_batch_autotune([A], [B], [C], [tau], prec, args.target, reps=3)
+        tune = {"best": best, "candidates": allc}
+        leaf = best["leaf"]
+        torch.cuda.empty_cache()
     bd = P.num_blocks(n, leaf)
     nA = torch.empty((bd, bd), dtype=torch.float64, device=dev)
     nB = torch.empty_like(nA)
@@ -390,6 +525,7 @@ def run_ours(args, rank, world):
             return g0.elapsed_time(g1) / reps
 
         base["fp32_spamm_ms"] = timed(step32, max(3, args.steps // 2))
+        base["fp32_spamm_leaf"] = leaf
         prev = torch.backends.cuda.matmul.allow_tf32
         torch.backends.cuda.matmul.allow_tf32 = False
         base["cublas_sgemm_ms"] = timed(lambda: torch.matmul(A, B, out=C32), 3)
@@ -403,6 +539,11 @@ def run_ours(args, rank, world):
     peaks = load_peaks()
     dense = 2.0 * n ** 3
     value = job_throughput(dense, ms, world) / 1e12
+    # the multiply phase against the tensor peak (useful flops over surviving triples only)
+    useful = 2.0 * leaf ** 3 * st["survivors"]
+    mul_frac = None
+    if prec != P.FP32 and part_ms["multiply_alone"] > 0:
+        mul_frac = useful / (part_ms["multiply_alone"] * 1e-3) / 1e12 / peaks["bf16_tflops"]
     # roofline of the dominant kernel: by the ncu launch list of this command the
     # norm map (two launches per step) has the largest share of device time
     norm_ms = 0.5 * (part_ms["normmap_A"] + part_ms["normmap_B"])
@@ -434,22 +575,30 @@ def run_ours(args, rank, world):
                     "unit": "TFLOP/s", "frac": ach / peak, "traffic": None,
                     "per_launch_ms": mul_ms, "algorithmic_flops": flops,
                     "peak_source": peaks["source"]}
+    gb = 4.0 * n * n / 1e9
     line = {
         "metric": METRIC, "value": value, "unit": "TFLOP/s (dense-equivalent, 2N^3/t)",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": {"fp32": "f32", "tf32x3": "tf32", "bf16_split": "bf16",
-                  "fp16_split": "f16", "fp16": "f16"}.get(args.precision, args.precision),
-        "data": "synthetic (seeded algebraic-decay matrices)",
-        "config": {"workload": f"algebraic decay (|i-j|+1)^-3 * (+-1), N={n}, leaf {leaf}, "
-                               f"tau={tau:g}, {args.precision}",
-                   "n": n, "leaf": leaf, "tau": tau, "precision": args.precision,
+        "dtype": {"fp32": "f32", "tf32x3": "tf32", "bf16_split": "bf16", "bf16": "bf16",
+                  "fp16_split": "f16", "fp16": "f16"}.get(prec_name, prec_name),
+        "data": "synthetic (seeded numpy PCG64 draws on the host, copied to the GPU)",
+        "config": {"workload": f"{workload_desc(args.workload, n, args.alpha)}, A and B "
+                               f"independent, leaf {leaf}"
+                               f"{' (autotuned)' if tune else ''}, tau={tau:g}, {prec_name}",
+                   "name": args.workload, "n": n, "leaf": leaf, "tau": tau,
+                   "precision": prec_name, "alpha": args.alpha if args.workload == "decay" else None,
                    "target_rel_err": args.target, "parallelism": f"replicas x{world}",
                    "launch": "eager" if graph is None else "cuda-graph replay of the API calls",
-                   "ms_per_step_eager": eager_ms,
-                   "l2": "inputs larger than L2 (A, B, C 268 MB each vs 126 MB L2)",
+                   "ms_per_step_eager": eager_ms, "autotune": tune,
+                   "host_generation_s": t_gen,
+                   "l2": f"inputs larger than L2 (A, B, C {gb:.2f} GB each vs 126 MB L2)",
                    "survivors": st["survivors"], "valid_ratio": st["valid_ratio"],
-                   "skipped_bound2_rel": st["skipped_bound2"] / (st["norm_a"] * st["norm_b"])},
+                   "nonempty_tiles": st["nonempty_tiles"],
+                   "skipped_bound2_rel": st["skipped_bound2"] / (st["norm_a"] * st["norm_b"]),
+                   "multiply_useful_tflops": useful / (part_ms["multiply_alone"] * 1e-3) / 1e12
+                   if part_ms["multiply_alone"] > 0 else None,
+                   "multiply_tensor_frac_of_bf16_peak": mul_frac},
         "breakdown_ms": part_ms,
         "baselines_same_gpu": base,
         "e2e": {"value": dense / (e2e_ms * 1e-3) / 1e12 * world,
@@ -465,8 +614,10 @@ def run_ours(args, rank, world):
     }
     if not args.no_cpu_baseline:
         c_host = C.cpu().numpy()
-        cb, _ = cpu_baseline(a_h, b_h, leaf, tau, rows=spread_rows(bd, args.cpu_rows), gpu_c=c_host)
+        cb, _ = cpu_baseline(a_h, b_h, leaf, tau, pool, single_rows=args.cpu_rows, gpu_c=c_host)
         line["cpu_baseline"] = cb
+    if pool is not None:
+        pool.close()
     return line
 
 
@@ -523,6 +674,7 @@ def run_batch(args, rank, world):
     local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
+    args.precision = args.precision or "bf16_split"
     prec = P.PRECISIONS[args.precision]
     ns = [s["n"] for s in specs]
     As = [torch.from_numpy(a).to(dev) for a, _ in mats]
@@ -764,7 +916,7 @@ def run_sparse(args, rank, world):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     n = args.n or 32768
-    prec = P.PRECISIONS[args.precision if args.precision != "bf16_split" else "bf16"]
+    prec = P.PRECISIONS[args.precision or "bf16"]
     prec_name = [k for k, v in P.PRECISIONS.items() if v == prec][0]
     A = synth.near_sparse_device(n, synth.config_seed(2, operand="A"), dev)
     B = synth.near_sparse_device(n, synth.config_seed(2, operand="B"), dev)
@@ -997,36 +1149,89 @@ def run_table2(args, rank, world):
 # ---------------------------------------------------------------------------
 
 def run_reference(args):
-    args.n = args.n or N_DEFAULT
-    a_h, b_h = workload(args.n)
-    leaf, tau = args.leaf, args.tau
-    bd = -(-args.n // leaf)
+    """The oracle as it stands on the host cores, on the same workload, metric and unit as
+    the GPU arm: every step times a bounded sample of the job (a different spread of output
+    block rows each step, one row per worker process) and extrapolates it to the whole job."""
+    wl = WORKLOADS[args.workload]
+    n = args.n or wl["n"]
+    tau = wl["tau"] if args.tau is None else args.tau
+    prec_name = args.precision or wl["precision"]
+    leaf = args.leaf or max(wl["leaves"])
+    a_h, b_h = workload(args.workload, n, args.alpha)
+    pool = OraclePool(a_h, b_h)
+    bd = -(-n // leaf)
+    rows_per_step = max(pool.cores, args.ref_rows)
     nB = None
-    for w in range(args.warmup):
-        _, nB = cpu_baseline(a_h, b_h, leaf, tau, spread_rows(bd, args.ref_rows, w), nB)
-    vals = []
-    t0 = time.perf_counter()
+    walls, vals = [], []
     cb = None
-    for k in range(args.steps):   # each step a different spread of block-rows
-        cb, nB = cpu_baseline(a_h, b_h, leaf, tau, spread_rows(bd, args.ref_rows, args.warmup + k), nB)
-        vals.append(cb["value"])
-    wall = time.perf_counter() - t0
+    try:
+        for k in range(args.warmup + args.steps):
+            t0 = time.perf_counter()
+            cb, nB_k = cpu_baseline(a_h, b_h, leaf, tau, pool, single_rows=1,
+                                    offset=k * rows_per_step)
+            if k >= args.warmup:
+                walls.append(time.perf_counter() - t0)
+                vals.append(cb["value"])
+    finally:
+        pool.close()
     value = statistics.median(vals)
     return {
         "impl": "reference", "metric": METRIC, "value": value,
         "unit": "TFLOP/s (dense-equivalent, 2N^3/t)", "n_gpus": 1, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": cb["seconds_full_extrapolated"] * 1e3,
+        "warmup": args.warmup, "ms_per_step": statistics.median(walls) * 1e3,
+        "ms_per_step_full_job_extrapolated": cb["seconds_full_extrapolated"] * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic (seeded algebraic-decay matrices)",
-        "config": {"workload": f"algebraic decay (|i-j|+1)^-3 * (+-1), N={args.n}, leaf {leaf}, "
-                               f"tau={tau:g}, {args.precision}",
-                   "n": args.n, "leaf": leaf, "tau": tau, "precision": args.precision},
-        "cpu_baseline": {"value": value, "unit": cb["unit"], "cores": blas_threads(),
-                         "kind": "oracle", "sample": cb["sample"]},
+        "data": "synthetic (seeded numpy PCG64 draws on the host)",
+        "config": {"workload": f"{workload_desc(args.workload, n, args.alpha)}, A and B "
+                               f"independent, leaf {leaf}, tau={tau:g}, {prec_name} (the GPU "
+                               f"arm's configuration; the oracle computes in FP64)",
+                   "name": args.workload, "n": n, "leaf": leaf, "tau": tau,
+                   "precision": prec_name},
+        "cpu_baseline": {"value": value, "unit": cb["unit"], "cores": cb["cores"],
+                         "nproc": cb["nproc"], "kind": "oracle",
+                         "sample": cb["sample"] + "; each step a different spread of rows",
+                         "single_thread": cb.get("single_thread")},
         "e2e": {"value": value, "unit": "TFLOP/s (dense-equivalent, 2N^3/t)",
                 "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
-        "wall_seconds": wall,
     }
+
+
+def run_extras(args, rank, world):
+    """Short summaries of two more configurations, timed in the same run after the main line:
+    the near-sparse N = 32768 product at a 50% valid ratio (where the multiply is
+    tensor-bound) and the N = 8192 algebraic-decay mixed-precision product.  Each is the
+    full workload of its own --workload run, with fewer steps and no CPU baseline."""
+    import copy
+    import torch
+    out = {}
+    for name, overrides in (("near_sparse_n32768_ratio0.5", {"workload": "sparse"}),
+                            ("c2_alg_decay_n8192", {"workload": "c2"})):
+        a = copy.copy(args)
+        a.n, a.tau, a.leaf, a.precision = None, None, None, None
+        a.no_cpu_baseline = True
+        a.steps = max(5, args.steps // 2)
+        for k, v in overrides.items():
+            setattr(a, k, v)
+        torch.cuda.empty_cache()
+        try:
+            ln = (run_sparse if a.workload == "sparse" else run_ours)(a, rank, world)
+        except Exception as exc:   # a summary that fails is reported, the main line stands
+            out[name] = {"error": f"{type(exc).__name__}: {exc}"}
+            continue
+        roof = ln.get("roofline", {})
+        out[name] = {"workload": ln["config"]["workload"], "ms_per_step": ln["ms_per_step"],
+                     "value": ln["value"], "unit": ln["unit"], "steps": ln["steps"],
+                     "breakdown_ms": ln.get("breakdown_ms"),
+                     "baselines_same_gpu": ln.get("baselines_same_gpu"),
+                     "roofline": {k: roof.get(k) for k in ("kernel", "bound", "achieved", "peak",
+                                                           "unit", "frac")},
+                     "clocks": ln.get("clocks")}
+        for k in ("rel_err_sampled_tiles_vs_fp64", "survivors", "valid_ratio", "leaf", "tau",
+                  "skipped_bound2_rel"):
+            if k in ln["config"]:
+                out[name][k] = ln["config"][k]
+    torch.cuda.empty_cache()
+    return out
 
 
 def main():
@@ -1035,25 +1240,31 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="bf16_split")
-    ap.add_argument("--tau", type=float, default=1e-2)
+    ap.add_argument("--workload", default="decay",
+                    choices=["decay", "c2", "batch", "sparse", "table2"],
+                    help="decay: exp(-alpha|i-j|) N(0,1) at N=32768 (default); c2: algebraic "
+                         "decay N=8192 mixed precision; batch: 256 uneven instances; sparse: "
+                         "near-sparse N=32768 at a target valid ratio; table2: the paper's "
+                         "Table 2 analogue")
+    ap.add_argument("--precision", default=None,
+                    help="fp32|tf32x3|bf16|fp16|bf16_split|fp16_split (default per workload)")
+    ap.add_argument("--tau", type=float, default=None, help="default per workload")
+    ap.add_argument("--alpha", type=float, default=0.5, help="decay: rate alpha")
     ap.add_argument("--target", type=float, default=1e-5)
-    ap.add_argument("--n", type=int, default=None,
-                    help="matrix size (default 8192; sparse workload 32768)")
-    ap.add_argument("--leaf", type=int, default=LEAF_DEFAULT)
-    ap.add_argument("--cpu-rows", type=int, default=128,
-                    help="output block-rows of the oracle's timed sample (cpu_baseline)")
+    ap.add_argument("--n", type=int, default=None, help="matrix size (default per workload)")
+    ap.add_argument("--leaf", type=int, default=None, help="default: autotuned / per workload")
+    ap.add_argument("--cpu-rows", type=int, default=4,
+                    help="output block-rows of the oracle's single-thread sample (cpu_baseline)")
     ap.add_argument("--ref-rows", type=int, default=8,
-                    help="output block-rows per step of --impl reference")
+                    help="output block-rows per step of --impl reference (at least the core count)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-baselines", action="store_true")
     ap.add_argument("--eager", action="store_true", help="time host-enqueued calls, no graph")
     ap.add_argument("--table2-sizes", default="1024,2048,4096,8192",
                     help="table2 workload: matrix sizes")
-    ap.add_argument("--workload", default="single", choices=["single", "batch", "sparse", "table2"],
-                    help="single: one N=8192 product; batch: 256 uneven instances; "
-                         "sparse: near-sparse N=32768 at a target valid ratio")
     ap.add_argument("--ratio", type=float, default=0.5, help="sparse: target valid ratio")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="decay: skip the near-sparse and N=8192 summaries added to the line")
     ap.add_argument("--count", type=int, default=BATCH_COUNT)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
@@ -1062,6 +1273,10 @@ def main():
     rank = int(os.environ.get("RANK", "0"))
     if args.impl == "reference":
         if rank != 0:
+            return
+        if args.workload not in WORKLOADS:
+            print(json.dumps({"impl": "reference", "unavailable":
+                              "the reference arm covers the single-product workloads"}), flush=True)
             return
         print(json.dumps(run_reference(args)), flush=True)
         return
@@ -1072,6 +1287,8 @@ def main():
         dist.init_process_group("nccl")
     runner = {"batch": run_batch, "sparse": run_sparse, "table2": run_table2}.get(args.workload, run_ours)
     line = runner(args, rank, world)
+    if args.workload == "decay" and not args.no_extras and world == 1 and line is not None:
+        line["extra_workloads"] = run_extras(args, rank, world)
     if line is not None:
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -340,14 +340,17 @@ def accumulation_bound(nA, nB, surv, mode: int, leaf: int) -> float:
 
 def apriori_tile_bounds(nA, nB, surv, mode: int, leaf: int, flags=None) -> np.ndarray:
     """t_ij = sum over surviving k of (c_ikj + g) p_ikj: bound on the tile's ||C_mode - C_exact||_F,
-    with c_ikj and g as in :func:`apriori_bound` (g from the largest survivor count)."""
-    bd = nA.shape[0]
+    with c_ikj and g as in :func:`apriori_bound` (g from the largest survivor count).
+
+    nA may hold only some block rows ([r, bd]; surv and flags then [r, bd, bd]): the result
+    is [r, bd] for those rows, g taken from their largest survivor count."""
+    rows = nA.shape[0]
     kmax = int(surv.sum(axis=1).max()) if surv.any() else 0
     g = accumulation_coeff(mode, leaf, kmax)
     c_plain = triple_error_coeff(mode, False, leaf)
     c_split = triple_error_coeff(mode, True, leaf) if mode != FP32 else 0.0
-    out = np.zeros((bd, bd))
-    for i in range(bd):
+    out = np.zeros((rows, nB.shape[1]))
+    for i in range(rows):
         p = nA[i, :, None] * nB                      # [k, j]
         if mode == TF32X3:
             coeff = np.full_like(p, c_split)
@@ -362,25 +365,25 @@ def apriori_tile_bounds(nA, nB, surv, mode: int, leaf: int, flags=None) -> np.nd
 def accumulation_tile_bounds(nA, nB, surv, mode: int, leaf: int) -> np.ndarray:
     """t_ij = sum over surviving k of g p_ikj (doubled in split modes, as in
     :func:`accumulation_bound`): bound on the tile's distance from the FP64 evaluation of
-    the same rounded operands."""
-    bd = nA.shape[0]
+    the same rounded operands (block rows as for :func:`apriori_tile_bounds`)."""
+    rows = nA.shape[0]
     kmax = int(surv.sum(axis=1).max()) if surv.any() else 0
     g = accumulation_coeff(mode, leaf, kmax)
     if mode_is_split(mode):
         g *= 2.0
-    out = np.zeros((bd, bd))
-    for i in range(bd):
+    out = np.zeros((rows, nB.shape[1]))
+    for i in range(rows):
         p = nA[i, :, None] * nB
         out[i] = np.where(surv[i], g * p, 0.0).sum(axis=0)
     return out
 
 
 def tile_errors(x: np.ndarray, y: np.ndarray, leaf: int) -> np.ndarray:
-    """||X[i,j] - Y[i,j]||_F per leaf tile of two n x n matrices ([bd, bd], FP64, the ragged
-    edge tiles cover only their in-range entries)."""
+    """||X[i,j] - Y[i,j]||_F per leaf tile of two equally shaped r x c matrices
+    ([ceil(r/leaf), ceil(c/leaf)], FP64; ragged edge tiles cover their in-range entries)."""
     d = np.asarray(x, dtype=np.float64) - np.asarray(y, dtype=np.float64)
-    n = d.shape[0]
-    bd = -(-n // leaf)
-    p = np.zeros((bd * leaf, bd * leaf))
-    p[:n, :n] = d * d
-    return np.sqrt(p.reshape(bd, leaf, bd, leaf).sum(axis=(1, 3)))
+    r, c = d.shape
+    br, bc = -(-r // leaf), -(-c // leaf)
+    p = np.zeros((br * leaf, bc * leaf))
+    p[:r, :c] = d * d
+    return np.sqrt(p.reshape(br, leaf, bc, leaf).sum(axis=(1, 3)))

@@ -322,6 +322,23 @@ def spamm_rows(a: np.ndarray, b: np.ndarray, leaf: int, tau: float, rows,
     return out
 
 
+def normmap_blocked(x: np.ndarray, leaf: int) -> np.ndarray:
+    """Eq. 2 for every leaf block with numpy's FP64 pairwise summation of the exact squares:
+    the form for matrices too large for :func:`normmap`'s exactly rounded sums (one leaf-row
+    strip at a time).  Not exactly rounded: each sum is within about log2(leaf^2) 2^-53
+    relative of the exact one, far inside the 1e-12 band in which skip decisions may differ."""
+    n = x.shape[0]
+    bd = num_blocks(n, leaf)
+    out = np.empty((bd, bd))
+    for i in range(bd):
+        lo, hi = i * leaf, min(n, (i + 1) * leaf)
+        strip = np.zeros((leaf, bd * leaf))
+        strip[:hi - lo, :n] = x[lo:hi]
+        blocks = (strip * strip).reshape(leaf, bd, leaf).transpose(1, 0, 2).reshape(bd, -1)
+        out[i] = np.sqrt(blocks.sum(axis=1))      # contiguous rows: pairwise sums
+    return out
+
+
 def needed_b_rows(nA_rows: np.ndarray, tau: float):
     """Block rows k of B's norm map that can decide a triple of the given block rows of C.
 

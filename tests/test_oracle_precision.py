@@ -419,3 +419,22 @@ def test_tile_check_catches_an_error_the_total_misses():
     t = P.apriori_tile_bounds(nA, nB, surv, P.BF16, leaf)
     assert not np.all(P.tile_errors(bad, exact, leaf) <= t)
     assert np.all(P.tile_errors(emu, exact, leaf) <= t)
+
+
+def test_tile_bounds_of_sampled_rows_match_the_full_map():
+    """The row form (nA holding only some block rows) gives those rows of the full result,
+    up to g, which the sampled rows' own largest survivor count can only lower."""
+    a, b = _decay_pair(alpha=0.1)
+    leaf = 64
+    nA, nB = S.normmap(a, leaf), S.normmap(b, leaf)
+    surv = S.flat_survivors(nA, nB, 1e-6)
+    rows = [0, 3]
+    full = P.apriori_tile_bounds(nA, nB, surv, P.FP16, leaf)
+    part = P.apriori_tile_bounds(nA[rows], nB, surv[rows], P.FP16, leaf)
+    assert part.shape == (2, nB.shape[1])
+    assert np.all(part <= full[rows]) and np.allclose(part, full[rows], rtol=1e-3)
+    emu = P.emulated_multiply(a, b, leaf, surv, P.FP16)
+    exact = S.multiply_with_skipset(a, b, leaf, surv)
+    for r, i in enumerate(rows):
+        strip = slice(i * leaf, (i + 1) * leaf)
+        assert np.all(P.tile_errors(emu[strip], exact[strip], leaf)[0] <= part[r])

@@ -349,3 +349,19 @@ def test_needed_b_rows_give_the_same_sampled_rows():
             assert np.array_equal(r_full[i][1], r_part[i][1])
     # tau = 0 needs every row (a zero block survives at tau = 0)
     assert S.needed_b_rows(nA_rows, 0.0).size == bd
+
+
+def test_blocked_norms_agree_with_exactly_rounded_norms():
+    """normmap_blocked (numpy pairwise FP64 sums) within 1e-14 relative of normmap (math.fsum,
+    exactly rounded) on wide-range, ragged and exactly-zero blocks; zero blocks stay 0."""
+    g = np.random.Generator(np.random.PCG64(404))
+    x = (g.standard_normal((333, 333)) * np.exp2(g.integers(-60, 60, (333, 333)))).astype(np.float32)
+    x[:64, 100:200] = 0.0
+    for leaf in (32, 64, 128):
+        exact = S.normmap(x, leaf)
+        fast = S.normmap_blocked(x, leaf)
+        assert np.array_equal(exact == 0, fast == 0)
+        nz = exact > 0
+        assert np.max(np.abs(fast[nz] - exact[nz]) / exact[nz]) <= 1e-14
+    y = synth.near_sparse(300, 405)
+    assert np.max(np.abs(S.normmap_blocked(y, 64) / S.normmap(y, 64) - 1.0)) <= 1e-14

@@ -66,12 +66,13 @@ def test_reference_arm_other_ranks_exit_silently():
 
 def test_reference_arm_prints_one_contract_line():
     """Rank 0 of the reference arm times the oracle on the host cores and prints one JSON line
-    with the contract's keys (a small sample here: the minimum of 8 output block-rows)."""
+    with the contract's keys (a small case here: the N = 2048 algebraic-decay workload, at
+    least 8 output block-rows per step, one per worker process)."""
     import json
     env = dict(os.environ, RANK="0", WORLD_SIZE="1", LOCAL_RANK="0")
     r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference",
-                        "--steps", "1", "--warmup", "3", "--cpu-rows", "8"], env=env,
-                       capture_output=True, text=True, timeout=300)
+                        "--workload", "c2", "--n", "2048", "--steps", "1", "--warmup", "3",
+                        "--ref-rows", "8"], env=env, capture_output=True, text=True, timeout=300)
     assert r.returncode == 0, r.stderr[-2000:]
     lines = [ln for ln in r.stdout.splitlines() if ln.strip()]
     assert len(lines) == 1
@@ -82,6 +83,9 @@ def test_reference_arm_prints_one_contract_line():
     assert d["dtype"] == "f64" and d["config"]["workload"]
     cb = d["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == d["value"]
-    assert "8 of 128" in cb["sample"]
+    assert cb["nproc"] >= cb["cores"] and cb["single_thread"]["cores"] == 1
+    assert " of 32 output block rows" in cb["sample"] and d["config"]["n"] == 2048
+    # the step time is the sampled step's own wall time, so K steps fit in the run
+    assert d["ms_per_step"] < d["ms_per_step_full_job_extrapolated"]
     assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0,
                         "d2h_bytes_per_step": 0}
