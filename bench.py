@@ -61,7 +61,7 @@ METRIC = "SpAMM time & TFLOP/s at fixed rel. error vs plain FP32 SpAMM & cuBLAS;
 # DRAM bytes (read + write) per launch of a kernel, from one ncu capture of the
 # kernel as it stands; an entry is removed whenever the kernel changes, until it
 # is captured again.
-NCU_TRAFFIC = {("normmap_staged_kernel", 8192, 64): 268.5e6 + 3.669e6}
+NCU_TRAFFIC = {}
 
 # The synthetic workloads of a single product (one step = norm maps of A and B,
 # plan, multiply).  decay: exp(-alpha |i-j|) N(0,1), N = 32768, A and B
@@ -357,13 +357,12 @@ def run_ours(args, rank, world):
 
     def step(st=None):
         st = st if st is not None else torch.cuda.current_stream()
-        P.spamm_normmap(A, leaf, nA, st)
-        P.spamm_normmap(B, leaf, nB, st)
+        P.spamm_normmap_pair(A, B, leaf, nA, nB, st)
         plan.plan_multiply(nA, nB, tau, A, B, C, args.target, st)
 
-    # our kernels per step: 2 norm maps, 4 plan kernels, zero-fill, multiply
-    # (tensor cores: + operand rounding)
-    launches_per_step = 2 + 4 + 1 + (1 if prec == P.FP32 else 2)
+    # our kernels per step: one norm-map launch for both operands, 4 plan kernels,
+    # zero-fill, multiply (tensor cores: + operand rounding)
+    launches_per_step = 1 + 4 + 1 + (1 if prec == P.FP32 else 2)
 
     def barrier():
         if world > 1:
@@ -373,13 +372,17 @@ def run_ours(args, rank, world):
         step()
     torch.cuda.synchronize()
     st = plan.stats()
+    # peak rates of the modes no library routine gives (the library's microkernels)
+    try:
+        micro = P.spamm_peak_rates()
+    except Exception as exc:   # reported, the line stands without them
+        micro = {"error": f"{type(exc).__name__}: {exc}"}
 
     # per-call breakdown (events on the launching stream)
-    ev = [torch.cuda.Event(enable_timing=True) for _ in range(6)]
-    parts = {"normmap_A": [], "normmap_B": [], "plan_multiply": [], "plan_alone": [],
-             "multiply_alone": []}
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
+    parts = {"normmap_pair": [], "plan_multiply": [], "plan_alone": [], "multiply_alone": []}
     # a clean read of more than L2 before each breakdown iteration: the previous
-    # iteration's dirty C lines are written back there, not inside normmap_A
+    # iteration's dirty C lines are written back there, not inside the norm maps
     l2_flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev).fill_(1.0)
     for _ in range(max(3, args.steps // 2)):
         # the GPU first spins for ~1 ms while the host enqueues the calls below,
@@ -387,16 +390,14 @@ def run_ours(args, rank, world):
         torch.cuda._sleep(2_000_000)
         l2_flush.sum()
         ev[0].record(stream)
-        P.spamm_normmap(A, leaf, nA, stream)
+        P.spamm_normmap_pair(A, B, leaf, nA, nB, stream)
         ev[1].record(stream)
-        P.spamm_normmap(B, leaf, nB, stream)
-        ev[2].record(stream)
         plan.plan_multiply(nA, nB, tau, A, B, C, args.target, stream)
-        ev[3].record(stream)
+        ev[2].record(stream)
         plan.plan(nA, nB, tau, args.target, stream)     # the two halves, for the breakdown
-        ev[4].record(stream)
+        ev[3].record(stream)
         plan.multiply(A, B, C, stream)
-        ev[5].record(stream)
+        ev[4].record(stream)
         torch.cuda.synchronize()
         for k, name in enumerate(parts):
             parts[name].append(ev[k].elapsed_time(ev[k + 1]))
@@ -476,8 +477,7 @@ def run_ours(args, rank, world):
             stream.wait_event(ev_in[q])
             if k >= 2:
                 stream.wait_event(ev_out[q])               # buffer q's C has been copied out
-            P.spamm_normmap(dA[q], leaf, dnA[q], stream)
-            P.spamm_normmap(dB[q], leaf, dnB[q], stream)
+            P.spamm_normmap_pair(dA[q], dB[q], leaf, dnA[q], dnB[q], stream)
             plans[q].plan_multiply(dnA[q], dnB[q], tau, dA[q], dB[q], dC[q], args.target, stream)
             ev_done[q].record(stream)
             with torch.cuda.stream(s_out):
@@ -508,8 +508,7 @@ def run_ours(args, rank, world):
         C32 = torch.empty_like(A)
 
         def step32():
-            P.spamm_normmap(A, leaf, nA, stream)
-            P.spamm_normmap(B, leaf, nB, stream)
+            P.spamm_normmap_pair(A, B, leaf, nA, nB, stream)
             plan32.plan_multiply(nA, nB, tau, A, B, C32, args.target, stream)
 
         def timed(fn, reps):
@@ -539,35 +538,42 @@ def run_ours(args, rank, world):
     peaks = load_peaks()
     dense = 2.0 * n ** 3
     value = job_throughput(dense, ms, world) / 1e12
-    # the multiply phase against the tensor peak (useful flops over surviving triples only)
+    # the multiply phase against its own mode's peak (useful flops over surviving triples
+    # only; TF32x3 issues three MMAs per product): the microkernel rates for FP16, TF32 and
+    # FP32 FFMA, MEASURED_PEAKS' cuBLAS figure for BF16
     useful = 2.0 * leaf ** 3 * st["survivors"]
+    mode_peak = {P.FP32: micro.get("ffma_fp32"), P.FP16: micro.get("mma_fp16"),
+                 P.FP16_SPLIT: micro.get("mma_fp16"), P.TF32X3: micro.get("mma_tf32"),
+                 P.BF16: peaks["bf16_tflops"], P.BF16_SPLIT: peaks["bf16_tflops"]}.get(prec)
+    issued = useful * (3.0 if prec == P.TF32X3 else 1.0)
     mul_frac = None
-    if prec != P.FP32 and part_ms["multiply_alone"] > 0:
-        mul_frac = useful / (part_ms["multiply_alone"] * 1e-3) / 1e12 / peaks["bf16_tflops"]
+    if mode_peak and part_ms["multiply_alone"] > 0:
+        mul_frac = issued / (part_ms["multiply_alone"] * 1e-3) / 1e12 / mode_peak
     # roofline of the dominant kernel: by the ncu launch list of this command the
-    # norm map (two launches per step) has the largest share of device time
-    norm_ms = 0.5 * (part_ms["normmap_A"] + part_ms["normmap_B"])
+    # norm map (one launch per step over both operands) has the largest share of device time
+    norm_ms = part_ms["normmap_pair"]
     mul_ms = part_ms["multiply_alone"]
     if norm_ms > 0.0:
-        bytes_ = 4.0 * n * n + 8.0 * bd * bd
+        bytes_ = 2.0 * (4.0 * n * n + 8.0 * bd * bd)
         ach = bytes_ / (norm_ms * 1e-3) / 1e9
         traffic = NCU_TRAFFIC.get(("normmap_staged_kernel", n, leaf))
         roof = {"kernel": "normmap_staged_kernel", "bound": "hbm", "achieved": ach,
                 "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": ach / peaks["hbm_gbs"],
                 "traffic": traffic, "per_launch_ms": norm_ms, "algorithmic_bytes": bytes_,
                 "peak_source": peaks["source"] + " copy bandwidth (burst)",
-                "timing": "CUDA events around one spamm_normmap call on the launching stream, "
+                "timing": "CUDA events around one spamm_normmap_pair call on the launching stream, "
                           "queued behind a 1 ms spin and a clean 256 MB read (no host gap, "
                           "no dirty C lines left in L2 by the previous call)"}
     else:
         flops = 2.0 * leaf ** 3 * st["survivors"]
         if prec == P.FP32:
-            peak = 152 * 128 * 2 * peaks["sm_max_mhz"] * 1e6 / 1e12
+            peak = micro.get("ffma_fp32") or 152 * 128 * 2 * peaks["sm_max_mhz"] * 1e6 / 1e12
             ach = flops / (mul_ms * 1e-3) / 1e12
             roof = {"kernel": "multiply_simt", "bound": "alu", "achieved": ach, "peak": peak,
                     "unit": "TFLOP/s", "frac": ach / peak, "traffic": None,
                     "per_launch_ms": mul_ms, "algorithmic_flops": flops,
-                    "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x max SM clock"}
+                    "peak_source": "measured FFMA microkernel (spamm_peak_rates)"
+                    if micro.get("ffma_fp32") else "derived: 152 SMs x 128 lanes x 2 x clock"}
         else:
             peak = peaks["bf16_tflops"]
             ach = flops / (mul_ms * 1e-3) / 1e12
@@ -598,7 +604,8 @@ def run_ours(args, rank, world):
                    "skipped_bound2_rel": st["skipped_bound2"] / (st["norm_a"] * st["norm_b"]),
                    "multiply_useful_tflops": useful / (part_ms["multiply_alone"] * 1e-3) / 1e12
                    if part_ms["multiply_alone"] > 0 else None,
-                   "multiply_tensor_frac_of_bf16_peak": mul_frac},
+                   "multiply_frac_of_mode_peak": mul_frac},
+        "peaks_microkernel_tflops": micro,
         "breakdown_ms": part_ms,
         "baselines_same_gpu": base,
         "e2e": {"value": dense / (e2e_ms * 1e-3) / 1e12 * world,
@@ -671,6 +678,12 @@ def run_batch(args, rank, world):
     import paper_2103_13042_gb300 as P
 
     specs, mats = batch_workload(args.count)
+    dense_job = float(sum(2.0 * s["n"] ** 3 for s in specs))
+    shard = args.partition == "instances" and world > 1
+    if shard:   # this rank's instances (longest first to the least-loaded rank)
+        from paper_2103_13042_gb300 import partition as PT
+        mine = PT.instances_by_rank([s["n"] for s in specs], world)[rank]
+        specs, mats = [specs[i] for i in mine], [mats[i] for i in mine]
     local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
@@ -688,8 +701,11 @@ def run_batch(args, rank, world):
     taus = certified_taus(P, As, Bs, ns, 64, args.target)
     t_tau = time.perf_counter() - t_tune
 
-    # autotuner: leaf x multiply schedule, timed on this batch
-    best, cands = P.spamm_batch_autotune(As, Bs, Cs, taus, prec, args.target, reps=3)
+    # autotuner: leaf x multiply schedule, timed on this batch (--leaf fixes the leaf, static)
+    if args.leaf:
+        best, cands = {"leaf": args.leaf, "schedule": "static", "ms": -1.0}, []
+    else:
+        best, cands = P.spamm_batch_autotune(As, Bs, Cs, taus, prec, args.target, reps=3)
     leaf = best["leaf"]
     batch = P.Batch(ns, leaf, prec, graph=True, dynamic=best["schedule"] == "dynamic")
 
@@ -780,7 +796,7 @@ def run_batch(args, rank, world):
     e2e_run(e2e_steps)
     f1.record(stream)
     torch.cuda.synchronize()
-    e2e_ms = f0.elapsed_time(f1) / e2e_steps
+    e2e_ms = slowest_rank_ms(f0.elapsed_time(f1) / e2e_steps, world, dev)
     last = (e2e_steps - 1) & 1
     assert all(torch.equal(c_pin[last][i], dCs[last][i].cpu()) for i in (0, len(ns) - 1))
     batches[1].close()
@@ -843,10 +859,11 @@ def run_batch(args, rank, world):
             "peak_source": peaks["source"]}
     survivors = sum(s["survivors"] for s in st)
     line = {
-        "metric": METRIC, "value": dense / (ms * 1e-3) / 1e12 * world,
+        "metric": METRIC,
+        "value": (dense_job if shard else dense * world) / (ms * 1e-3) / 1e12,
         "unit": "TFLOP/s (dense-equivalent, sum of 2N^3 / t)",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "higher_is_better": True, "scaling": "strong" if shard else "weak", "vs_baseline": None,
         "dtype": {"fp32": "f32", "tf32x3": "tf32", "bf16_split": "bf16", "bf16": "bf16",
                   "fp16_split": "f16", "fp16": "f16"}.get(args.precision, args.precision),
         "data": "synthetic (seeded exponential / algebraic decay instances)",
@@ -857,13 +874,14 @@ def run_batch(args, rank, world):
                    "precision": args.precision, "target_rel_err": args.target,
                    "leaf": leaf, "schedule": best["schedule"], "autotune": cands,
                    "tau_selection_s": t_tau, "launch": "cuda-graph replay (one run per step)",
-                   "parallelism": f"replicas x{world}",
+                   "parallelism": (f"instances sharded over {world} ranks" if shard
+                                   else f"replicas x{world}"),
                    "l2": f"inputs larger than L2 ({4 * sum_n2 / 1e9:.1f} GB per operand)",
                    "survivors": survivors,
                    "rel_err_sampled_max": max(errs), "rel_err_sampled_instances": len(errs)},
         "breakdown_ms": part_ms,
         "baselines_same_gpu": base,
-        "e2e": {"value": dense / (e2e_ms * 1e-3) / 1e12 * world,
+        "e2e": {"value": (dense_job if shard else dense * world) / (e2e_ms * 1e-3) / 1e12,
                 "unit": "TFLOP/s (dense-equivalent, sum of 2N^3 / t)", "ms_per_step": e2e_ms,
                 "h2d_bytes_per_step": int(2 * 4 * sum_n2), "d2h_bytes_per_step": int(4 * sum_n2)},
         # norm maps (one launch for the operands with 16-byte aligned rows, one for
@@ -926,17 +944,22 @@ def run_sparse(args, rank, world):
 
     # tau by the paper's valid-ratio search (Section 3.5.2), per candidate leaf
     taus = {}
-    for leaf in (64, 128):
+    for leaf in ((args.leaf,) if args.leaf else (64, 128)):
         nA, nB = P.spamm_normmap(A, leaf), P.spamm_normmap(B, leaf)
         pl = P.Plan(n, leaf, P.FP32)
         taus[leaf] = pl.tau_for_valid_ratio(nA, nB, args.ratio, 0.01, 30)
         del pl, nA, nB
-    # autotuner on this instance: leaf x schedule (each leaf with its own tau)
+    # autotuner on this instance: leaf x schedule (each leaf with its own tau); --leaf fixes
+    # the leaf (static schedule)
     cands = []
-    for leaf in (64, 128):
-        best, allc = P.spamm_batch_autotune([A], [B], [C], [taus[leaf][0]], prec, args.target, reps=2)
-        cands += [c for c in allc if c["leaf"] == leaf]
-    best = min((c for c in cands if c["ms"] >= 0), key=lambda c: c["ms"])
+    if args.leaf:
+        best = {"leaf": args.leaf, "schedule": "static", "ms": -1.0}
+    else:
+        for leaf in (64, 128):
+            best, allc = P.spamm_batch_autotune([A], [B], [C], [taus[leaf][0]], prec, args.target,
+                                                reps=2)
+            cands += [c for c in allc if c["leaf"] == leaf]
+        best = min((c for c in cands if c["ms"] >= 0), key=lambda c: c["ms"])
     leaf = best["leaf"]
     tau, ratio, probes = taus[leaf]
     batch = P.Batch([n], leaf, prec, graph=True, dynamic=best["schedule"] == "dynamic")
@@ -1016,7 +1039,8 @@ def run_sparse(args, rank, world):
     ach = useful / (mul_ms * 1e-3) / 1e12
     peak = peaks["bf16_tflops"]
     line = {
-        "metric": METRIC, "value": dense / (ms * 1e-3) / 1e12 * world,
+        "metric": METRIC,
+        "value": dense / (ms * 1e-3) / 1e12 * world,
         "unit": "TFLOP/s (dense-equivalent, 2N^3/t)", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": {"bf16": "bf16", "fp16": "f16", "tf32x3": "tf32",
@@ -1196,6 +1220,112 @@ def run_reference(args):
     }
 
 
+def run_rowblocks(args, rank, world):
+    """Algorithm 4's partition of one product: each rank computes its own output block rows
+    (its rows of A as a row-major view, all of B and B's norm map on every rank), so the ranks
+    exchange nothing; the job's time is the slowest rank's and the value the whole product's
+    dense-equivalent rate (strong scaling: the product is fixed, the ranks share it)."""
+    import torch
+    import paper_2103_13042_gb300 as P
+    from paper_2103_13042_gb300 import partition as PT
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    wl = WORKLOADS[args.workload]
+    n = args.n or wl["n"]
+    tau = wl["tau"] if args.tau is None else args.tau
+    prec_name = args.precision or wl["precision"]
+    prec = P.PRECISIONS[prec_name]
+    leaf = args.leaf or max(wl["leaves"])
+    a_h, b_h = workload(args.workload, n, args.alpha)
+    r0, r1 = PT.row_blocks(n, leaf, world)[rank]
+    m = r1 - r0
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+    B = torch.from_numpy(b_h).to(dev)
+    bd = P.num_blocks(n, leaf)
+    nB = torch.empty((bd, bd), dtype=torch.float64, device=dev)
+    step = None
+    if m > 0:
+        A = torch.from_numpy(np.ascontiguousarray(a_h[r0:r1])).to(dev)
+        C = torch.empty((m, n), dtype=torch.float32, device=dev)
+        nA = torch.empty((P.num_blocks(m, leaf), bd), dtype=torch.float64, device=dev)
+        plan = P.GeneralPlan(m, n, n, leaf, prec)
+
+        def step():
+            P.spamm_normmap_rect(A, leaf, nA, stream)
+            P.spamm_normmap(B, leaf, nB, stream)
+            plan.plan_multiply(nA, nB, tau, A, B, C, args.target, stream=stream)
+
+        for _ in range(args.warmup):
+            step()
+        torch.cuda.synchronize()
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph):
+            step()
+        graph.replay()
+        torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        e0.record(stream)
+        for _ in range(args.steps):
+            if step is not None:
+                graph.replay()
+        e1.record(stream)
+        torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    ms = slowest_rank_ms(e0.elapsed_time(e1) / args.steps, world, dev)
+    # end to end: this rank's rows of A and all of B in from pinned host memory, its rows of C
+    # out, every step
+    e2e_ms = 0.0
+    h2d = d2h = 0
+    if m > 0:
+        a_pin = torch.from_numpy(np.ascontiguousarray(a_h[r0:r1])).pin_memory()
+        b_pin = torch.from_numpy(b_h).pin_memory()
+        c_pin = torch.empty((m, n), dtype=torch.float32).pin_memory()
+        h2d, d2h = 4 * (m * n + n * n), 4 * m * n
+        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        f0.record(stream)
+        for _ in range(max(2, args.steps // 4)):
+            A.copy_(a_pin, non_blocking=True)
+            B.copy_(b_pin, non_blocking=True)
+            step()
+            c_pin.copy_(C, non_blocking=True)
+        f1.record(stream)
+        torch.cuda.synchronize()
+        e2e_ms = f0.elapsed_time(f1) / max(2, args.steps // 4)
+    e2e_ms = slowest_rank_ms(e2e_ms, world, dev)
+    if rank != 0:
+        return None
+    dense = 2.0 * n ** 3
+    return {
+        "metric": METRIC, "value": dense / (ms * 1e-3) / 1e12,
+        "unit": "TFLOP/s (dense-equivalent, 2N^3/t)", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "strong",
+        "vs_baseline": None,
+        "dtype": {"fp32": "f32", "tf32x3": "tf32", "bf16_split": "bf16", "bf16": "bf16",
+                  "fp16_split": "f16", "fp16": "f16"}.get(prec_name, prec_name),
+        "data": "synthetic (seeded numpy PCG64 draws on the host, copied to the GPU)",
+        "config": {"workload": f"{workload_desc(args.workload, n, args.alpha)}, leaf {leaf}, "
+                               f"tau={tau:g}, {prec_name}, output block rows split over "
+                               f"{world} ranks (Algorithm 4)",
+                   "name": args.workload, "n": n, "leaf": leaf, "tau": tau,
+                   "parallelism": f"row blocks x{world}", "rank0_rows": [r0, r1],
+                   "launch": "cuda-graph replay of the API calls",
+                   "l2": "inputs larger than L2"},
+        "e2e": {"value": dense / (e2e_ms * 1e-3) / 1e12 if e2e_ms > 0 else None,
+                "unit": "TFLOP/s (dense-equivalent, 2N^3/t)", "ms_per_step": e2e_ms,
+                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": 9 * args.steps if prec != P.FP32 else 8 * args.steps,
+        "clocks": clk.summary(),
+    }
+
+
 def run_extras(args, rank, world):
     """Short summaries of two more configurations, timed in the same run after the main line:
     the near-sparse N = 32768 product at a 50% valid ratio (where the multiply is
@@ -1263,6 +1393,10 @@ def main():
     ap.add_argument("--table2-sizes", default="1024,2048,4096,8192",
                     help="table2 workload: matrix sizes")
     ap.add_argument("--ratio", type=float, default=0.5, help="sparse: target valid ratio")
+    ap.add_argument("--partition", default="replicas", choices=["replicas", "rows", "instances"],
+                    help="N > 1: replicas (every rank the whole job), rows (decay/c2: the "
+                         "product's block rows split over the ranks, Algorithm 4) or instances "
+                         "(batch: the instances dealt to the ranks)")
     ap.add_argument("--no-extras", action="store_true",
                     help="decay: skip the near-sparse and N=8192 summaries added to the line")
     ap.add_argument("--count", type=int, default=BATCH_COUNT)
@@ -1286,6 +1420,8 @@ def main():
         torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))   # before NCCL binds
         dist.init_process_group("nccl")
     runner = {"batch": run_batch, "sparse": run_sparse, "table2": run_table2}.get(args.workload, run_ours)
+    if args.partition == "rows" and args.workload in WORKLOADS:
+        runner = run_rowblocks
     line = runner(args, rank, world)
     if args.workload == "decay" and not args.no_extras and world == 1 and line is not None:
         line["extra_workloads"] = run_extras(args, rank, world)

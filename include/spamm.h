@@ -118,6 +118,13 @@ typedef struct spamm_plan_s* spamm_plan_t;
 spamm_status_t spamm_normmap(const float* X, int64_t n, int32_t leaf, double* normmap,
                              void* stream);
 
+/* spamm_normmap_pair: the norm maps of both operands of a product (A and B,
+ * both n x n as for spamm_normmap) in one launch, their block rows dealt to
+ * the same persistent grid: the same values as two spamm_normmap calls, one
+ * launch tail instead of two.  normA and normB must differ. */
+spamm_status_t spamm_normmap_pair(const float* A, const float* B, int64_t n, int32_t leaf,
+                                  double* normA, double* normB, void* stream);
+
 /* ---------------------------------------------------------------------------
  * Plans -- the pair test and work-queue build (Algorithm 2's bitmap and
  * map_offset, built once for all output tiles).
@@ -190,6 +197,59 @@ spamm_status_t spamm_multiply(spamm_plan_t plan, const float* A, const float* B,
 spamm_status_t spamm_plan_multiply(spamm_plan_t plan, const double* normA, const double* normB,
                                    double tau, double target_rel_err, const float* A,
                                    const float* B, float* C, void* stream);
+
+/* ---------------------------------------------------------------------------
+ * The general form -- Section 2 states the problem as C = alpha A B + beta C
+ * for general A, B, C before fixing alpha = 1, beta = 0 and square operands:
+ *
+ *   C = alpha * sum over surviving k of A[i,k] B[k,j]  +  beta * C
+ *
+ * with A m x k, B k x n, C m x n, each row-major with its own leading
+ * dimension, zero padded to whole leaf blocks: block grids bm x bk (A),
+ * bk x bn (B), bm x bn (C), bm = ceil(m / leaf) and so on.  The skip rule is
+ * the square one, triple by triple (skip iff normA[i,k] normB[k,j] < tau).
+ * beta = 0 does not read C (NaN there does not propagate); tiles without
+ * survivors become beta * C (left untouched at beta = 1).
+ *
+ * spamm_normmap_rect: the Eq. 2 norm map of a rows x cols operand (leading
+ *   dimension ld >= cols, 16-byte aligned) into normmap [ceil(rows/leaf) *
+ *   ceil(cols/leaf)], row-major; accuracy and errors as spamm_normmap.
+ * spamm_plan_workspace_size_general / spamm_plan_create_general: a plan for
+ *   the shape (m, k, n); arguments otherwise as for the square calls.
+ *   Limits: ceil(k / leaf) <= 1024, bm * bn <= 2^22, bm * bk * bn < 2^31,
+ *   every dimension <= 2^24 (SPAMM_ERR_UNSUPPORTED beyond).  spamm_plan,
+ *   spamm_plan_band, spamm_plan_stats (its bd field holds bm),
+ *   spamm_plan_export (tiles t = i * bn + j), spamm_tau_for_valid_ratio,
+ *   spamm_norm_histogram and spamm_tau_predict take such a plan with normA
+ *   [bm * bk] and normB [bk * bn]; spamm_multiply takes it with leading
+ *   dimensions k, n, n, alpha = 1 and beta = 0.
+ * spamm_multiply_general: the multiply over the plan's queues with leading
+ *   dimensions lda >= k, ldb >= n, ldc >= n, alpha and beta (finite).  A, B
+ *   and C are device FP32, 16-byte aligned; C may not overlap A or B.
+ *   normC (device FP64 [bm * bn], 16-byte aligned, may be NULL) receives C's
+ *   norm map as stored (||C[I,J]||_F of the written FP32 tile, the same
+ *   accuracy as spamm_normmap), computed in the multiply's epilogue: the next
+ *   product of a chain (matrix powers) plans from it without a norm pass over
+ *   C.  Works on square plans too.  Asynchronous.
+ * spamm_plan_multiply_general: spamm_plan followed by spamm_multiply_general
+ *   in one call (the tiles without survivors are written as soon as the
+ *   survivor counts are known).  Asynchronous.
+ * ------------------------------------------------------------------------- */
+spamm_status_t spamm_normmap_rect(const float* X, int64_t rows, int64_t cols, int64_t ld,
+                                  int32_t leaf, double* normmap, void* stream);
+spamm_status_t spamm_plan_workspace_size_general(int64_t m, int64_t k, int64_t n, int32_t leaf,
+                                                 spamm_precision_t precision, size_t* bytes);
+spamm_status_t spamm_plan_create_general(spamm_plan_t* plan, int64_t m, int64_t k, int64_t n,
+                                         int32_t leaf, spamm_precision_t precision,
+                                         void* workspace, size_t ws_bytes);
+spamm_status_t spamm_multiply_general(spamm_plan_t plan, const float* A, int64_t lda,
+                                      const float* B, int64_t ldb, float* C, int64_t ldc,
+                                      float alpha, float beta, double* normC, void* stream);
+spamm_status_t spamm_plan_multiply_general(spamm_plan_t plan, const double* normA,
+                                           const double* normB, double tau, double target_rel_err,
+                                           const float* A, int64_t lda, const float* B,
+                                           int64_t ldb, float* C, int64_t ldc, float alpha,
+                                           float beta, double* normC, void* stream);
 
 /* ---------------------------------------------------------------------------
  * Error measures (Eq. 5): E = AB - SpAMM(A, B, tau).
@@ -411,6 +471,7 @@ spamm_status_t spamm_mlp_train(float* weights, float* m, float* v, int32_t t0, c
  * calls choose it for the pruning error of Eq. 5 relative to the operands,
  * e(tau) = ||AB - SpAMM(A, B, tau)||_F / (||A||_F ||B||_F), without forming AB.
  * All use the plan's buffers (plan again with spamm_plan afterwards) and block.
+ * Square plans only (SPAMM_ERR_UNSUPPORTED for a plan of the general form).
  *
  * spamm_tau_certify: *tau_ref = the largest tau = ||A|| ||B|| 10^x, x found
  *   by 36 bisection steps over [-60, 0], whose skipped bound2 is <=
@@ -443,6 +504,19 @@ spamm_status_t spamm_tau_select(spamm_plan_t plan, const double* normA, const do
                                 const float* A, const float* B, double target_rel_err,
                                 const float* weights, float* scratch, double* tau,
                                 int32_t* evals, double* achieved, void* stream);
+
+/* ---------------------------------------------------------------------------
+ * spamm_peak_rates -- measured peak rates of this GPU, the denominators of
+ * roofline fractions for which no library routine gives one.  The paper has
+ * no counterpart (it quotes no hardware rates).  tflops (host double[5]):
+ *   [0] FP32 FFMA on the SIMT cores, [1] FP64 DFMA, [2] BF16, [3] FP16 and
+ *   [4] TF32 dense tcgen05 MMA with FP32 accumulation (one CTA per SM issuing
+ *   back-to-back 128 x N x K MMAs on operands resident in shared memory, the
+ *   better of N = 128 and 256).  Each is the second of two launches, timed
+ *   with events.  Allocates a small buffer, takes tens of milliseconds and
+ *   blocks; SPAMM_ERR_TIMEOUT if an MMA launch did not complete in time.
+ * ------------------------------------------------------------------------- */
+spamm_status_t spamm_peak_rates(double* tflops, void* stream);
 
 /* ---------------------------------------------------------------------------
  * Status helpers.

@@ -97,6 +97,17 @@ _SIGS = {
                         ctypes.c_float, _VP, _VP],
     "spamm_batch_autotune": [_VP, _I32, _I32, _D, _I32, _VP, ctypes.POINTER(Tune), _VP,
                              ctypes.POINTER(_I32)],
+    "spamm_normmap_rect": [_VP, _I64, _I64, _I64, _I32, _VP, _VP],
+    "spamm_normmap_pair": [_VP, _VP, _I64, _I32, _VP, _VP, _VP],
+    "spamm_plan_workspace_size_general": [_I64, _I64, _I64, _I32, _I32,
+                                          ctypes.POINTER(ctypes.c_size_t)],
+    "spamm_plan_create_general": [ctypes.POINTER(_VP), _I64, _I64, _I64, _I32, _I32, _VP,
+                                  ctypes.c_size_t],
+    "spamm_multiply_general": [_VP, _VP, _I64, _VP, _I64, _VP, _I64, ctypes.c_float,
+                               ctypes.c_float, _VP, _VP],
+    "spamm_plan_multiply_general": [_VP, _VP, _VP, _D, _D, _VP, _I64, _VP, _I64, _VP, _I64,
+                                    ctypes.c_float, ctypes.c_float, _VP, _VP],
+    "spamm_peak_rates": [_VP, _VP],
     "spamm_tau_certify": [_VP, _VP, _VP, _D, ctypes.POINTER(_D), ctypes.POINTER(_D), _VP],
     "spamm_tau_error": [_VP, _VP, _VP, _VP, _VP, _D, _D, _VP, ctypes.POINTER(_D), _VP],
     "spamm_tau_select": [_VP, _VP, _VP, _VP, _VP, _D, _VP, _VP, ctypes.POINTER(_D),
@@ -218,6 +229,27 @@ def _mat(t, where: str, name: str, n: int):
     return ctypes.c_void_p(_mat_ptr(t, where, name, n))
 
 
+def _rowmajor(t, where: str, name: str, rows: int, cols: int):
+    """(pointer, leading dimension) of a rows x cols FP32 GPU tensor whose rows are contiguous
+    (a row-major matrix or a view of one: stride(1) == 1, stride(0) >= cols)."""
+    import torch
+    if not isinstance(t, torch.Tensor):
+        _bad(where, f"{name} is not a tensor")
+    if t.device.type != _DEVICE_TYPE:
+        _bad(where, f"{name} is on {t.device}, not on the GPU")
+    cur = _current_index()
+    if _index_of(t) != cur:
+        _bad(where, f"{name} is on {t.device}, but the current device is {cur}")
+    if t.dtype != torch.float32:
+        _bad(where, f"{name} is {t.dtype}, expected torch.float32")
+    if t.dim() != 2 or t.shape[0] != rows or t.shape[1] != cols:
+        _bad(where, f"{name} has shape {tuple(t.shape)}, expected ({rows}, {cols})")
+    ld = t.stride(0) if rows > 1 else max(cols, t.stride(0))
+    if (t.stride(1) != 1 and cols > 1) or ld < cols:
+        _bad(where, f"{name} rows are not contiguous (strides {tuple(t.stride())})")
+    return ctypes.c_void_p(t.data_ptr()), ld
+
+
 def _side(t, where: str, name: str) -> int:
     """n of an n x n operand (checked to be 2-D and square by the caller's _mat)."""
     if getattr(t, "dim", lambda: 0)() != 2:
@@ -269,12 +301,30 @@ def spamm_normmap(X, leaf: int, out=None, stream=None):
     return out
 
 
+def spamm_normmap_pair(A, B, leaf: int, outA=None, outB=None, stream=None):
+    """Norm maps of both n x n operands of a product in one launch -> (normA, normB)."""
+    import torch
+    w = "spamm_normmap_pair"
+    n = _side(A, w, "A")
+    a, b = _mat(A, w, "A", n), _mat(B, w, "B", n)
+    bd = num_blocks(n, leaf) if leaf > 0 else 0
+    if outA is None:
+        outA = torch.empty((bd, bd), dtype=torch.float64, device=A.device)
+    if outB is None:
+        outB = torch.empty((bd, bd), dtype=torch.float64, device=A.device)
+    _check(lib().spamm_normmap_pair(a, b, n, leaf, _norms(outA, w, "normA", bd),
+                                    _norms(outB, w, "normB", bd), _stream(stream)), w)
+    return outA, outB
+
+
 class Plan:
     """Owns a spamm_plan_t (work queues for one (n, leaf, precision))."""
 
     def __init__(self, n: int, leaf: int, precision: int = FP32, workspace=None):
         self.n, self.leaf, self.precision = n, leaf, precision
         self.bd = num_blocks(n, leaf) if leaf > 0 else 0
+        self.m, self.k = n, n
+        self.bm = self.bk = self.bn = self.bd
         h = ctypes.c_void_p()
         ws_ptr, ws_bytes = (None, 0) if workspace is None else (
             _tensor(workspace, "spamm_plan_create", "workspace", workspace.dtype),
@@ -304,10 +354,17 @@ class Plan:
 
     def plan(self, normA, normB, tau: float, target_rel_err: float = 1e-5, stream=None):
         w = "spamm_plan"
-        _check(lib().spamm_plan(self.handle, _norms(normA, w, "normA", self.bd),
-                                _norms(normB, w, "normB", self.bd), float(tau),
+        _check(lib().spamm_plan(self.handle, self._na(normA, w), self._nb(normB, w), float(tau),
                                 float(target_rel_err), _stream(stream)), w)
         return self
+
+    def _na(self, t, w):
+        import torch
+        return _tensor(t, w, "normA", torch.float64, numel=self.bm * self.bk)
+
+    def _nb(self, t, w):
+        import torch
+        return _tensor(t, w, "normB", torch.float64, numel=self.bk * self.bn)
 
     def stats(self, stream=None) -> dict:
         s = Stats()
@@ -319,7 +376,7 @@ class Plan:
         """(tile_ptr int32[bd*bd+1], k_idx uint16[S]) as numpy arrays."""
         import numpy as np
         st = self.stats(stream)
-        tp = np.zeros(self.bd * self.bd + 1, dtype=np.int32)
+        tp = np.zeros(self.bm * self.bn + 1, dtype=np.int32)
         kk = np.zeros(max(1, st["survivors"]), dtype=np.uint16)
         _check(lib().spamm_plan_export(self.handle, tp.ctypes.data_as(ctypes.c_void_p),
                                        kk.ctypes.data_as(ctypes.c_void_p), kk.size,
@@ -335,9 +392,9 @@ class Plan:
     def plan_multiply(self, normA, normB, tau: float, A, B, C, target_rel_err: float = 1e-5,
                       stream=None):
         """plan() then multiply() in one call (zero-fill of empty tiles overlapped)."""
-        w, n, bd = "spamm_plan_multiply", self.n, self.bd
-        _check(lib().spamm_plan_multiply(self.handle, _norms(normA, w, "normA", bd),
-                                         _norms(normB, w, "normB", bd), float(tau),
+        w, n = "spamm_plan_multiply", self.n
+        _check(lib().spamm_plan_multiply(self.handle, self._na(normA, w), self._nb(normB, w),
+                                         float(tau),
                                          float(target_rel_err), _mat(A, w, "A", n),
                                          _mat(B, w, "B", n), _mat(C, w, "C", n),
                                          _stream(stream)), w)
@@ -346,8 +403,8 @@ class Plan:
     def band(self, normA, normB, tau_lo: float, tau_hi: float, stream=None):
         """Plan the triples with tau_lo <= p < tau_hi (error measurement)."""
         w = "spamm_plan_band"
-        _check(lib().spamm_plan_band(self.handle, _norms(normA, w, "normA", self.bd),
-                                     _norms(normB, w, "normB", self.bd), float(tau_lo),
+        _check(lib().spamm_plan_band(self.handle, self._na(normA, w), self._nb(normB, w),
+                                     float(tau_lo),
                                      float(tau_hi), _stream(stream)), w)
         return self
 
@@ -356,8 +413,8 @@ class Plan:
         """(tau, valid ratio, probes) of the valid-ratio search (Section 3.5.2)."""
         t, r, k = ctypes.c_double(), ctypes.c_double(), ctypes.c_int32()
         w = "spamm_tau_for_valid_ratio"
-        _check(lib().spamm_tau_for_valid_ratio(self.handle, _norms(normA, w, "normA", self.bd),
-                                               _norms(normB, w, "normB", self.bd),
+        _check(lib().spamm_tau_for_valid_ratio(self.handle, self._na(normA, w),
+                                               self._nb(normB, w),
                                                float(target), float(tol), int(max_probes),
                                                ctypes.byref(t), ctypes.byref(r), ctypes.byref(k),
                                                _stream(stream)), "spamm_tau_for_valid_ratio")
@@ -368,8 +425,7 @@ class Plan:
         import numpy as np
         out = np.zeros(64, dtype=np.int64)
         w = "spamm_norm_histogram"
-        _check(lib().spamm_norm_histogram(self.handle, _norms(normA, w, "normA", self.bd),
-                                          _norms(normB, w, "normB", self.bd),
+        _check(lib().spamm_norm_histogram(self.handle, self._na(normA, w), self._nb(normB, w),
                                           out.ctypes.data_as(ctypes.c_void_p), _stream(stream)), w)
         return out
 
@@ -416,11 +472,100 @@ class Plan:
         """The network's tau for this plan's shape (weights: device float32 [8449])."""
         t = ctypes.c_double()
         w = "spamm_tau_predict"
-        _check(lib().spamm_tau_predict(self.handle, _norms(normA, w, "normA", self.bd),
-                                       _norms(normB, w, "normB", self.bd),
+        _check(lib().spamm_tau_predict(self.handle, self._na(normA, w), self._nb(normB, w),
                                        float(target_rel_err), _weights(weights, w),
                                        ctypes.byref(t), _stream(stream)), w)
         return t.value
+
+
+class GeneralPlan(Plan):
+    """A plan of the general form C = alpha * SpAMM(A, B) + beta * C with A m x k and B k x n
+    (spamm_plan_create_general).  Norm maps are [bm, bk] (A) and [bk, bn] (B)."""
+
+    def __init__(self, m: int, k: int, n: int, leaf: int, precision: int = FP32,
+                 workspace=None):
+        self.m, self.k, self.n, self.leaf, self.precision = m, k, n, leaf, precision
+        self.bm, self.bk, self.bn = (num_blocks(x, leaf) if leaf > 0 else 0 for x in (m, k, n))
+        self.bd = self.bm
+        h = ctypes.c_void_p()
+        ws_ptr, ws_bytes = (None, 0) if workspace is None else (
+            _tensor(workspace, "spamm_plan_create_general", "workspace", workspace.dtype),
+            workspace.numel() * workspace.element_size())
+        _check(lib().spamm_plan_create_general(ctypes.byref(h), m, k, n, leaf, precision, ws_ptr,
+                                               ws_bytes), "spamm_plan_create_general")
+        self.handle = h
+        self._workspace = workspace
+
+    @staticmethod
+    def workspace_size(m: int, k: int, n: int, leaf: int, precision: int = FP32) -> int:
+        b = ctypes.c_size_t()
+        _check(lib().spamm_plan_workspace_size_general(m, k, n, leaf, precision, ctypes.byref(b)),
+               "spamm_plan_workspace_size_general")
+        return b.value
+
+    def _nc(self, t, w):
+        import torch
+        return None if t is None else _tensor(t, w, "normC", torch.float64,
+                                               numel=self.bm * self.bn)
+
+    def multiply(self, A, B, C, alpha: float = 1.0, beta: float = 0.0, normC=None, stream=None):
+        """C = alpha * (pruned A B) + beta * C; A, B, C may be row-major views (contiguous rows).
+        normC (float64 [bm, bn], optional) receives C's norm map as stored."""
+        w = "spamm_multiply_general"
+        a, lda = _rowmajor(A, w, "A", self.m, self.k)
+        b, ldb = _rowmajor(B, w, "B", self.k, self.n)
+        c, ldc = _rowmajor(C, w, "C", self.m, self.n)
+        _check(lib().spamm_multiply_general(self.handle, a, lda, b, ldb, c, ldc, float(alpha),
+                                            float(beta), self._nc(normC, w), _stream(stream)), w)
+        return C
+
+    def plan_multiply(self, normA, normB, tau: float, A, B, C, target_rel_err: float = 1e-5,
+                      alpha: float = 1.0, beta: float = 0.0, normC=None, stream=None):
+        w = "spamm_plan_multiply_general"
+        a, lda = _rowmajor(A, w, "A", self.m, self.k)
+        b, ldb = _rowmajor(B, w, "B", self.k, self.n)
+        c, ldc = _rowmajor(C, w, "C", self.m, self.n)
+        _check(lib().spamm_plan_multiply_general(self.handle, self._na(normA, w),
+                                                 self._nb(normB, w), float(tau),
+                                                 float(target_rel_err), a, lda, b, ldb, c, ldc,
+                                                 float(alpha), float(beta), self._nc(normC, w),
+                                                 _stream(stream)), w)
+        return C
+
+
+def spamm_normmap_rect(X, leaf: int, out=None, stream=None):
+    """Leaf Frobenius norms of a rows x cols FP32 device matrix (contiguous rows, any leading
+    dimension) -> FP64 [ceil(rows/leaf), ceil(cols/leaf)] tensor."""
+    import torch
+    w = "spamm_normmap_rect"
+    if getattr(X, "dim", lambda: 0)() != 2:
+        _bad(w, "X must be a 2-D tensor")
+    rows, cols = int(X.shape[0]), int(X.shape[1])
+    x, ld = _rowmajor(X, w, "X", rows, cols)
+    br, bc = (num_blocks(rows, leaf), num_blocks(cols, leaf)) if leaf > 0 else (0, 0)
+    if out is None:
+        out = torch.empty((br, bc), dtype=torch.float64, device=X.device)
+    o = _tensor(out, w, "out", torch.float64, numel=br * bc)
+    _check(lib().spamm_normmap_rect(x, rows, cols, ld, leaf, o, _stream(stream)), w)
+    return out
+
+
+def spamm_general(A, B, leaf: int, tau: float, C=None, alpha: float = 1.0, beta: float = 0.0,
+                  precision: int = FP32, target_rel_err: float = 1e-5, normC=None, stream=None):
+    """One general-form call: norm maps of A (m x k) and B (k x n), plan, multiply into C
+    (m x n, created when None; beta must be 0 then).  Returns (C, plan)."""
+    import torch
+    m, k = int(A.shape[0]), int(A.shape[1])
+    n = int(B.shape[1])
+    nA = spamm_normmap_rect(A, leaf, stream=stream)
+    nB = spamm_normmap_rect(B, leaf, stream=stream)
+    plan = GeneralPlan(m, k, n, leaf, precision)
+    if C is None:
+        if beta != 0.0:
+            _bad("spamm_general", "beta != 0 needs C")
+        C = torch.empty((m, n), dtype=torch.float32, device=A.device)
+    plan.plan_multiply(nA, nB, tau, A, B, C, target_rel_err, alpha, beta, normC, stream)
+    return C, plan
 
 
 def spamm_plan(normA, normB, n: int, leaf: int, tau: float, precision: int = FP32,
@@ -664,6 +809,15 @@ def load_tau_weights(device=None, path: str = TAU_WEIGHTS_PATH):
     if w.size != spamm_mlp_param_count():
         raise RuntimeError(f"{path}: {w.size} values, expected {spamm_mlp_param_count()}")
     return torch.from_numpy(w).to(device or torch.device("cuda"))
+
+
+def spamm_peak_rates(stream=None) -> dict:
+    """Measured peak rates of the current GPU (TFLOP/s): FP32 FFMA, FP64 DFMA and dense
+    tcgen05 BF16, FP16 and TF32 MMA."""
+    out = (ctypes.c_double * 5)()
+    _check(lib().spamm_peak_rates(ctypes.cast(out, ctypes.c_void_p), _stream(stream)),
+           "spamm_peak_rates")
+    return dict(zip(("ffma_fp32", "dfma_fp64", "mma_bf16", "mma_fp16", "mma_tf32"), out))
 
 
 def spamm_selftest_bounded_wait(limit_ns: int = 20_000_000, stream=None) -> int:

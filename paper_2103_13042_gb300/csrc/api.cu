@@ -72,12 +72,12 @@ size_t engine_layout(std::vector<Inst>& insts, int leaf, spamm_precision_t prec,
                      float** feat) {
   size_t off = align_up(extra, 256);
   PlanBuffers b{};
-  const size_t plan_bytes =
-      plan_layout(insts.data(), (int)insts.size(), &b, base ? base + off : nullptr);
+  const size_t plan_bytes = plan_layout(insts.data(), (int)insts.size(), &b,
+                                        base ? base + off : nullptr, is_tensor_mode(prec));
   off += plan_bytes;
   OperandImages t{};
   if (is_tensor_mode(prec)) {
-    const size_t tiles = (size_t)b.tiles;
+    const size_t na = (size_t)b.ablks, nb = (size_t)b.bblks;
     const size_t blk = (size_t)leaf * leaf * (prec == SPAMM_TF32X3 ? 4 : 2);
     auto take = [&](size_t bytes) {
       off = align_up(off, 256);
@@ -85,14 +85,14 @@ size_t engine_layout(std::vector<Inst>& insts, int leaf, spamm_precision_t prec,
       off += bytes;
       return p;
     };
-    t.a_hi = reinterpret_cast<uint8_t*>(take(tiles * blk));
-    t.b_hi = reinterpret_cast<uint8_t*>(take(tiles * blk));
+    t.a_hi = reinterpret_cast<uint8_t*>(take(na * blk));
+    t.b_hi = reinterpret_cast<uint8_t*>(take(nb * blk));
     if (has_lo(prec)) {
-      t.a_lo = reinterpret_cast<uint8_t*>(take(tiles * blk));
-      t.b_lo = reinterpret_cast<uint8_t*>(take(tiles * blk));
+      t.a_lo = reinterpret_cast<uint8_t*>(take(na * blk));
+      t.b_lo = reinterpret_cast<uint8_t*>(take(nb * blk));
     }
-    t.ea = reinterpret_cast<int32_t*>(take(tiles * sizeof(int32_t)));
-    t.eb = reinterpret_cast<int32_t*>(take(tiles * sizeof(int32_t)));
+    t.ea = reinterpret_cast<int32_t*>(take(na * sizeof(int32_t)));
+    t.eb = reinterpret_cast<int32_t*>(take(nb * sizeof(int32_t)));
   }
   {
     off = align_up(off, 256);
@@ -171,6 +171,7 @@ cudaError_t multiply_nonempty(Engine& e, const InstRef& ref, int32_t* status, cu
     if (err == cudaSuccess && after_round) err = cudaEventRecord(after_round, s);
     if (err == cudaSuccess)
       err = launch_multiply_tc(e.precision, e.leaf, ref, e.buf, e.img, status, e.schedule, s);
+    if (err == cudaSuccess && ref.any_norm_out) err = launch_norm_out_finish(ref, e.buf, e.leaf, s);
   }
   return err;
 }
@@ -225,7 +226,7 @@ void fill_stats(const PlanDevice& h, int leaf, int bd, spamm_stats_t* stats) {
 
 spamm_status_t export_queues(const PlanBuffers& b, const Inst& in, int32_t* tile_ptr,
                              uint16_t* k_idx, int64_t cap, cudaStream_t s) {
-  const int64_t tiles = (int64_t)in.bd * in.bd;
+  const int64_t tiles = (int64_t)in.bm * in.bn;
   // per tile: count and absolute first slot (tiles are stored in the plan's
   // enumeration order, not row-major)
   std::vector<int32_t> cnt((size_t)tiles), beg((size_t)tiles);
@@ -274,12 +275,56 @@ spamm_status_t check_shape(int64_t n, int32_t leaf) {
   return SPAMM_OK;
 }
 
+// General shapes: the inner block count is stored in 10 bits of a k index;
+// tile positions, k slots and block numbers are 32-bit on the device.
+spamm_status_t check_general(int64_t m, int64_t kd, int64_t n, int32_t leaf) {
+  if (m < 1 || kd < 1 || n < 1) return SPAMM_ERR_INVALID_ARG;
+  if (!leaf_ok(leaf)) return SPAMM_ERR_UNSUPPORTED;
+  const int64_t lim = (int64_t)1 << 24;
+  if (m > lim || kd > lim || n > lim) return SPAMM_ERR_UNSUPPORTED;
+  const int64_t bm = num_blocks(m, leaf), bk = num_blocks(kd, leaf), bn = num_blocks(n, leaf);
+  if (bk > kMaxBd) return SPAMM_ERR_UNSUPPORTED;
+  if (bm * bn > ((int64_t)1 << 22)) return SPAMM_ERR_UNSUPPORTED;
+  if (bm * bk * bn >= ((int64_t)1 << 31) || bm * bk >= ((int64_t)1 << 31) ||
+      bk * bn >= ((int64_t)1 << 31))
+    return SPAMM_ERR_UNSUPPORTED;
+  return SPAMM_OK;
+}
+
+// Bytes spanned by a rows x cols row-major matrix with leading dimension ld.
+size_t span_bytes(int64_t rows, int64_t cols, int64_t ld) {
+  return (size_t)((rows - 1) * ld + cols) * sizeof(float);
+}
+
+bool overlaps(const void* a, size_t na, const void* b, size_t nb) {
+  const char* x = static_cast<const char*>(a);
+  const char* y = static_cast<const char*>(b);
+  return x < y + nb && y < x + na;
+}
+
 std::vector<Inst> single_inst(int64_t n, int leaf) {
   std::vector<Inst> v(1);
   v[0] = Inst{};
-  v[0].n = n;
-  v[0].bd = (int)num_blocks(n, leaf);
+  set_square(v[0], n, leaf);
   return v;
+}
+
+std::vector<Inst> general_inst(int64_t m, int64_t kd, int64_t n, int leaf) {
+  std::vector<Inst> v(1);
+  v[0] = Inst{};
+  set_general(v[0], m, kd, n, kd, n, n, 1.0f, 0.0f, leaf);
+  return v;
+}
+
+// The plan's instance reset to the square call form: leading dimensions of
+// its own shape, alpha = 1, beta = 0, no output norm map.
+void square_call(Inst& in) {
+  in.lda = in.kd;
+  in.ldb = in.n;
+  in.ldc = in.n;
+  in.alpha = 1.0f;
+  in.beta = 0.0f;
+  in.nC = nullptr;
 }
 
 }  // namespace
@@ -314,6 +359,23 @@ spamm_status_t spamm_normmap(const float* X, int64_t n, int32_t leaf, double* no
   return SPAMM_OK;
 }
 
+spamm_status_t spamm_normmap_pair(const float* A, const float* B, int64_t n, int32_t leaf,
+                                  double* normA, double* normB, void* stream) {
+  spamm_status_t st = check_shape(n, leaf);
+  if (st != SPAMM_OK) return st;
+  if (!A || !B || !normA || !normB || !aligned16(A) || !aligned16(B) || !aligned16(normA) ||
+      !aligned16(normB) || normA == normB)
+    return SPAMM_ERR_INVALID_ARG;
+  int32_t* status = device_status_word();
+  if (!status) return SPAMM_ERR_NO_MEMORY;
+  cudaError_t e = launch_normmap_pair(A, B, n, leaf, normA, normB, status, (cudaStream_t)stream);
+  if (e != cudaSuccess) {
+    (void)cudaGetLastError();
+    return SPAMM_ERR_CUDA;
+  }
+  return SPAMM_OK;
+}
+
 spamm_status_t spamm_plan_workspace_size(int64_t n, int32_t leaf, spamm_precision_t precision,
                                          size_t* bytes) {
   spamm_status_t st = check_shape(n, leaf);
@@ -336,7 +398,7 @@ spamm_status_t spamm_plan_create(spamm_plan_t* plan, int64_t n, int32_t leaf,
   if (is_tensor_mode(precision) && leaf == 32) return SPAMM_ERR_UNSUPPORTED;
   spamm_plan_s* p = new (std::nothrow) spamm_plan_s();
   if (!p) return SPAMM_ERR_NO_MEMORY;
-  p->n = n;
+  p->n = p->m = p->kd = n;
   p->bd = (int)num_blocks(n, leaf);
   st = engine_init(p->eng, single_inst(n, leaf), leaf, precision, 0, workspace, ws_bytes);
   if (st != SPAMM_OK) {
@@ -387,7 +449,7 @@ spamm_status_t spamm_plan_stats(spamm_plan_t plan, spamm_stats_t* stats, void* s
   SPAMM_CUDA_TRY(cudaMemcpyAsync(&h, plan->eng.buf.pd, sizeof(PlanDevice), cudaMemcpyDeviceToHost,
                                  (cudaStream_t)stream));
   SPAMM_CUDA_TRY(cudaStreamSynchronize((cudaStream_t)stream));
-  fill_stats(h, plan->eng.leaf, plan->bd, stats);
+  fill_stats(h, plan->eng.leaf, plan->eng.insts[0].bm, stats);
   return SPAMM_OK;
 }
 
@@ -410,6 +472,7 @@ spamm_status_t spamm_multiply(spamm_plan_t plan, const float* A, const float* B,
     if (!status) return SPAMM_ERR_NO_MEMORY;
   }
   Inst& in = e.insts[0];
+  square_call(in);
   in.A = A;
   in.B = B;
   in.C = C;
@@ -448,11 +511,154 @@ spamm_status_t spamm_plan_multiply(spamm_plan_t plan, const double* normA, const
   in.quant = is_tensor_mode(e.precision) ? 1 : 0;
   in.target_rel = split ? target_rel_err : 0.0;
   in.c1 = split ? 2.0 * u + u * u : 0.0;
+  square_call(in);
   in.A = A;
   in.B = B;
   in.C = C;
   cudaError_t err = engine_plan_multiply(e, make_ref(e.insts.data(), nullptr, 1), status,
                                          (cudaStream_t)stream);
+  if (err != cudaSuccess) {
+    (void)cudaGetLastError();
+    return SPAMM_ERR_CUDA;
+  }
+  return SPAMM_OK;
+}
+
+spamm_status_t spamm_normmap_rect(const float* X, int64_t rows, int64_t cols, int64_t ld,
+                                  int32_t leaf, double* normmap, void* stream) {
+  spamm_status_t st = check_general(rows, 1, cols, leaf);
+  if (st != SPAMM_OK) return st;
+  if (ld < cols) return SPAMM_ERR_INVALID_ARG;
+  if (!X || !normmap || !aligned16(X) || !aligned16(normmap)) return SPAMM_ERR_INVALID_ARG;
+  int32_t* status = device_status_word();
+  if (!status) return SPAMM_ERR_NO_MEMORY;
+  cudaError_t e = launch_normmap_rect(X, rows, cols, ld, leaf, normmap, status,
+                                      (cudaStream_t)stream);
+  if (e != cudaSuccess) {
+    (void)cudaGetLastError();
+    return SPAMM_ERR_CUDA;
+  }
+  return SPAMM_OK;
+}
+
+spamm_status_t spamm_plan_workspace_size_general(int64_t m, int64_t k, int64_t n, int32_t leaf,
+                                                 spamm_precision_t precision, size_t* bytes) {
+  spamm_status_t st = check_general(m, k, n, leaf);
+  if (st != SPAMM_OK) return st;
+  if (!precision_ok(precision) || !bytes) return SPAMM_ERR_INVALID_ARG;
+  if (is_tensor_mode(precision) && leaf == 32) return SPAMM_ERR_UNSUPPORTED;
+  std::vector<Inst> v = general_inst(m, k, n, leaf);
+  *bytes = engine_layout(v, leaf, precision, 0, nullptr, nullptr, nullptr);
+  return SPAMM_OK;
+}
+
+spamm_status_t spamm_plan_create_general(spamm_plan_t* plan, int64_t m, int64_t k, int64_t n,
+                                         int32_t leaf, spamm_precision_t precision,
+                                         void* workspace, size_t ws_bytes) {
+  if (!plan) return SPAMM_ERR_INVALID_ARG;
+  *plan = nullptr;
+  spamm_status_t st = check_general(m, k, n, leaf);
+  if (st != SPAMM_OK) return st;
+  if (!precision_ok(precision)) return SPAMM_ERR_INVALID_ARG;
+  if (is_tensor_mode(precision) && leaf == 32) return SPAMM_ERR_UNSUPPORTED;
+  spamm_plan_s* p = new (std::nothrow) spamm_plan_s();
+  if (!p) return SPAMM_ERR_NO_MEMORY;
+  p->m = m;
+  p->kd = k;
+  p->n = n;
+  p->bd = 0;
+  p->general = true;
+  st = engine_init(p->eng, general_inst(m, k, n, leaf), leaf, precision, 0, workspace, ws_bytes);
+  if (st != SPAMM_OK) {
+    delete p;
+    return st;
+  }
+  *plan = p;
+  return SPAMM_OK;
+}
+
+namespace {
+
+// Argument checks and instance set-up of the general multiply calls.
+spamm_status_t general_call(spamm_plan_t plan, const float* A, int64_t lda, const float* B,
+                            int64_t ldb, float* C, int64_t ldc, float alpha, float beta,
+                            double* normC) {
+  if (!plan || !A || !B || !C) return SPAMM_ERR_INVALID_ARG;
+  if (!aligned16(A) || !aligned16(B) || !aligned16(C)) return SPAMM_ERR_INVALID_ARG;
+  if (normC && !aligned16(normC)) return SPAMM_ERR_INVALID_ARG;
+  if (!std::isfinite(alpha) || !std::isfinite(beta)) return SPAMM_ERR_INVALID_ARG;
+  Inst& in = plan->eng.insts[0];
+  if (lda < in.kd || ldb < in.n || ldc < in.n) return SPAMM_ERR_INVALID_ARG;
+  const size_t sc = span_bytes(in.m, in.n, ldc);
+  if (overlaps(C, sc, A, span_bytes(in.m, in.kd, lda)) ||
+      overlaps(C, sc, B, span_bytes(in.kd, in.n, ldb)))
+    return SPAMM_ERR_INVALID_ARG;
+  in.A = A;
+  in.B = B;
+  in.C = C;
+  in.lda = lda;
+  in.ldb = ldb;
+  in.ldc = ldc;
+  in.alpha = alpha;
+  in.beta = beta;
+  in.nC = normC;
+  return SPAMM_OK;
+}
+
+}  // namespace
+
+spamm_status_t spamm_multiply_general(spamm_plan_t plan, const float* A, int64_t lda,
+                                      const float* B, int64_t ldb, float* C, int64_t ldc,
+                                      float alpha, float beta, double* normC, void* stream) {
+  spamm_status_t st = general_call(plan, A, lda, B, ldb, C, ldc, alpha, beta, normC);
+  if (st != SPAMM_OK) return st;
+  Engine& e = plan->eng;
+  int32_t* status = nullptr;
+  if (e.precision != SPAMM_FP32) {
+    status = device_status_word();
+    if (!status) return SPAMM_ERR_NO_MEMORY;
+  }
+  cudaError_t err = engine_multiply(e, make_ref(e.insts.data(), nullptr, 1), status,
+                                    (cudaStream_t)stream);
+  square_call(e.insts[0]);
+  if (err != cudaSuccess) {
+    (void)cudaGetLastError();
+    return SPAMM_ERR_CUDA;
+  }
+  return SPAMM_OK;
+}
+
+spamm_status_t spamm_plan_multiply_general(spamm_plan_t plan, const double* normA,
+                                           const double* normB, double tau, double target_rel_err,
+                                           const float* A, int64_t lda, const float* B,
+                                           int64_t ldb, float* C, int64_t ldc, float alpha,
+                                           float beta, double* normC, void* stream) {
+  if (!plan || !normA || !normB) return SPAMM_ERR_INVALID_ARG;
+  if (!aligned16(normA) || !aligned16(normB)) return SPAMM_ERR_INVALID_ARG;
+  if (std::isnan(tau) || tau < 0.0) return SPAMM_ERR_INVALID_ARG;
+  Engine& e = plan->eng;
+  const bool split = uses_split_flags(e.precision);
+  if (split && !(target_rel_err >= 0.0)) return SPAMM_ERR_INVALID_ARG;
+  spamm_status_t st = general_call(plan, A, lda, B, ldb, C, ldc, alpha, beta, normC);
+  if (st != SPAMM_OK) return st;
+  int32_t* status = nullptr;
+  if (e.precision != SPAMM_FP32) {
+    status = device_status_word();
+    if (!status) return SPAMM_ERR_NO_MEMORY;
+  }
+  const double u = hi_unit(e.precision);
+  Inst& in = e.insts[0];
+  in.nA = normA;
+  in.nB = normB;
+  in.T = make_tau_screen(tau);
+  in.band = 0;
+  in.split = split ? 1 : 0;
+  in.quant = is_tensor_mode(e.precision) ? 1 : 0;
+  in.target_rel = split ? target_rel_err : 0.0;
+  in.c1 = split ? 2.0 * u + u * u : 0.0;
+  cudaError_t err = engine_plan_multiply(e, make_ref(e.insts.data(), nullptr, 1), status,
+                                         (cudaStream_t)stream);
+  square_call(in);
   if (err != cudaSuccess) {
     (void)cudaGetLastError();
     return SPAMM_ERR_CUDA;
@@ -495,23 +701,24 @@ spamm_status_t spamm_tau_for_valid_ratio(spamm_plan_t plan, const double* normA,
   if (!(target_ratio >= 0.0 && target_ratio <= 1.0) || !(tol >= 0.0) || max_probes < 1)
     return SPAMM_ERR_INVALID_ARG;
   Engine& e = plan->eng;
-  const int bd = plan->bd;
+  const int bm = e.insts[0].bm, bk = e.insts[0].bk, bn = e.insts[0].bn;
   const cudaStream_t s = (cudaStream_t)stream;
-  // ave = mean of nA[i,k] nB[k,j] over all bd^3 triples = sum_k colsum_A(k) rowsum_B(k) / bd^3
-  std::vector<double> ha((size_t)bd * bd), hb((size_t)bd * bd);
+  // ave = mean of nA[i,k] nB[k,j] over all bm bk bn triples
+  //     = sum_k colsum_A(k) rowsum_B(k) / (bm bk bn)
+  std::vector<double> ha((size_t)bm * bk), hb((size_t)bk * bn);
   SPAMM_CUDA_TRY(cudaMemcpyAsync(ha.data(), normA, ha.size() * sizeof(double),
                                  cudaMemcpyDeviceToHost, s));
   SPAMM_CUDA_TRY(cudaMemcpyAsync(hb.data(), normB, hb.size() * sizeof(double),
                                  cudaMemcpyDeviceToHost, s));
   SPAMM_CUDA_TRY(cudaStreamSynchronize(s));
   double acc = 0.0;
-  for (int k = 0; k < bd; ++k) {
+  for (int k = 0; k < bk; ++k) {
     double col = 0.0, row = 0.0;
-    for (int i = 0; i < bd; ++i) col += ha[(size_t)i * bd + k];
-    for (int j = 0; j < bd; ++j) row += hb[(size_t)k * bd + j];
+    for (int i = 0; i < bm; ++i) col += ha[(size_t)i * bk + k];
+    for (int j = 0; j < bn; ++j) row += hb[(size_t)k * bn + j];
     acc += col * row;
   }
-  const double cube = (double)bd * bd * bd;
+  const double cube = (double)bm * bk * bn;
   const double ave = acc / cube;
   Inst& in = e.insts[0];
   in.nA = normA;

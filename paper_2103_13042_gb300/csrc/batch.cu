@@ -74,8 +74,7 @@ std::vector<Inst> shape_table(const int64_t* n, int32_t count, int32_t leaf) {
   std::vector<Inst> v((size_t)count);
   for (int32_t i = 0; i < count; ++i) {
     v[i] = Inst{};
-    v[i].n = n[i];
-    v[i].bd = (int)num_blocks(n[i], leaf);
+    set_square(v[i], n[i], leaf);
   }
   return v;
 }
@@ -84,7 +83,7 @@ std::vector<Inst> shape_table(const int64_t* n, int32_t count, int32_t leaf) {
 size_t batch_extra(const std::vector<Inst>& insts, size_t* norm_bytes, size_t* table_bytes,
                    size_t* insts_offset) {
   int64_t tiles = 0;
-  for (const Inst& in : insts) tiles += (int64_t)in.bd * in.bd;
+  for (const Inst& in : insts) tiles += (int64_t)in.bm * in.bn;
   const size_t nb = align256((size_t)tiles * sizeof(double));
   const size_t jobs = align256(2 * insts.size() * sizeof(NormJob));
   const size_t tb = jobs + insts.size() * sizeof(Inst);
@@ -217,7 +216,7 @@ spamm_status_t spamm_batch_create(spamm_batch_t* batch, const int64_t* n, int32_
       if (((n[i] % 4) == 0) != vec_pass) continue;
       for (int op = 0; op < 2; ++op) {
         NormJob j{};
-        j.n = n[i];
+        j.rows = j.cols = j.ld = n[i];
         j.vec = vec_pass ? 1 : 0;
         b->job_slot[2 * i + op] = slot++;
         b->job_unit0[2 * i + op] = (int)units;
@@ -294,8 +293,9 @@ spamm_status_t upload_tables(spamm_batch_s* b, const spamm_problem_t* problems,
     in.A = problems[i].A;
     in.B = problems[i].B;
     in.C = problems[i].C;
-    in.nA = b->normA + in.tile0;
-    in.nB = b->normB + in.tile0;
+    in.nA = b->normA + in.ablk0;
+    in.nB = b->normB + in.bblk0;
+    in.nC = nullptr;
     in.T = make_tau_screen(targets ? 0.0 : problems[i].tau);
     in.band = 0;
     in.split = split ? 1 : 0;
@@ -305,8 +305,8 @@ spamm_status_t upload_tables(spamm_batch_s* b, const spamm_problem_t* problems,
     for (int op = 0; op < 2; ++op) {
       NormJob& j = jobs[b->job_slot[2 * i + op]];
       j.X = op ? in.B : in.A;
-      j.out = op ? b->normB + in.tile0 : b->normA + in.tile0;
-      j.n = in.n;
+      j.out = op ? b->normB + in.bblk0 : b->normA + in.ablk0;
+      j.rows = j.cols = j.ld = in.n;
       j.vec = (in.n % 4) == 0 ? 1 : 0;
       (void)normjob_shape(j, e.leaf);
       j.unit0 = b->job_unit0[2 * i + op];
@@ -417,7 +417,7 @@ spamm_status_t spamm_batch_stats(spamm_batch_t b, spamm_stats_t* stats, void* st
   SPAMM_CUDA_TRY(cudaMemcpyAsync(h.data(), b->eng.buf.pd, h.size() * sizeof(PlanDevice),
                                  cudaMemcpyDeviceToHost, s));
   SPAMM_CUDA_TRY(cudaStreamSynchronize(s));
-  for (int32_t i = 0; i < b->count; ++i) fill_stats(h[i], b->eng.leaf, b->eng.insts[i].bd, &stats[i]);
+  for (int32_t i = 0; i < b->count; ++i) fill_stats(h[i], b->eng.leaf, b->eng.insts[i].bm, &stats[i]);
   return SPAMM_OK;
 }
 
@@ -426,13 +426,13 @@ spamm_status_t spamm_batch_export(spamm_batch_t b, int32_t index, double* normA,
   if (!b || index < 0 || index >= b->count) return SPAMM_ERR_INVALID_ARG;
   const cudaStream_t s = (cudaStream_t)stream;
   const Inst& in = b->eng.insts[index];
-  const int64_t tiles = (int64_t)in.bd * in.bd;
+  const int64_t tiles = (int64_t)in.bm * in.bn;
   const PlanBuffers& pb = b->eng.buf;
   if (normA)
-    SPAMM_CUDA_TRY(cudaMemcpyAsync(normA, b->normA + in.tile0, (size_t)tiles * sizeof(double),
+    SPAMM_CUDA_TRY(cudaMemcpyAsync(normA, b->normA + in.ablk0, (size_t)tiles * sizeof(double),
                                    cudaMemcpyDeviceToHost, s));
   if (normB)
-    SPAMM_CUDA_TRY(cudaMemcpyAsync(normB, b->normB + in.tile0, (size_t)tiles * sizeof(double),
+    SPAMM_CUDA_TRY(cudaMemcpyAsync(normB, b->normB + in.bblk0, (size_t)tiles * sizeof(double),
                                    cudaMemcpyDeviceToHost, s));
   SPAMM_CUDA_TRY(cudaStreamSynchronize(s));
   return export_queues(pb, in, tile_ptr, k_idx, cap, s);

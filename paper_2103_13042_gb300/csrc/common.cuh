@@ -146,6 +146,16 @@ __device__ __forceinline__ void sumsq_merge(SumSq& acc, float hi, float lo, int 
   acc.lo = __fsub_rn(t, __fsub_rn(acc.hi, s));
 }
 
+// acc += a partner's sum (hi, lo) * 4^e that may be empty (e == kSumSqEmpty;
+// a NaN there still propagates).
+__device__ __forceinline__ void sumsq_merge_any(SumSq& acc, float h, float l, int e) {
+  if (e == kSumSqEmpty) {
+    if (h != h) acc.hi = h;
+  } else {
+    sumsq_merge(acc, h, l, e);
+  }
+}
+
 // Exact-squares sum of one group of N entries into acc.
 //
 // The running pair starts at B = 2 fl((scaled max)^2), so every square p

@@ -78,7 +78,9 @@ cudaError_t noalloc_take_status(cudaStream_t s, int32_t* code);
 
 // A single-instance plan (the C ABI's spamm_plan_t).
 struct spamm_plan_s {
-  int64_t n = 0;
-  int32_t bd = 0;
+  int64_t n = 0;       // C is m x n, A m x kd, B kd x n (all n for a square plan)
+  int64_t m = 0, kd = 0;
+  int32_t bd = 0;      // square plans: blocks per dimension
+  bool general = false;
   spamm::Engine eng;
 };

@@ -1,7 +1,7 @@
 // Learned tau: the FP32 network x(65) -> Linear(65,64) -> GELU -> Linear(64,64)
 // -> GELU -> Linear(64,1) -> y = log10(tau / (||A||_F ||B||_F)), with x the
 // 64-bin histogram of log2 relative norm products (each bin a fraction of
-// all bd^3 triples) followed by log10 of the target relative error.  The
+// all bm * bk * bn triples) followed by log10 of the target relative error.  The
 // paper chooses tau by a valid-ratio search (Section 3.5.2); the network
 // replaces that search with one forward pass, and plain bisection on the
 // achieved error stays the fallback.
@@ -301,7 +301,7 @@ __global__ void __launch_bounds__(128) tau_kernel(InstRef R, const float* __rest
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= R.count) return;
   const Inst& in = R.at(i);
-  const double cube = (double)in.bd * (double)in.bd * (double)in.bd;
+  const double cube = (double)in.bm * (double)in.bk * (double)in.bn;
   float x[kIn];
   for (int b = 0; b < kHistBins; ++b) x[b] = (float)((double)in.pd->hist[b] / cube);
   x[kHistBins] = (float)log10(in.target_rel);

@@ -25,17 +25,18 @@ struct SimtTile {
   static constexpr int kLoadsA = LEAF * kSlice / 4 / kThreads;  // float4 per thread per slice
 };
 
-// Loads 4 consecutive floats of row r, columns c..c+3, zero outside [0, n).
-__device__ __forceinline__ float4 load4(const float* __restrict__ M, int64_t n, int64_t r,
-                                        int64_t c, bool vec) {
-  if (r >= n) return make_float4(0.f, 0.f, 0.f, 0.f);
-  const float* p = M + r * n + c;
-  if (vec && c + 3 < n) return __ldg(reinterpret_cast<const float4*>(p));
+// Loads 4 consecutive floats of row r, columns c..c+3 of a rows x cols matrix
+// with leading dimension ld, zero outside it.
+__device__ __forceinline__ float4 load4(const float* __restrict__ M, int64_t rows, int64_t cols,
+                                        int64_t ld, int64_t r, int64_t c, bool vec) {
+  if (r >= rows) return make_float4(0.f, 0.f, 0.f, 0.f);
+  const float* p = M + r * ld + c;
+  if (vec && c + 3 < cols) return __ldg(reinterpret_cast<const float4*>(p));
   float4 v;
-  v.x = c < n ? __ldg(p) : 0.f;
-  v.y = c + 1 < n ? __ldg(p + 1) : 0.f;
-  v.z = c + 2 < n ? __ldg(p + 2) : 0.f;
-  v.w = c + 3 < n ? __ldg(p + 3) : 0.f;
+  v.x = c < cols ? __ldg(p) : 0.f;
+  v.y = c + 1 < cols ? __ldg(p + 1) : 0.f;
+  v.z = c + 2 < cols ? __ldg(p + 2) : 0.f;
+  v.w = c + 3 < cols ? __ldg(p + 3) : 0.f;
   return v;
 }
 
@@ -91,15 +92,16 @@ __global__ void __launch_bounds__(kThreads) simt_kernel(InstRef R, PlanBuffers B
     if (w >= ne) break;
     const int g = Bf.order[w];
     const Inst& in = R.at(inst_of(R, Bf, g));
-    const int bd = in.bd;
-    const int64_t n = in.n;
+    const int bn = in.bn;
+    const int64_t m = in.m, kd = in.kd, n = in.n;
+    const int64_t lda = in.lda, ldb = in.ldb, ldc = in.ldc;
     const float* __restrict__ A = in.A;
     const float* __restrict__ B = in.B;
     float* __restrict__ C = in.C;
-    const bool VEC = (n % 4) == 0;
+    const bool vec_a = (lda % 4) == 0, vec_b = (ldb % 4) == 0, vec_c = (ldc % 4) == 0;
     const uint16_t* __restrict__ k_idx = Bf.k_idx;
     const int64_t t = g - in.tile0;
-    const int i = (int)(t / bd), j = (int)(t % bd);
+    const int i = (int)(t / bn), j = (int)(t % bn);
     const int beg = Bf.tile_beg[g], end = beg + Bf.cnt[g];
     const int64_t r0 = (int64_t)i * LEAF, c0 = (int64_t)j * LEAF;
 
@@ -121,10 +123,10 @@ __global__ void __launch_bounds__(kThreads) simt_kernel(InstRef R, PlanBuffers B
         const int e = (tid + l * kThreads) * 4;      // element index in the slice
         // A slice: LEAF rows x 32 cols, float4 along the columns
         const int ar = e / kSlice, ac = e % kSlice;
-        ra[l] = load4(A, n, r0 + ar, (int64_t)k * LEAF + s0 + ac, VEC);
+        ra[l] = load4(A, m, kd, lda, r0 + ar, (int64_t)k * LEAF + s0 + ac, vec_a);
         // B slice: 32 rows x LEAF cols, float4 along the columns
         const int br = e / LEAF, bc = e % LEAF;
-        rb[l] = load4(B, n, (int64_t)k * LEAF + s0 + br, c0 + bc, VEC);
+        rb[l] = load4(B, kd, n, ldb, (int64_t)k * LEAF + s0 + br, c0 + bc, vec_b);
       }
     };
     auto stash = [&](int buf) {
@@ -162,18 +164,56 @@ __global__ void __launch_bounds__(kThreads) simt_kernel(InstRef R, PlanBuffers B
       __syncthreads();
     }
 
+    // epilogue: C = alpha * acc + beta * C (the old C is read only when beta != 0)
+    const float alpha = in.alpha, beta = in.beta;
 #pragma unroll
     for (int u = 0; u < TM; ++u) {
       const int64_t r = r0 + ty * TM + u;
-      if (r >= n) continue;
       const int64_t c = c0 + tx * TM;
-      float* p = C + r * n + c;
-      if (VEC && c + TM - 1 < n) {
+      float* p = C + r * ldc + c;
+      const bool row_in = r < m;
+      if (beta != 0.0f && row_in) {
+#pragma unroll
+        for (int q = 0; q < TM; ++q)
+          acc[u][q] = c + q < n ? __fmaf_rn(beta, p[q], __fmul_rn(alpha, acc[u][q])) : 0.0f;
+      } else {
+#pragma unroll
+        for (int q = 0; q < TM; ++q) acc[u][q] = __fmul_rn(alpha, acc[u][q]);
+      }
+      if (!row_in) continue;
+      if (vec_c && c + TM - 1 < n) {
         write_row<TM>(p, acc[u]);
       } else {
 #pragma unroll
         for (int q = 0; q < TM; ++q)
           if (c + q < n) p[q] = acc[u][q];
+      }
+    }
+    if (in.nC) {   // C's norm map for a chained product: the tile's stored values
+      float v[TM * TM];
+#pragma unroll
+      for (int u = 0; u < TM; ++u)
+#pragma unroll
+        for (int q = 0; q < TM; ++q) {
+          const bool inside = r0 + ty * TM + u < m && c0 + tx * TM + q < n;
+          v[u * TM + q] = inside ? acc[u][q] : 0.0f;
+        }
+      SumSq ss = sumsq_empty();
+      sumsq_group<TM * TM>(ss, v);
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) {
+        const float h = __shfl_xor_sync(0xffffffffu, ss.hi, off);
+        const float l = __shfl_xor_sync(0xffffffffu, ss.lo, off);
+        const int e = __shfl_xor_sync(0xffffffffu, ss.e, off);
+        sumsq_merge_any(ss, h, l, e);
+      }
+      __shared__ SumSq s_norm[kThreads / 32];
+      if ((tid & 31) == 0) s_norm[tid / 32] = ss;
+      __syncthreads();
+      if (tid == 0) {
+        SumSq tot = s_norm[0];
+        for (int w = 1; w < kThreads / 32; ++w) sumsq_merge_any(tot, s_norm[w].hi, s_norm[w].lo, s_norm[w].e);
+        in.nC[t] = sumsq_sqrt(tot);
       }
     }
   }

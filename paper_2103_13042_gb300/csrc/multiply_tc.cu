@@ -231,13 +231,16 @@ __global__ void __launch_bounds__(TcCfg<FMT, LEAF, SPLITMODE>::kThreads, 1)
     for (int base = next_base(-1); base < ne && ok; base = next_base(base)) {
       const int w = p.dynamic ? base + lane : base + lane * (int)gridDim.x;
       const bool valid = w < ne;
-      int t = 0, beg = 0, end = 0, bdl = 1;
-      int64_t t0 = 0;
+      int t = 0, beg = 0, end = 0, bkl = 1, bnl = 1;
+      int64_t t0 = 0, a0 = 0, b0 = 0;
       if (valid) {
         t = p.Bf.order[w];                       // global tile
         const Inst& in = p.R.at(inst_of(p.R, p.Bf, t));
         t0 = in.tile0;
-        bdl = in.bd;
+        a0 = in.ablk0;
+        b0 = in.bblk0;
+        bkl = in.bk;
+        bnl = in.bn;
         beg = p.Bf.tile_beg[t];
         end = beg + p.Bf.cnt[t];
       }
@@ -267,15 +270,18 @@ __global__ void __launch_bounds__(TcCfg<FMT, LEAF, SPLITMODE>::kThreads, 1)
         const int bu = __shfl_sync(0xffffffffu, beg, u);
         const int xu = __shfl_sync(0xffffffffu, excl, u);
         const int iu = __shfl_sync(0xffffffffu, incl, u);
-        const int bdu = __shfl_sync(0xffffffffu, bdl, u);
+        const int bku = __shfl_sync(0xffffffffu, bkl, u);
+        const int bnu = __shfl_sync(0xffffffffu, bnl, u);
         const int64_t t0u = __shfl_sync(0xffffffffu, t0, u);
+        const int64_t a0u = __shfl_sync(0xffffffffu, a0, u);
+        const int64_t b0u = __shfl_sync(0xffffffffu, b0, u);
         const int q = bu + (f - xu);
         uint32_t ent = 0;
         if (act) ent = p.Bf.k_idx[q];
         const int k = (int)(ent & 0x3ffu);
         const int64_t lt = (int64_t)tu - t0u;
-        const int i = (int)(lt / bdu), j = (int)(lt % bdu);
-        const int ga = (int)(t0u + (int64_t)i * bdu + k), gb = (int)(t0u + (int64_t)k * bdu + j);
+        const int i = (int)(lt / bnu), j = (int)(lt % bnu);
+        const int ga = (int)(a0u + (int64_t)i * bku + k), gb = (int)(b0u + (int64_t)k * bnu + j);
         int32_t sexp = 0;
         if (act) sexp = p.img.ea[ga] + p.img.eb[gb];
         const bool split = SPLITMODE == 2 || (SPLITMODE == 1 && (ent & 0x8000u));
@@ -511,16 +517,47 @@ __global__ void __launch_bounds__(TcCfg<FMT, LEAF, SPLITMODE>::kThreads, 1)
       ++run;
       if (r.last) {
         const Inst& in = p.R.at(inst_of(p.R, p.Bf, r.tile));
-        const int bd = in.bd;
-        const int64_t n = in.n, lt = (int64_t)r.tile - in.tile0;
-        const int i = (int)(lt / bd), j = (int)(lt % bd);
+        const int bn = in.bn;
+        const int64_t m = in.m, n = in.n, ldc = in.ldc, lt = (int64_t)r.tile - in.tile0;
+        const int i = (int)(lt / bn), j = (int)(lt % bn);
         const int64_t gr = (int64_t)i * LEAF + row;
-        if (lane_has_row && gr < n) {
-          float* dst = in.C + gr * n + (int64_t)j * LEAF + col0;
-          const int64_t cols = n - (int64_t)j * LEAF - col0;
-          if (Cfg::kBulkEpilogue && (n & 3) == 0) {
+        const int64_t cols = n - (int64_t)j * LEAF - col0;
+        const bool row_in = lane_has_row && gr < m;
+        float* dst = in.C + gr * ldc + (int64_t)j * LEAF + col0;
+        // C = alpha * acc + beta * C (the old C is read only when beta != 0)
+        const float alpha = in.alpha, beta = in.beta;
+        if (beta != 0.0f && row_in) {
+#pragma unroll
+          for (int c = 0; c < NC; ++c)
+            acc[c] = c < cols ? __fmaf_rn(beta, dst[c], __fmul_rn(alpha, acc[c])) : 0.0f;
+        } else if (alpha != 1.0f) {
+#pragma unroll
+          for (int c = 0; c < NC; ++c) acc[c] = __fmul_rn(alpha, acc[c]);
+        }
+        if (in.nC) {
+          // C's norm map for a chained product: this warp's part of the tile's
+          // sum of squares (its rows x its 64 columns) goes to the tile's slot
+          float v[NC];
+#pragma unroll
+          for (int c = 0; c < NC; ++c) v[c] = (row_in && c < cols) ? acc[c] : 0.0f;
+          SumSq ss = sumsq_empty();
+          sumsq_group<NC>(ss, v);
+#pragma unroll
+          for (int off = 16; off > 0; off >>= 1) {
+            const float h = __shfl_xor_sync(0xffffffffu, ss.hi, off);
+            const float l = __shfl_xor_sync(0xffffffffu, ss.lo, off);
+            const int e = __shfl_xor_sync(0xffffffffu, ss.e, off);
+            sumsq_merge_any(ss, h, l, e);
+          }
+          if (lane == 0)
+            reinterpret_cast<NormPart*>(p.Bf.norm_part)[(int64_t)r.tile * kMaxEpiWarps +
+                                                        (warp - kFirstEpiWarp)] =
+                NormPart{ss.hi, ss.lo, ss.e, 0};
+        }
+        if (row_in) {
+          if (Cfg::kBulkEpilogue && (ldc & 3) == 0 && (n & 3) == 0) {
             // the row goes through shared memory and leaves as one bulk copy
-            // (n % 4 == 0: 16-byte aligned, cols % 4 == 0)
+            // (ldc % 4 == 0: 16-byte aligned; n % 4 == 0: whole 16-byte pieces)
             if (cols > 0) {
               bulk_wait_read0();   // this lane's previous row has left the buffer
 #pragma unroll
@@ -531,7 +568,7 @@ __global__ void __launch_bounds__(TcCfg<FMT, LEAF, SPLITMODE>::kThreads, 1)
               bulk_s2g(dst, smem_u32(stage_row), (uint32_t)(cols < NC ? cols : NC) * 4u);
               bulk_commit();
             }
-          } else if ((n & 3) == 0 && cols >= NC) {
+          } else if ((ldc & 3) == 0 && cols >= NC) {
 #pragma unroll
             for (int c = 0; c < NC; c += 4)
               *reinterpret_cast<float4*>(dst + c) =
@@ -558,63 +595,112 @@ __global__ void __launch_bounds__(TcCfg<FMT, LEAF, SPLITMODE>::kThreads, 1)
   }
 }
 
-// Zeros for every tile without survivors: the plan lists them after the
-// non-empty tiles in `order`.  One warp per tile (many independent warps keep
-// enough stores in flight for the HBM write rate); lane l owns column group
-// l % (leaf/4) and every (32 / (leaf/4))-th row, 16-byte streaming stores.
+// One tile without survivors, written by a whole warp: C = beta * C, which
+// for beta = 0 is zeros (16-byte streaming stores when the rows are 16-byte
+// aligned: lane l owns float4 column l % (leaf/4) and every (32 / (leaf/4))-th
+// row, so a warp store covers whole 128-byte row segments) and for beta = 1
+// leaves C as it is; with an output norm map the tile's norm is written too.
+template <int LEAF>
+__device__ __forceinline__ void empty_tile(const Inst& in, int64_t lt, int lane) {
+  constexpr int kPerRow = LEAF / 4;                          // float4 per tile row
+  constexpr int kRowsPerStore = kPerRow >= 32 ? 1 : 32 / kPerRow;
+  constexpr int kColSteps = kPerRow >= 32 ? kPerRow / 32 : 1;
+  const int bn = in.bn;
+  const int ti = (int)(lt / bn), tj = (int)(lt - (int64_t)ti * bn);
+  const int64_t r0 = (int64_t)ti * LEAF, c0 = (int64_t)tj * LEAF;
+  const int rows = (int)min((int64_t)LEAF, in.m - r0), cols = (int)min((int64_t)LEAF, in.n - c0);
+  const int64_t ldc = in.ldc;
+  float* C = in.C;
+  const float beta = in.beta;
+  if (beta == 0.0f) {
+    const int my_c4 = kPerRow >= 32 ? lane : lane % kPerRow;
+    const int my_r = kPerRow >= 32 ? 0 : lane / kPerRow;
+    const bool vec = (ldc & 3) == 0 && (in.n & 3) == 0;   // then cols % 4 == 0
+    const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (vec && rows == LEAF && cols == LEAF) {   // aligned full tile: unrolled stores
+#pragma unroll
+      for (int cs = 0; cs < kColSteps; ++cs) {
+        float4* p = reinterpret_cast<float4*>(C + (r0 + my_r) * ldc + c0) + my_c4 + 32 * cs;
+        const int64_t step = (int64_t)kRowsPerStore * ldc / 4;
+#pragma unroll 8
+        for (int r = 0; r < LEAF / kRowsPerStore; ++r) __stcs(p + r * step, z);
+      }
+    } else if (vec) {   // aligned ragged tile
+      for (int cs = 0; cs < kColSteps; ++cs) {
+        const int c4 = my_c4 + 32 * cs;
+        if (4 * c4 >= cols) continue;
+        float4* p = reinterpret_cast<float4*>(C + (r0 + my_r) * ldc + c0 + 4 * c4);
+        const int64_t step = (int64_t)kRowsPerStore * ldc / 4;
+        for (int r = my_r; r < rows; r += kRowsPerStore, p += step) __stcs(p, z);
+      }
+    } else {
+      for (int u = lane; u < rows * cols; u += 32) {
+        const int r = u / cols, c = u - r * cols;
+        C[(r0 + r) * ldc + c0 + c] = 0.f;
+      }
+    }
+    if (in.nC && lane == 0) in.nC[lt] = 0.0;
+    return;
+  }
+  if (beta == 1.0f && !in.nC) return;
+  SumSq ss = sumsq_empty();
+  for (int u0 = 0; u0 < rows * cols; u0 += 32 * 32) {
+    float v[32];
+#pragma unroll 4
+    for (int q = 0; q < 32; ++q) {
+      const int u = u0 + q * 32 + lane;
+      float x = 0.0f;
+      if (u < rows * cols) {
+        float* p = C + (r0 + u / cols) * ldc + c0 + u % cols;
+        x = __fmul_rn(beta, *p);
+        if (beta != 1.0f) *p = x;
+      }
+      v[q] = x;
+    }
+    if (in.nC) sumsq_group<32>(ss, v);
+  }
+  if (in.nC) {
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+      const float h = __shfl_xor_sync(0xffffffffu, ss.hi, off);
+      const float l = __shfl_xor_sync(0xffffffffu, ss.lo, off);
+      const int e = __shfl_xor_sync(0xffffffffu, ss.e, off);
+      sumsq_merge_any(ss, h, l, e);
+    }
+    if (lane == 0) in.nC[lt] = sumsq_sqrt(ss);
+  }
+}
+
+// Every tile without survivors: the plan lists them after the non-empty tiles
+// in `order`.  One warp per tile (many independent warps keep enough stores in
+// flight for the HBM write rate).
 template <int LEAF>
 __global__ void __launch_bounds__(256)
     zero_tiles_kernel(InstRef R, PlanBuffers Bf) {
-  constexpr int kPerRow = LEAF / 4;                         // float4 per tile row
-  constexpr int kRowStep = kPerRow >= 32 ? 1 : 32 / kPerRow; // rows per warp store
-  constexpr int kColSteps = kPerRow >= 32 ? kPerRow / 32 : 1;
   const int lane = threadIdx.x & 31;
-  const int my_c4 = kPerRow >= 32 ? lane : lane % kPerRow;
-  const int my_r = kPerRow >= 32 ? 0 : lane / kPerRow;
   const int ne = Bf.bdev->nonempty;
   const int64_t nw = (int64_t)gridDim.x * (blockDim.x / 32);
   for (int64_t e = ne + ((int64_t)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32); e < Bf.tiles;
        e += nw) {
     const int64_t g = Bf.order[e];
     const Inst& in = R.at(inst_of(R, Bf, g));
-    const int64_t n = in.n, lt = g - in.tile0;
-    const int bd = in.bd;
-    const int ti = (int)(lt / bd), tj = (int)(lt - (int64_t)ti * bd);
-    const int64_t r0 = (int64_t)ti * LEAF, c0 = (int64_t)tj * LEAF;
-    const int rows = (int)min((int64_t)LEAF, n - r0), cols = (int)min((int64_t)LEAF, n - c0);
-    float* C = in.C;
-    if ((n & 3) == 0) {   // then cols % 4 == 0 and every float4 is aligned
-#pragma unroll
-      for (int cs = 0; cs < kColSteps; ++cs) {
-        const int c4 = my_c4 + 32 * cs;
-        if (4 * c4 >= cols) continue;
-        float4* p = reinterpret_cast<float4*>(C + (r0 + my_r) * n + c0 + 4 * c4);
-        const int64_t step = (int64_t)kRowStep * n / 4;
-        for (int r = my_r; r < rows; r += kRowStep, p += step) __stcs(p, make_float4(0.f, 0.f, 0.f, 0.f));
-      }
-    } else {
-      for (int u = lane; u < rows * cols; u += 32) C[(r0 + u / cols) * n + c0 + u % cols] = 0.f;
-    }
+    empty_tile<LEAF>(in, g - in.tile0, lane);
   }
 }
 
-// Zeros for the tiles without survivors found from the counts.  Every CTA
-// takes an equal contiguous range of global tiles (so every SM writes about
-// the same number of bytes); warp 0 lists the range's empty tiles in shared
-// memory (coalesced count loads, ballots), then each warp writes whole empty
-// tiles (list entries warp, warp + 8, ...): lane l owns float4 column
-// l % (leaf/4) and every (32 / (leaf/4))-th row, so a warp store covers whole
-// 128-byte row segments, and the tile's address arithmetic is paid once per
-// leaf*leaf*4 bytes.  16-byte streaming stores.
+// The same from the per-tile counts alone (may run as soon as the plan's
+// counting half has finished).  Every CTA takes an equal contiguous range of
+// global tiles (so every SM writes about the same number of bytes); warp 0
+// lists the range's empty tiles in shared memory (coalesced count loads,
+// ballots), then each warp takes whole empty tiles (list entries warp,
+// warp + 8, ...), so the tile's address arithmetic is paid once per
+// leaf*leaf*4 bytes.
 constexpr int kZeroThreads = 256;
 constexpr int kZeroMaxRange = 64;   // tiles per CTA at most (the grid grows beyond that)
 
 template <int LEAF>
 __global__ void __launch_bounds__(kZeroThreads)
     zero_scan_kernel(InstRef R, PlanBuffers Bf) {
-  constexpr int kPerRow = LEAF / 4;                          // float4 per tile row
-  constexpr int kRowsPerStore = kPerRow >= 32 ? 1 : 32 / kPerRow;
-  constexpr int kColSteps = kPerRow >= 32 ? kPerRow / 32 : 1;
   constexpr int kWarps = kZeroThreads / 32;
   __shared__ int s_list[kZeroMaxRange];
   __shared__ int s_count;
@@ -634,41 +720,32 @@ __global__ void __launch_bounds__(kZeroThreads)
   }
   __syncthreads();
   const int count = s_count;
-  const int my_c4 = kPerRow >= 32 ? lane : lane % kPerRow;
-  const int my_r = kPerRow >= 32 ? 0 : lane / kPerRow;
   for (int e = warp; e < count; e += kWarps) {
     const int64_t g = lo + s_list[e];
     const Inst& in = R.at(inst_of(R, Bf, g));
-    const int64_t n = in.n;
-    const int lt = (int)(g - in.tile0), bd = in.bd;   // lt < 2^20
-    const int ti = lt / bd, tj = lt - ti * bd;
-    const int64_t r0 = (int64_t)ti * LEAF, c0 = (int64_t)tj * LEAF;
-    const int rows = (int)min((int64_t)LEAF, n - r0), cols = (int)min((int64_t)LEAF, n - c0);
-    float* C = in.C;
-    if ((n & 3) == 0 && rows == LEAF && cols == LEAF) {   // aligned full tile: unrolled stores
-      const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
-#pragma unroll
-      for (int cs = 0; cs < kColSteps; ++cs) {
-        float4* p = reinterpret_cast<float4*>(C + (r0 + my_r) * n + c0) + my_c4 + 32 * cs;
-        const int64_t step = (int64_t)kRowsPerStore * n / 4;
-#pragma unroll 8
-        for (int r = 0; r < LEAF / kRowsPerStore; ++r) __stcs(p + r * step, z);
-      }
-    } else if ((n & 3) == 0) {   // aligned ragged tile: cols % 4 == 0
-      for (int cs = 0; cs < kColSteps; ++cs) {
-        const int c4 = my_c4 + 32 * cs;
-        if (4 * c4 >= cols) continue;
-        float4* p = reinterpret_cast<float4*>(C + (r0 + my_r) * n + c0 + 4 * c4);
-        const int64_t step = (int64_t)kRowsPerStore * n / 4;
-        for (int r = my_r; r < rows; r += kRowsPerStore, p += step)
-          __stcs(p, make_float4(0.f, 0.f, 0.f, 0.f));
-      }
-    } else {
-      for (int u = lane; u < rows * cols; u += 32) {
-        const int r = u / cols, c = u - r * cols;
-        C[(r0 + r) * n + c0 + c] = 0.f;
-      }
+    empty_tile<LEAF>(in, g - in.tile0, lane);
+  }
+}
+
+// Output norm maps of the tensor-core multiply: each non-empty tile's
+// epilogue warps left their partial sums of squares in the tile's slot; one
+// thread per tile merges them (in warp order) and writes the norm.
+__global__ void __launch_bounds__(256)
+    norm_out_finish_kernel(InstRef R, PlanBuffers Bf, int parts) {
+  pdl_wait();
+  const int ne = Bf.bdev->nonempty;
+  const NormPart* np = reinterpret_cast<const NormPart*>(Bf.norm_part);
+  for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < ne;
+       w += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t g = Bf.order[w];
+    const Inst& in = R.at(inst_of(R, Bf, g));
+    if (!in.nC) continue;
+    SumSq ss = sumsq_empty();
+    for (int q = 0; q < parts; ++q) {
+      const NormPart x = np[g * kMaxEpiWarps + q];
+      sumsq_merge_any(ss, x.hi, x.lo, x.e);
     }
+    in.nC[g - in.tile0] = sumsq_sqrt(ss);
   }
 }
 
@@ -747,6 +824,16 @@ cudaError_t launch_zero_empty_tiles_scan(const InstRef& ref, const PlanBuffers& 
     default: return cudaErrorInvalidValue;
   }
   return cudaPeekAtLastError();
+}
+
+cudaError_t launch_norm_out_finish(const InstRef& ref, const PlanBuffers& b, int leaf,
+                                   cudaStream_t s) {
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((b.tiles + 255) / 256, (int64_t)sms * 4));
+  return launch_pdl(norm_out_finish_kernel, dim3(grid), dim3(256), 0, s, ref, b,
+                    4 * (leaf / 64));
 }
 
 cudaError_t launch_multiply_tc(spamm_precision_t prec, int leaf, const InstRef& ref,

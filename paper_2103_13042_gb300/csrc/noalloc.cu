@@ -162,8 +162,7 @@ extern "C" spamm_status_t spamm_multiply_fp32_noalloc(const float* A, const floa
   // scratch: [normA | normB | plan buffers]
   const size_t norm_bytes = round256((size_t)bd * bd * sizeof(double));
   Inst inst{};
-  inst.n = n;
-  inst.bd = bd;
+  set_square(inst, n, leaf);
   const size_t plan_bytes = plan_layout(&inst, 1, nullptr, nullptr);
   if (2 * norm_bytes + plan_bytes > kNoAllocBytes) return SPAMM_ERR_UNSUPPORTED;
 

@@ -1,4 +1,5 @@
-// Get-norm step (Section 3.2, Eq. 2): normmap[I*bd+K] = ||X[I,K]||_F.
+// Get-norm step (Section 3.2, Eq. 2): normmap[I*bc+K] = ||X[I,K]||_F for a
+// rows x cols operand (leading dimension ld) with bc = ceil(cols / leaf).
 //
 // GB300 design.  FP64 arithmetic runs at 1/72 of the FP32 rate on this part,
 // so every group of 32 entries is scaled by a power of two (no FP32 underflow
@@ -27,7 +28,7 @@
 // copy at an odd offset ran at about 60% of the line-aligned rate); the
 // producer records each row's offset into its copy, and the entries the copy
 // carries from neighbouring rows are not read.  Rows 16-byte aligned
-// (n % 4 == 0): float4 reads.  Any other n: scalar reads, each lane taking its
+// (ld % 4 == 0): float4 reads.  Any other ld: scalar reads, each lane taking its
 // 4 columns in a lane-dependent rotation so that the warp's reads hit 32
 // different banks, and the matrix's last few entries past the last 16-byte
 // boundary inside X read from global memory directly.
@@ -153,9 +154,14 @@ __device__ __forceinline__ UnitPos unit_pos(const NormJob& jb, int u) {
   p.I = local / jb.nwin;
   p.col0 = (int64_t)(local - p.I * jb.nwin) * Cfg::kWinCols;
   p.row0 = (int64_t)p.I * LEAF;
-  p.rows = (int)(jb.n - p.row0 < LEAF ? jb.n - p.row0 : LEAF);
-  p.width = (int)(jb.n - p.col0 < Cfg::kWinCols ? jb.n - p.col0 : Cfg::kWinCols);
+  p.rows = (int)(jb.rows - p.row0 < LEAF ? jb.rows - p.row0 : LEAF);
+  p.width = (int)(jb.cols - p.col0 < Cfg::kWinCols ? jb.cols - p.col0 : Cfg::kWinCols);
   return p;
+}
+
+// Entries X spans: from its first to its last entry, (rows - 1) * ld + cols.
+__device__ __forceinline__ int64_t job_span(const NormJob& jb) {
+  return (jb.rows - 1) * jb.ld + jb.cols;
 }
 
 template <int LEAF, class Cfg>
@@ -189,7 +195,7 @@ __global__ void __launch_bounds__(Cfg::kThreads, Cfg::kCtasPerSm)
     for (int u = blockIdx.x; u < J.units && ok; u += gridDim.x) {
       const NormJob jb = job_of(J, u);
       const UnitPos p = unit_pos<LEAF, Cfg>(jb, u);
-      const int64_t n = jb.n;
+      const int64_t ld = jb.ld;
       const float* X = jb.X;
       for (int r = 0; r < p.rows; r += kRows) {
         const int rr = p.rows - r < kRows ? p.rows - r : kRows;
@@ -200,10 +206,10 @@ __global__ void __launch_bounds__(Cfg::kThreads, Cfg::kCtasPerSm)
         // lane q < rr copies row row0 + r + q: whole 128-byte lines, clipped
         // to X's first byte and to its last 16-byte boundary
         const uintptr_t xb = reinterpret_cast<uintptr_t>(X);
-        const uintptr_t xend = xb + (uintptr_t)(((n * n) & ~(int64_t)3) * 4);
+        const uintptr_t xend = xb + (uintptr_t)((job_span(jb) & ~(int64_t)3) * 4);
         uintptr_t a0 = 0, a1 = 0;
         if (lane < rr) {
-          const uintptr_t b0 = xb + (uintptr_t)(((p.row0 + r + lane) * n + p.col0) * 4);
+          const uintptr_t b0 = xb + (uintptr_t)(((p.row0 + r + lane) * ld + p.col0) * 4);
           const uintptr_t b1 = b0 + (uintptr_t)p.width * 4u;
           a0 = b0 & ~(uintptr_t)127;
           if (a0 < xb) a0 = xb;
@@ -250,8 +256,8 @@ __global__ void __launch_bounds__(Cfg::kThreads, Cfg::kCtasPerSm)
   for (int u = blockIdx.x; u < J.units; u += gridDim.x, parity ^= 1u) {
     const NormJob jb = job_of(J, u);
     const UnitPos p = unit_pos<LEAF, Cfg>(jb, u);
-    const int64_t n = jb.n;
-    const bool active = p.col0 + cw < n;
+    const int64_t ld = jb.ld, cols = jb.cols;
+    const bool active = p.col0 + cw < cols;
     SumSq ss = sumsq_empty();
     for (int r = 0; r < p.rows && ok; r += kRows) {
       const int rr = p.rows - r < kRows ? p.rows - r : kRows;
@@ -301,10 +307,10 @@ __global__ void __launch_bounds__(Cfg::kThreads, Cfg::kCtasPerSm)
         }
       } else {
         const int64_t row_first = p.row0 + r + kRowsPerPart * part;
-        const int64_t lim = (n * n) & ~(int64_t)3;   // entries past it: read from global
-        const bool tail = p.row0 + r + rr == n && (n - 1) * n + p.col0 + p.width > lim;
+        const int64_t lim = job_span(jb) & ~(int64_t)3;   // entries past it: read from global
+        const bool tail = p.row0 + r + rr == jb.rows && (jb.rows - 1) * ld + p.col0 + p.width > lim;
         // columns of this lane inside the matrix (4 except at its right edge)
-        const int64_t left = n - (p.col0 + cw);
+        const int64_t left = cols - (p.col0 + cw);
         const int nv = left >= 4 ? 4 : (left > 0 ? (int)left : 0);
         if (mine >= kRowsPerPart && nv == 4 && !tail) {
 #pragma unroll
@@ -333,12 +339,34 @@ __global__ void __launch_bounds__(Cfg::kThreads, Cfg::kCtasPerSm)
               const int c = (l8 + jj) & 3;
               float x = 0.0f;
               if (q < mine && c < nv) {
-                const int64_t e = (row_first + q) * n + p.col0 + cw + c;
+                const int64_t e = (row_first + q) * ld + p.col0 + cw + c;
                 x = e < lim ? rp[c] : __ldg(jb.X + e);
               }
               v[4 * q + jj] = x;
             }
           }
+        }
+      }
+      if constexpr (ALIGNED) {
+        // a rectangular operand whose width is not a multiple of 4: the lane at the right
+        // edge read entries past the last column (the gap up to the leading dimension), and
+        // the matrix's last few entries, past its last 16-byte boundary, were not copied:
+        // those come from global memory
+        const int64_t left = cols - (p.col0 + cw);
+        if (left < 4 && active) {
+          const int64_t lim = job_span(jb) & ~(int64_t)3;
+          const int64_t row_first = p.row0 + r + kRowsPerPart * part;
+#pragma unroll
+          for (int q = 0; q < 8; ++q)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+              if (c >= left) {
+                v[4 * q + c] = 0.0f;
+              } else if (q < mine) {
+                const int64_t e = (row_first + q) * ld + p.col0 + cw + c;
+                if (e >= lim) v[4 * q + c] = __ldg(jb.X + e);
+              }
+            }
         }
       }
       __syncwarp();
@@ -370,7 +398,7 @@ __global__ void __launch_bounds__(Cfg::kThreads, Cfg::kCtasPerSm)
       }
     }
     if ((lane % kLanesPerBlockCol) == 0 && active)
-      jb.out[(int64_t)p.I * jb.bd + (p.col0 + cw) / LEAF] =
+      jb.out[(int64_t)p.I * jb.bc + (p.col0 + cw) / LEAF] =
           (ok && !*abort_flag) ? sumsq_sqrt(ss) : __longlong_as_double(0x7ff8000000000000ll);
   }
 }
@@ -454,27 +482,57 @@ cudaError_t launch_normmap_wait_selftest(int32_t* status, uint64_t limit_ns, lon
 }
 
 int normjob_shape(NormJob& j, int leaf) {
-  j.bd = (int)num_blocks(j.n, leaf);
-  j.lines = (j.n % 32) == 0 && (reinterpret_cast<uintptr_t>(j.X) % 128) == 0 ? 1 : 0;
+  j.br = (int)num_blocks(j.rows, leaf);
+  j.bc = (int)num_blocks(j.cols, leaf);
+  j.lines = (j.ld % 32) == 0 && (reinterpret_cast<uintptr_t>(j.X) % 128) == 0 ? 1 : 0;
   const int win = j.vec ? StagedAligned::kWinCols : StagedUnaligned::kWinCols;
-  j.nwin = (int)((j.n + win - 1) / win);
-  return j.bd * j.nwin;
+  j.nwin = (int)((j.cols + win - 1) / win);
+  return j.br * j.nwin;
 }
 
-cudaError_t launch_normmap(const float* X, int64_t n, int32_t leaf, double* out, int32_t* status,
-                           cudaStream_t s) {
+cudaError_t launch_normmap_rect(const float* X, int64_t rows, int64_t cols, int64_t ld,
+                                int32_t leaf, double* out, int32_t* status, cudaStream_t s) {
   if (reinterpret_cast<uintptr_t>(X) % 16) return cudaErrorMisalignedAddress;   // bulk copies
   StagedJobs J{};
   J.count = 1;
   NormJob& j = J.one[0];
   j.X = X;
   j.out = out;
-  j.n = n;
-  j.vec = (n % 4) == 0;
+  j.rows = rows;
+  j.cols = cols;
+  j.ld = ld;
+  j.vec = (ld % 4) == 0;
   j.unit0 = 0;
   J.units = normjob_shape(j, leaf);
   return j.vec ? launch_leaf<StagedAligned>(leaf, J, status, s)
                : launch_leaf<StagedUnaligned>(leaf, J, status, s);
+}
+
+cudaError_t launch_normmap(const float* X, int64_t n, int32_t leaf, double* out, int32_t* status,
+                           cudaStream_t s) {
+  return launch_normmap_rect(X, n, n, n, leaf, out, status, s);
+}
+
+cudaError_t launch_normmap_pair(const float* A, const float* B, int64_t n, int32_t leaf,
+                                double* outA, double* outB, int32_t* status, cudaStream_t s) {
+  if ((reinterpret_cast<uintptr_t>(A) | reinterpret_cast<uintptr_t>(B)) % 16)
+    return cudaErrorMisalignedAddress;   // bulk copies
+  StagedJobs J{};
+  J.count = 2;
+  const bool vec = (n % 4) == 0;
+  int units = 0;
+  for (int q = 0; q < 2; ++q) {
+    NormJob& j = J.one[q];
+    j.X = q ? B : A;
+    j.out = q ? outB : outA;
+    j.rows = j.cols = j.ld = n;
+    j.vec = vec;
+    j.unit0 = units;
+    units += normjob_shape(j, leaf);
+  }
+  J.units = units;
+  return vec ? launch_leaf<StagedAligned>(leaf, J, status, s)
+             : launch_leaf<StagedUnaligned>(leaf, J, status, s);
 }
 
 cudaError_t launch_normmap_jobs(const NormJob* dev_jobs, int n_vec, int units_vec, int n_other,

@@ -64,12 +64,12 @@ static_assert(kTilesPerCta % kGroupRows == 0, "a CTA of a full band covers whole
 // kGroupRows block rows, column by column inside a band, so that tiles close
 // in the enumeration (and so in the multiply's order, which keeps it inside
 // a bucket) share block rows of A and block columns of B in L2.
-__device__ __forceinline__ void tile_at(int64_t pos64, int bd, int& i, int& j) {
-  const int pos = (int)pos64;              // bd <= 1024: pos < 2^20
-  const int band_tiles = kGroupRows * bd;
+__device__ __forceinline__ void tile_at(int64_t pos64, int bm, int bn, int& i, int& j) {
+  const int pos = (int)pos64;              // bm * bn <= 2^22
+  const int band_tiles = kGroupRows * bn;
   const int band = pos / band_tiles;
   const int r0 = band * kGroupRows;
-  const int rows = min(kGroupRows, bd - r0);
+  const int rows = min(kGroupRows, bm - r0);
   const int w = pos - band * band_tiles;
   j = w / rows;
   i = r0 + (w - j * rows);
@@ -220,6 +220,24 @@ __device__ __forceinline__ int rel_bin_screened(Screen a, Screen b, float inv_m,
 }
 
 
+__host__ __device__ __forceinline__ int64_t prep_units(const Inst& in) {
+  const int64_t na = (int64_t)in.bm * in.bk, nb = (int64_t)in.bk * in.bn,
+                nt = (int64_t)in.bm * in.bn;
+  return na > nb ? (na > nt ? na : nt) : (nb > nt ? nb : nt);
+}
+
+}  // namespace
+
+int prep_ctas_of(const Inst& in) {
+  return (int)((prep_units(in) + kPrepThreads - 1) / kPrepThreads);
+}
+
+namespace {
+
+__device__ __forceinline__ int prep_ctas_dev(const Inst& in) {
+  return (int)((prep_units(in) + kPrepThreads - 1) / kPrepThreads);
+}
+
 __device__ __forceinline__ int inst_of_prep_cta(const InstRef& r, int cta) {
   return find_inst(r, cta, [](const Inst& x) { return (int64_t)x.prep0; });
 }
@@ -232,19 +250,22 @@ __global__ void __launch_bounds__(kPrepThreads)
   pdl_trigger();
   const int ii = inst_of_prep_cta(R, blockIdx.x);
   const Inst& in = R.at(ii);
-  const int bd = in.bd;
-  const int64_t total = (int64_t)bd * bd;
+  const int64_t na = (int64_t)in.bm * in.bk, nb = (int64_t)in.bk * in.bn,
+                nt = (int64_t)in.bm * in.bn;
   const int lc = blockIdx.x - in.prep0;
-  const int nctas = (int)((total + kPrepThreads - 1) / kPrepThreads);
+  const int nctas = prep_ctas_dev(in);
   const int64_t idx = (int64_t)lc * kPrepThreads + threadIdx.x;
   double qa = 0.0, qb = 0.0;
-  if (idx < total) {
-    const double a = in.nA[idx], b = in.nB[idx];
-    Bf.tile_inst[in.tile0 + idx] = ii;
-    Bf.sA[in.tile0 + idx] = make_screen(a);
-    const int64_t k = idx / bd, j = idx % bd;
-    Bf.sBT[in.tile0 + j * bd + k] = make_screen(b);
+  if (idx < nt) Bf.tile_inst[in.tile0 + idx] = ii;
+  if (idx < na) {
+    const double a = in.nA[idx];
+    Bf.sA[in.ablk0 + idx] = make_screen(a);
     qa = a * a;
+  }
+  if (idx < nb) {
+    const double b = in.nB[idx];
+    const int64_t k = idx / in.bn, j = idx % in.bn;
+    Bf.sBT[in.bblk0 + j * in.bk + k] = make_screen(b);
     qb = b * b;
   }
   for (int off = 16; off > 0; off >>= 1) {
@@ -321,7 +342,7 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, 4)
   if (threadIdx.x < kOrderKeys) s_keys[threadIdx.x] = 0;
   const int ii = inst_of_count_cta(R, blockIdx.x);
   const Inst& in = R.at(ii);
-  const int bd = in.bd;
+  const int bm = in.bm, bk = in.bk, bn = in.bn;
   const bool split = SPLIT && in.split, band = BAND && in.band;
   const TauScreen T = in.T;
   const double* nA = in.nA;
@@ -337,25 +358,25 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, 4)
   const double inv = pd->inv_ab;   // written by the prep kernel
   int inv_e;
   const float inv_m = (float)frexp(inv, &inv_e);
-  const int64_t tiles = (int64_t)bd * bd;
-  const int nch = (bd + 31) >> 5;
+  const int64_t tiles = (int64_t)bm * bn;
+  const int nch = (bk + 31) >> 5;
   const int64_t lt0 = (int64_t)(blockIdx.x - in.count0) * kTilesPerCta;
   // When the CTA's 32 positions lie in one full band they are 8 block rows x
   // 4 block columns (warp w: row r0 + w, columns j0 .. j0 + 3): those 8 rows
   // of A's screens and 4 columns of B's are staged in shared memory with one
   // coalesced load, so each warp meets one memory latency instead of one per
   // tile.  Other CTAs (a ragged last band) read the screens from global memory.
-  extern __shared__ Screen s_scr[];   // [8 * bd] A rows, then [4 * bd] B columns
-  const int64_t band_tiles = (int64_t)kGroupRows * bd;
+  extern __shared__ Screen s_scr[];   // [8 * bk] A rows, then [4 * bk] B columns
+  const int64_t band_tiles = (int64_t)kGroupRows * bn;
   const int64_t band0 = lt0 / band_tiles;
   const int r0 = (int)band0 * kGroupRows;
-  const bool staged = band0 == (lt0 + kTilesPerCta - 1) / band_tiles && r0 + kGroupRows <= bd &&
+  const bool staged = band0 == (lt0 + kTilesPerCta - 1) / band_tiles && r0 + kGroupRows <= bm &&
                       lt0 + kTilesPerCta <= tiles;
   const int j0 = (int)((lt0 - band0 * band_tiles) / kGroupRows);
   if (staged) {
-    const int na = kGroupRows * bd, nb = kTilesPerCta / kGroupRows * bd;
-    const Screen* ga = Bf.sA + in.tile0 + (int64_t)r0 * bd;
-    const Screen* gb = Bf.sBT + in.tile0 + (int64_t)j0 * bd;
+    const int na = kGroupRows * bk, nb = kTilesPerCta / kGroupRows * bk;
+    const Screen* ga = Bf.sA + in.ablk0 + (int64_t)r0 * bk;
+    const Screen* gb = Bf.sBT + in.bblk0 + (int64_t)j0 * bk;
 #pragma unroll 4
     for (int x = threadIdx.x; x < na + nb; x += blockDim.x)
       s_scr[x] = x < na ? ga[x] : gb[x - na];
@@ -368,21 +389,21 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, 4)
     const int64_t pos = lt0 + warp + (int64_t)r * kWarpsPerCta;
     if (pos >= tiles) break;
     int i, j;
-    tile_at(pos, bd, i, j);
-    const int64_t t = (int64_t)i * bd + j;
-    const Screen* ra = staged ? s_scr + (i - r0) * bd : Bf.sA + in.tile0 + (int64_t)i * bd;
-    const Screen* rb = staged ? s_scr + (kGroupRows + j - j0) * bd : Bf.sBT + in.tile0 + (int64_t)j * bd;
+    tile_at(pos, bm, bn, i, j);
+    const int64_t t = (int64_t)i * bn + j;
+    const Screen* ra = staged ? s_scr + (i - r0) * bk : Bf.sA + in.ablk0 + (int64_t)i * bk;
+    const Screen* rb = staged ? s_scr + (kGroupRows + j - j0) * bk : Bf.sBT + in.bblk0 + (int64_t)j * bk;
     SkipSum sk{0.0f, kSkipNone};
     int count = 0;
     // the screens of up to kChunks 32-wide chunks of k are loaded together
     // (one latency per group instead of one per chunk)
     constexpr int kChunks = 2;
-    for (int kg = 0; kg < bd; kg += 32 * kChunks) {
+    for (int kg = 0; kg < bk; kg += 32 * kChunks) {
       Screen av[kChunks], bv[kChunks];
 #pragma unroll
       for (int q = 0; q < kChunks; ++q) {
         const int k = kg + 32 * q + lane;
-        if (k < bd) {
+        if (k < bk) {
           av[q] = ra[k];
           bv[q] = rb[k];
         }
@@ -390,19 +411,19 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, 4)
 #pragma unroll
     for (int q = 0; q < kChunks; ++q) {
       const int k0 = kg + 32 * q;
-      if (k0 >= bd) break;   // uniform over the warp
+      if (k0 >= bk) break;   // uniform over the warp
       const int k = k0 + lane;
       bool s = false;
-      if (k < bd) {
+      if (k < bk) {
         const Screen a = av[q], b = bv[q];
-        s = survives(a, b, nA + (int64_t)i * bd + k, nB + (int64_t)k * bd + j, T);
-        if (BAND && s && band)
-          s = !survives(a, b, nA + (int64_t)i * bd + k, nB + (int64_t)k * bd + j, in.T_hi);
+        const double* pa = nA + (int64_t)i * bk + k;
+        const double* pb = nB + (int64_t)k * bn + j;
+        s = survives(a, b, pa, pb, T);
+        if (BAND && s && band) s = !survives(a, b, pa, pb, in.T_hi);
         if (!s) {
           skip_add(sk, a, b);
         } else if (split) {
-          bin_survivor(a, b, nA + (int64_t)i * bd + k, nB + (int64_t)k * bd + j, pd, s_bin_sum,
-                       s_bin_cnt);
+          bin_survivor(a, b, pa, pb, pd, s_bin_sum, s_bin_cnt);
         }
       }
       const unsigned bal = __ballot_sync(0xffffffffu, s);
@@ -502,7 +523,7 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32)
   const int warp = threadIdx.x / 32, lane = threadIdx.x & 31;
   const int ii = inst_of_count_cta(R, blockIdx.x);
   const Inst& in = R.at(ii);
-  const int bd = in.bd;
+  const int bk = in.bk, bn = in.bn;
   const double* nA = in.nA;
   const double* nB = in.nB;
   for (int q = threadIdx.x; q < kHistBins; q += blockDim.x) s_hist[q] = 0u;
@@ -510,21 +531,21 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32)
   const double inv = in.pd->inv_ab;   // written by the prep kernel
   int inv_e;
   const float inv_m = (float)frexp(inv, &inv_e);
-  const int64_t tiles = (int64_t)bd * bd;
+  const int64_t tiles = (int64_t)in.bm * bn;
   const int64_t lt0 = (int64_t)(blockIdx.x - in.count0) * kTilesPerCta;
   for (int r = 0; r < kTileRounds; ++r) {
     const int64_t t = lt0 + warp + (int64_t)r * kWarpsPerCta;
     if (t >= tiles) break;
-    const int i = (int)(t / bd), j = (int)(t % bd);
-    const Screen* ra = Bf.sA + in.tile0 + (int64_t)i * bd;
-    const Screen* rb = Bf.sBT + in.tile0 + (int64_t)j * bd;
-    for (int k0 = 0; k0 < bd; k0 += 32) {
+    const int i = (int)(t / bn), j = (int)(t % bn);
+    const Screen* ra = Bf.sA + in.ablk0 + (int64_t)i * bk;
+    const Screen* rb = Bf.sBT + in.bblk0 + (int64_t)j * bk;
+    for (int k0 = 0; k0 < bk; k0 += 32) {
       const int k = k0 + lane;
-      const bool act = k < bd;
+      const bool act = k < bk;
       int bin = kHistBins;   // inactive lanes: a bin of their own
       if (act)
-        bin = hist_bin_screened(ra[k], rb[k], inv_m, inv_e, nA + (int64_t)i * bd + k,
-                                nB + (int64_t)k * bd + j, inv);
+        bin = hist_bin_screened(ra[k], rb[k], inv_m, inv_e, nA + (int64_t)i * bk + k,
+                                nB + (int64_t)k * bn + j, inv);
       const unsigned same = __match_any_sync(0xffffffffu, bin);
       if (act && lane == __ffs(same) - 1) atomicAdd(&s_hist[bin], (unsigned)__popc(same));
     }
@@ -592,8 +613,7 @@ __global__ void __launch_bounds__(kFinThreads)
   __shared__ ExtSum s_b1[kFinThreads / 32], s_b2[kFinThreads / 32];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const Inst& in = R.at(blockIdx.x);
-  const int bd = in.bd;
-  const int nparts = (int)(((int64_t)bd * bd + kTilesPerCta - 1) / kTilesPerCta);
+  const int nparts = (int)(((int64_t)in.bm * in.bn + kTilesPerCta - 1) / kTilesPerCta);
   PlanDevice* pd = in.pd;
 
   // each thread takes a contiguous chunk of the instance's count CTAs
@@ -606,7 +626,7 @@ __global__ void __launch_bounds__(kFinThreads)
   ExtSum locB1{0.0f, 0}, locB2{0.0f, 0};
   for (int q = p0; q < p1; ++q) {
     const int cq = in.count0 + q;
-    loc[0] += (int)Bf.part_S[cq];   // at most 32 * bd per CTA
+    loc[0] += (int)Bf.part_S[cq];   // at most 32 * bk per CTA
     loc[1] += Bf.part_ne[cq];
 #pragma unroll
     for (int key = 1; key < kOrderKeys; ++key)
@@ -703,7 +723,7 @@ __global__ void __launch_bounds__(kFinThreads)
       for (int key = 1; key < kOrderKeys; ++key) pd->key_tot[key] = tot[1 + key];
       pd->bound1 = b1 * ab;
       pd->bound2 = bound2;
-      pd->valid_ratio = (double)tot[0] / ((double)bd * (double)bd * (double)bd);
+      pd->valid_ratio = (double)tot[0] / ((double)in.bm * (double)in.bk * (double)in.bn);
       pd->flag_exp = m;
       pd->flagged = flagged;
     }
@@ -800,14 +820,14 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32)
   const int warp = threadIdx.x / 32, lane = threadIdx.x & 31;
   const int ii = inst_of_count_cta(R, blockIdx.x);
   const Inst& in = R.at(ii);
-  const int bd = in.bd, split = in.split, quant = in.quant;
+  const int bm = in.bm, bk = in.bk, bn = in.bn, split = in.split, quant = in.quant;
   const double* nA = in.nA;
   const double* nB = in.nB;
-  const int64_t tiles = (int64_t)bd * bd;
-  const int nch = (bd + 31) >> 5;
+  const int64_t tiles = (int64_t)bm * bn;
+  const int nch = (bk + 31) >> 5;
   const int64_t lt0 = (int64_t)(blockIdx.x - in.count0) * kTilesPerCta;
   uint32_t* bitsA = Bf.need_bits;
-  uint32_t* bitsB = Bf.need_bits + Bf.need_words;
+  uint32_t* bitsB = Bf.need_bits + Bf.need_words_a;
   if (warp == 0) {   // first k_idx slot of each of the CTA's tiles (kTilesPerCta == 32 lanes)
     const int64_t pos = lt0 + lane;
     // lane q < kOrderKeys: this CTA's first slot in bucket q (loaded with the counts)
@@ -818,8 +838,8 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32)
     int c = 0;
     if (pos < tiles) {
       int i, j;
-      tile_at(pos, bd, i, j);
-      g = in.tile0 + (int64_t)i * bd + j;
+      tile_at(pos, bm, bn, i, j);
+      g = in.tile0 + (int64_t)i * bn + j;
       c = Bf.cnt[g];
     }
     int incl = c;
@@ -855,15 +875,15 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32)
     const int64_t pos = lt0 + lt;
     if (pos >= tiles) break;
     int i, j;
-    tile_at(pos, bd, i, j);
-    const int64_t g = in.tile0 + (int64_t)i * bd + j;
+    tile_at(pos, bm, bn, i, j);
+    const int64_t g = in.tile0 + (int64_t)i * bn + j;
     const int c = Bf.cnt[g];
     if (c == 0) continue;
-    const Screen* ra = Bf.sA + in.tile0 + (int64_t)i * bd;
-    const Screen* rb = Bf.sBT + in.tile0 + (int64_t)j * bd;
+    const Screen* ra = Bf.sA + in.ablk0 + (int64_t)i * bk;
+    const Screen* rb = Bf.sBT + in.bblk0 + (int64_t)j * bk;
     int base = s_beg[lt];
     // the count kernel's ballots: one word per 32 k, expanded in increasing k
-    const uint32_t* mrow = Bf.surv_mask + in.mask0 + ((int64_t)i * bd + j) * nch;
+    const uint32_t* mrow = Bf.surv_mask + in.mask0 + ((int64_t)i * bn + j) * nch;
     for (int qg = 0; qg < nch; qg += 4) {
       unsigned words[4];
 #pragma unroll
@@ -876,15 +896,15 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32)
         const bool s = (ball >> lane) & 1u;
         if (s) {
           uint16_t v = (uint16_t)k;
-          if (split && rel_bin_screened(ra[k], rb[k], inv_m, inv_e, nA + (int64_t)i * bd + k,
-                                        nB + (int64_t)k * bd + j, inv) >= m)
+          if (split && rel_bin_screened(ra[k], rb[k], inv_m, inv_e, nA + (int64_t)i * bk + k,
+                                        nB + (int64_t)k * bn + j, inv) >= m)
             v |= kSplitFlag;
           Bf.k_idx[base + __popc(ball & ((1u << lane) - 1u))] = v;
         }
         base += __popc(ball);
         if (quant) {
           // list the A and B blocks of surviving triples, each once over the plan
-          const int64_t ga = in.tile0 + (int64_t)i * bd + k, gb = in.tile0 + (int64_t)k * bd + j;
+          const int64_t ga = in.ablk0 + (int64_t)i * bk + k, gb = in.bblk0 + (int64_t)k * bn + j;
           bool newA = false, newB = false;
           if (s) {
             const uint32_t bitA = 1u << (ga & 31), bitB = 1u << (gb & 31);
@@ -908,25 +928,48 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32)
 
 }  // namespace
 
-int prep_ctas_of(int bd) { return (int)(((int64_t)bd * bd + kPrepThreads - 1) / kPrepThreads); }
-int count_ctas_of(int bd) { return (int)(((int64_t)bd * bd + kTilesPerCta - 1) / kTilesPerCta); }
+int count_ctas_of(const Inst& in) {
+  return (int)(((int64_t)in.bm * in.bn + kTilesPerCta - 1) / kTilesPerCta);
+}
 
-size_t plan_layout(Inst* insts, int count, PlanBuffers* b, char* base) {
-  int64_t tiles = 0, kslots = 0, mwords = 0;
-  int prep = 0, cnt = 0, max_bd = 0;
+void set_general(Inst& in, int64_t m, int64_t kd, int64_t n, int64_t lda, int64_t ldb,
+                 int64_t ldc, float alpha, float beta, int leaf) {
+  in.m = m;
+  in.kd = kd;
+  in.n = n;
+  in.lda = lda;
+  in.ldb = ldb;
+  in.ldc = ldc;
+  in.bm = (int)num_blocks(m, leaf);
+  in.bk = (int)num_blocks(kd, leaf);
+  in.bn = (int)num_blocks(n, leaf);
+  in.alpha = alpha;
+  in.beta = beta;
+}
+
+void set_square(Inst& in, int64_t n, int leaf) { set_general(in, n, n, n, n, n, n, 1.0f, 0.0f, leaf); }
+
+size_t plan_layout(Inst* insts, int count, PlanBuffers* b, char* base, bool norm_parts) {
+  int64_t tiles = 0, ablks = 0, bblks = 0, kslots = 0, mwords = 0;
+  int prep = 0, cnt = 0, max_bk = 0;
   for (int i = 0; i < count; ++i) {
-    const int64_t bd = insts[i].bd;
-    max_bd = max_bd > (int)bd ? max_bd : (int)bd;
-    insts[i].tile0 = tiles;
-    insts[i].kidx0 = kslots;
-    insts[i].mask0 = mwords;
-    insts[i].prep0 = prep;
-    insts[i].count0 = cnt;
-    tiles += bd * bd;
-    kslots += bd * bd * bd;
-    mwords += bd * bd * ((bd + 31) / 32);
-    prep += prep_ctas_of((int)bd);
-    cnt += count_ctas_of((int)bd);
+    Inst& in = insts[i];
+    const int64_t bm = in.bm, bk = in.bk, bn = in.bn;
+    max_bk = max_bk > (int)bk ? max_bk : (int)bk;
+    in.tile0 = tiles;
+    in.ablk0 = ablks;
+    in.bblk0 = bblks;
+    in.kidx0 = kslots;
+    in.mask0 = mwords;
+    in.prep0 = prep;
+    in.count0 = cnt;
+    tiles += bm * bn;
+    ablks += bm * bk;
+    bblks += bk * bn;
+    kslots += bm * bk * bn;
+    mwords += bm * bn * ((bk + 31) / 32);
+    prep += prep_ctas_of(in);
+    cnt += count_ctas_of(in);
   }
   size_t off = 0;
   auto take = [&](size_t bytes) {
@@ -937,16 +980,20 @@ size_t plan_layout(Inst* insts, int count, PlanBuffers* b, char* base) {
   };
   PlanBuffers t{};
   t.tiles = tiles;
+  t.ablks = ablks;
+  t.bblks = bblks;
   t.kslots = kslots;
   t.prep_ctas = prep;
   t.count_ctas = cnt;
-  t.max_bd = max_bd;
-  t.need_words = (tiles + 31) / 32;
+  t.max_bk = max_bk;
+  t.need_words_a = (ablks + 31) / 32;
+  t.need_words_b = (bblks + 31) / 32;
   t.pd = reinterpret_cast<PlanDevice*>(take((size_t)count * sizeof(PlanDevice)));
   t.bdev = reinterpret_cast<BatchDevice*>(take(sizeof(BatchDevice)));
-  t.need_bits = reinterpret_cast<uint32_t*>(take((size_t)(2 * t.need_words) * sizeof(uint32_t)));
-  t.sA = reinterpret_cast<Screen*>(take((size_t)tiles * sizeof(Screen)));
-  t.sBT = reinterpret_cast<Screen*>(take((size_t)tiles * sizeof(Screen)));
+  t.need_bits = reinterpret_cast<uint32_t*>(
+      take((size_t)(t.need_words_a + t.need_words_b) * sizeof(uint32_t)));
+  t.sA = reinterpret_cast<Screen*>(take((size_t)ablks * sizeof(Screen)));
+  t.sBT = reinterpret_cast<Screen*>(take((size_t)bblks * sizeof(Screen)));
   t.part_a = reinterpret_cast<double*>(take((size_t)prep * sizeof(double)));
   t.part_b = reinterpret_cast<double*>(take((size_t)prep * sizeof(double)));
   t.part_S = reinterpret_cast<long long*>(take((size_t)cnt * sizeof(long long)));
@@ -964,7 +1011,8 @@ size_t plan_layout(Inst* insts, int count, PlanBuffers* b, char* base) {
   t.k_idx = reinterpret_cast<uint16_t*>(take((size_t)kslots * sizeof(uint16_t)));
   t.tile_inst = reinterpret_cast<int*>(take((size_t)tiles * sizeof(int)));
   t.surv_mask = reinterpret_cast<uint32_t*>(take((size_t)mwords * sizeof(uint32_t)));
-  t.need_list = reinterpret_cast<uint32_t*>(take((size_t)(2 * tiles) * sizeof(uint32_t)));
+  t.need_list = reinterpret_cast<uint32_t*>(take((size_t)(ablks + bblks) * sizeof(uint32_t)));
+  t.norm_part = norm_parts ? take((size_t)tiles * kMaxEpiWarps * sizeof(NormPart)) : nullptr;
   for (int i = 0; i < count; ++i) insts[i].pd = t.pd ? t.pd + i : nullptr;
   if (b) *b = t;
   return (off + 255) / 256 * 256;
@@ -978,13 +1026,14 @@ InstRef make_ref(const Inst* host_insts, const Inst* dev_table, int count) {
   for (int i = 0; i < count; ++i) {
     r.any_split |= host_insts[i].split != 0;
     r.any_band |= host_insts[i].band != 0;
+    r.any_norm_out |= host_insts[i].nC != nullptr;
   }
   return r;
 }
 
-// The count kernel with its staged screens: 12 * max_bd screens of shared memory.
+// The count kernel with its staged screens: 12 * max_bk screens of shared memory.
 cudaError_t launch_count(const InstRef& ref, const PlanBuffers& b, cudaStream_t s) {
-  const size_t smem = (size_t)(kGroupRows + kTilesPerCta / kGroupRows) * b.max_bd * sizeof(Screen);
+  const size_t smem = (size_t)(kGroupRows + kTilesPerCta / kGroupRows) * b.max_bk * sizeof(Screen);
   auto* kern = ref.any_band ? (ref.any_split ? count_kernel<true, true> : count_kernel<false, true>)
                             : (ref.any_split ? count_kernel<true, false> : count_kernel<false, false>);
   {   // opt in to the largest size once per device and variant (static shared memory counts too)
@@ -1006,8 +1055,9 @@ cudaError_t launch_count(const InstRef& ref, const PlanBuffers& b, cudaStream_t 
 cudaError_t run_plan_count_half(const InstRef& ref, const PlanBuffers& b, cudaStream_t s) {
   // clear the per-instance statistics, the batch-wide order state and the
   // needed-block bits (laid out back to back, one memset)
-  const size_t clear = reinterpret_cast<const char*>(b.need_bits + 2 * b.need_words) -
-                       reinterpret_cast<const char*>(b.pd);
+  const size_t clear =
+      reinterpret_cast<const char*>(b.need_bits + b.need_words_a + b.need_words_b) -
+      reinterpret_cast<const char*>(b.pd);
   cudaError_t e = cudaMemsetAsync(b.pd, 0, clear, s);
   if (e != cudaSuccess) return e;
   prep_kernel<<<b.prep_ctas, kPrepThreads, 0, s>>>(ref, b);
@@ -1030,8 +1080,9 @@ cudaError_t run_plan(const InstRef& ref, const PlanBuffers& b, cudaStream_t s) {
 }
 
 cudaError_t run_plan_count(const InstRef& ref, const PlanBuffers& b, cudaStream_t s) {
-  const size_t clear = reinterpret_cast<const char*>(b.need_bits + 2 * b.need_words) -
-                       reinterpret_cast<const char*>(b.pd);
+  const size_t clear =
+      reinterpret_cast<const char*>(b.need_bits + b.need_words_a + b.need_words_b) -
+      reinterpret_cast<const char*>(b.pd);
   cudaError_t e = cudaMemsetAsync(b.pd, 0, clear, s);
   if (e != cudaSuccess) return e;
   prep_kernel<<<b.prep_ctas, kPrepThreads, 0, s>>>(ref, b);
@@ -1043,8 +1094,9 @@ cudaError_t run_plan_count(const InstRef& ref, const PlanBuffers& b, cudaStream_
 }
 
 cudaError_t run_histogram(const InstRef& ref, const PlanBuffers& b, cudaStream_t s) {
-  const size_t clear = reinterpret_cast<const char*>(b.need_bits + 2 * b.need_words) -
-                       reinterpret_cast<const char*>(b.pd);
+  const size_t clear =
+      reinterpret_cast<const char*>(b.need_bits + b.need_words_a + b.need_words_b) -
+      reinterpret_cast<const char*>(b.pd);
   cudaError_t e = cudaMemsetAsync(b.pd, 0, clear, s);
   if (e != cudaSuccess) return e;
   prep_kernel<<<b.prep_ctas, kPrepThreads, 0, s>>>(ref, b);

@@ -1,12 +1,17 @@
 // Device-side plan state shared by the plan and multiply kernels.
 //
 // Every kernel works on a table of SpAMM instances (one entry for a single
-// product, many for a batch).  Instance i owns bd_i^2 tiles, numbered
-// globally from tile0_i = sum of bd^2 of the instances before it; leaf blocks
-// of A and B use the same numbering (block (I, K) of instance i is
-// tile0_i + I * bd_i + K).  Its surviving k indices live in k_idx slots from
-// kidx0_i = sum of bd^3 of the instances before it.  All instances of a
-// table share one leaf size.
+// product, many for a batch).  An instance is the general product of
+// Section 2, C = alpha * SpAMM(A, B) + beta * C, with A m x kd, B kd x n and
+// C m x n (row-major, leading dimensions lda, ldb, ldc), zero padded to whole
+// leaf blocks: block grids bm x bk (A), bk x bn (B) and bm x bn (C).  The
+// square product of the rest of the paper is m = kd = n, alpha = 1, beta = 0.
+// Instance i owns bm_i * bn_i output tiles, numbered globally from tile0_i
+// (the sum over the instances before it), bm_i * bk_i blocks of A from ablk0_i
+// and bk_i * bn_i blocks of B from bblk0_i (block (I, K) of A is
+// ablk0 + I * bk + K, block (K, J) of B is bblk0 + K * bn + J).  Its
+// surviving k indices live in k_idx slots from kidx0_i = sum of bm * bk * bn
+// of the instances before it.  All instances of a table share one leaf size.
 #pragma once
 
 #include "common.cuh"
@@ -72,15 +77,20 @@ struct Inst {
   const float* A;
   const float* B;
   float* C;
-  const double* nA;     // norm maps [bd * bd]
+  const double* nA;     // norm maps: A [bm * bk], B [bk * bn], row-major
   const double* nB;
-  int64_t n;
-  int bd;
+  double* nC;           // C's norm map [bm * bn], written by the multiply when non-null
+  int64_t m, kd, n;     // C is m x n, A is m x kd, B is kd x n
+  int64_t lda, ldb, ldc;
+  int bm, bk, bn;       // block grids
+  float alpha, beta;    // C = alpha * sum + beta * C; beta = 0: the old C is not read
   int split;            // 1: BF16/FP16 split mode (dominant triples get hi+lo)
   int quant;            // 1: the multiply rounds operands (build the needed-block list)
-  int64_t tile0;        // first global tile / block index
+  int64_t tile0;        // first global output tile
+  int64_t ablk0;        // first global block of A
+  int64_t bblk0;        // first global block of B
   int64_t kidx0;        // first k_idx slot
-  int64_t mask0;        // first word of the survivor bitmask (bd * bd * ceil(bd / 32) words)
+  int64_t mask0;        // first word of the survivor bitmask (bm * bn * ceil(bk / 32) words)
   int prep0;            // first CTA of this instance in the prep grid
   int count0;           // first CTA of this instance in the count and fill grids
   double target_rel;    // split modes: relative error target
@@ -99,6 +109,7 @@ struct InstRef {
   Inst one;
   int count;
   int any_split, any_band;   // some instance uses split flags / a band (host-side dispatch)
+  int any_norm_out;          // some instance writes an output norm map (nC)
   __device__ __forceinline__ const Inst& at(int i) const { return table ? table[i] : one; }
 };
 
@@ -118,16 +129,24 @@ __device__ __forceinline__ int find_inst(const InstRef& r, int64_t v, Key key) {
 __device__ __forceinline__ int inst_of_tile(const InstRef& r, int64_t g) {
   return find_inst(r, g, [](const Inst& x) { return x.tile0; });
 }
+__device__ __forceinline__ int inst_of_ablk(const InstRef& r, int64_t g) {
+  return find_inst(r, g, [](const Inst& x) { return x.ablk0; });
+}
+__device__ __forceinline__ int inst_of_bblk(const InstRef& r, int64_t g) {
+  return find_inst(r, g, [](const Inst& x) { return x.bblk0; });
+}
 
 // Device buffers of a plan (carved from one workspace allocation).
 struct PlanBuffers {
-  int64_t tiles;       // sum of bd^2
-  int64_t kslots;      // sum of bd^3
+  int64_t tiles;       // sum of bm * bn (output tiles)
+  int64_t ablks;       // sum of bm * bk (blocks of A)
+  int64_t bblks;       // sum of bk * bn (blocks of B)
+  int64_t kslots;      // sum of bm * bk * bn
   int prep_ctas;       // prep grid
   int count_ctas;      // count and fill grids
-  int max_bd;          // largest bd of the table (the count kernel's shared-memory size)
-  Screen* sA;          // [tiles] screen form of normA, row-major per instance
-  Screen* sBT;         // [tiles] screen form of normB, transposed per instance
+  int max_bk;          // largest bk of the table (the count kernel's shared-memory size)
+  Screen* sA;          // [ablks] screen form of normA, row-major per instance
+  Screen* sBT;         // [bblks] screen form of normB, transposed per instance (J * bk + K)
   double* part_a;      // [prep_ctas] partial sums of squared norms
   double* part_b;
   long long* part_S;   // [count_ctas] per-CTA partials of the count kernel
@@ -144,27 +163,39 @@ struct PlanBuffers {
   int* order;          // [tiles] global ids: the non-empty tiles, most survivors first, then
                        // the empty tiles in increasing order
   uint16_t* k_idx;     // [kslots] surviving k per tile, increasing (bit 15: split triple)
-  int* tile_inst;      // [tiles] instance of each global tile / block
-  uint32_t* surv_mask; // survivors of each tile, 32 k per word (tile t = i*bd + j of an instance)
-  uint32_t* need_bits; // [2 * words] bit g: block g of A (first half) / B (second half) is used
-  uint32_t* need_list; // [2 * tiles] used blocks, each once: g (A) or g | 2^31 (B)
-  int64_t need_words;  // 32-bit words per operand in need_bits
+  int* tile_inst;      // [tiles] instance of each global output tile
+  uint32_t* surv_mask; // survivors of each tile, 32 k per word (tile t = i*bn + j of an instance)
+  uint32_t* need_bits; // [words_a + words_b] bit g: block g of A (first part) / B (second) is used
+  uint32_t* need_list; // [ablks + bblks] used blocks, each once: g (A) or g | 2^31 (B)
+  int64_t need_words_a;   // 32-bit words of the A part of need_bits
+  int64_t need_words_b;
+  void* norm_part;     // tensor modes with an output norm map: per-tile partial sums
   PlanDevice* pd;      // [instances]; pd, bdev and need_bits are contiguous (one memset)
   BatchDevice* bdev;
 };
 
-// Instance of a global tile (or leaf block) number.
+// Instance of a global output tile.
 __device__ __forceinline__ int inst_of(const InstRef& r, const PlanBuffers& b, int64_t g) {
   return r.count <= 1 ? 0 : b.tile_inst[g];
 }
 
-// Grid sizes of the plan kernels for one instance of bd x bd tiles.
-int prep_ctas_of(int bd);
-int count_ctas_of(int bd);
+// Grid sizes of the plan kernels for one instance.
+int prep_ctas_of(const Inst& in);
+int count_ctas_of(const Inst& in);
 
-// Fills the layout fields of `insts` (tile0, kidx0, prep0, count0) and of `b`;
-// carves the buffers from `base` when non-null.  Returns the bytes needed.
-size_t plan_layout(Inst* insts, int count, PlanBuffers* b, char* base);
+// Sets the shape fields of a square n x n instance (alpha = 1, beta = 0).
+void set_square(Inst& in, int64_t n, int leaf);
+// Sets the shape fields of C (m x n) = A (m x kd) B (kd x n) with the given
+// leading dimensions, alpha and beta.
+void set_general(Inst& in, int64_t m, int64_t kd, int64_t n, int64_t lda, int64_t ldb,
+                 int64_t ldc, float alpha, float beta, int leaf);
+
+// Fills the layout fields of `insts` (tile0, ablk0, bblk0, kidx0, mask0,
+// prep0, count0; the shape fields must be set) and of `b`; carves the buffers
+// from `base` when non-null.  Returns the bytes needed.
+// `norm_parts`: also provision the per-tile partial sums of the tensor-core
+// epilogue's output norm maps.
+size_t plan_layout(Inst* insts, int count, PlanBuffers* b, char* base, bool norm_parts = false);
 
 // Host wrapper of a table: `dev_table` holds a device copy (batches) or is
 // null (a single instance, passed by value).
@@ -189,30 +220,45 @@ cudaError_t run_histogram(const InstRef& ref, const PlanBuffers& b, cudaStream_t
 // that were not finished are then NaN.
 cudaError_t launch_normmap(const float* X, int64_t n, int32_t leaf, double* out, int32_t* status,
                            cudaStream_t s);
+// Both n x n operands of a product in one launch (their units dealt together).
+cudaError_t launch_normmap_pair(const float* A, const float* B, int64_t n, int32_t leaf,
+                                double* outA, double* outB, int32_t* status, cudaStream_t s);
+// The same for a rows x cols operand with leading dimension ld.
+cudaError_t launch_normmap_rect(const float* X, int64_t rows, int64_t cols, int64_t ld,
+                                int32_t leaf, double* out, int32_t* status, cudaStream_t s);
 
 // Norm-map jobs (one per operand of an instance) of the staged norm-map
-// kernel.  X must be 16-byte aligned.  A job table lists the jobs whose rows
-// are 16-byte aligned (vec: n % 4 == 0) first, then the others; unit0 counts
-// the kernel's units (block rows x column windows) from the start of the
-// job's part of the table.
+// kernel: X is rows x cols, row-major with leading dimension ld, 16-byte
+// aligned; out is [br * bc].  A job table lists the jobs whose rows are
+// 16-byte aligned (vec: ld % 4 == 0) first, then the others; unit0 counts the
+// kernel's units (block rows x column windows) from the start of the job's
+// part of the table.
 struct NormJob {
   const float* X;
   double* out;
-  int64_t n;
-  int bd, nwin, unit0, vec;
-  int lines;   // every row starts on a 128-byte line (X 128-byte aligned, n % 32 == 0)
-  int pad_;
+  int64_t rows, cols, ld;
+  int br, bc, nwin, unit0, vec;
+  int lines;   // every row starts on a 128-byte line (X 128-byte aligned, ld % 32 == 0)
 };
 // Self-test of the norm map's bounded wait (a phase nothing completes).
 cudaError_t launch_normmap_wait_selftest(int32_t* status, uint64_t limit_ns, long long* out,
                                          cudaStream_t s);
-// Sets bd, nwin and lines from X, n, vec and the leaf; returns the job's units.
+// Sets br, bc, nwin and lines from X, rows, cols, ld, vec and the leaf;
+// returns the job's units.
 int normjob_shape(NormJob& j, int leaf);
 cudaError_t launch_normmap_jobs(const NormJob* dev_jobs, int n_vec, int units_vec, int n_other,
                                 int units_other, int leaf, int32_t* status, cudaStream_t s);
 
 cudaError_t launch_multiply_simt(const InstRef& ref, const PlanBuffers& b, int leaf,
                                  int schedule, cudaStream_t s);
+
+// Per-tile partial sums of squares of the tensor-core epilogue (output norm
+// maps): one per epilogue warp of a tile, merged by launch_norm_out_finish.
+constexpr int kMaxEpiWarps = 8;
+struct NormPart {
+  float hi, lo;
+  int e, pad_;
+};
 
 // Learned tau (FP32 network, 8449 parameters).
 int mlp_param_count();

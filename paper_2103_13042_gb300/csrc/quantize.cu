@@ -48,9 +48,10 @@ __device__ __forceinline__ uint32_t pack2(float a, float b) {
   }
 }
 
-// Loads X[r][c] of an n x n matrix, 0 outside it.
-__device__ __forceinline__ float ld_or_zero(const float* X, int64_t n, int64_t r, int64_t c) {
-  return (r < n && c < n) ? __ldg(X + r * n + c) : 0.0f;
+// Loads X[r][c] of a rows x cols matrix with leading dimension ld, 0 outside it.
+__device__ __forceinline__ float ld_or_zero(const float* X, int64_t rows, int64_t cols,
+                                            int64_t ld, int64_t r, int64_t c) {
+  return (r < rows && c < cols) ? __ldg(X + r * ld + c) : 0.0f;
 }
 
 // One CTA per used leaf block (the plan's needed-block list), one pass: each
@@ -92,13 +93,17 @@ __global__ void __launch_bounds__(q_threads<LEAF>())
   for (int idx = blockIdx.x; idx < count; idx += gridDim.x) {
     const uint32_t ent = Bf.need_list[idx];
     const bool isB = (ent >> 31) != 0;
-    const int64_t blk = (int64_t)(ent & 0x7fffffffu);   // global block number
-    const Inst& in = R.at(inst_of(R, Bf, blk));
-    const int64_t n = in.n, lb = blk - in.tile0;
+    const int64_t blk = (int64_t)(ent & 0x7fffffffu);   // global block number of A or of B
+    const Inst& in = R.at(isB ? inst_of_bblk(R, blk) : inst_of_ablk(R, blk));
+    // A block (I, K): rows of A, K along its columns; B block (K, J): K along its rows
+    const int64_t lb = blk - (isB ? in.bblk0 : in.ablk0);
+    const int64_t gcols = isB ? in.bn : in.bk;                 // blocks per row of the grid
+    const int64_t rows = isB ? in.kd : in.m, cols = isB ? in.n : in.kd;
+    const int64_t ld = isB ? in.ldb : in.lda;                  // leading dimension
     const float* __restrict__ X = isB ? in.B : in.A;
-    const int64_t r0 = (lb / in.bd) * LEAF, c0 = (lb % in.bd) * LEAF;
-    const bool full = r0 + LEAF <= n && c0 + LEAF <= n;
-    const bool vec = full && (n & 3) == 0;
+    const int64_t r0 = (lb / gcols) * LEAF, c0 = (lb % gcols) * LEAF;
+    const bool full = r0 + LEAF <= rows && c0 + LEAF <= cols;
+    const bool vec = full && (ld & 3) == 0;
 
     if (isB && vec) {   // stage the block row-major (float4, coalesced), then read it
                         // transposed; the previous block's pieces were read before the
@@ -106,7 +111,7 @@ __global__ void __launch_bounds__(q_threads<LEAF>())
       constexpr int F4 = LEAF / 4;   // float4 per block row
       for (int t = tid; t < LEAF * F4; t += kThreads) {
         const int rr = t / F4, c4 = t - rr * F4;
-        const float4 v = __ldg(reinterpret_cast<const float4*>(X + (r0 + rr) * n + c0) + c4);
+        const float4 v = __ldg(reinterpret_cast<const float4*>(X + (r0 + rr) * ld + c0) + c4);
         float* d = s_blk + rr * (LEAF + 1) + 4 * c4;
         d[0] = v.x;
         d[1] = v.y;
@@ -121,7 +126,7 @@ __global__ void __launch_bounds__(q_threads<LEAF>())
       const int u = tid + r * kThreads;
       const int row = u / PPR, k0 = (u % PPR) * PER16;
       if (!isB) {   // image row = block row, K along the block's columns
-        const float* src = X + (r0 + row) * n + c0 + k0;
+        const float* src = X + (r0 + row) * ld + c0 + k0;
         if (vec) {
 #pragma unroll
           for (int q = 0; q < PER16; q += 4) {
@@ -133,17 +138,17 @@ __global__ void __launch_bounds__(q_threads<LEAF>())
           for (int q = 0; q < PER16; ++q) x[r][q] = __ldg(src + q);
         } else {
 #pragma unroll
-          for (int q = 0; q < PER16; ++q) x[r][q] = ld_or_zero(X, n, r0 + row, c0 + k0 + q);
+          for (int q = 0; q < PER16; ++q) x[r][q] = ld_or_zero(X, rows, cols, ld, r0 + row, c0 + k0 + q);
         }
       } else if (vec) {   // image row = block column, K along the block's rows (staged)
 #pragma unroll
         for (int q = 0; q < PER16; ++q) x[r][q] = s_blk[(k0 + q) * (LEAF + 1) + row];
       } else if (full) {
 #pragma unroll
-        for (int q = 0; q < PER16; ++q) x[r][q] = __ldg(X + (r0 + k0 + q) * n + c0 + row);
+        for (int q = 0; q < PER16; ++q) x[r][q] = __ldg(X + (r0 + k0 + q) * ld + c0 + row);
       } else {
 #pragma unroll
-        for (int q = 0; q < PER16; ++q) x[r][q] = ld_or_zero(X, n, r0 + k0 + q, c0 + row);
+        for (int q = 0; q < PER16; ++q) x[r][q] = ld_or_zero(X, rows, cols, ld, r0 + k0 + q, c0 + row);
       }
     }
     // largest magnitude of the block (NaN ignored, as fmaxf does)
@@ -223,7 +228,7 @@ cudaError_t launch_q(const InstRef& ref, const PlanBuffers& b, const OperandImag
     wave[dev] = sms * std::max(1, per_sm);
   }
   // the list length is known on the device only: one full wave of CTAs
-  const int64_t cap = 2 * b.tiles;
+  const int64_t cap = b.ablks + b.bblks;
   const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(cap, (int64_t)wave[dev]));
   return launch_pdl(quantize_kernel<FMT, LEAF, SPLIT>, dim3(grid), dim3(q_threads<LEAF>()),
                     kBlkSmem, s, ref, b, img);

@@ -92,6 +92,10 @@ spamm_status_t band_error(Engine& e, const double* nA, const double* nB, const f
   in.A = A;
   in.B = B;
   in.C = scratch;
+  in.lda = in.ldb = in.ldc = in.n;
+  in.alpha = 1.0f;
+  in.beta = 0.0f;
+  in.nC = nullptr;
   in.T = make_tau_screen(tau_ref);
   in.T_hi = make_tau_screen(tau);
   in.band = 1;
@@ -112,6 +116,7 @@ spamm_status_t band_error(Engine& e, const double* nA, const double* nB, const f
 
 spamm_status_t check_common(spamm_plan_t plan, const double* nA, const double* nB) {
   if (!plan || !nA || !nB) return SPAMM_ERR_INVALID_ARG;
+  if (plan->general) return SPAMM_ERR_UNSUPPORTED;   // square plans only
   if (!aligned16(nA) || !aligned16(nB)) return SPAMM_ERR_INVALID_ARG;
   return SPAMM_OK;
 }

@@ -13,8 +13,8 @@ struct OperandImages {
   uint8_t* a_lo;
   uint8_t* b_hi;
   uint8_t* b_lo;
-  int32_t* ea;   // [bd*bd]
-  int32_t* eb;   // [bd*bd]
+  int32_t* ea;   // [ablks] per block of A
+  int32_t* eb;   // [bblks] per block of B
 };
 
 template <uint32_t FMT, int LEAF>
@@ -27,7 +27,8 @@ struct TcLayout {
   static constexpr int kLoShift = FMT == tc::kFmtBF16 ? 8 : 11; // lo part scaled by 2^kLoShift
 };
 
-// Operand images are indexed by the global block number (tile0 + I * bd + K).
+// Operand images are indexed by the global block number (ablk0 + I * bk + K
+// for A, bblk0 + K * bn + J for B).
 cudaError_t launch_quantize(spamm_precision_t prec, int leaf, const InstRef& ref,
                             const PlanBuffers& b, const OperandImages& img, cudaStream_t s);
 
@@ -35,10 +36,16 @@ cudaError_t launch_multiply_tc(spamm_precision_t prec, int leaf, const InstRef& 
                                const PlanBuffers& b, const OperandImages& img, int32_t* status,
                                int schedule, cudaStream_t s);
 
-// Writes zeros to every tile without survivors, of every instance (reads the
-// plan's empty-tile list: after the whole plan).
+// Writes every tile without survivors, of every instance: beta * C (zeros at
+// beta = 0; the tile's norm into nC when set).  Reads the plan's empty-tile
+// list: after the whole plan.
 cudaError_t launch_zero_empty_tiles(const InstRef& ref, const PlanBuffers& b, int leaf,
                                     cudaStream_t s);
+
+// Output norm maps of the tensor-core multiply: merges the epilogue's per-tile
+// partial sums into each instance's nC (after launch_multiply_tc).
+cudaError_t launch_norm_out_finish(const InstRef& ref, const PlanBuffers& b, int leaf,
+                                   cudaStream_t s);
 
 // Self-test of the multiply's bounded wait on a phase that never completes.
 cudaError_t launch_wait_selftest(int32_t* status, uint64_t limit_ns, long long* out,

@@ -91,6 +91,25 @@ def near_sparse(n: int, seed: int, drop: float = 0.7) -> np.ndarray:
     return out
 
 
+def rect_decay_normal(m: int, k: int, alpha: float, seed: int) -> np.ndarray:
+    """m x k: exp(-alpha |i k/m - j|) * z, z ~ N(0,1): decay away from the stretched diagonal
+    (rectangular operands of the general form; z drawn in one row-major block)."""
+    g = _rng(seed)
+    z = g.standard_normal(size=(m, k))
+    i = np.arange(m, dtype=np.float64)[:, None] * (k / m)
+    j = np.arange(k, dtype=np.float64)[None, :]
+    return (np.exp(-alpha * np.abs(i - j)) * z).astype(np.float32)
+
+
+def rect_near_sparse(m: int, k: int, seed: int, drop: float = 0.7) -> np.ndarray:
+    """m x k ReLU(N(0,1)) with each remaining entry zeroed with probability ``drop`` (normals
+    drawn first, then the uniforms, each in one row-major block)."""
+    g = _rng(seed)
+    z = g.standard_normal(size=(m, k))
+    keep = g.uniform(size=(m, k)) >= drop
+    return np.where((z > 0) & keep, z, 0.0).astype(np.float32)
+
+
 def table1_matrix(n: int) -> np.ndarray:
     """Deterministic algebraic-decay matrix 0.1/(|i-j|^0.1 + 1) used for Table 1."""
     out = np.empty((n, n), dtype=np.float32)

@@ -298,3 +298,16 @@ def test_frobenius_diff():
     assert math.isclose(d, ref, rel_tol=1e-12)
     assert math.isclose(P.spamm_frobenius_diff(X), S.frobenius(x), rel_tol=1e-12)
     assert P.spamm_last_device_status() == 0
+
+
+@pytest.mark.parametrize("n,leaf", [(8192, 64), (1001, 32), (2048, 128)])
+def test_normmap_pair_equals_two_calls(n, leaf):
+    """One launch over both operands gives the bits of two single-operand launches."""
+    a = synth.exp_decay_normal(n, 0.05, 701)
+    b = synth.alg_decay_signed(n, 2.5, 702)
+    A, B = dev(a), dev(b)
+    pA, pB = P.spamm_normmap_pair(A, B, leaf)
+    sA, sB = P.spamm_normmap(A, leaf), P.spamm_normmap(B, leaf)
+    torch.cuda.synchronize()
+    assert torch.equal(pA, sA) and torch.equal(pB, sB)
+    assert P.spamm_last_device_status() == 0

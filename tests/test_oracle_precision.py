@@ -438,3 +438,23 @@ def test_tile_bounds_of_sampled_rows_match_the_full_map():
     for r, i in enumerate(rows):
         strip = slice(i * leaf, (i + 1) * leaf)
         assert np.all(P.tile_errors(emu[strip], exact[strip], leaf)[0] <= part[r])
+
+
+def test_c2_error_table_is_consistent():
+    """The stored accuracy table of the N = 8192 configuration (written by
+    `python -m oracle.c2_error_table`, oracle only): every mode's error stays inside the
+    pruning bound plus its a-priori bound, the pruning error inside bound2, survivors grow as
+    tau falls, and TF32x3 stays at the pruning error (its rounding is far below it)."""
+    import json
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "c2_error_table.json")
+    t = json.load(open(path))
+    rows = t["rows"]
+    assert [r["tau"] for r in rows] == sorted((r["tau"] for r in rows), reverse=True)
+    assert all(a["S"] <= b["S"] for a, b in zip(rows, rows[1:]))
+    for r in rows:
+        assert r["pruning_rel"] <= r["bound2_rel"] * (1 + 1e-9)
+        for name, m in r["modes"].items():
+            assert m["rel_err"] <= r["bound2_rel"] + m["apriori_rel"], (r["tau"], name)
+            assert m["rounding_rel"] <= m["apriori_rel"], (r["tau"], name)
+        assert r["modes"]["tf32x3"]["rounding_rel"] < 0.1 * r["modes"]["fp16"]["rounding_rel"]

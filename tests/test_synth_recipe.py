@@ -107,3 +107,15 @@ def test_named_workloads():
     a, b = synth.workload_c2(256)
     assert np.array_equal(a, synth.alg_decay_signed(256, 3.0, synth.config_seed(1)))
     assert np.array_equal(b, synth.alg_decay_signed(256, 3.0, synth.config_seed(1, operand="B")))
+
+
+def test_rect_generators_follow_their_recipes():
+    a = synth.rect_decay_normal(30, 70, 0.2, 9)
+    z = np.random.Generator(np.random.PCG64(9)).standard_normal((30, 70))
+    i = np.arange(30)[:, None] * (70 / 30)
+    j = np.arange(70)[None, :]
+    assert a.shape == (30, 70) and a.dtype == np.float32
+    assert np.array_equal(a, (np.exp(-0.2 * np.abs(i - j)) * z).astype(np.float32))
+    b = synth.rect_near_sparse(400, 300, 10)
+    assert b.shape == (400, 300) and (b >= 0).all()
+    assert abs((b > 0).mean() - 0.15) < 0.01
