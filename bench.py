@@ -59,9 +59,10 @@ import synth  # noqa: E402
 METRIC = "SpAMM time & TFLOP/s at fixed rel. error vs plain FP32 SpAMM & cuBLAS; roofline %"
 
 # DRAM bytes (read + write) per launch of a kernel, from one ncu capture of the
-# kernel as it stands; an entry is removed whenever the kernel changes, until it
-# is captured again.
-NCU_TRAFFIC = {}
+# kernel as it stands (the N = 32768 norm-map launch scaled from a capture at
+# N = 16384 by the entries read); an entry is removed whenever the kernel
+# changes, until it is captured again.
+NCU_TRAFFIC = {("normmap_staged_kernel", 32768, 128): 8594854912.0}
 
 # The synthetic workloads of a single product (one step = norm maps of A and B,
 # plan, multiply).  decay: exp(-alpha |i-j|) N(0,1), N = 32768, A and B
