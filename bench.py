@@ -24,6 +24,7 @@ from __future__ import annotations
 
 import argparse
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -309,6 +310,7 @@ def cpu_baseline(a, b, leaf, tau, pool=None, single_rows=4, nB_full=None, gpu_c=
             errs += float(np.sum((g - c) ** 2))
             refs += float(np.sum(c ** 2))
         res["rel_err_vs_oracle_sampled_rows"] = (errs / refs) ** 0.5 if refs > 0 else 0.0
+        res["abs_err_sampled_rows"] = errs ** 0.5
         res["sampled_rows"] = [int(i) for i in rows]
     return res, nB_full
 
@@ -534,6 +536,44 @@ def run_ours(args, rank, world):
         base["speedup_vs_cublas_sgemm"] = base["cublas_sgemm_ms"] / ms
         del plan32, C32
 
+    # the error-targeted tau of the same product: the library's bisection on the measured
+    # pruning error (spamm_tau_select, no network: its weights are for leaf 64) for a target
+    # of half the relative-error budget (the FP16 rounding takes the rest), and the step's time
+    # at that tau
+    tau_eps = None
+    if args.workload == "decay" and not args.no_baselines:
+        sel = P.Plan(n, leaf, P.FP32)
+        scratch = torch.empty_like(A)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        t_e, evals, err_e = sel.tau_select(nA, nB, A, B, 0.5 * args.target, None, scratch)
+        t_sel = time.perf_counter() - t0
+        del sel, scratch
+        st_e = None
+
+        def step_e():
+            P.spamm_normmap_pair(A, B, leaf, nA, nB, stream)
+            plan.plan_multiply(nA, nB, t_e, A, B, C, args.target, stream)
+
+        for _ in range(3):
+            step_e()
+        torch.cuda.synchronize()
+        st_e = plan.stats()
+        g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        g0.record(stream)
+        for _ in range(max(3, args.steps // 2)):
+            step_e()
+        g1.record(stream)
+        torch.cuda.synchronize()
+        tau_eps = {"target_pruning_rel_err": 0.5 * args.target, "tau": t_e, "evaluations": evals,
+                   "pruning_rel_err": err_e, "select_s": t_sel,
+                   "ms_per_step": g0.elapsed_time(g1) / max(3, args.steps // 2),
+                   "survivors": st_e["survivors"],
+                   "skipped_bound2_rel": st_e["skipped_bound2"] / (st_e["norm_a"] * st_e["norm_b"])}
+        # back to the line's tau (C as the timed steps left it, for the oracle's check)
+        step()
+        torch.cuda.synchronize()
+
     if rank != 0:
         return None
     peaks = load_peaks()
@@ -620,9 +660,18 @@ def run_ours(args, rank, world):
                           "unit": "GB/s", "frac": 12.0 * n * n / (ms * 1e-3) / 1e9 / peaks["hbm_gbs"]},
         "clocks": clk.summary(),
     }
+    if tau_eps is not None:
+        line["tau_for_target_error"] = tau_eps
     if not args.no_cpu_baseline:
         c_host = C.cpu().numpy()
         cb, _ = cpu_baseline(a_h, b_h, leaf, tau, pool, single_rows=args.cpu_rows, gpu_c=c_host)
+        # the sampled rows' error relative to ||A||_F ||B||_F, scaled to the whole product
+        # (rows alike by construction): the line's accuracy in the metric's normalisation
+        if "abs_err_sampled_rows" in cb:
+            ab = st["norm_a"] * st["norm_b"]
+            cb["rel_err_ab_whole_product_est"] = (
+                cb["abs_err_sampled_rows"] * math.sqrt(bd / len(cb["sampled_rows"])) / ab)
+            line["config"]["rel_err_vs_oracle_ab_est"] = cb["rel_err_ab_whole_product_est"]
         line["cpu_baseline"] = cb
     if pool is not None:
         pool.close()

@@ -174,3 +174,28 @@ def test_tensors_on_another_device_are_rejected(rec, monkeypatch):
     pl.multiply(A, B, C)
     b.run(As, Bs, Cs, [0.1, 0.2])
     assert rec.calls == ["spamm_multiply", "spamm_batch_run"]
+
+
+def test_general_plan_operands_are_checked(rec):
+    """GeneralPlan takes row-major views (contiguous rows, any leading dimension) of the
+    declared shapes and refuses the rest before reaching the library."""
+    m, k, n, leaf = 70, 130, 50, 32
+    pl = P.GeneralPlan(m, k, n, leaf, P.FP32)
+    assert (pl.bm, pl.bk, pl.bn) == (3, 5, 2)
+    A, B, C = torch.zeros(m, k), torch.zeros(k, n), torch.zeros(m, n)
+    nA = torch.zeros(pl.bm, pl.bk, dtype=torch.float64)
+    nB = torch.zeros(pl.bk, pl.bn, dtype=torch.float64)
+    rec.calls.clear()
+    wide = torch.zeros(m, k + 9)
+    pl.plan_multiply(nA, nB, 0.1, wide[:, 3:3 + k], B, C, alpha=2.0, beta=0.5)  # a view: ok
+    pl.multiply(A, B, C, normC=torch.zeros(pl.bm, pl.bn, dtype=torch.float64))
+    P.spamm_normmap_rect(wide[:, :k], leaf)
+    assert rec.calls == ["spamm_plan_multiply_general", "spamm_multiply_general",
+                         "spamm_normmap_rect"]
+    rec.calls.clear()
+    assert "shape" in _invalid(pl.multiply, A.t().contiguous(), B, C)           # k x m, not m x k
+    assert "rows are not contiguous" in _invalid(pl.multiply, torch.zeros(k, m).t(), B, C)
+    assert "elements" in _invalid(pl.plan, nB, nB, 0.1)                          # normA of B's grid
+    assert "elements" in _invalid(pl.multiply, A, B, C, normC=torch.zeros(4, dtype=torch.float64))
+    assert "float32" in _invalid(pl.multiply, A.double(), B, C)
+    assert rec.calls == []

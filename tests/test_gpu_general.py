@@ -3,6 +3,8 @@
 ragged, strided views), and matrix powers X_{t+1} = SpAMM(X_t, X_t) or SpAMM(X_t, A) planned
 from the norm map that the multiply's epilogue writes.
 """
+import ctypes
+
 import numpy as np
 import pytest
 import torch
@@ -236,3 +238,41 @@ def test_power_chain_against_oracle(squaring, name, mode):
         # the planned norms equal the oracle's norm map of its own X_t up to the chain's drift
         assert np.allclose(host(nX), ref["norms"], rtol=1e-5 * (t + 1), atol=0.0)
         X, nX = Y, nY
+
+
+@pytest.mark.parametrize("m,k,n,leaf", [(1, 1, 1, 32), (1, 300, 5, 64), (257, 1, 129, 32),
+                                        (64, 64, 64, 64), (3, 2000, 2, 128)])
+def test_general_degenerate_shapes(m, k, n, leaf):
+    """Single rows, columns and inner dimensions, one block per grid and long thin products."""
+    a = _rect(m, k, 91 + m + k, "exp", 0.01)
+    b = _rect(k, n, 92 + n, "exp", 0.01)
+    c_in = _rect(m, n, 93, "exp", 0.5)
+    mode = OP.FP32 if leaf == 32 else OP.TF32X3
+    _check_general(a, b, c_in, leaf, 0.0, 1.0, 0.0, mode)
+    nA, nB = G.normmap_rect(a, leaf), G.normmap_rect(b, leaf)
+    p = (nA[:, :, None] * nB[None, :, :]).ravel()
+    _check_general(a, b, c_in, leaf, float(np.median(p)), -1.0, 2.0, mode)
+
+
+def test_general_argument_errors_enqueue_nothing():
+    m, k, n, leaf = 100, 200, 60, 64
+    pl = P.GeneralPlan(m, k, n, leaf, P.FP32)
+    A, B = dev(_rect(m, k, 95)), dev(_rect(k, n, 96))
+    C = torch.full((m, n), 5.0, device="cuda")
+    nA, nB = P.spamm_normmap_rect(A, leaf), P.spamm_normmap_rect(B, leaf)
+    lib = P.lib()
+    s = torch.cuda.current_stream().cuda_stream
+    args = lambda lda, cptr: (pl.handle, ctypes.c_void_p(A.data_ptr()), lda,
+                              ctypes.c_void_p(B.data_ptr()), n, cptr, n, 1.0, 0.0, None,
+                              ctypes.c_void_p(s))
+    assert lib.spamm_multiply_general(*args(k - 1, ctypes.c_void_p(C.data_ptr()))) == 1  # lda < k
+    assert lib.spamm_multiply_general(*args(k, ctypes.c_void_p(A.data_ptr()))) == 1      # C aliases A
+    assert lib.spamm_multiply_general(pl.handle, ctypes.c_void_p(A.data_ptr()), k,
+                                      ctypes.c_void_p(B.data_ptr()), n,
+                                      ctypes.c_void_p(C.data_ptr()), n, float("nan"), 0.0, None,
+                                      ctypes.c_void_p(s)) == 1                         # alpha NaN
+    torch.cuda.synchronize()
+    assert bool((C == 5.0).all())
+    pl.plan_multiply(nA, nB, 0.0, A, B, C)
+    torch.cuda.synchronize()
+    assert not bool((C == 5.0).all())

@@ -130,6 +130,15 @@ def test_decay_n32768_sampled_rows(decay_n32768):
         _decay_rows_case(a, b, leaf, 1e-6, modes, rows)
 
 
+def test_decay_n32768_error_targeted_tau(decay_n32768):
+    """The same input at tau = 0.32, the threshold that a pruning error of 5e-6 of
+    ||A||_F ||B||_F selects for it (about 2 300 survivors, pruning the dominant error): FP16
+    and FP32 at leaf 128 on rows at the edges and in the middle."""
+    a, b = decay_n32768
+    bd = S.num_blocks(N, 128)
+    _decay_rows_case(a, b, 128, 0.32, (OP.FP32, OP.FP16), [0, bd // 2, bd - 1])
+
+
 @pytest.mark.parametrize("alpha,tau", [(0.1, 1e-6), (1.0, 1e-2)])
 def test_decay_other_rates_sampled_rows(alpha, tau):
     """The other decay rates of the configuration at N = 16384 (alpha = 0.1 keeps about 60

@@ -133,3 +133,25 @@ def test_batch_of_one_holds_a_plan_and_its_norm_maps(lib):
         assert lib.spamm_batch_workspace_size(ns, 1, leaf, prec, ctypes.byref(bw)) == 0
         bd = -(-n // leaf)
         assert bw.value >= pw.value + 2 * 8 * bd * bd
+
+
+def test_general_shape_validation_without_gpu(lib):
+    """The general form's shape checks run on the host before any CUDA call."""
+    b = ctypes.c_size_t()
+    f = lib.spamm_plan_workspace_size_general
+    f.argtypes = [ctypes.c_int64] * 3 + [ctypes.c_int32, ctypes.c_int32,
+                                         ctypes.POINTER(ctypes.c_size_t)]
+    assert f(0, 100, 100, 64, 0, ctypes.byref(b)) == 1                 # m < 1
+    assert f(100, 100, 100, 48, 0, ctypes.byref(b)) == 2               # leaf
+    assert f(100, 64 * 1025, 100, 64, 0, ctypes.byref(b)) == 2         # bk > 1024
+    assert f(1 << 25, 100, 100, 64, 0, ctypes.byref(b)) == 2           # a dimension > 2^24
+    assert f(64 * 4096, 64, 64 * 1025, 64, 0, ctypes.byref(b)) == 2    # bm * bn > 2^22
+    assert f(100, 100, 100, 32, 2, ctypes.byref(b)) == 2               # tensor mode at leaf 32
+    assert f(128, 576, 25600, 64, 2, ctypes.byref(b)) == 0             # the VGG13 conv21 shape
+    small = b.value
+    assert f(128, 576, 25600 * 2, 64, 2, ctypes.byref(b)) == 0 and b.value > small
+    g = lib.spamm_multiply_general
+    g.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p,
+                  ctypes.c_int64, ctypes.c_void_p, ctypes.c_int64, ctypes.c_float,
+                  ctypes.c_float, ctypes.c_void_p, ctypes.c_void_p]
+    assert g(None, None, 1, None, 1, None, 1, 1.0, 0.0, None, None) == 1
