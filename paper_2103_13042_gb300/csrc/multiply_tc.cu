@@ -493,7 +493,11 @@ __global__ void __launch_bounds__(TcCfg<FMT, LEAF, SPLITMODE>::kThreads, 1)
       const int buf = run % NA;
       if (!wait_ab(&acc_full[buf], ((uint32_t)(run / NA)) & 1u, abort_flag, p.status)) break;
       fence_after_sync();
-      const float scale = ldexpf(1.0f, r.s);
+      // 2^s in one factor when it is a normal float, else in two (coarse
+      // BF16/TF32 exponents can put s outside [-126, 127] for representable C)
+      const bool one = r.s >= -126 && r.s <= 127;
+      const int s1 = one ? r.s : r.s / 2;
+      const float scale = ldexpf(1.0f, s1), scale2 = ldexpf(1.0f, r.s - s1);
       const uint32_t base = tmem + (uint32_t)(buf * Cfg::kAccCols + col0) +
                             ((uint32_t)(quarter * 32) << 16);
 #pragma unroll
@@ -508,8 +512,13 @@ __global__ void __launch_bounds__(TcCfg<FMT, LEAF, SPLITMODE>::kThreads, 1)
             for (int q = 0; q < 32; ++q) v[q] = fmaf(x[q], lo_w, v[q]);
           }
         }
+        if (one) {
 #pragma unroll
-        for (int q = 0; q < 32; ++q) acc[c0 + q] = fmaf(v[q], scale, acc[c0 + q]);
+          for (int q = 0; q < 32; ++q) acc[c0 + q] = fmaf(v[q], scale, acc[c0 + q]);
+        } else {
+#pragma unroll
+          for (int q = 0; q < 32; ++q) acc[c0 + q] = fmaf(v[q] * scale, scale2, acc[c0 + q]);
+        }
       }
       fence_before_sync();
       __syncwarp();

@@ -166,6 +166,15 @@ __global__ void __launch_bounds__(q_threads<LEAF>())
     for (int w = 0; w < kThreads / 32; ++w) mx = fmaxf(mx, s_max[w]);
     int ex = 0;
     if (mx > 0.0f && mx <= 3.402823466e38f) frexpf(mx, &ex);
+    // BF16 and TF32 have FP32's exponent range: the scaling only has to keep
+    // products and sums inside it, so e is rounded up to a multiple of 32
+    // (scaled maximum in [2^-33, 1)).  The roundings are those of the exact
+    // exponent for every entry above 2^-94 of the block's maximum (hi parts)
+    // and above 2^-80 (lo parts of the split modes), and
+    // the blocks of a tile mostly share one exponent sum: the multiply's runs
+    // (one accumulator pass per change of the sum) stay long.  FP16 keeps the
+    // exact exponent: its range is the constraint.
+    if constexpr (FMT != tc::kFmtF16) ex = ((ex + 31) >> 5) << 5;
     if (tid == 0) (isB ? img.eb : img.ea)[blk] = ex;
     // 2^-ex as a float when it is a normal number (the usual case), else ldexpf
     const bool pow2_ok = ex >= -126 && ex <= 126;

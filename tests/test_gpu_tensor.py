@@ -164,3 +164,27 @@ def test_plan_multiply_equals_plan_then_multiply(name, mode):
     torch.cuda.synchronize()
     assert torch.equal(C1, C2)
     assert torch.isfinite(C2).all()
+
+
+@pytest.mark.parametrize("name,mode", [("bf16", OP.BF16), ("bf16_split", OP.BF16_SPLIT),
+                                       ("tf32x3", OP.TF32X3), ("fp16", OP.FP16)])
+@pytest.mark.parametrize("ea,eb", [(97, -22), (-60, 40), (100, 20)])
+def test_tc_wide_magnitudes(name, mode, ea, eb):
+    """Operands far from 1 (A ~ 2^ea, B ~ 2^eb, C representable): BF16 and TF32 blocks are
+    scaled on a 2^32 grid, so the exponent sum of a product can leave [-126, 127] (2^97 x 2^-22:
+    128) while C stays finite; FP16 keeps the exact block exponent.  The result must match the
+    oracle's emulation with exact exponents under the accumulation bound."""
+    n, leaf = 384, 64
+    a0, b0 = _pair("exp", n, 4242)
+    a = (a0 * 2.0 ** ea).astype(np.float32)
+    b = (b0 * 2.0 ** eb).astype(np.float32)
+    assert np.isfinite(a).all() and np.isfinite(b).all()
+    nA, nB = S.normmap(a, leaf), S.normmap(b, leaf)
+    p = S.triple_products(nA, nB)
+    tau = float(np.quantile(p[p > 0], 0.5))
+    got, surv, flags, st, _, _ = _run(a, b, leaf, tau, mode, 1e-6)
+    assert np.isfinite(got).all()
+    emu = OP.emulated_multiply(a, b, leaf, surv, mode, flags)
+    t_acc = OP.accumulation_tile_bounds(nA, nB, surv, mode, leaf)
+    assert np.all(OP.tile_errors(got, emu, leaf) <= t_acc)
+    assert S.frobenius(got - emu) <= OP.accumulation_bound(nA, nB, surv, mode, leaf)
