@@ -757,7 +757,8 @@ def run_batch(args, rank, world):
     else:
         best, cands = P.spamm_batch_autotune(As, Bs, Cs, taus, prec, args.target, reps=3)
     leaf = best["leaf"]
-    batch = P.Batch(ns, leaf, prec, graph=True, dynamic=best["schedule"] == "dynamic")
+    batch = P.Batch(ns, leaf, prec, graph=True, dynamic=best["schedule"] == "dynamic",
+                    groups=best["schedule"] == "groups")
 
     def step():
         batch.run(As, Bs, Cs, taus, args.target)
@@ -769,7 +770,8 @@ def run_batch(args, rank, world):
     assert P.spamm_last_device_status() == 0
 
     # phase breakdown (same configuration, events between phases, no graph)
-    tb = P.Batch(ns, leaf, prec, graph=False, dynamic=best["schedule"] == "dynamic", timing=True)
+    tb = P.Batch(ns, leaf, prec, graph=False, dynamic=best["schedule"] == "dynamic",
+                    groups=best["schedule"] == "groups", timing=True)
     ph = {"normmap": [], "plan": [], "round": [], "multiply": []}
     for _ in range(max(3, args.steps // 4)):
         tb.run(As, Bs, Cs, taus, args.target)
@@ -808,7 +810,8 @@ def run_batch(args, rank, world):
     dAs = [As, [torch.empty_like(x) for x in As]]
     dBs = [Bs, [torch.empty_like(x) for x in Bs]]
     dCs = [Cs, [torch.empty_like(x) for x in Cs]]
-    batches = [batch, P.Batch(ns, leaf, prec, graph=True, dynamic=best["schedule"] == "dynamic")]
+    batches = [batch, P.Batch(ns, leaf, prec, graph=True, dynamic=best["schedule"] == "dynamic",
+                    groups=best["schedule"] == "groups")]
     s_in, s_out = torch.cuda.Stream(device=dev), torch.cuda.Stream(device=dev)
     ev_in = [torch.cuda.Event(), torch.cuda.Event()]
     ev_done = [torch.cuda.Event(), torch.cuda.Event()]
@@ -1012,8 +1015,10 @@ def run_sparse(args, rank, world):
         best = min((c for c in cands if c["ms"] >= 0), key=lambda c: c["ms"])
     leaf = best["leaf"]
     tau, ratio, probes = taus[leaf]
-    batch = P.Batch([n], leaf, prec, graph=True, dynamic=best["schedule"] == "dynamic")
-    tb = P.Batch([n], leaf, prec, graph=False, dynamic=best["schedule"] == "dynamic", timing=True)
+    batch = P.Batch([n], leaf, prec, graph=True, dynamic=best["schedule"] == "dynamic",
+                    groups=best["schedule"] == "groups")
+    tb = P.Batch([n], leaf, prec, graph=False, dynamic=best["schedule"] == "dynamic",
+                    groups=best["schedule"] == "groups", timing=True)
 
     def step():
         batch.run([A], [B], [C], [tau], args.target)

@@ -311,7 +311,13 @@ spamm_status_t spamm_multiply_fp32_noalloc(const float* A, const float* B, float
  *   graph and replays it on later runs (the instance table is re-uploaded,
  *   from pinned host memory, only when it changed).  SPAMM_BATCH_DYNAMIC
  *   makes the persistent multiply take its tiles in 32-tile chunks from a
- *   global counter instead of a fixed interleave.  SPAMM_BATCH_TIMING
+ *   global counter instead of a fixed interleave.  SPAMM_BATCH_GROUPS (not
+ *   with SPAMM_BATCH_DYNAMIC) multiplies the output tiles in groups of four
+ *   consecutive tiles of a block row, staging each A_ik once for all tiles of
+ *   the group that keep k: fewer staged bytes per product on dense-ish skip
+ *   sets.  It takes effect for SPAMM_BF16 and SPAMM_FP16 at leaf 128; other
+ *   configurations run the per-tile schedule.  The results equal those of
+ *   the per-tile schedules bit for bit.  SPAMM_BATCH_TIMING
  *   records events around the three phases of every run (runs are then
  *   enqueued directly, never from the graph) for spamm_batch_timings.
  *   Creation allocates host staging memory and blocks.
@@ -327,7 +333,8 @@ spamm_status_t spamm_multiply_fp32_noalloc(const float* A, const float* B, float
  *   last three); blocks.
  * spamm_batch_autotune: times every candidate configuration on the given
  *   problems and returns the fastest in *best: leaf 64 and 128 (32, 64 and
- *   128 for FP32) times the static and dynamic multiply schedules, each
+ *   128 for FP32) times the static and dynamic multiply schedules (and the
+ *   grouped one for BF16 and FP16 at leaf 128), each
  *   with graph replay, median of `reps` timed runs after two untimed ones.
  *   results[*nresults] (both may be NULL) receives every candidate, ms < 0
  *   for one that did not fit in memory; *nresults is set to the number of
@@ -351,6 +358,7 @@ typedef struct spamm_batch_s* spamm_batch_t;
 #define SPAMM_BATCH_GRAPH 1
 #define SPAMM_BATCH_DYNAMIC 2
 #define SPAMM_BATCH_TIMING 4
+#define SPAMM_BATCH_GROUPS 8
 
 typedef struct {
   int32_t leaf;

@@ -46,7 +46,7 @@ class Problem(ctypes.Structure):
                 ("n", ctypes.c_int64), ("tau", ctypes.c_double)]
 
 
-BATCH_GRAPH, BATCH_DYNAMIC, BATCH_TIMING = 1, 2, 4
+BATCH_GRAPH, BATCH_DYNAMIC, BATCH_TIMING, BATCH_GROUPS = 1, 2, 4, 8
 
 
 class Tune(ctypes.Structure):
@@ -54,8 +54,9 @@ class Tune(ctypes.Structure):
     _fields_ = [("leaf", ctypes.c_int32), ("flags", ctypes.c_int32), ("ms", ctypes.c_float)]
 
     def as_dict(self):
-        return {"leaf": self.leaf, "schedule": "dynamic" if self.flags & BATCH_DYNAMIC else "static",
-                "flags": self.flags, "ms": self.ms}
+        sched = ("dynamic" if self.flags & BATCH_DYNAMIC else
+                 "groups" if self.flags & BATCH_GROUPS else "static")
+        return {"leaf": self.leaf, "schedule": sched, "flags": self.flags, "ms": self.ms}
 
 _lib = None
 
@@ -624,7 +625,8 @@ class Batch:
     """Owns a spamm_batch_t: many independent products of fixed shapes."""
 
     def __init__(self, ns, leaf: int, precision: int = FP32, graph: bool = True,
-                 workspace=None, dynamic: bool = False, timing: bool = False):
+                 workspace=None, dynamic: bool = False, timing: bool = False,
+                 groups: bool = False):
         self.ns = [int(n) for n in ns]
         self.leaf, self.precision = leaf, precision
         self.count = len(self.ns)
@@ -634,7 +636,7 @@ class Batch:
             workspace.numel() * workspace.element_size())
         h = ctypes.c_void_p()
         flags = ((BATCH_GRAPH if graph else 0) | (BATCH_DYNAMIC if dynamic else 0) |
-                 (BATCH_TIMING if timing else 0))
+                 (BATCH_TIMING if timing else 0) | (BATCH_GROUPS if groups else 0))
         _check(lib().spamm_batch_create(ctypes.byref(h), ctypes.cast(n_arr, ctypes.c_void_p),
                                         self.count, leaf, precision, flags, ws_ptr, ws_bytes),
                "spamm_batch_create")

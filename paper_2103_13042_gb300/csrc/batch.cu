@@ -183,8 +183,9 @@ spamm_status_t spamm_batch_create(spamm_batch_t* batch, const int64_t* n, int32_
   *batch = nullptr;
   spamm_status_t st = check_shapes(n, count, leaf, precision);
   if (st != SPAMM_OK) return st;
-  if (flags & ~(SPAMM_BATCH_GRAPH | SPAMM_BATCH_DYNAMIC | SPAMM_BATCH_TIMING))
+  if (flags & ~(SPAMM_BATCH_GRAPH | SPAMM_BATCH_DYNAMIC | SPAMM_BATCH_TIMING | SPAMM_BATCH_GROUPS))
     return SPAMM_ERR_INVALID_ARG;
+  if ((flags & SPAMM_BATCH_DYNAMIC) && (flags & SPAMM_BATCH_GROUPS)) return SPAMM_ERR_INVALID_ARG;
   spamm_batch_s* b = new (std::nothrow) spamm_batch_s();
   if (!b) return SPAMM_ERR_NO_MEMORY;
   b->count = count;
@@ -198,7 +199,9 @@ spamm_status_t spamm_batch_create(spamm_batch_t* batch, const int64_t* n, int32_
     delete b;
     return st;
   }
-  b->eng.schedule = (flags & SPAMM_BATCH_DYNAMIC) ? kScheduleDynamic : kScheduleStatic;
+  b->eng.schedule = (flags & SPAMM_BATCH_DYNAMIC)  ? kScheduleDynamic
+                    : (flags & SPAMM_BATCH_GROUPS) ? kScheduleGroups
+                                                   : kScheduleStatic;
   char* base = static_cast<char*>(b->eng.base);
   b->normA = reinterpret_cast<double*>(base);
   b->normB = reinterpret_cast<double*>(base + norm_bytes);
@@ -469,7 +472,11 @@ spamm_status_t spamm_batch_autotune(const spamm_problem_t* problems, int32_t cou
   best->flags = 0;
   best->ms = -1.0f;
   for (int32_t leaf : leaves) {
-    for (int32_t sched : {0, SPAMM_BATCH_DYNAMIC}) {
+    for (int32_t sched : {0, SPAMM_BATCH_DYNAMIC, SPAMM_BATCH_GROUPS}) {
+      // the grouped multiply exists for BF16 and FP16 at leaf 128 only
+      if (sched == SPAMM_BATCH_GROUPS &&
+          !(leaf == 128 && (precision == SPAMM_BF16 || precision == SPAMM_FP16)))
+        continue;
       spamm_tune_t r{leaf, SPAMM_BATCH_GRAPH | sched, -1.0f};
       spamm_batch_t b = nullptr;
       spamm_status_t cs = spamm_batch_create(&b, n.data(), count, leaf, precision, r.flags,

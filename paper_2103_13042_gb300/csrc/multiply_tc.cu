@@ -36,8 +36,6 @@ using namespace tc;
 constexpr int kRunRing = 16;
 constexpr int kGroups = 4;           // scheduler ring: groups of 32 entry records
 constexpr int kFirstEpiWarp = 3;
-constexpr uint64_t kWaitLimitNs = 2000000000ull;   // 2 s: a safety net, never hit normally
-constexpr uint64_t kDrainLimitNs = 100000000ull;   // 100 ms for the abort drain
 
 struct StageMeta {
   int32_t flags;   // 1: first chunk of a run, 2: last chunk of a tile, 4: split, 8: end of work
@@ -114,30 +112,6 @@ struct TcCfg {
   static_assert(kSmemBytes <= 227 * 1024, "shared memory");
 };
 
-// Bounded wait that also returns when another role raised the abort flag.
-__device__ __forceinline__ bool wait_ab(uint64_t* bar, uint32_t parity, volatile int* abort_flag,
-                                        int32_t* status, uint64_t limit_ns = kWaitLimitNs) {
-  if (mbar_try_wait(bar, parity)) return true;
-  const uint64_t t0 = globaltimer_ns();
-  for (uint32_t it = 1;; ++it) {
-    if (mbar_try_wait(bar, parity)) return true;
-    if ((it & 63u) == 0) {
-      if (*abort_flag) return false;
-      if (globaltimer_ns() - t0 > limit_ns) {
-        *abort_flag = 1;
-        atomicExch(status, (int32_t)SPAMM_ERR_TIMEOUT);
-        return false;
-      }
-    }
-  }
-}
-
-template <uint32_t FMT>
-__device__ __forceinline__ void mma(uint32_t d, uint64_t a, uint64_t b, uint32_t id,
-                                    uint32_t accumulate) {
-  if constexpr (FMT == kFmtTF32) mma_tf32(d, a, b, id, accumulate);
-  else mma_f16(d, a, b, id, accumulate);
-}
 
 template <uint32_t FMT, int LEAF, int SPLITMODE>
 __global__ void __launch_bounds__(TcCfg<FMT, LEAF, SPLITMODE>::kThreads, 1)
@@ -848,6 +822,8 @@ cudaError_t launch_norm_out_finish(const InstRef& ref, const PlanBuffers& b, int
 cudaError_t launch_multiply_tc(spamm_precision_t prec, int leaf, const InstRef& ref,
                                const PlanBuffers& b, const OperandImages& img, int32_t* status,
                                int schedule, cudaStream_t s) {
+  if (schedule == kScheduleGroups && multiply_tc_groups_supported(prec, leaf, ref))
+    return launch_multiply_tc_groups(prec, ref, b, img, status, s);
   TcParams prm{ref, b, img, status, schedule == kScheduleDynamic ? 1 : 0};
   const bool l64 = leaf == 64;
   switch (prec) {

@@ -950,7 +950,7 @@ void set_general(Inst& in, int64_t m, int64_t kd, int64_t n, int64_t lda, int64_
 void set_square(Inst& in, int64_t n, int leaf) { set_general(in, n, n, n, n, n, n, 1.0f, 0.0f, leaf); }
 
 size_t plan_layout(Inst* insts, int count, PlanBuffers* b, char* base, bool norm_parts) {
-  int64_t tiles = 0, ablks = 0, bblks = 0, kslots = 0, mwords = 0;
+  int64_t tiles = 0, ablks = 0, bblks = 0, kslots = 0, mwords = 0, groups = 0;
   int prep = 0, cnt = 0, max_bk = 0;
   for (int i = 0; i < count; ++i) {
     Inst& in = insts[i];
@@ -961,6 +961,7 @@ size_t plan_layout(Inst* insts, int count, PlanBuffers* b, char* base, bool norm
     in.bblk0 = bblks;
     in.kidx0 = kslots;
     in.mask0 = mwords;
+    in.grp0 = groups;
     in.prep0 = prep;
     in.count0 = cnt;
     tiles += bm * bn;
@@ -968,6 +969,7 @@ size_t plan_layout(Inst* insts, int count, PlanBuffers* b, char* base, bool norm
     bblks += bk * bn;
     kslots += bm * bk * bn;
     mwords += bm * bn * ((bk + 31) / 32);
+    groups += bm * ((bn + kGroupTiles - 1) / kGroupTiles);
     prep += prep_ctas_of(in);
     cnt += count_ctas_of(in);
   }
@@ -980,6 +982,7 @@ size_t plan_layout(Inst* insts, int count, PlanBuffers* b, char* base, bool norm
   };
   PlanBuffers t{};
   t.tiles = tiles;
+  t.groups = groups;
   t.ablks = ablks;
   t.bblks = bblks;
   t.kslots = kslots;
@@ -1027,6 +1030,7 @@ InstRef make_ref(const Inst* host_insts, const Inst* dev_table, int count) {
     r.any_split |= host_insts[i].split != 0;
     r.any_band |= host_insts[i].band != 0;
     r.any_norm_out |= host_insts[i].nC != nullptr;
+    r.any_scaled |= host_insts[i].alpha != 1.0f || host_insts[i].beta != 0.0f;
   }
   return r;
 }

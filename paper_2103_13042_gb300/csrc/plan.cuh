@@ -63,8 +63,14 @@ struct BatchDevice {
 };
 
 // Multiply schedules: CTAs walk the longest-first order with a fixed
-// interleave (static) or take 32-slot chunks from a global counter (dynamic).
-enum Schedule { kScheduleStatic = 0, kScheduleDynamic = 1 };
+// interleave (static) or take 32-slot chunks from a global counter (dynamic);
+// or (tensor modes, leaf 128) take groups of four tiles of one block row that
+// share their A operands (groups).
+enum Schedule { kScheduleStatic = 0, kScheduleDynamic = 1, kScheduleGroups = 2 };
+
+// Tiles per group of the grouped multiply: one block row, kGroupTiles
+// consecutive block columns.
+constexpr int kGroupTiles = 4;
 
 // Extended-range FP32 sum: value = m * 2^e with an integer exponent.
 struct ExtSum {
@@ -91,6 +97,7 @@ struct Inst {
   int64_t bblk0;        // first global block of B
   int64_t kidx0;        // first k_idx slot
   int64_t mask0;        // first word of the survivor bitmask (bm * bn * ceil(bk / 32) words)
+  int64_t grp0;         // first global tile group (bm * ceil(bn / kGroupTiles) groups)
   int prep0;            // first CTA of this instance in the prep grid
   int count0;           // first CTA of this instance in the count and fill grids
   double target_rel;    // split modes: relative error target
@@ -110,6 +117,7 @@ struct InstRef {
   int count;
   int any_split, any_band;   // some instance uses split flags / a band (host-side dispatch)
   int any_norm_out;          // some instance writes an output norm map (nC)
+  int any_scaled;            // some instance has alpha != 1 or beta != 0
   __device__ __forceinline__ const Inst& at(int i) const { return table ? table[i] : one; }
 };
 
@@ -135,10 +143,14 @@ __device__ __forceinline__ int inst_of_ablk(const InstRef& r, int64_t g) {
 __device__ __forceinline__ int inst_of_bblk(const InstRef& r, int64_t g) {
   return find_inst(r, g, [](const Inst& x) { return x.bblk0; });
 }
+__device__ __forceinline__ int inst_of_group(const InstRef& r, int64_t g) {
+  return find_inst(r, g, [](const Inst& x) { return x.grp0; });
+}
 
 // Device buffers of a plan (carved from one workspace allocation).
 struct PlanBuffers {
   int64_t tiles;       // sum of bm * bn (output tiles)
+  int64_t groups;      // sum of bm * ceil(bn / kGroupTiles) (tile groups)
   int64_t ablks;       // sum of bm * bk (blocks of A)
   int64_t bblks;       // sum of bk * bn (blocks of B)
   int64_t kslots;      // sum of bm * bk * bn

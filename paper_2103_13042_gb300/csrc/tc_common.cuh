@@ -27,6 +27,37 @@ struct TcLayout {
   static constexpr int kLoShift = FMT == tc::kFmtBF16 ? 8 : 11; // lo part scaled by 2^kLoShift
 };
 
+// Waits of the persistent tensor-core multiplies: 2 s is a safety net, never
+// hit normally; 100 ms for the drain after an abort.
+constexpr uint64_t kWaitLimitNs = 2000000000ull;
+constexpr uint64_t kDrainLimitNs = 100000000ull;
+
+// Bounded wait that also returns when another role raised the abort flag.
+__device__ __forceinline__ bool wait_ab(uint64_t* bar, uint32_t parity, volatile int* abort_flag,
+                                        int32_t* status, uint64_t limit_ns = kWaitLimitNs) {
+  if (tc::mbar_try_wait(bar, parity)) return true;
+  const uint64_t t0 = tc::globaltimer_ns();
+  for (uint32_t it = 1;; ++it) {
+    if (tc::mbar_try_wait(bar, parity)) return true;
+    if ((it & 63u) == 0) {
+      if (*abort_flag) return false;
+      if (tc::globaltimer_ns() - t0 > limit_ns) {
+        *abort_flag = 1;
+        atomicExch(status, (int32_t)SPAMM_ERR_TIMEOUT);
+        return false;
+      }
+    }
+  }
+}
+
+// One MMA of the format's kind (kind::tf32 or kind::f16).
+template <uint32_t FMT>
+__device__ __forceinline__ void mma(uint32_t d, uint64_t a, uint64_t b, uint32_t id,
+                                    uint32_t accumulate) {
+  if constexpr (FMT == tc::kFmtTF32) tc::mma_tf32(d, a, b, id, accumulate);
+  else tc::mma_f16(d, a, b, id, accumulate);
+}
+
 // Operand images are indexed by the global block number (ablk0 + I * bk + K
 // for A, bblk0 + K * bn + J for B).
 cudaError_t launch_quantize(spamm_precision_t prec, int leaf, const InstRef& ref,
@@ -35,6 +66,13 @@ cudaError_t launch_quantize(spamm_precision_t prec, int leaf, const InstRef& ref
 cudaError_t launch_multiply_tc(spamm_precision_t prec, int leaf, const InstRef& ref,
                                const PlanBuffers& b, const OperandImages& img, int32_t* status,
                                int schedule, cudaStream_t s);
+
+// The grouped multiply (groups of four tiles of a block row sharing their A
+// operands): leaf 128, BF16 or FP16, alpha = 1, beta = 0, no output norm map.
+bool multiply_tc_groups_supported(spamm_precision_t prec, int leaf, const InstRef& ref);
+cudaError_t launch_multiply_tc_groups(spamm_precision_t prec, const InstRef& ref,
+                                      const PlanBuffers& b, const OperandImages& img,
+                                      int32_t* status, cudaStream_t s);
 
 // Writes every tile without survivors, of every instance: beta * C (zeros at
 // beta = 0; the tile's norm into nC when set).  Reads the plan's empty-tile

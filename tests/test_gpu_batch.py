@@ -234,7 +234,74 @@ def test_autotune_returns_a_measured_candidate():
     Cs = [torch.zeros_like(A) for A in As]
     taus = _taus(pairs, 64, 0.5)
     best, allc = P.spamm_batch_autotune(As, Bs, Cs, taus, P.BF16, reps=2)
-    assert len(allc) == 4
+    assert len(allc) == 5
     assert {(c["leaf"], c["schedule"]) for c in allc} == {(64, "static"), (64, "dynamic"),
-                                                          (128, "static"), (128, "dynamic")}
+                                                          (128, "static"), (128, "dynamic"),
+                                                          (128, "groups")}
     assert best["ms"] == min(c["ms"] for c in allc if c["ms"] >= 0)
+
+
+def _groups_vs_static(As, Bs, taus, prec):
+    ns = [A.shape[0] for A in As]
+    Cs = [torch.full_like(A, float("nan")) for A in As]
+    Cg = [torch.full_like(A, float("nan")) for A in As]
+    st = P.Batch(ns, 128, prec, graph=False)
+    gr = P.Batch(ns, 128, prec, graph=True, groups=True)
+    st.run(As, Bs, Cs, taus, 1e-6)
+    for _ in range(2):   # graph capture, then replay
+        for C in Cg:
+            C.fill_(float("nan"))
+        gr.run(As, Bs, Cg, taus, 1e-6)
+        torch.cuda.synchronize()
+        assert P.spamm_last_device_status() == 0
+        for i in range(len(As)):
+            assert torch.equal(Cs[i], Cg[i]), i
+    stats = gr.stats()
+    st.close()
+    gr.close()
+    return Cg, stats
+
+
+@pytest.mark.parametrize("prec", [P.BF16, P.FP16])
+def test_groups_schedule_equals_per_tile_decay(prec):
+    """Grouped multiply (four tiles of a block row share A) against the per-tile schedule,
+    bit for bit: uneven decay instances (block columns not a multiple of four, ragged last
+    tiles), FP16 with exact block exponents (several accumulator runs per tile: partial sums
+    kept in C) and BF16 on the 2^32 grid."""
+    specs, pairs = _instances(6, 777 + prec, 200, 1300, 0.5)
+    taus = _taus(pairs, 128, 0.5)
+    As = [dev(a) for a, _ in pairs]
+    Bs = [dev(b) for _, b in pairs]
+    _groups_vs_static(As, Bs, taus, prec)
+
+
+@pytest.mark.parametrize("n,q", [(1000, 0.5), (700, 0.2), (1536, 0.9)])
+def test_groups_schedule_near_sparse_against_oracle(n, q):
+    """Near-sparse BF16 at leaf 128 (the dense-ish skip sets the grouped multiply is for):
+    bit-equal to the per-tile schedule, and every tile within its accumulation share of the
+    oracle's emulation of the rounded operands."""
+    from oracle import precision as OP
+    a, b = synth.near_sparse(n, 51 + n), synth.near_sparse(n, 52 + n)
+    leaf = 128
+    nA, nB = S.normmap(a, leaf), S.normmap(b, leaf)
+    p = S.triple_products(nA, nB)
+    tau = float(np.quantile(p[p > 0], q))
+    A, B = dev(a), dev(b)
+    Cg, _ = _groups_vs_static([A], [B], [tau], P.BF16)
+    gA, gB = P.spamm_normmap(A, leaf), P.spamm_normmap(B, leaf)
+    plan = P.Plan(n, leaf, P.BF16).plan(gA, gB, tau, 1e-6)
+    surv, _ = plan_mask(plan)
+    got = host(Cg[0]).astype(np.float64)
+    emu = OP.emulated_multiply(a, b, leaf, surv, OP.BF16)
+    t_acc = OP.accumulation_tile_bounds(nA, nB, surv, OP.BF16, leaf)
+    assert np.all(OP.tile_errors(got, emu, leaf) <= t_acc)
+
+
+def test_groups_schedule_wide_magnitudes():
+    """A ~ 2^97, B ~ 2^-22: exponent sums past 127 on the BF16 grid (two-factor scaling)."""
+    n = 640
+    a = (synth.exp_decay_normal(n, 0.01, 61) * 2.0 ** 97).astype(np.float32)
+    b = (synth.exp_decay_normal(n, 0.01, 62) * 2.0 ** -22).astype(np.float32)
+    taus = _taus([(a, b)], 128, 0.3)
+    Cg, _ = _groups_vs_static([dev(a)], [dev(b)], taus, P.BF16)
+    assert bool(torch.isfinite(Cg[0]).all())

@@ -70,7 +70,8 @@ def test_batch_validation_without_gpu(lib):
     bad = (ctypes.c_int64 * 2)(256, 0)
     assert lib.spamm_batch_workspace_size(bad, 2, 64, 0, ctypes.byref(b)) == 1    # n < 1
     h = ctypes.c_void_p()
-    assert lib.spamm_batch_create(ctypes.byref(h), ns, 3, 64, 0, 8, None, 0) == 1  # flags
+    assert lib.spamm_batch_create(ctypes.byref(h), ns, 3, 64, 0, 16, None, 0) == 1  # flags
+    assert lib.spamm_batch_create(ctypes.byref(h), ns, 3, 64, 0, 2 | 8, None, 0) == 1  # dynamic + groups
     assert lib.spamm_batch_run(None, None, 0.0, None) == 1
     assert lib.spamm_batch_destroy(None) == 1
 
