@@ -751,9 +751,10 @@ def run_batch(args, rank, world):
     taus = certified_taus(P, As, Bs, ns, 64, args.target)
     t_tau = time.perf_counter() - t_tune
 
-    # autotuner: leaf x multiply schedule, timed on this batch (--leaf fixes the leaf, static)
+    # autotuner: leaf x multiply schedule, timed on this batch (--leaf fixes the leaf and
+    # --schedule the schedule)
     if args.leaf:
-        best, cands = {"leaf": args.leaf, "schedule": "static", "ms": -1.0}, []
+        best, cands = {"leaf": args.leaf, "schedule": args.schedule, "ms": -1.0}, []
     else:
         best, cands = P.spamm_batch_autotune(As, Bs, Cs, taus, prec, args.target, reps=3)
     leaf = best["leaf"]
@@ -1003,10 +1004,10 @@ def run_sparse(args, rank, world):
         taus[leaf] = pl.tau_for_valid_ratio(nA, nB, args.ratio, 0.01, 30)
         del pl, nA, nB
     # autotuner on this instance: leaf x schedule (each leaf with its own tau); --leaf fixes
-    # the leaf (static schedule)
+    # the leaf and --schedule the schedule
     cands = []
     if args.leaf:
-        best = {"leaf": args.leaf, "schedule": "static", "ms": -1.0}
+        best = {"leaf": args.leaf, "schedule": args.schedule, "ms": -1.0}
     else:
         for leaf in (64, 128):
             best, allc = P.spamm_batch_autotune([A], [B], [C], [taus[leaf][0]], prec, args.target,
@@ -1438,6 +1439,8 @@ def main():
     ap.add_argument("--target", type=float, default=1e-5)
     ap.add_argument("--n", type=int, default=None, help="matrix size (default per workload)")
     ap.add_argument("--leaf", type=int, default=None, help="default: autotuned / per workload")
+    ap.add_argument("--schedule", default="static", choices=["static", "dynamic", "groups"],
+                    help="sparse / batch with --leaf: the multiply schedule (else autotuned)")
     ap.add_argument("--cpu-rows", type=int, default=4,
                     help="output block-rows of the oracle's single-thread sample (cpu_baseline)")
     ap.add_argument("--ref-rows", type=int, default=8,

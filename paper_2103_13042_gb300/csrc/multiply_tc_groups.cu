@@ -13,14 +13,15 @@
 //
 // Roles, as in the per-tile kernel:
 //   warp 2   scheduler: takes groups in column panels of kPanelGroups groups
-//            (row-major inside a panel, so the SMs work on a compact block of
-//            tiles), reads the four tiles' survivor bitmasks, and publishes
+//            (row-major inside a panel: the SMs work down a narrow band of
+//            block columns, sharing its B blocks in L2; measured best among
+//            panel widths 1 to 64 at N = 8192 to 32768), reads the four tiles' survivor bitmasks, and publishes
 //            one record per k of the union: A block, the B block of the
 //            group's first column, the mask of tiles that keep k, which of
 //            them start an accumulator run (a change of the exponent sum
 //            ea + eb) and which end their tile, and the four exponent sums.
-//   warp 0   producer: per record one 32 KB slot of the A ring (two slots),
-//            then one slot of the B ring (four) per kept B, each filled by
+//   warp 0   producer: per record one 32 KB slot of the A ring (three slots),
+//            then one slot of the B ring (three) per kept B, each filled by
 //            one bulk copy.  Separate rings: an A slot is held while its
 //            record's B slots are multiplied, and must not hold up the reuse
 //            of B slots that are already free.
@@ -46,12 +47,18 @@ namespace {
 using namespace tc;
 
 constexpr int kG = kGroupTiles;      // tiles per group
-constexpr int kASlots = 2;           // 32 KB slots for A blocks (one held per record)
-constexpr int kBSlots = 4;           // 32 KB slots for B blocks
+#ifndef SPAMM_GROUP_ASLOTS
+#define SPAMM_GROUP_ASLOTS 3
+#endif
+#ifndef SPAMM_GROUP_PANEL
+#define SPAMM_GROUP_PANEL 2
+#endif
+constexpr int kASlots = SPAMM_GROUP_ASLOTS;   // 32 KB slots for A blocks (one held per record)
+constexpr int kBSlots = 6 - kASlots;          // 32 KB slots for B blocks
 constexpr int kSlots = kASlots + kBSlots;
 constexpr int kRecGroups = 2;        // record ring: groups of 32 records
 constexpr int kRuns = 16;            // run ring
-constexpr int kPanelGroups = 8;      // groups per panel row of the group order
+constexpr int kPanelGroups = SPAMM_GROUP_PANEL;   // groups per panel row of the group order
 constexpr int kEpi0 = 3;             // first epilogue warp
 
 // One k of a group's union: A block ga, B block gb0 + q for tile q; flags:
