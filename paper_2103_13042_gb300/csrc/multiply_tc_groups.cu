@@ -21,7 +21,7 @@
 //            them start an accumulator run (a change of the exponent sum
 //            ea + eb) and which end their tile, and the four exponent sums.
 //   warp 0   producer: per record one 32 KB slot of the A ring (three slots),
-//            then one slot of the B ring (three) per kept B, each filled by
+//            then one slot of the B ring (four) per kept B, each filled by
 //            one bulk copy.  Separate rings: an A slot is held while its
 //            record's B slots are multiplied, and must not hold up the reuse
 //            of B slots that are already free.
@@ -53,11 +53,16 @@ constexpr int kG = kGroupTiles;      // tiles per group
 #ifndef SPAMM_GROUP_PANEL
 #define SPAMM_GROUP_PANEL 2
 #endif
+#ifndef SPAMM_GROUP_SLOTS
+#define SPAMM_GROUP_SLOTS 7
+#endif
 constexpr int kASlots = SPAMM_GROUP_ASLOTS;   // 32 KB slots for A blocks (one held per record)
-constexpr int kBSlots = 6 - kASlots;          // 32 KB slots for B blocks
+constexpr int kBSlots = SPAMM_GROUP_SLOTS - kASlots;   // 32 KB slots for B blocks
 constexpr int kSlots = kASlots + kBSlots;
 constexpr int kRecGroups = 2;        // record ring: groups of 32 records
-constexpr int kRuns = 16;            // run ring
+// run ring: a closed run waits here for the epilogue (at most one per
+// accumulator is open); kept short so that seven slots fit in shared memory
+constexpr int kRuns = SPAMM_GROUP_SLOTS > 6 ? 4 : 16;
 constexpr int kPanelGroups = SPAMM_GROUP_PANEL;   // groups per panel row of the group order
 constexpr int kEpi0 = 3;             // first epilogue warp
 
@@ -66,7 +71,7 @@ constexpr int kEpi0 = 3;             // first epilogue warp
 // whose last k this is; tile0 = global tile of q = 0; s[q] = ea + eb.
 struct GRec {
   int ga, gb0, flags, tile0;
-  int s[kG];
+  short s[kG];
 };
 
 // B-slot flags: the record's first B (take the next A slot), the tile's run
@@ -105,7 +110,7 @@ struct GCfg {
   static constexpr size_t kRecOffset = up16(kRunOffset + (size_t)kRuns * sizeof(GRun));
   static constexpr size_t kMiscOffset =
       up16(kRecOffset + (size_t)kRecGroups * 32 * sizeof(GRec) + kRecGroups * sizeof(int));
-  static constexpr size_t kSmemBytes = kMiscOffset + 64 + 1024;   // + alignment slack
+  static constexpr size_t kSmemBytes = kMiscOffset + 16 + 1024;   // + alignment slack
   static_assert(kSlotBytes == 32768 && kBarOffset % 1024 == 0, "slot layout");
   static_assert(kSmemBytes <= 227 * 1024, "shared memory");
   static_assert(kTmemCols == 512, "four 128-column accumulators");
@@ -285,7 +290,7 @@ __global__ void __launch_bounds__(GCfg<FMT>::kThreads, 1) tc_group_kernel(GParam
           r.flags = jm | (first << 4) | (last << 8);
           r.tile0 = gtile0;
 #pragma unroll
-          for (int q = 0; q < kG; ++q) r.s[q] = s[q];
+          for (int q = 0; q < kG; ++q) r.s[q] = (short)s[q];   // |ea + eb| <= 512
           recs[grp * 32 + gfill + __popc(am & ((1u << lane) - 1u))] = r;
         }
         gfill += nact;
