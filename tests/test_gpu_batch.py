@@ -305,3 +305,18 @@ def test_groups_schedule_wide_magnitudes():
     taus = _taus([(a, b)], 128, 0.3)
     Cg, _ = _groups_vs_static([dev(a)], [dev(b)], taus, P.BF16)
     assert bool(torch.isfinite(Cg[0]).all())
+
+
+def test_groups_schedule_edges():
+    """Grouped multiply: no survivors at all (tau = inf: the end-of-work path only, C all
+    zeros), every triple kept (tau = 0), and more than 32 block columns of k (several mask
+    words per tile, n = 4224: 33 blocks, a ragged last block) next to a small instance."""
+    a, b = synth.near_sparse(640, 71), synth.near_sparse(640, 72)
+    A, B = dev(a), dev(b)
+    Cg, st = _groups_vs_static([A], [B], [math.inf], P.BF16)
+    assert st[0]["survivors"] == 0 and not bool(Cg[0].any())
+    Cg, st = _groups_vs_static([A], [B], [0.0], P.BF16)
+    assert st[0]["survivors"] == 5 ** 3
+    big = synth.exp_decay_normal(4224, 0.002, 73), synth.exp_decay_normal(4224, 0.002, 74)
+    taus = _taus([big, (a, b)], 128, 0.6)
+    _groups_vs_static([dev(big[0]), A], [dev(big[1]), B], taus, P.FP16)
