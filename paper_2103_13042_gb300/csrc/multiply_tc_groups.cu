@@ -15,8 +15,9 @@
 //   warp 2   scheduler: takes groups in column panels of kPanelGroups groups
 //            (row-major inside a panel: the SMs work down a narrow band of
 //            block columns, sharing its B blocks in L2; measured best among
-//            panel widths 1 to 64 at N = 8192 to 32768), reads the four tiles' survivor bitmasks, and publishes
-//            one record per k of the union: A block, the B block of the
+//            panel widths 1 to 64 at N = 8192 to 32768), reads the four
+//            tiles' survivor bitmasks, and publishes one record per k of
+//            the union: A block, the B block of the
 //            group's first column, the mask of tiles that keep k, which of
 //            them start an accumulator run (a change of the exponent sum
 //            ea + eb) and which end their tile, and the four exponent sums.

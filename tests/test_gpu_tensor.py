@@ -188,3 +188,48 @@ def test_tc_wide_magnitudes(name, mode, ea, eb):
     t_acc = OP.accumulation_tile_bounds(nA, nB, surv, mode, leaf)
     assert np.all(OP.tile_errors(got, emu, leaf) <= t_acc)
     assert S.frobenius(got - emu) <= OP.accumulation_bound(nA, nB, surv, mode, leaf)
+
+
+@pytest.mark.parametrize("name,mode", [("fp32", OP.FP32), ("bf16", OP.BF16)])
+@pytest.mark.parametrize("t", [-2, 0, 3])
+def test_empty_tiles_match_the_plan_at_ties(name, mode, t):
+    """The one-call form writes the empty tiles from the counting half's per-tile counts,
+    beside the rest of the plan, the two-call form from the finished plan's order: both must
+    give the oracle's empty tiles, ties at tau included.  Blocks of constant value 2^a
+    have the exact norm leaf 2^a, so with tau = leaf^2 2^t many products equal tau exactly;
+    zero blocks and a NaN block are mixed in.  Tiles the oracle's flat rule leaves empty are
+    zero, the others equal the two-call result bit for bit."""
+    leaf, bd = 64, 8                                     # (the tensor modes take 64 and 128)
+    n = leaf * bd
+    g = np.random.Generator(np.random.PCG64(100 + t))
+    ea = g.integers(-3, 4, size=(bd, bd))
+    eb = g.integers(-3, 4, size=(bd, bd))
+    a = np.kron(np.exp2(ea), np.ones((leaf, leaf))).astype(np.float32)
+    b = np.kron(np.exp2(eb), np.ones((leaf, leaf))).astype(np.float32)
+    a[0:leaf, 2 * leaf:3 * leaf] = 0.0
+    b[5 * leaf:6 * leaf, :leaf] = 0.0
+    a[3 * leaf + 1, 6 * leaf + 2] = np.nan
+    tau = float(leaf * leaf * 2.0 ** t)
+    nA, nB = S.normmap(a, leaf), S.normmap(b, leaf)
+    surv = S.flat_survivors(nA, nB, tau)
+    p = nA[:, :, None] * nB[None, :, :]
+    assert np.any(p == tau)                              # ties present
+    A, B = dev(a), dev(b)
+    gA, gB = P.spamm_normmap(A, leaf), P.spamm_normmap(B, leaf)
+    C1 = torch.full_like(A, 7.0)
+    C2 = torch.full_like(A, 7.0)
+    pl = P.Plan(n, leaf, mode)
+    pl.plan(gA, gB, tau, 1e-6).multiply(A, B, C1)
+    pl.plan_multiply(gA, gB, tau, A, B, C2, 1e-6)
+    torch.cuda.synchronize()
+    assert P.spamm_last_device_status() == 0
+    assert torch.equal(C1.view(torch.int32), C2.view(torch.int32))
+    got = host(C2)
+    nonempty = surv.any(axis=1)                          # [i, j]
+    for i in range(bd):
+        for j in range(bd):
+            blk = got[i * leaf:(i + 1) * leaf, j * leaf:(j + 1) * leaf]
+            if not nonempty[i, j]:
+                assert not blk.any(), (i, j)
+            else:
+                assert not np.all(blk == 7.0), (i, j)
