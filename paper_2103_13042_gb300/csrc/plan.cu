@@ -907,9 +907,14 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32)
           const int64_t ga = in.ablk0 + (int64_t)i * bk + k, gb = in.bblk0 + (int64_t)k * bn + j;
           bool newA = false, newB = false;
           if (s) {
+            // a bit once set stays set: a plain read from L2 that already shows it
+            // spares the atomic (on dense skip sets nearly every survivor's blocks
+            // are listed already, and atomics on the same words serialise)
             const uint32_t bitA = 1u << (ga & 31), bitB = 1u << (gb & 31);
-            newA = (atomicOr(&bitsA[ga >> 5], bitA) & bitA) == 0u;
-            newB = (atomicOr(&bitsB[gb >> 5], bitB) & bitB) == 0u;
+            newA = (__ldcg(&bitsA[ga >> 5]) & bitA) == 0u &&
+                   (atomicOr(&bitsA[ga >> 5], bitA) & bitA) == 0u;
+            newB = (__ldcg(&bitsB[gb >> 5]) & bitB) == 0u &&
+                   (atomicOr(&bitsB[gb >> 5], bitB) & bitB) == 0u;
           }
           const unsigned ma = __ballot_sync(0xffffffffu, newA), mb = __ballot_sync(0xffffffffu, newB);
           if (ma | mb) {
