@@ -616,10 +616,11 @@ __device__ __forceinline__ void empty_tile(const Inst& in, int64_t lt, int lane)
         const int64_t step = (int64_t)kRowsPerStore * ldc / 4;
         for (int r = my_r; r < rows; r += kRowsPerStore, p += step) __stcs(p, z);
       }
-    } else {
-      for (int u = lane; u < rows * cols; u += 32) {
-        const int r = u / cols, c = u - r * cols;
-        C[(r0 + r) * ldc + c0 + c] = 0.f;
+    } else {   // rows not 16-byte aligned: row by row, the lanes over the columns
+               // (coalesced 4-byte streaming stores, no index division)
+      for (int r = 0; r < rows; ++r) {
+        float* p = C + (r0 + r) * ldc + c0;
+        for (int c = lane; c < cols; c += 32) __stcs(p + c, 0.f);
       }
     }
     if (in.nC && lane == 0) in.nC[lt] = 0.0;
