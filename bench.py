@@ -356,6 +356,8 @@ def run_ours(args, rank, world):
     nA = torch.empty((bd, bd), dtype=torch.float64, device=dev)
     nB = torch.empty_like(nA)
     plan = P.Plan(n, leaf, prec)
+    schedule = tune["best"]["schedule"] if tune is not None else args.schedule
+    plan.set_schedule(schedule)   # the autotuner's multiply schedule, or --schedule
     stream = torch.cuda.current_stream()
 
     def step(st=None):
@@ -637,7 +639,7 @@ def run_ours(args, rank, world):
                    "precision": prec_name, "alpha": args.alpha if args.workload == "decay" else None,
                    "target_rel_err": args.target, "parallelism": f"replicas x{world}",
                    "launch": "eager" if graph is None else "cuda-graph replay of the API calls",
-                   "ms_per_step_eager": eager_ms, "autotune": tune,
+                   "ms_per_step_eager": eager_ms, "schedule": schedule, "autotune": tune,
                    "host_generation_s": t_gen,
                    "l2": f"inputs larger than L2 (A, B, C {gb:.2f} GB each vs 126 MB L2)",
                    "survivors": st["survivors"], "valid_ratio": st["valid_ratio"],

@@ -143,6 +143,16 @@ spamm_status_t spamm_plan_create(spamm_plan_t* plan, int64_t n, int32_t leaf,
                                  spamm_precision_t precision, void* workspace, size_t ws_bytes);
 spamm_status_t spamm_plan_destroy(spamm_plan_t plan);
 
+/* spamm_plan_set_schedule: the tile order of the plan's later multiplies
+ *   (square and general plans): 0, the default (most survivors first, fixed
+ *   interleave of the persistent CTAs); SPAMM_BATCH_DYNAMIC (32-tile chunks
+ *   from a global counter); SPAMM_BATCH_GROUPS (groups of four tiles of a
+ *   block row sharing each staged A block -- SPAMM_BF16 and SPAMM_FP16 at
+ *   leaf 128 with alpha = 1, beta = 0 and no output norm map; other calls
+ *   keep the per-tile order).  Every schedule gives the same bits.  Host-side
+ *   only.  SPAMM_ERR_INVALID_ARG for a NULL plan or another value. */
+spamm_status_t spamm_plan_set_schedule(spamm_plan_t plan, int32_t schedule);
+
 /* ---------------------------------------------------------------------------
  * spamm_plan -- evaluate the skip rule of Algorithm 1 / Algorithm 2 for every
  * leaf triple (i, k, j) and build per-output-tile work queues.

@@ -66,6 +66,7 @@ _SIGS = {
     "spamm_plan_workspace_size": [_I64, _I32, _I32, ctypes.POINTER(ctypes.c_size_t)],
     "spamm_plan_create": [ctypes.POINTER(_VP), _I64, _I32, _I32, _VP, ctypes.c_size_t],
     "spamm_plan_destroy": [_VP],
+    "spamm_plan_set_schedule": [_VP, _I32],
     "spamm_plan": [_VP, _VP, _VP, _D, _D, _VP],
     "spamm_plan_stats": [_VP, ctypes.POINTER(Stats), _VP],
     "spamm_plan_export": [_VP, _VP, _VP, _I64, _VP],
@@ -341,6 +342,14 @@ class Plan:
         _check(lib().spamm_plan_workspace_size(n, leaf, precision, ctypes.byref(b)),
                "spamm_plan_workspace_size")
         return b.value
+
+    def set_schedule(self, schedule: str = "static"):
+        """Tile order of later multiplies: "static", "dynamic" or "groups" (same bits)."""
+        flags = {"static": 0, "dynamic": BATCH_DYNAMIC, "groups": BATCH_GROUPS}
+        if schedule not in flags:
+            raise SpammError(1, "spamm_plan_set_schedule")
+        _check(lib().spamm_plan_set_schedule(self.handle, flags[schedule]), "spamm_plan_set_schedule")
+        return self
 
     def close(self):
         if self.handle:

@@ -409,6 +409,16 @@ spamm_status_t spamm_plan_create(spamm_plan_t* plan, int64_t n, int32_t leaf,
   return SPAMM_OK;
 }
 
+spamm_status_t spamm_plan_set_schedule(spamm_plan_t plan, int32_t schedule) {
+  if (!plan) return SPAMM_ERR_INVALID_ARG;
+  switch (schedule) {
+    case 0: plan->eng.schedule = kScheduleStatic; return SPAMM_OK;
+    case SPAMM_BATCH_DYNAMIC: plan->eng.schedule = kScheduleDynamic; return SPAMM_OK;
+    case SPAMM_BATCH_GROUPS: plan->eng.schedule = kScheduleGroups; return SPAMM_OK;
+    default: return SPAMM_ERR_INVALID_ARG;
+  }
+}
+
 spamm_status_t spamm_plan_destroy(spamm_plan_t plan) {
   if (!plan) return SPAMM_ERR_INVALID_ARG;
   spamm_status_t st = SPAMM_OK;

@@ -233,3 +233,36 @@ def test_empty_tiles_match_the_plan_at_ties(name, mode, t):
                 assert not blk.any(), (i, j)
             else:
                 assert not np.all(blk == 7.0), (i, j)
+
+
+@pytest.mark.parametrize("mode", [OP.BF16, OP.FP16])
+def test_plan_schedules_give_the_same_bits(mode):
+    """A plan's multiply under the per-tile static, dynamic and grouped schedules: the same bits,
+    for the square form and (grouped falling back to per-tile) for a general plan with alpha and
+    beta; an unknown schedule is refused."""
+    n, leaf = 1000, 128
+    a, b = _pair("sparse", n, 515)
+    A, B = dev(a), dev(b)
+    nA, nB = P.spamm_normmap(A, leaf), P.spamm_normmap(B, leaf)
+    p = S.triple_products(S.normmap(a, leaf), S.normmap(b, leaf))
+    tau = float(np.quantile(p[p > 0], 0.4))
+    pl = P.Plan(n, leaf, mode).plan(nA, nB, tau, 1e-6)
+    out = {}
+    for sched in ("static", "dynamic", "groups"):
+        C = torch.full_like(A, float("nan"))
+        pl.set_schedule(sched).multiply(A, B, C)
+        torch.cuda.synchronize()
+        assert P.spamm_last_device_status() == 0
+        out[sched] = C
+    assert torch.equal(out["static"], out["dynamic"]) and torch.equal(out["static"], out["groups"])
+    with pytest.raises(P.SpammError):
+        pl.set_schedule("panels")
+    gp = P.GeneralPlan(n, n, n, leaf, mode)
+    C0 = dev(synth.near_sparse(n, 516))
+    res = []
+    for sched in ("static", "groups"):
+        C = C0.clone()
+        gp.set_schedule(sched).plan_multiply(nA, nB, tau, A, B, C, alpha=2.0, beta=0.5)
+        torch.cuda.synchronize()
+        res.append(C)
+    assert torch.equal(res[0], res[1])

@@ -53,6 +53,7 @@ def test_argument_validation_without_gpu(lib):
     assert lib.spamm_normmap(ctypes.c_void_p(16), 1024, 40, ctypes.c_void_p(16), None) == 2
     assert lib.spamm_normmap(ctypes.c_void_p(18), 1024, 64, ctypes.c_void_p(16), None) == 1
     assert lib.spamm_plan(None, None, None, 0.0, 0.0, None) == 1
+    assert lib.spamm_plan_set_schedule(None, 0) == 1
 
 
 def test_batch_validation_without_gpu(lib):
