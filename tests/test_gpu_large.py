@@ -12,8 +12,8 @@ benchmark's seeds), on sampled output block rows:
     rows to FP64 resolution; the GPU's error against them stays inside the pruning bound
     plus the rounding bound.
 Near-sparse ReLU(N(0,1)) with 70% of the rest zeroed, BF16 at leaf 128, tau from the
-oracle's valid-ratio search (50%): 64 sampled output tiles plus every diagonal tile against
-the oracle (FP64 block norms by pairwise sums, pinned against the exactly rounded ones);
+oracle's valid-ratio search (50%), per-tile and grouped schedules bit-equal: 64 sampled output
+tiles plus every diagonal tile against the oracle (FP64 block norms by pairwise sums, pinned against the exactly rounded ones);
 the rest of C is parity unpinned (sampled).
 """
 import math
@@ -173,6 +173,13 @@ def test_near_sparse_n32768_sampled_tiles(near_sparse_n32768):
     plan.multiply(A, B, C)
     torch.cuda.synchronize()
     assert P.spamm_last_device_status() == 0
+    # the grouped schedule (the autotuner's pick for this input) gives the same bits
+    Cg = torch.full_like(A, float("nan"))
+    plan.set_schedule("groups").multiply(A, B, Cg)
+    torch.cuda.synchronize()
+    assert P.spamm_last_device_status() == 0
+    assert torch.equal(C, Cg)
+    del Cg
     tp, kk = plan.export()
     g = np.random.Generator(np.random.PCG64(32768))
     tiles = [(i, i) for i in range(bd)] + [tuple(int(x) for x in g.integers(0, bd, 2))
