@@ -13,8 +13,8 @@ benchmark's seeds), on sampled output block rows:
     plus the rounding bound.
 Near-sparse ReLU(N(0,1)) with 70% of the rest zeroed, BF16 at leaf 128, tau from the
 oracle's valid-ratio search (50%), per-tile and grouped schedules bit-equal: 64 sampled output
-tiles plus every diagonal tile against the oracle (FP64 block norms by pairwise sums, pinned against the exactly rounded ones);
-the rest of C is parity unpinned (sampled).
+tiles plus every diagonal tile against the oracle (FP64 block norms by pairwise sums, pinned
+against the exactly rounded ones); the rest of C is parity unpinned (sampled).
 """
 import math
 
