@@ -870,6 +870,11 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32)
   int inv_e;
   const float inv_m = (float)frexp(inv, &inv_e);
   const int m = in.pd->flag_exp;
+  // dense skip sets (more than 4 survivors per block on average): most blocks are
+  // listed after the first few triples, so a plain read of the bit spares the
+  // atomic; on sparse ones the read would only add latency
+  const bool read_first =
+      quant && in.pd->survivors > 4 * ((int64_t)bm * bk + (int64_t)bk * bn);
   for (int r = 0; r < kTileRounds; ++r) {
     const int lt = warp + r * kWarpsPerCta;
     const int64_t pos = lt0 + lt;
@@ -908,12 +913,11 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32)
           bool newA = false, newB = false;
           if (s) {
             // a bit once set stays set: a plain read from L2 that already shows it
-            // spares the atomic (on dense skip sets nearly every survivor's blocks
-            // are listed already, and atomics on the same words serialise)
+            // spares the atomic (atomics on the same words serialise)
             const uint32_t bitA = 1u << (ga & 31), bitB = 1u << (gb & 31);
-            newA = (__ldcg(&bitsA[ga >> 5]) & bitA) == 0u &&
+            newA = (!read_first || (__ldcg(&bitsA[ga >> 5]) & bitA) == 0u) &&
                    (atomicOr(&bitsA[ga >> 5], bitA) & bitA) == 0u;
-            newB = (__ldcg(&bitsB[gb >> 5]) & bitB) == 0u &&
+            newB = (!read_first || (__ldcg(&bitsB[gb >> 5]) & bitB) == 0u) &&
                    (atomicOr(&bitsB[gb >> 5], bitB) & bitB) == 0u;
           }
           const unsigned ma = __ballot_sync(0xffffffffu, newA), mb = __ballot_sync(0xffffffffu, newB);

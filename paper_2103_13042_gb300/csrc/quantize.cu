@@ -70,14 +70,14 @@ __device__ __forceinline__ float ld_or_zero(const float* X, int64_t rows, int64_
 // thread at most).
 template <int LEAF>
 constexpr int q_threads() { return LEAF == 128 ? 512 : 256; }
-// Resident CTAs per SM the register allocation is held to at leaf 64: the
-// rounding is bound by the HBM reads in flight, so eight CTAs beat six
-// (leaf-64 batch rounding 0.96 -> 0.85 ms).  At leaf 128 three CTAs spill
-// registers and measured slower at N = 32768 (2.79 -> 3.42 ms): the compiler's
-// choice (two CTAs) stays.  TF32 images hold twice the pieces.
+// Resident CTAs per SM the register allocation is held to: the rounding is
+// bound by the HBM reads in flight.  Leaf 64: eight CTAs beat six (batch
+// rounding 0.96 -> 0.85 ms).  Leaf 128: two CTAs (64 registers); one CTA
+// (up to 128 registers) measured 2.79 -> 4.0 ms at N = 32768 and three spill
+// (3.42 ms).  TF32 images hold twice the pieces.
 template <uint32_t FMT, int LEAF>
 constexpr int q_min_blocks() {
-  return LEAF == 128 ? 1 : (FMT == tc::kFmtTF32 ? 6 : 8);
+  return LEAF == 128 ? 2 : (FMT == tc::kFmtTF32 ? 6 : 8);
 }
 
 template <uint32_t FMT, int LEAF, bool SPLIT>
