@@ -132,7 +132,8 @@ cudaError_t enqueue(spamm_batch_s* b, cudaStream_t s, bool timing) {
   cudaError_t e = timing ? cudaEventRecord(b->phase[0], s) : cudaSuccess;
   if (e == cudaSuccess)
     e = launch_normmap_jobs(b->jobs_dev, b->n_vec_jobs, b->units_vec, 2 * b->count - b->n_vec_jobs,
-                            b->units_other, b->eng.leaf, b->status, s);
+                            b->units_other, b->eng.leaf, b->status, s, b->eng.side, b->eng.fork,
+                            b->eng.join);
   if (e == cudaSuccess && timing) e = cudaEventRecord(b->phase[1], s);
   if (e == cudaSuccess)
     e = engine_plan_multiply(b->eng, ref, b->status, s, timing ? b->phase[2] : nullptr,

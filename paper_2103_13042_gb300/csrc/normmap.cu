@@ -34,6 +34,8 @@
 // boundary inside X read from global memory directly.
 // Every wait is bounded; on expiry the CTA raises SPAMM_ERR_TIMEOUT, writes
 // NaN to the norms it did not finish and lets its copies land before it exits.
+#include <algorithm>
+
 #include "plan.cuh"
 #include "tc.cuh"
 
@@ -429,12 +431,16 @@ cudaError_t staged_capacity(int* cap) {
 
 // The units are dealt round-robin; the grid is the smallest that keeps the
 // number of rounds, so every CTA takes `rounds` or `rounds - 1` units.
+// share in (0, 1]: the fraction of the resident CTAs this launch may take (the
+// rest go to a launch running beside it).
 template <int LEAF, class Cfg>
-cudaError_t launch_staged_jobs(const StagedJobs& J, int32_t* status, cudaStream_t s) {
+cudaError_t launch_staged_jobs(const StagedJobs& J, int32_t* status, cudaStream_t s,
+                               double share = 1.0) {
   if (J.units <= 0) return cudaSuccess;
   int cap = 0;
   cudaError_t e = staged_capacity<LEAF, Cfg>(&cap);
   if (e != cudaSuccess) return e;
+  cap = std::max(1, (int)(cap * share));
   const int rounds = (J.units + cap - 1) / cap;
   const int grid = (J.units + rounds - 1) / rounds;
   normmap_staged_kernel<LEAF, Cfg><<<grid, Cfg::kThreads, Cfg::kSmem, s>>>(J, status);
@@ -442,11 +448,12 @@ cudaError_t launch_staged_jobs(const StagedJobs& J, int32_t* status, cudaStream_
 }
 
 template <class Cfg>
-cudaError_t launch_leaf(int leaf, const StagedJobs& J, int32_t* status, cudaStream_t s) {
+cudaError_t launch_leaf(int leaf, const StagedJobs& J, int32_t* status, cudaStream_t s,
+                        double share = 1.0) {
   switch (leaf) {
-    case 32: return launch_staged_jobs<32, Cfg>(J, status, s);
-    case 64: return launch_staged_jobs<64, Cfg>(J, status, s);
-    case 128: return launch_staged_jobs<128, Cfg>(J, status, s);
+    case 32: return launch_staged_jobs<32, Cfg>(J, status, s, share);
+    case 64: return launch_staged_jobs<64, Cfg>(J, status, s, share);
+    case 128: return launch_staged_jobs<128, Cfg>(J, status, s, share);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -536,22 +543,30 @@ cudaError_t launch_normmap_pair(const float* A, const float* B, int64_t n, int32
 }
 
 cudaError_t launch_normmap_jobs(const NormJob* dev_jobs, int n_vec, int units_vec, int n_other,
-                                int units_other, int leaf, int32_t* status, cudaStream_t s) {
+                                int units_other, int leaf, int32_t* status, cudaStream_t s,
+                                cudaStream_t side, cudaEvent_t fork, cudaEvent_t join) {
+  StagedJobs Jv{}, Jo{};
+  Jv.table = dev_jobs;
+  Jv.count = n_vec;
+  Jv.units = units_vec;
+  Jo.table = dev_jobs + n_vec;
+  Jo.count = n_other;
+  Jo.units = units_other;
   cudaError_t e = cudaSuccess;
-  if (n_vec > 0) {
-    StagedJobs J{};
-    J.table = dev_jobs;
-    J.count = n_vec;
-    J.units = units_vec;
-    e = launch_leaf<StagedAligned>(leaf, J, status, s);
+  if (n_vec > 0 && n_other > 0 && side && fork && join) {
+    // both kinds at once, on two streams, the resident CTAs shared in proportion
+    // to the units: they end together instead of one after the other
+    const double fv = (double)units_vec / ((double)units_vec + (double)units_other);
+    e = cudaEventRecord(fork, s);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(side, fork, 0);
+    if (e == cudaSuccess) e = launch_leaf<StagedUnaligned>(leaf, Jo, status, side, 1.0 - fv);
+    if (e == cudaSuccess) e = cudaEventRecord(join, side);
+    if (e == cudaSuccess) e = launch_leaf<StagedAligned>(leaf, Jv, status, s, fv);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s, join, 0);
+    return e;
   }
-  if (e == cudaSuccess && n_other > 0) {
-    StagedJobs J{};
-    J.table = dev_jobs + n_vec;
-    J.count = n_other;
-    J.units = units_other;
-    e = launch_leaf<StagedUnaligned>(leaf, J, status, s);
-  }
+  if (n_vec > 0) e = launch_leaf<StagedAligned>(leaf, Jv, status, s);
+  if (e == cudaSuccess && n_other > 0) e = launch_leaf<StagedUnaligned>(leaf, Jo, status, s);
   return e;
 }
 

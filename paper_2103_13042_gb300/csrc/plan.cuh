@@ -258,8 +258,12 @@ cudaError_t launch_normmap_wait_selftest(int32_t* status, uint64_t limit_ns, lon
 // Sets br, bc, nwin and lines from X, rows, cols, ld, vec and the leaf;
 // returns the job's units.
 int normjob_shape(NormJob& j, int leaf);
+// Both kinds of jobs (16-byte aligned rows, others); with a side stream and two
+// events they run at once, sharing the SMs in proportion to their units.
 cudaError_t launch_normmap_jobs(const NormJob* dev_jobs, int n_vec, int units_vec, int n_other,
-                                int units_other, int leaf, int32_t* status, cudaStream_t s);
+                                int units_other, int leaf, int32_t* status, cudaStream_t s,
+                                cudaStream_t side = nullptr, cudaEvent_t fork = nullptr,
+                                cudaEvent_t join = nullptr);
 
 cudaError_t launch_multiply_simt(const InstRef& ref, const PlanBuffers& b, int leaf,
                                  int schedule, cudaStream_t s);
