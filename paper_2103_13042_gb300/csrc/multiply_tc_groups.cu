@@ -48,23 +48,19 @@ namespace {
 using namespace tc;
 
 constexpr int kG = kGroupTiles;      // tiles per group
-#ifndef SPAMM_GROUP_ASLOTS
-#define SPAMM_GROUP_ASLOTS 3
-#endif
-#ifndef SPAMM_GROUP_PANEL
-#define SPAMM_GROUP_PANEL 2
-#endif
-#ifndef SPAMM_GROUP_SLOTS
-#define SPAMM_GROUP_SLOTS 7
-#endif
-constexpr int kASlots = SPAMM_GROUP_ASLOTS;   // 32 KB slots for A blocks (one held per record)
-constexpr int kBSlots = SPAMM_GROUP_SLOTS - kASlots;   // 32 KB slots for B blocks
-constexpr int kSlots = kASlots + kBSlots;
+// Seven 32 KB operand slots (all of shared memory but the bookkeeping): three
+// for A blocks (one is held per record), four for B blocks (the B ring bounds
+// the bytes in flight); groups in column panels two groups wide.  Measured at
+// near-sparse N = 8192 to 32768: splits 1/5 to 4/3 of six and seven slots,
+// panel widths 1 to 64.
+constexpr int kSlots = 7;
+constexpr int kASlots = 3;
+constexpr int kBSlots = kSlots - kASlots;
 constexpr int kRecGroups = 2;        // record ring: groups of 32 records
 // run ring: a closed run waits here for the epilogue (at most one per
 // accumulator is open); kept short so that seven slots fit in shared memory
-constexpr int kRuns = SPAMM_GROUP_SLOTS > 6 ? 4 : 16;
-constexpr int kPanelGroups = SPAMM_GROUP_PANEL;   // groups per panel row of the group order
+constexpr int kRuns = 4;
+constexpr int kPanelGroups = 2;      // groups per panel row of the group order
 constexpr int kEpi0 = 3;             // first epilogue warp
 
 // One k of a group's union: A block ga, B block gb0 + q for tile q; flags:
