@@ -812,7 +812,7 @@ __global__ void __launch_bounds__(kFinThreads)
   }
 }
 
-__global__ void __launch_bounds__(kWarpsPerCta * 32)
+__global__ void __launch_bounds__(kWarpsPerCta * 32, 4)
     fill_kernel(InstRef R, PlanBuffers Bf) {
   pdl_wait();
   pdl_trigger();
