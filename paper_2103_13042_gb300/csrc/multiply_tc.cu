@@ -116,7 +116,6 @@ struct TcCfg {
 template <uint32_t FMT, int LEAF, int SPLITMODE>
 __global__ void __launch_bounds__(TcCfg<FMT, LEAF, SPLITMODE>::kThreads, 1)
     tc_multiply_kernel(TcParams p) {
-  pdl_wait();
   using Cfg = TcCfg<FMT, LEAF, SPLITMODE>;
   using L = typename Cfg::L;
   constexpr int S = Cfg::kStages, N = Cfg::N;
@@ -173,6 +172,9 @@ __global__ void __launch_bounds__(TcCfg<FMT, LEAF, SPLITMODE>::kThreads, 1)
   __syncthreads();
   fence_after_sync();
   const uint32_t tmem = *tmem_slot;
+  // the set-up above (barriers, tensor memory) overlaps the previous kernel's
+  // tail; everything below reads what it wrote
+  pdl_wait();
   const int ne = p.Bf.bdev->nonempty;
 
   if (warp == 2) {

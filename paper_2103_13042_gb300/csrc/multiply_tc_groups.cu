@@ -127,7 +127,6 @@ __device__ __forceinline__ void group_at(const Inst& in, int64_t lg, int& i, int
 
 template <uint32_t FMT>
 __global__ void __launch_bounds__(GCfg<FMT>::kThreads, 1) tc_group_kernel(GParams p) {
-  pdl_wait();
   using Cfg = GCfg<FMT>;
   using L = typename Cfg::L;
   constexpr uint32_t SB = Cfg::kSlotBytes, CH = L::kChunkBytes;
@@ -183,6 +182,9 @@ __global__ void __launch_bounds__(GCfg<FMT>::kThreads, 1) tc_group_kernel(GParam
   __syncthreads();
   fence_after_sync();
   const uint32_t tmem = *tmem_slot;
+  // the set-up above (barriers, tensor memory) overlaps the previous kernel's
+  // tail; everything below reads what it wrote
+  pdl_wait();
 
   if (warp == 2) {
     // ------------------------------------------------------------ scheduler
